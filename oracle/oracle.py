@@ -1,0 +1,208 @@
+"""ctypes wrapper of lfem_oracle.c plus the pattern definition in numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function cites
+the passage of the paper it follows; the C file holds the element loops.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lfem_oracle.c")
+_lock = threading.Lock()
+_libs: dict = {}
+
+
+def _lib_path(mutation: int) -> str:
+    tag = "" if mutation == 0 else f"_mut{mutation}"
+    return os.path.join(_HERE, f"liblfem_oracle{tag}.so")
+
+
+def build(mutation: int = 0, force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no fast-math).  `mutation` > 0 builds a
+    copy with one planted mistake, used only by the tests that check the pins
+    catch it."""
+    path = _lib_path(mutation)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = f"{path}.{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", f"-DORACLE_MUTATION={mutation}",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, path)
+    return path
+
+
+def _lib(mutation: int = 0):
+    with _lock:
+        if mutation in _libs:
+            return _libs[mutation]
+        lib = ctypes.CDLL(build(mutation))
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        L = ctypes.c_int64
+        lib.oracle_tabulate.argtypes = [I, I, I, P, P, P]
+        lib.oracle_eval_points.argtypes = [P, I, P, L, I, I, I, P, P]
+        lib.oracle_geometry.argtypes = [P, I, P, L, I, I, I, P, P, P, P]
+        lib.oracle_local.argtypes = [P, I, P, L, I, I, I, P, P, P, P, P, P]
+        lib.oracle_assemble.argtypes = [P, I, P, L, I, I, I, P, P, P, P, P, L, P, P, P]
+        lib.oracle_adjoint.argtypes = [P, I, P, L, L, I, I, I, P, P, P, P, P, P, P, P, P, P]
+        for f in ("oracle_tabulate", "oracle_eval_points", "oracle_geometry", "oracle_local",
+                  "oracle_assemble", "oracle_adjoint", "oracle_mutation_id"):
+            getattr(lib, f).restype = ctypes.c_int
+        _libs[mutation] = lib
+        return lib
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def n_ref(dim: int, order: int) -> int:
+    """Local nodes per element, C(p+d, d) (Sec. 4, dim(E))."""
+    return {1: dim + 1, 2: (dim + 1) * (dim + 2) // 2}[order]
+
+
+def tabulate(dim, order, xi, mutation=0):
+    """Basis values phi [Q][ref] and reference gradients [Q][ref][dim] (Lagrange
+    P1/P2 on the reference simplex; Eq. form_functions_s2dp2 read as Lagrange)."""
+    xi = _f64(xi).reshape(-1, dim)
+    nq = xi.shape[0]
+    ref = n_ref(dim, order)
+    phi = np.zeros((nq, ref))
+    dphi = np.zeros((nq, ref, dim))
+    rc = _lib(mutation).oracle_tabulate(dim, order, nq, _p(xi), _p(phi), _p(dphi))
+    if rc:
+        raise ValueError("unsupported element")
+    return phi, dphi
+
+
+def pattern(conn, n_nodes):
+    """CSR pattern of all structural pairs (E[e,a], E[e,b]) with duplicates merged,
+    the index set that sparse(I(:), J(:), .) builds (Sec. 3.4 (b), Sec. 3.3):
+    sort lexicographically, unique.  Returns (row_ptr int64 [N+1], col_idx int32)."""
+    conn = np.asarray(conn, dtype=np.int64)
+    ref = conn.shape[1]
+    I = np.repeat(conn, ref, axis=1).ravel()
+    J = np.tile(conn, (1, ref)).ravel()
+    key = np.unique(I * np.int64(n_nodes) + J)
+    rows = key // n_nodes
+    cols = (key % n_nodes).astype(np.int32)
+    row_ptr = np.zeros(n_nodes + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n_nodes), out=row_ptr[1:])
+    return row_ptr, cols
+
+
+def eval_points(coords, conn, dim, order, xi, mutation=0):
+    """Physical points F_E(xi_q) for every element (Eq. F_map): [nE][Q][n]."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    n = coords.shape[1]
+    out = np.zeros((conn.shape[0], xi.shape[0], n))
+    rc = _lib(mutation).oracle_eval_points(_p(coords), n, _p(conn), conn.shape[0], dim, order, xi.shape[0],
+                                           _p(xi), _p(out))
+    if rc:
+        raise ValueError("unsupported element")
+    return out
+
+
+def geometry(coords, conn, dim, order, xi, mutation=0):
+    """J [nE][Q][n][d], s = |det DF| [nE][Q], G^{-1} [nE][Q][d][d] (Sec. 3.2.1)."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    n = coords.shape[1]
+    nE, nq = conn.shape[0], xi.shape[0]
+    J = np.zeros((nE, nq, n, dim))
+    s = np.zeros((nE, nq))
+    Gi = np.zeros((nE, nq, dim, dim))
+    rc = _lib(mutation).oracle_geometry(_p(coords), n, _p(conn), nE, dim, order, nq, _p(xi), _p(J), _p(s), _p(Gi))
+    if rc:
+        raise ValueError("unsupported element")
+    return J, s, Gi
+
+
+def local_matrices(coords, conn, dim, order, xi, w, coef=None, mutation=0):
+    """Element matrices M_loc, A_loc, MC_loc [nE][ref][ref] by quadrature
+    (Eqs. reference_quadrature_mass, reference_quadrature_stiffness)."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    w = _f64(w)
+    coef = _f64(coef)
+    n = coords.shape[1]
+    nE, nq = conn.shape[0], xi.shape[0]
+    ref = n_ref(dim, order)
+    M = np.zeros((nE, ref, ref))
+    A = np.zeros((nE, ref, ref))
+    C = np.zeros((nE, ref, ref))
+    rc = _lib(mutation).oracle_local(_p(coords), n, _p(conn), nE, dim, order, nq, _p(xi), _p(w), _p(coef),
+                                     _p(M), _p(A), _p(C))
+    if rc:
+        raise ValueError("unsupported element")
+    return M, A, C
+
+
+def assemble(coords, conn, dim, order, xi, w, coef=None, pat=None, mutation=0):
+    """Global M, A, MC values over the CSR pattern (Eqs. M matrix, A matrix).
+    Returns (row_ptr, col_idx, M, A, MC); MC is zero when coef is None."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    w = _f64(w)
+    coef = _f64(coef)
+    n = coords.shape[1]
+    if pat is None:
+        pat = pattern(conn, coords.shape[0])
+    row_ptr, col_idx = pat
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = _i32(col_idx)
+    nnz = col_idx.shape[0]
+    M = np.zeros(nnz)
+    A = np.zeros(nnz)
+    C = np.zeros(nnz)
+    rc = _lib(mutation).oracle_assemble(_p(coords), n, _p(conn), conn.shape[0], dim, order, xi.shape[0], _p(xi),
+                                        _p(w), _p(coef), _p(row_ptr), _p(col_idx), nnz, _p(M), _p(A), _p(C))
+    if rc:
+        raise ValueError(f"oracle_assemble failed ({rc})")
+    return row_ptr, col_idx, M, A, C
+
+
+def adjoint(coords, conn, dim, order, xi, w, coef, pat, gM=None, gA=None, gMC=None, mutation=0):
+    """dL/dx [N][n] and dL/dc [nE][Q] for L = gM.M + gA.A + gMC.MC (closed forms in
+    lfem_oracle.c; derived from Eqs. reference_quadrature_mass / _stiffness)."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    w = _f64(w)
+    coef = _f64(coef)
+    row_ptr, col_idx = pat
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = _i32(col_idx)
+    n = coords.shape[1]
+    gx = np.zeros_like(coords)
+    gc = np.zeros((conn.shape[0], xi.shape[0]))
+    rc = _lib(mutation).oracle_adjoint(_p(coords), n, _p(conn), conn.shape[0], coords.shape[0], dim, order,
+                                       xi.shape[0], _p(xi), _p(w), _p(coef), _p(row_ptr), _p(col_idx),
+                                       _p(_f64(gM)), _p(_f64(gA)), _p(_f64(gMC)), _p(gx), _p(gc))
+    if rc:
+        raise ValueError(f"oracle_adjoint failed ({rc})")
+    return gx, gc
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(int(sys.argv[1]) if len(sys.argv) > 1 else 0))
