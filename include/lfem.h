@@ -1,0 +1,184 @@
+/*
+ * lfem.h -- C ABI of the GB300 (sm_103a) isoparametric finite-element assembly library.
+ *
+ * The library assembles, for P1/P2 Lagrange elements on curves and surfaces
+ * (d = 1, 2 in R^{d+1}) and in bulk domains (d = n = 2, 3):
+ *   mass                    M_ij  = int phi_i phi_j                  (Sec. 2.2; Eq. M matrix)
+ *   stiffness               A_ij  = int grad_G phi_i . grad_G phi_j   (Sec. 2.2; Eq. A matrix)
+ *   coefficient-weighted    MC_ij = int c phi_i phi_j, c given at quadrature points
+ *                                   (the quadrature-point weighting of Sec. 5.2)
+ * element by element with a quadrature rule (Eqs. reference_quadrature_mass,
+ * reference_quadrature_stiffness), summed into a CSR matrix whose pattern is
+ * every structural pair (E[e,a], E[e,b]) (the index set sparse(I,J,V) builds,
+ * Sec. 3.3/3.4; "precomputing the sparsity structure", Sec. 3.3).
+ *
+ * Conventions shared by every entry point
+ *  - Node coordinates  coords: double [n_nodes][ambient], row-major (Sec. 4: array N).
+ *  - Connectivity      conn:   int32  [n_elem][ref], ref = C(order+dim, dim), 0-based,
+ *                              corners first then edge nodes (Sec. 4.1: array E).
+ *                              Edge-node order: segment (0,1); triangle (0,1),(1,2),(2,0);
+ *                              tetrahedron (0,1),(1,2),(2,0),(0,3),(1,3),(2,3).
+ *  - Supported (dim, ambient): (1,1) (1,2) (1,3) (2,2) (2,3) (3,3); order 1 or 2
+ *    (Table ellFEM_overview).  Anything else: LFEM_E_UNSUPPORTED.
+ *  - Quadrature rules are host arrays on the reference simplex (interval [0,1],
+ *    triangle conv{0,e1,e2}, tetrahedron conv{0,e1,e2,e3}); weights sum to its
+ *    measure.  n_pts <= LFEM_MAX_QPTS.
+ *  - Device pointers are caller-owned unless stated.  Outputs are overwritten,
+ *    never accumulated into.
+ *  - All work is enqueued on the given CUDA stream (NULL = legacy default
+ *    stream) and is asynchronous, except where an entry point says it
+ *    synchronises.  A pattern may be used by one stream at a time.
+ *  - Errors that the host can see are returned at once.  Errors found on the
+ *    device (node index out of range, zero or non-finite |det DF|) are
+ *    recorded in the pattern's status word and returned by lfem_sync_status.
+ *    lfem_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef LFEM_H
+#define LFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFEM_MAX_QPTS 64
+
+typedef struct lfem_pattern_s* lfem_pattern_t;
+typedef struct lfem_batch_s* lfem_batch_t;
+
+typedef enum {
+  LFEM_OK = 0,
+  LFEM_E_ARG = 1,          /* null pointer, negative size, bad flag */
+  LFEM_E_INDEX = 2,        /* node index outside [0, n_nodes) */
+  LFEM_E_UNSUPPORTED = 3,  /* (dim, ambient, order) not supported, or too many quadrature points */
+  LFEM_E_TOO_LARGE = 4,    /* a size limit below is exceeded */
+  LFEM_E_NOMEM = 5,        /* a device or host allocation failed */
+  LFEM_E_CUDA = 6,         /* a CUDA runtime call failed (message in lfem_last_error) */
+  LFEM_E_DEGENERATE = 7,   /* |det DF| zero or non-finite at a quadrature point (values still written) */
+  LFEM_E_TIMEOUT = 8       /* a bounded device wait gave up */
+} lfem_status;
+
+typedef enum {
+  LFEM_FP64 = 0,  /* every step in double; outputs double */
+  LFEM_MIXED = 1  /* geometry and local matrices in float (Jacobian from double
+                     coordinate differences), elements with an ill-conditioned
+                     metric redone in double, compensated (two-float) sums;
+                     outputs float */
+} lfem_precision;
+
+enum { LFEM_MASS = 1, LFEM_STIFF = 2, LFEM_CMASS = 4 };
+
+/* Quadrature rule, host arrays: xi [n_pts][dim], w [n_pts]. */
+typedef struct {
+  int n_pts;
+  const double* xi;
+  const double* w;
+} lfem_quad;
+
+/* ---------------------------------------------------------------------------
+ * Pattern (once per topology).
+ *
+ * lfem_pattern builds, on the device, the CSR pattern of all pairs
+ * (conn[e][a], conn[e][b]) (rows ascending, columns ascending within a row,
+ * duplicates merged; rows of unreferenced nodes are empty) and the maps the
+ * assembly kernels use.  conn is a device pointer; it is copied, so the caller
+ * may free it afterwards.  The call synchronises the stream once (to size the
+ * column array) and returns LFEM_E_INDEX if any node index is outside
+ * [0, n_nodes).
+ * Limits: n_elem * ref < 2^31; every CSR row shorter than the tile capacity
+ * (default 4096 slots); at most 2048 elements meet at one node; nnz < 2^31.
+ * Ownership: *out owns all of its device memory until lfem_pattern_destroy.
+ */
+lfem_status lfem_pattern(const int32_t* conn, int64_t n_elem, int32_t n_nodes, int dim, int order,
+                         void* cuda_stream, lfem_pattern_t* out);
+
+/* Read-only views of the pattern's CSR arrays (device pointers owned by the pattern). */
+lfem_status lfem_pattern_csr(lfem_pattern_t p, int64_t* n_rows, int64_t* nnz, const int64_t** row_ptr,
+                             const int32_t** col_idx);
+
+/* Copy the CSR arrays into caller buffers (device pointers: row_ptr int64 [n_rows+1],
+ * col_idx int32 [nnz]); asynchronous on the stream. */
+lfem_status lfem_pattern_copy_csr(lfem_pattern_t p, int64_t* row_ptr, int32_t* col_idx, void* cuda_stream);
+
+/* Pattern statistics: tiles, elements computed per tile pass (halo recompute
+ * factor x 1000), maximum row length.  Host values; no synchronisation. */
+lfem_status lfem_pattern_info(lfem_pattern_t p, int64_t* n_tiles, int64_t* recompute_x1000, int32_t* max_row,
+                              int32_t* tile_slots);
+
+/* Rebuild the row tiles with a different capacity (slots per tile, 256..16384). */
+lfem_status lfem_pattern_retile(lfem_pattern_t p, int32_t tile_slots, void* cuda_stream);
+
+void lfem_pattern_destroy(lfem_pattern_t p);
+
+/* ---------------------------------------------------------------------------
+ * Assembly: fills the CSR values of the requested matrices.
+ *   which:  bitmask of LFEM_MASS / LFEM_STIFF / LFEM_CMASS.
+ *   coef:   [n_elem][n_pts] quadrature-point coefficient for LFEM_CMASS, double,
+ *           or float when coef_is_fp32 != 0 (the value at the physical point
+ *           F_E(xi_q), see lfem_eval_points).  NULL only if LFEM_CMASS is not requested.
+ *   M, A, MC: [nnz] outputs, double for LFEM_FP64 and float for LFEM_MIXED;
+ *           a matrix not requested may be NULL.
+ * Work per CSR slot is summed in a fixed order; the result does not depend on
+ * scheduling (bit-identical reruns).  No atomics are used.
+ */
+lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                          const void* coef, int coef_is_fp32, unsigned which, lfem_precision prec, void* M,
+                          void* A, void* MC, void* cuda_stream);
+
+/* Launch configuration of the assembly kernels (elements per chunk, threads
+ * per block); 0 keeps the current value.  Used by the autotuner. */
+lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t threads);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint: for L = gM.M + gA.A + gMC.MC (dot products over the CSR values),
+ * g_coords [n_nodes][ambient] = dL/d coords (overwritten) and, when g_coef is
+ * not NULL, g_coef [n_elem][n_pts] = dL/d coef.  FP64 throughout.  gM, gA,
+ * gMC are [nnz] doubles; any may be NULL (treated as zero).  Geometry is
+ * recomputed, not stored.  (Not in the paper: the derivative of its local
+ * matrices, Eqs. reference_quadrature_mass / _stiffness, with respect to the
+ * node positions.)
+ */
+lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                                  const double* coef, const double* gM, const double* gA, const double* gMC,
+                                  double* g_coords, double* g_coef, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Element-level stages (no global scatter).  Useful on their own (matrix-free
+ * use, coefficient evaluation) and to test each stage.
+ *
+ * lfem_eval_points: x_q = F_E(xi_q) = sum_a x_a phi_a(xi_q) (Eq. F_map),
+ *   out double [n_elem][n_pts][ambient].
+ * lfem_geometry: per quadrature point, J = DF (Eq. jacobian_inv's rows) as
+ *   double [n_elem][n_pts][ambient][dim], s = |det DF| (surface: |d1F x d2F|)
+ *   [n_elem][n_pts], and G^{-1} with G = J^T J, [n_elem][n_pts][dim][dim];
+ *   any output may be NULL.
+ * lfem_local: element matrices by quadrature, upper triangle (a <= b, row-major
+ *   order (0,0),(0,1)..(0,ref-1),(1,1)..), double [n_elem][ref(ref+1)/2] each.
+ * conn and coords are device pointers; these calls are asynchronous and set
+ * no status word (non-finite results are written as computed).
+ */
+lfem_status lfem_eval_points(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords,
+                             int ambient, const lfem_quad* quad, double* out, void* cuda_stream);
+lfem_status lfem_geometry(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords,
+                          int ambient, const lfem_quad* quad, double* J, double* s, double* Ginv,
+                          void* cuda_stream);
+lfem_status lfem_local(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords, int ambient,
+                       const lfem_quad* quad, const double* coef, double* Mloc, double* Aloc, double* MCloc,
+                       void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Status word: synchronises the stream, returns and clears the device status
+ * of pattern p (LFEM_OK, LFEM_E_DEGENERATE, LFEM_E_INDEX), and reports how
+ * many elements the last LFEM_MIXED assembly redid in double.
+ */
+lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream);
+lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64_t* n_fp64_elements);
+
+const char* lfem_last_error(void);
+const char* lfem_status_string(lfem_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFEM_H */

@@ -1,0 +1,44 @@
+// Kernels for elements of dimension 2 (all supported ambient dimensions, orders 1 and 2).
+#include "dispatch.cuh"
+
+namespace lfem {
+
+lfem_status run_tiles_d2(int NA, int P, bool mixed, const AsmArgs& a, int64_t T, int threads, int pos_bytes,
+                            cudaStream_t st) {
+  LFEM_DEFINE_CASE_TILES(2, 2, 1)
+  LFEM_DEFINE_CASE_TILES(2, 2, 2)
+  LFEM_DEFINE_CASE_TILES(2, 3, 1)
+  LFEM_DEFINE_CASE_TILES(2, 3, 2)
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
+lfem_status run_stage_d2(int NA, int P, int kind, const StageArgs& s, cudaStream_t st) {
+  LFEM_DEFINE_CASE_STAGE(2, 2, 1)
+  LFEM_DEFINE_CASE_STAGE(2, 2, 2)
+  LFEM_DEFINE_CASE_STAGE(2, 3, 1)
+  LFEM_DEFINE_CASE_STAGE(2, 3, 2)
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
+lfem_status run_adjoint_d2(int NA, int P, const AdjArgs& a, int64_t T, int pos_bytes, cudaStream_t st) {
+  LFEM_DEFINE_CASE_ADJ(2, 2, 1)
+  LFEM_DEFINE_CASE_ADJ(2, 2, 2)
+  LFEM_DEFINE_CASE_ADJ(2, 3, 1)
+  LFEM_DEFINE_CASE_ADJ(2, 3, 2)
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
+size_t tile_smem_d2(int NA, int P, bool mixed, int nm, int slots, int chunk) {
+  LFEM_DEFINE_CASE_SMEM(2, 2, 1)
+  LFEM_DEFINE_CASE_SMEM(2, 2, 2)
+  LFEM_DEFINE_CASE_SMEM(2, 3, 1)
+  LFEM_DEFINE_CASE_SMEM(2, 3, 2)
+  return 0;
+}
+
+lfem_status bank_upload_d2(const void* src, size_t bytes, size_t offset) {
+  LFEM_CUDA(cudaMemcpyToSymbol(c_bank, src, bytes, offset, cudaMemcpyHostToDevice));
+  return LFEM_OK;
+}
+
+}  // namespace lfem

@@ -1,0 +1,424 @@
+// C ABI of the library: argument checks, reference tables, dispatch.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "dispatch.cuh"
+
+namespace lfem {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+lfem_status fail(lfem_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+lfem_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return LFEM_E_CUDA;
+}
+
+bool supported(int dim, int ambient, int order) {
+  if (order != 1 && order != 2) return false;
+  if (dim < 1 || dim > 3 || ambient < dim || ambient > 3) return false;
+  if (dim == 2 && ambient == 3) return true;
+  if (dim == ambient) return true;
+  return dim == 1;
+}
+
+// ---------------------------------------------------------------------------
+// Reference tables: Lagrange P1/P2 basis (corner functions l_a, or
+// l_a (2 l_a - 1) and edge functions 4 l_i l_j) with their reference gradients
+// at the quadrature points, and the gradients of the edge bubbles 4 l_i l_j.
+// ---------------------------------------------------------------------------
+static void edge_nodes(int dim, int k, int& i, int& j) {
+  static const int E1[1][2] = {{0, 1}};
+  static const int E2[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+  static const int E3[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+  const int(*E)[2] = dim == 1 ? E1 : (dim == 2 ? E2 : E3);
+  i = E[k][0];
+  j = E[k][1];
+}
+
+static void host_tables(int dim, int order, const lfem_quad* quad, std::vector<double>& out) {
+  const int Q = quad->n_pts, REF = n_ref(dim, order), NE = n_edges(dim, order);
+  out.assign((size_t)Q * (1 + REF + REF * dim + NE * dim), 0.0);
+  double* w = out.data();
+  double* phi = w + Q;
+  double* dphi = phi + Q * REF;
+  double* dpsi = dphi + Q * REF * dim;
+  for (int q = 0; q < Q; ++q) {
+    w[q] = quad->w[q];
+    double lam[4], dlam[4][3];
+    double sum = 0.0;
+    for (int m = 0; m < dim; ++m) sum += quad->xi[q * dim + m];
+    lam[0] = 1.0 - sum;
+    for (int m = 0; m < dim; ++m) lam[m + 1] = quad->xi[q * dim + m];
+    for (int i = 0; i <= dim; ++i)
+      for (int m = 0; m < dim; ++m) dlam[i][m] = (i == 0) ? -1.0 : (i == m + 1 ? 1.0 : 0.0);
+    for (int a = 0; a <= dim; ++a) {
+      phi[q * REF + a] = order == 1 ? lam[a] : lam[a] * (2.0 * lam[a] - 1.0);
+      for (int m = 0; m < dim; ++m) dphi[(q * REF + a) * dim + m] = order == 1 ? dlam[a][m] : (4.0 * lam[a] - 1.0) * dlam[a][m];
+    }
+    for (int k = 0; k < NE; ++k) {
+      int i, j;
+      edge_nodes(dim, k, i, j);
+      phi[q * REF + dim + 1 + k] = 4.0 * lam[i] * lam[j];
+      for (int m = 0; m < dim; ++m) {
+        double g = 4.0 * (lam[i] * dlam[j][m] + lam[j] * dlam[i][m]);
+        dphi[(q * REF + dim + 1 + k) * dim + m] = g;
+        dpsi[(q * NE + k) * dim + m] = g;
+      }
+    }
+  }
+}
+
+struct TabKey {
+  int dev, dim, order, q;
+  std::vector<double> data;
+  bool operator<(const TabKey& o) const {
+    return std::tie(dev, dim, order, q, data) < std::tie(o.dev, o.dim, o.order, o.q, o.data);
+  }
+};
+
+static std::mutex g_tab_mu;
+static std::map<TabKey, TabRef> g_tabs;
+static std::map<int, size_t> g_bank_used;  // bytes per device
+
+lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t st, TabRef* out) {
+  if (!quad || quad->n_pts <= 0 || !quad->xi || !quad->w) return fail(LFEM_E_ARG, "quadrature rule missing");
+  if (quad->n_pts > LFEM_MAX_QPTS) return fail(LFEM_E_UNSUPPORTED, "more than LFEM_MAX_QPTS quadrature points");
+  int dev = 0;
+  LFEM_CUDA(cudaGetDevice(&dev));
+  TabKey key{dev, dim, order, quad->n_pts, {}};
+  key.data.assign(quad->xi, quad->xi + (size_t)quad->n_pts * dim);
+  key.data.insert(key.data.end(), quad->w, quad->w + quad->n_pts);
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  auto it = g_tabs.find(key);
+  if (it != g_tabs.end()) {
+    *out = it->second;
+    return LFEM_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st) cudaStreamIsCapturing(st, &cs);
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(LFEM_E_ARG, "first use of a quadrature rule inside stream capture; call once before capturing");
+  std::vector<double> t64;
+  host_tables(dim, order, quad, t64);
+  std::vector<float> t32(t64.begin(), t64.end());
+  const size_t b64 = t64.size() * sizeof(double);
+  const size_t b32 = ((t32.size() * sizeof(float) + 7) / 8) * 8;
+  size_t& used = g_bank_used[dev];
+  if (used + b64 + b32 > sizeof(double) * 8192) {
+    // bank full: start over (kernels in flight may still read old entries)
+    LFEM_CUDA(cudaDeviceSynchronize());
+    for (auto i = g_tabs.begin(); i != g_tabs.end();) i = (i->first.dev == dev) ? g_tabs.erase(i) : std::next(i);
+    used = 0;
+    if (b64 + b32 > sizeof(double) * 8192) return fail(LFEM_E_TOO_LARGE, "reference tables exceed constant memory");
+  }
+  std::vector<unsigned char> blob(b64 + b32, 0);
+  memcpy(blob.data(), t64.data(), b64);
+  memcpy(blob.data() + b64, t32.data(), t32.size() * sizeof(float));
+  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3}) {
+    lfem_status us = up(blob.data(), blob.size(), used);
+    if (us != LFEM_OK) return us;
+  }
+  TabRef r;
+  r.q = quad->n_pts;
+  r.off64 = (int)(used / sizeof(double));
+  r.off32 = (int)((used + b64) / sizeof(float));
+  used += blob.size();
+  g_tabs[key] = r;
+  *out = r;
+  return LFEM_OK;
+}
+
+lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_t st);
+
+static lfem_status run_tiles(int dim, int NA, int P, bool mixed, const AsmArgs& a, int64_t T, int thr, int pb,
+                             cudaStream_t st) {
+  if (dim == 1) return run_tiles_d1(NA, P, mixed, a, T, thr, pb, st);
+  if (dim == 2) return run_tiles_d2(NA, P, mixed, a, T, thr, pb, st);
+  return run_tiles_d3(NA, P, mixed, a, T, thr, pb, st);
+}
+static lfem_status run_stage(int dim, int NA, int P, int kind, const StageArgs& s, cudaStream_t st) {
+  if (dim == 1) return run_stage_d1(NA, P, kind, s, st);
+  if (dim == 2) return run_stage_d2(NA, P, kind, s, st);
+  return run_stage_d3(NA, P, kind, s, st);
+}
+static lfem_status run_adjoint(int dim, int NA, int P, const AdjArgs& a, int64_t T, int pb, cudaStream_t st) {
+  if (dim == 1) return run_adjoint_d1(NA, P, a, T, pb, st);
+  if (dim == 2) return run_adjoint_d2(NA, P, a, T, pb, st);
+  return run_adjoint_d3(NA, P, a, T, pb, st);
+}
+static size_t tile_smem(int dim, int NA, int P, bool mixed, int nm, int slots, int chunk) {
+  if (dim == 1) return tile_smem_d1(NA, P, mixed, nm, slots, chunk);
+  if (dim == 2) return tile_smem_d2(NA, P, mixed, nm, slots, chunk);
+  return tile_smem_d3(NA, P, mixed, nm, slots, chunk);
+}
+
+static void destroy_dev(PatternDev& d) {
+  void* ptrs[] = {d.conn, d.row_ptr, d.col_idx, d.inc_ptr, d.inc_key, d.inc_pos, d.elem_inc,
+                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d = PatternDev{};
+}
+
+
+}  // namespace lfem
+
+using namespace lfem;
+
+extern "C" {
+
+const char* lfem_last_error(void) { return g_err.c_str(); }
+
+const char* lfem_status_string(lfem_status s) {
+  switch (s) {
+    case LFEM_OK: return "ok";
+    case LFEM_E_ARG: return "invalid argument";
+    case LFEM_E_INDEX: return "node index out of range";
+    case LFEM_E_UNSUPPORTED: return "unsupported element or rule";
+    case LFEM_E_TOO_LARGE: return "size limit exceeded";
+    case LFEM_E_NOMEM: return "out of device memory";
+    case LFEM_E_CUDA: return "CUDA error";
+    case LFEM_E_DEGENERATE: return "degenerate element";
+    case LFEM_E_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+lfem_status lfem_pattern(const int32_t* conn, int64_t n_elem, int32_t n_nodes, int dim, int order, void* cuda_stream,
+                         lfem_pattern_t* out) {
+  if (!out) return fail(LFEM_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_elem < 0 || n_nodes < 0) return fail(LFEM_E_ARG, "negative size");
+  if (n_elem > 0 && !conn) return fail(LFEM_E_ARG, "conn is NULL");
+  if (dim < 1 || dim > 3 || (order != 1 && order != 2)) return fail(LFEM_E_UNSUPPORTED, "dim/order");
+  const int ref = n_ref(dim, order);
+  if (n_elem >= (1ll << 27) || n_elem * ref >= (1ll << 31)) return fail(LFEM_E_TOO_LARGE, "too many elements");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  lfem_pattern_s* p = new lfem_pattern_s();
+  cudaGetDevice(&p->device);
+  p->dim = dim;
+  p->order = order;
+  p->ref = ref;
+  p->n_elem = n_elem;
+  p->n_nodes = n_nodes;
+  lfem_status s = build_pattern(p, conn, st);
+  if (s != LFEM_OK) {
+    std::string keep = g_err;
+    destroy_dev(p->d);
+    delete p;
+    g_err = keep;
+    return s;
+  }
+  *out = p;
+  return LFEM_OK;
+}
+
+lfem_status lfem_pattern_csr(lfem_pattern_t p, int64_t* n_rows, int64_t* nnz, const int64_t** row_ptr,
+                             const int32_t** col_idx) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (n_rows) *n_rows = p->n_nodes;
+  if (nnz) *nnz = p->nnz;
+  if (row_ptr) *row_ptr = p->d.row_ptr;
+  if (col_idx) *col_idx = p->d.col_idx;
+  return LFEM_OK;
+}
+
+lfem_status lfem_pattern_copy_csr(lfem_pattern_t p, int64_t* row_ptr, int32_t* col_idx, void* cuda_stream) {
+  if (!p || !row_ptr || (!col_idx && p->nnz > 0)) return fail(LFEM_E_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  LFEM_CUDA(cudaMemcpyAsync(row_ptr, p->d.row_ptr, sizeof(int64_t) * ((size_t)p->n_nodes + 1), cudaMemcpyDeviceToDevice, st));
+  if (p->nnz > 0)
+    LFEM_CUDA(cudaMemcpyAsync(col_idx, p->d.col_idx, sizeof(int32_t) * (size_t)p->nnz, cudaMemcpyDeviceToDevice, st));
+  return LFEM_OK;
+}
+
+lfem_status lfem_pattern_info(lfem_pattern_t p, int64_t* n_tiles, int64_t* recompute_x1000, int32_t* max_row,
+                              int32_t* tile_slots) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (n_tiles) *n_tiles = p->n_tiles;
+  if (recompute_x1000) *recompute_x1000 = p->n_elem ? (p->tile_elems_total * 1000) / p->n_elem : 0;
+  if (max_row) *max_row = p->max_row;
+  if (tile_slots) *tile_slots = p->tile_slots;
+  return LFEM_OK;
+}
+
+lfem_status lfem_pattern_retile(lfem_pattern_t p, int32_t tile_slots, void* cuda_stream) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  return build_tiles(p, tile_slots, (cudaStream_t)cuda_stream);
+}
+
+void lfem_pattern_destroy(lfem_pattern_t p) {
+  if (!p) return;
+  destroy_dev(p->d);
+  delete p;
+}
+
+lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t threads) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (elems_per_chunk < 0 || threads < 0 || (threads && (threads % 32 || threads > 256)))
+    return fail(LFEM_E_ARG, "launch configuration");
+  if (elems_per_chunk) p->chunk = elems_per_chunk;
+  if (threads) p->threads = threads;
+  return LFEM_OK;
+}
+
+lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                          const void* coef, int coef_is_fp32, unsigned which, lfem_precision prec, void* M, void* A,
+                          void* MC, void* cuda_stream) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
+  if (which == 0 || (which & ~7u)) return fail(LFEM_E_ARG, "which");
+  if (prec != LFEM_FP64 && prec != LFEM_MIXED) return fail(LFEM_E_ARG, "precision");
+  if ((which & LFEM_MASS) && !M) return fail(LFEM_E_ARG, "M is NULL");
+  if ((which & LFEM_STIFF) && !A) return fail(LFEM_E_ARG, "A is NULL");
+  if ((which & LFEM_CMASS) && (!MC || !coef)) return fail(LFEM_E_ARG, "MC or coef is NULL");
+  if (p->n_elem > 0 && !coords) return fail(LFEM_E_ARG, "coords is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TabRef tab;
+  lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
+  if (s != LFEM_OK) return s;
+  const bool mixed = prec == LFEM_MIXED;
+  AsmArgs a{};
+  a.conn = p->d.conn;
+  a.coords = coords;
+  a.coef = coef;
+  a.coef_f32 = coef_is_fp32 ? 1 : 0;
+  a.row_ptr = p->d.row_ptr;
+  a.inc_ptr = p->d.inc_ptr;
+  a.inc_pos = p->d.inc_pos;
+  a.inc_local = p->d.inc_local;
+  a.tile_row0 = p->d.tile_row0;
+  a.tile_elem_ptr = p->d.tile_elem_ptr;
+  a.tile_elem = p->d.tile_elem;
+  a.which = which;
+  int nm = 0;
+  if (which & LFEM_MASS) { a.out[nm] = M; a.mat[nm++] = 0; }
+  if (which & LFEM_STIFF) { a.out[nm] = A; a.mat[nm++] = 1; }
+  if (which & LFEM_CMASS) { a.out[nm] = MC; a.mat[nm++] = 2; }
+  a.nm = nm;
+  a.tab = tab;
+  a.slots_cap = p->tile_slots;
+  a.qmin = 0.25f;
+  a.status = p->d.status;
+  a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
+  const int threads = p->threads ? p->threads : 256;
+  int chunk = p->chunk;
+  if (!chunk) {
+    // largest multiple of 32 (<= 256) that fits the shared-memory budget
+    chunk = 256;
+    while (chunk > 32 && tile_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk) > 200 * 1024) chunk -= 32;
+  }
+  a.chunk = chunk;
+  if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
+  return run_tiles(p->dim, ambient, p->order, mixed, a, p->n_tiles, threads, p->pos_bytes, st);
+}
+
+lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                                  const double* coef, const double* gM, const double* gA, const double* gMC,
+                                  double* g_coords, double* g_coef, void* cuda_stream) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
+  if (!g_coords && p->n_nodes > 0) return fail(LFEM_E_ARG, "g_coords is NULL");
+  if (p->n_elem > 0 && !coords) return fail(LFEM_E_ARG, "coords is NULL");
+  if (gMC && !coef) return fail(LFEM_E_ARG, "gMC given without coef");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TabRef tab;
+  lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
+  if (s != LFEM_OK) return s;
+  AdjArgs a{};
+  a.conn = p->d.conn;
+  a.coords = coords;
+  a.coef = coef;
+  a.gM = gM;
+  a.gA = gA;
+  a.gC = gMC;
+  a.g_coords = g_coords;
+  a.g_coef = g_coef;
+  a.row_ptr = p->d.row_ptr;
+  a.inc_ptr = p->d.inc_ptr;
+  a.inc_pos = p->d.inc_pos;
+  a.inc_local = p->d.inc_local;
+  a.elem_inc = p->d.elem_inc;
+  a.tile_row0 = p->d.tile_row0;
+  a.tile_elem_ptr = p->d.tile_elem_ptr;
+  a.tile_elem = p->d.tile_elem;
+  a.tab = tab;
+  a.chunk = 128;
+  if (g_coef && !gMC && p->n_elem > 0) {
+    // dL/dc is zero without gMC
+    LFEM_CUDA(cudaMemsetAsync(g_coef, 0, sizeof(double) * p->n_elem * quad->n_pts, st));
+    a.g_coef = nullptr;
+  }
+  return run_adjoint(p->dim, ambient, p->order, a, p->n_tiles, p->pos_bytes, st);
+}
+
+static lfem_status stage_common(int kind, const int32_t* conn, int64_t n_elem, int dim, int order,
+                                const double* coords, int ambient, const lfem_quad* quad, const double* coef,
+                                unsigned which, double* o0, double* o1, double* o2, void* cuda_stream) {
+  if (n_elem < 0) return fail(LFEM_E_ARG, "negative size");
+  if (!supported(dim, ambient, order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
+  if (n_elem > 0 && (!conn || !coords)) return fail(LFEM_E_ARG, "conn or coords is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TabRef tab;
+  lfem_status s = get_tables(dim, order, quad, st, &tab);
+  if (s != LFEM_OK) return s;
+  StageArgs a{conn, n_elem, coords, tab, coef, which, o0, o1, o2};
+  return run_stage(dim, ambient, order, kind, a, st);
+}
+
+lfem_status lfem_eval_points(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords,
+                             int ambient, const lfem_quad* quad, double* out, void* cuda_stream) {
+  if (!out && n_elem > 0) return fail(LFEM_E_ARG, "out is NULL");
+  return stage_common(0, conn, n_elem, dim, order, coords, ambient, quad, nullptr, 0, out, nullptr, nullptr,
+                      cuda_stream);
+}
+
+lfem_status lfem_geometry(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords,
+                          int ambient, const lfem_quad* quad, double* J, double* s, double* Ginv,
+                          void* cuda_stream) {
+  return stage_common(1, conn, n_elem, dim, order, coords, ambient, quad, nullptr, 0, J, s, Ginv, cuda_stream);
+}
+
+lfem_status lfem_local(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords, int ambient,
+                       const lfem_quad* quad, const double* coef, double* Mloc, double* Aloc, double* MCloc,
+                       void* cuda_stream) {
+  unsigned which = (Mloc ? LFEM_MASS : 0) | (Aloc ? LFEM_STIFF : 0) | (MCloc ? LFEM_CMASS : 0);
+  if (!which) return fail(LFEM_E_ARG, "no output requested");
+  if (MCloc && !coef) return fail(LFEM_E_ARG, "MCloc requested without coef");
+  return stage_common(2, conn, n_elem, dim, order, coords, ambient, quad, coef, which, Mloc, Aloc, MCloc,
+                      cuda_stream);
+}
+
+lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int32_t h = 0;
+  LFEM_CUDA(cudaMemcpyAsync(&h, p->d.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaMemsetAsync(p->d.status, 0, sizeof(int32_t), st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (h & ST_INDEX) return fail(LFEM_E_INDEX, "node index out of range");
+  if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
+  return LFEM_OK;
+}
+
+lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64_t* n_fp64_elements) {
+  if (!p || !n_fp64_elements) return fail(LFEM_E_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  unsigned long long h = 0;
+  LFEM_CUDA(cudaMemcpyAsync(&h, p->d.status + 2, sizeof(h), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  *n_fp64_elements = (int64_t)h;
+  return LFEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,346 @@
+// Internal declarations of the lfem CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lfem.h"
+
+namespace lfem {
+
+// ----------------------------------------------------------------------------
+// Host-side error plumbing
+// ----------------------------------------------------------------------------
+void set_error(const std::string& msg);
+lfem_status fail(lfem_status s, const std::string& msg);
+lfem_status cuda_fail(cudaError_t e, const char* what);
+
+#define LFEM_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::lfem::cuda_fail(_e, #call); \
+  } while (0)
+
+// Device status bits (pattern status word).
+enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2 };
+
+// Tile limits.
+constexpr int kMaxTileIncidences = 4096;  // incidences (e, a) per tile; local index fits 12 bits
+constexpr int kMaxDegree = 2048;          // elements meeting at one node
+constexpr int kMaxSegSort = 16384;        // longest row of raw column entries sorted in one block
+
+// ----------------------------------------------------------------------------
+// Element types
+// ----------------------------------------------------------------------------
+__host__ __device__ constexpr int n_ref(int d, int p) { return p == 1 ? d + 1 : (d + 1) * (d + 2) / 2; }
+__host__ __device__ constexpr int n_upper(int ref) { return ref * (ref + 1) / 2; }
+__host__ __device__ constexpr int n_edges(int d, int p) { return p == 2 ? n_ref(d, 2) - (d + 1) : 0; }
+
+bool supported(int dim, int ambient, int order);
+
+// Reference tables (Lagrange basis, Sec. 3.1; quadrature rule, Sec. 3.2.2) in
+// constant memory.  One 64 KB bank per device, append-only registry keyed by
+// (dim, order, rule).  Layout of one entry (precision T = float or double):
+//   w[Q], phi[Q][REF], dphi[Q][REF][D], dpsi[Q][NE][D]
+// dpsi are the gradients of the edge bubbles 4 l_i l_j, used to build the
+// Jacobian in hierarchical form (corner edge vectors + edge-node deviations).
+struct TabRef {
+  int q = 0;
+  int off32 = 0;  // offset in floats into the bank
+  int off64 = 0;  // offset in doubles into the bank
+};
+lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t st, TabRef* out);
+
+// One bank per translation unit (no relocatable device code); every unit's
+// copy receives the same uploads (see bank_upload_d*).
+static __constant__ double c_bank[8192];
+
+template <typename T>
+__device__ __forceinline__ const T* bank();
+template <>
+__device__ __forceinline__ const float* bank<float>() {
+  return reinterpret_cast<const float*>(c_bank);
+}
+template <>
+__device__ __forceinline__ const double* bank<double>() {
+  return c_bank;
+}
+
+template <int D, int P>
+struct Ref {
+  static constexpr int REF = n_ref(D, P);
+  static constexpr int U = n_upper(REF);
+  static constexpr int NE = n_edges(D, P);
+};
+
+// Edge k of the P2 element joins corners (edge_i(k), edge_j(k)).
+template <int D>
+__host__ __device__ constexpr int edge_i(int k) {
+  return D == 1 ? 0 : (D == 2 ? (k == 2 ? 2 : k) : (k < 3 ? (k == 2 ? 2 : k) : k - 3));
+}
+template <int D>
+__host__ __device__ constexpr int edge_j(int k) {
+  return D == 1 ? 1 : (D == 2 ? (k == 2 ? 0 : k + 1) : (k < 3 ? (k == 2 ? 0 : k + 1) : 3));
+}
+
+// Upper-triangle index of local pair (a, b), a <= b.
+__host__ __device__ constexpr int upper_index(int ref, int a, int b) {
+  return a * ref - a * (a - 1) / 2 + (b - a);
+}
+__host__ __device__ constexpr int sym_index(int ref, int a, int b) {
+  return a <= b ? upper_index(ref, a, b) : upper_index(ref, b, a);
+}
+
+template <typename T>
+struct TabView {
+  const T* w;
+  const T* phi;
+  const T* dphi;
+  const T* dpsi;
+  int q;
+};
+
+template <int D, int P, typename T>
+__device__ __forceinline__ TabView<T> tab_view(const TabRef& t) {
+  constexpr int REF = Ref<D, P>::REF, NE = Ref<D, P>::NE;
+  const T* base = bank<T>() + (sizeof(T) == 4 ? t.off32 : t.off64);
+  TabView<T> v;
+  v.q = t.q;
+  v.w = base;
+  v.phi = v.w + t.q;
+  v.dphi = v.phi + t.q * REF;
+  v.dpsi = v.dphi + t.q * REF * D;
+  (void)NE;
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Per-element geometry and local matrices (Sec. 3.2), compute precision R.
+//
+//   J   = [x_1 - x_0, ..., x_D - x_0] + sum_k delta_k (grad psi_k)^T
+//         (delta_k = x_{edge k} - (x_i + x_j)/2; equal to sum_a x_a grad phi_a^T
+//          for the Lagrange P2 map, Eq. F_map, with the affine part exact)
+//   s   = |det DF|: |det J| (D = n), |t1 x t2| (D=2, n=3), |t| (D=1)
+//   H   = w s G^{-1} = (w / s) adj(G),  G = J^T J
+//   M_ab  += w s phi_a phi_b,  MC_ab += w s c phi_a phi_b,
+//   A_ab  += grad^phi_a . (H grad^phi_b)
+// ----------------------------------------------------------------------------
+template <int D, int NA, int P>
+struct ElemGeom {
+  static constexpr int REF = Ref<D, P>::REF;
+  static constexpr int NE = Ref<D, P>::NE;
+};
+
+template <int D, int NA, int P, typename R>
+struct ElemData {
+  static constexpr int REF = Ref<D, P>::REF;
+  static constexpr int NE = Ref<D, P>::NE;
+  R e[D][NA];                      // corner edge vectors x_{m+1} - x_0
+  R dl[NE > 0 ? NE : 1][NA];       // edge-node deviations
+};
+
+template <int D, int NA, int P, typename R>
+__device__ __forceinline__ void load_element_data(const double (&X)[Ref<D, P>::REF][NA], ElemData<D, NA, P, R>& ed) {
+#pragma unroll
+  for (int m = 0; m < D; ++m)
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ed.e[m][i] = (R)(X[m + 1][i] - X[0][i]);
+#pragma unroll
+  for (int k = 0; k < Ref<D, P>::NE; ++k)
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+      ed.dl[k][i] = (R)(X[D + 1 + k][i] - 0.5 * (X[edge_i<D>(k)][i] + X[edge_j<D>(k)][i]));
+}
+
+// Geometry at quadrature point q: J (NA x D), s, H (D x D sym, stored full), metric quality.
+template <int D, int NA, int P, typename R>
+struct QpGeom {
+  R J[NA][D];
+  R s;
+  R H[D][D];      // w s G^{-1}
+  R quality;      // det G / (tr G / D)^D in (0, 1]; 1 for D = 1
+};
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_(R x);
+template <>
+__device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+
+template <int D, int NA, int P, typename R>
+__device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb, int q, R wq,
+                                            QpGeom<D, NA, P, R>& g) {
+  constexpr int NE = Ref<D, P>::NE;
+#pragma unroll
+  for (int i = 0; i < NA; ++i)
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      R acc = ed.e[m][i];
+#pragma unroll
+      for (int k = 0; k < NE; ++k) acc = fma(ed.dl[k][i], tb.dpsi[(q * NE + k) * D + m], acc);
+      g.J[i][m] = acc;
+    }
+  if constexpr (D == 1) {
+    R tt = 0;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) tt = fma(g.J[i][0], g.J[i][0], tt);
+    R s = sqrt(tt);
+    g.s = s;
+    g.H[0][0] = wq / s;
+    g.quality = (R)1;
+  } else if constexpr (D == 2) {
+    R g11 = 0, g12 = 0, g22 = 0;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      g11 = fma(g.J[i][0], g.J[i][0], g11);
+      g12 = fma(g.J[i][0], g.J[i][1], g12);
+      g22 = fma(g.J[i][1], g.J[i][1], g22);
+    }
+    R s;
+    if constexpr (NA == 2) {
+      s = fabs(g.J[0][0] * g.J[1][1] - g.J[0][1] * g.J[1][0]);
+    } else {
+      R n0 = g.J[1][0] * g.J[2][1] - g.J[2][0] * g.J[1][1];
+      R n1 = g.J[2][0] * g.J[0][1] - g.J[0][0] * g.J[2][1];
+      R n2 = g.J[0][0] * g.J[1][1] - g.J[1][0] * g.J[0][1];
+      s = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    }
+    g.s = s;
+    R ws_inv = wq / s;
+    g.H[0][0] = ws_inv * g22;
+    g.H[1][1] = ws_inv * g11;
+    g.H[0][1] = g.H[1][0] = -ws_inv * g12;
+    R tr = (R)0.5 * (g11 + g22);
+    g.quality = (s * s) / (tr * tr);
+  } else {
+    // D = NA = 3: cofactor vectors c_m = t_{m+1} x t_{m+2}; adj(G)_mk = c_m . c_k
+    R c[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+      c[m][0] = g.J[1][m1] * g.J[2][m2] - g.J[2][m1] * g.J[1][m2];
+      c[m][1] = g.J[2][m1] * g.J[0][m2] - g.J[0][m1] * g.J[2][m2];
+      c[m][2] = g.J[0][m1] * g.J[1][m2] - g.J[1][m1] * g.J[0][m2];
+    }
+    R det = g.J[0][0] * c[0][0] + g.J[1][0] * c[0][1] + g.J[2][0] * c[0][2];
+    R s = fabs(det);
+    g.s = s;
+    R ws_inv = wq / s;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int k = m; k < 3; ++k) {
+        R dot = c[m][0] * c[k][0] + c[m][1] * c[k][1] + c[m][2] * c[k][2];
+        g.H[m][k] = g.H[k][m] = ws_inv * dot;
+      }
+    R tr = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) tr = fma(g.J[i][m], g.J[i][m], tr);
+    tr *= (R)(1.0 / 3.0);
+    g.quality = (s * s) / (tr * tr * tr);
+  }
+}
+
+// Accumulate one quadrature point's contributions into the local upper-triangle
+// accumulators (compile-time selection of which matrices this pass computes).
+template <int D, int NA, int P, typename R, bool DO_M, bool DO_A, bool DO_C>
+__device__ __forceinline__ void qp_accumulate(const QpGeom<D, NA, P, R>& g, const TabView<R>& tb, int q, R wq, R cq,
+                                              R (&Mo)[Ref<D, P>::U], R (&Ao)[Ref<D, P>::U],
+                                              R (&Co)[Ref<D, P>::U]) {
+  constexpr int REF = Ref<D, P>::REF;
+  const R* ph = tb.phi + q * REF;
+  const R* dph = tb.dphi + q * REF * D;
+  const R ws = wq * g.s;
+  if constexpr (DO_M || DO_C) {
+#pragma unroll
+    for (int a = 0; a < REF; ++a) {
+      R wpa = ws * ph[a];
+      R wca = wpa * cq;
+#pragma unroll
+      for (int b = a; b < REF; ++b) {
+        const int u = upper_index(REF, a, b);
+        if constexpr (DO_M) Mo[u] = fma(wpa, ph[b], Mo[u]);
+        if constexpr (DO_C) Co[u] = fma(wca, ph[b], Co[u]);
+      }
+    }
+  }
+  if constexpr (DO_A) {
+#pragma unroll
+    for (int b = 0; b < REF; ++b) {
+      R y[D];
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        R acc = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc = fma(g.H[m][k], dph[b * D + k], acc);
+        y[m] = acc;
+      }
+#pragma unroll
+      for (int a = 0; a <= b; ++a) {
+        const int u = upper_index(REF, a, b);
+        R acc = Ao[u];
+#pragma unroll
+        for (int m = 0; m < D; ++m) acc = fma(dph[a * D + m], y[m], acc);
+        Ao[u] = acc;
+      }
+    }
+  }
+}
+
+// Load the REF x NA coordinates of element e (FP64, read-only path).
+template <int D, int NA, int P>
+__device__ __forceinline__ void gather_coords(const double* __restrict__ coords, const int32_t* __restrict__ cn,
+                                              double (&X)[Ref<D, P>::REF][NA]) {
+#pragma unroll
+  for (int a = 0; a < Ref<D, P>::REF; ++a) {
+    const double* p = coords + (int64_t)cn[a] * NA;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) X[a][i] = __ldg(p + i);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Pattern handle
+// ----------------------------------------------------------------------------
+struct PatternDev {
+  int32_t* conn = nullptr;       // [nE][ref] device copy
+  int64_t* row_ptr = nullptr;    // [N+1]
+  int32_t* col_idx = nullptr;    // [nnz]
+  int32_t* inc_ptr = nullptr;    // [N+1] node-incidence offsets
+  int32_t* inc_key = nullptr;    // [nInc] e * 16 + a, ascending per node
+  uint8_t* inc_pos = nullptr;    // [nInc][ref] column position of conn[e][b] in row conn[e][a] (u8 or u16)
+  int32_t* elem_inc = nullptr;   // [nE][ref] incidence index of (e, a)
+  int32_t* tile_row0 = nullptr;  // [T+1]
+  int32_t* tile_elem_ptr = nullptr;  // [T+1]
+  int32_t* tile_elem = nullptr;  // [sum] ascending element ids per tile
+  uint16_t* inc_local = nullptr; // [nInc] (index of e in its tile's list) << 4 | a
+  int32_t* status = nullptr;     // [4]: status bits, pad, fallback count (int64 at [2])
+};
+
+}  // namespace lfem
+
+struct lfem_pattern_s {
+  int device = 0;
+  int dim = 0, order = 0, ref = 0;
+  int64_t n_elem = 0;
+  int32_t n_nodes = 0;
+  int64_t nnz = 0;
+  int64_t n_inc = 0;
+  int32_t max_row = 0, max_deg = 0;
+  int pos_bytes = 1;
+  int32_t tile_slots = 4096;
+  int64_t n_tiles = 0;
+  int64_t tile_elems_total = 0;
+  int32_t chunk = 0;    // elements per chunk (0 = default)
+  int32_t threads = 0;  // threads per block (0 = default)
+  lfem::PatternDev d;
+};
+
+namespace lfem {
+lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st);
+}

@@ -1,0 +1,555 @@
+// Pattern builder (once per topology): integer sort / unique of the element
+// index pairs (E[e,a], E[e,b]) into CSR, plus the maps the assembly kernels
+// use.  All integer work; the result is bit-exact and independent of thread
+// scheduling (atomics only count, every list is sorted before use).
+//
+// This replaces the per-assembly sort inside sparse(I, J, V) (Sec. 3.3: the
+// log-linear cost comes from sorting and merging duplicates; precomputing the
+// sparsity structure removes it from the assembly).
+#include <climits>
+#include <cstdio>
+#include <vector>
+
+#include "lfem_internal.cuh"
+
+namespace lfem {
+
+// ----------------------------------------------------------------------------
+// Exclusive scan (3 phases, recursive on block sums).
+// ----------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename TI, typename TO>
+__global__ void k_scan_tiles(const TI* __restrict__ in, TO* __restrict__ out, int64_t n, TO* __restrict__ tile_sums) {
+  __shared__ TO warp_tot[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  TO v[kScanItems];
+  TO run = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    TO x = (base + i < n) ? (TO)in[base + i] : (TO)0;
+    v[i] = run;
+    run += x;
+  }
+  // inclusive scan of per-thread totals within the block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  TO t = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    TO y = __shfl_up_sync(0xffffffffu, t, o);
+    if (lane >= o) t += y;
+  }
+  if (lane == 31) warp_tot[wid] = t;
+  __syncthreads();
+  if (wid == 0) {
+    TO w = (lane < kScanThreads / 32) ? warp_tot[lane] : (TO)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      TO y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  TO excl = t - run + (wid > 0 ? warp_tot[wid - 1] : (TO)0);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) out[base + i] = v[i] + excl;
+  if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = excl + run;
+}
+
+template <typename TO>
+__global__ void k_scan_add(TO* __restrict__ out, int64_t n, const TO* __restrict__ tile_off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_off[i / kScanTile];
+}
+
+// out[0..n] = exclusive scan of in[0..n) with out[n] = total.  `scratch` needs
+// scan_scratch_elems(n) elements of TO.
+inline int64_t scan_scratch_elems(int64_t n) {
+  int64_t tot = 0;
+  int64_t m = n + 1;
+  while (true) {
+    int64_t tiles = (m + kScanTile - 1) / kScanTile;
+    tot += tiles;
+    if (tiles <= 1) break;
+    m = tiles;
+  }
+  return tot + 8;
+}
+
+template <typename TI, typename TO>
+void scan_exclusive(const TI* in, TO* out, int64_t n, TO* scratch, cudaStream_t st) {
+  // treat the input as n+1 items with a trailing zero so out[n] is the total
+  int64_t m = n + 1;
+  int64_t tiles = (m + kScanTile - 1) / kScanTile;
+  TO* sums = scratch;
+  // in[n] is out of range: scan n items then write the total from the tile sums
+  k_scan_tiles<TI, TO><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, sums);
+  if (tiles > 1) {
+    TO* sums_scanned = scratch + tiles;
+    scan_exclusive<TO, TO>(sums, sums_scanned, tiles, scratch + 2 * tiles + 1, st);
+    k_scan_add<TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, sums_scanned);
+    cudaMemcpyAsync(out + n, sums_scanned + tiles, sizeof(TO), cudaMemcpyDeviceToDevice, st);
+  } else {
+    cudaMemcpyAsync(out + n, sums, sizeof(TO), cudaMemcpyDeviceToDevice, st);
+  }
+}
+
+static int64_t scan_scratch_bytes(int64_t n, size_t elem) {
+  // generous: 3 levels of tile sums plus recursion
+  int64_t t = (n + 1 + kScanTile - 1) / kScanTile;
+  return (4 * t + 64) * (int64_t)elem;
+}
+
+// ----------------------------------------------------------------------------
+// Segmented sort of int32 keys: segment i is [off[i]*scale, off[i+1]*scale).
+// Bitonic networks in shared memory: a warp per segment up to 1024 keys, a
+// block per segment up to kMaxSegSort keys.
+// ----------------------------------------------------------------------------
+template <bool BLOCK>
+__device__ void bitonic_smem(int32_t* s, int n, int tid, int nthr) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < n; i += nthr) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          int32_t a = s[i], b = s[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            s[i] = b;
+            s[ixj] = a;
+          }
+        }
+      }
+      if (BLOCK) __syncthreads();
+      else __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ int next_pow2(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+constexpr int kWarpSegMax = 1024;
+constexpr int kSegWarps = 4;
+
+__global__ void k_segsort_warp(int32_t* __restrict__ keys, const int32_t* __restrict__ off, int64_t nseg, int scale,
+                               int32_t* __restrict__ long_list, int32_t* __restrict__ long_count) {
+  __shared__ int32_t buf[kSegWarps][kWarpSegMax];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t seg = (int64_t)blockIdx.x * kSegWarps + w;
+  if (seg >= nseg) return;
+  const int64_t b = (int64_t)off[seg] * scale, e = (int64_t)off[seg + 1] * scale;
+  const int len = (int)(e - b);
+  if (len <= 1) return;
+  if (len > kWarpSegMax) {
+    if (lane == 0) long_list[atomicAdd(long_count, 1)] = (int32_t)seg;
+    return;
+  }
+  const int n = next_pow2(len);
+  for (int i = lane; i < n; i += 32) buf[w][i] = i < len ? keys[b + i] : INT_MAX;
+  __syncwarp();
+  bitonic_smem<false>(buf[w], n, lane, 32);
+  for (int i = lane; i < len; i += 32) keys[b + i] = buf[w][i];
+}
+
+__global__ void k_segsort_block(int32_t* __restrict__ keys, const int32_t* __restrict__ off, int scale,
+                                const int32_t* __restrict__ long_list) {
+  extern __shared__ int32_t sbuf[];
+  const int32_t seg = long_list[blockIdx.x];
+  const int64_t b = (int64_t)off[seg] * scale, e = (int64_t)off[seg + 1] * scale;
+  const int len = (int)(e - b);
+  const int n = next_pow2(len);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sbuf[i] = i < len ? keys[b + i] : INT_MAX;
+  __syncthreads();
+  bitonic_smem<true>(sbuf, n, threadIdx.x, blockDim.x);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) keys[b + i] = sbuf[i];
+}
+
+static lfem_status segsort(int32_t* keys, const int32_t* off, int64_t nseg, int scale, int max_len,
+                           int32_t* scratch /* nseg + 1 ints */, cudaStream_t st) {
+  if (max_len > kMaxSegSort) return fail(LFEM_E_TOO_LARGE, "segment longer than the sort limit");
+  int32_t* count = scratch;
+  int32_t* list = scratch + 1;
+  LFEM_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), st));
+  if (nseg > 0) {
+    unsigned grid = (unsigned)((nseg + kSegWarps - 1) / kSegWarps);
+    k_segsort_warp<<<grid, 32 * kSegWarps, 0, st>>>(keys, off, nseg, scale, list, count);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  if (max_len > kWarpSegMax) {
+    int32_t h = 0;
+    LFEM_CUDA(cudaMemcpyAsync(&h, count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LFEM_CUDA(cudaStreamSynchronize(st));
+    if (h > 0) {
+      int np2 = 1;
+      while (np2 < max_len) np2 <<= 1;
+      size_t smem = (size_t)np2 * sizeof(int32_t);
+      LFEM_CUDA(cudaFuncSetAttribute(k_segsort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_segsort_block<<<h, 512, smem, st>>>(keys, off, scale, list);
+      LFEM_CUDA(cudaGetLastError());
+    }
+  }
+  return LFEM_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Pattern kernels
+// ----------------------------------------------------------------------------
+__global__ void k_count_degree(const int32_t* __restrict__ conn, int64_t total, int32_t n_nodes,
+                               int32_t* __restrict__ deg, int32_t* __restrict__ status) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = conn[k];
+    if (v < 0 || v >= n_nodes) {
+      atomicOr(status, ST_INDEX);
+      continue;
+    }
+    atomicAdd(&deg[v], 1);
+  }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ a, int64_t n, int32_t* __restrict__ out) {
+  int32_t m = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, a[k]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_fill_incidence(const int32_t* __restrict__ conn, int64_t n_elem, int ref,
+                                 const int32_t* __restrict__ inc_ptr, int32_t* __restrict__ cursor,
+                                 int32_t* __restrict__ inc_key) {
+  const int64_t total = n_elem * ref;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = conn[k];
+    int64_t e = k / ref;
+    int a = (int)(k - e * ref);
+    int32_t slot = inc_ptr[v] + atomicAdd(&cursor[v], 1);
+    inc_key[slot] = (int32_t)(e * 16 + a);
+  }
+}
+
+__global__ void k_elem_inc_and_raw(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ inc_key,
+                                   int64_t n_inc, int32_t* __restrict__ elem_inc, int32_t* __restrict__ raw) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_inc; k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t key = inc_key[k];
+    int64_t e = key >> 4;
+    int a = key & 15;
+    elem_inc[e * ref + a] = (int32_t)k;
+    for (int b = 0; b < ref; ++b) raw[k * ref + b] = conn[e * ref + b];
+  }
+}
+
+__global__ void k_row_unique_count(const int32_t* __restrict__ raw, const int32_t* __restrict__ inc_ptr, int ref,
+                                   int32_t n_nodes, int32_t* __restrict__ rowlen) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = (int64_t)inc_ptr[i] * ref, e = (int64_t)inc_ptr[i + 1] * ref;
+    int32_t cnt = 0;
+    int32_t prev = -1;
+    for (int64_t k = b; k < e; ++k) {
+      int32_t v = raw[k];
+      cnt += (v != prev);
+      prev = v;
+    }
+    rowlen[i] = cnt;
+  }
+}
+
+__global__ void k_row_compact(const int32_t* __restrict__ raw, const int32_t* __restrict__ inc_ptr, int ref,
+                              int32_t n_nodes, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = (int64_t)inc_ptr[i] * ref, e = (int64_t)inc_ptr[i + 1] * ref;
+    int64_t o = row_ptr[i];
+    int32_t prev = -1;
+    for (int64_t k = b; k < e; ++k) {
+      int32_t v = raw[k];
+      if (v != prev) col_idx[o++] = v;
+      prev = v;
+    }
+  }
+}
+
+template <typename PosT>
+__global__ void k_positions(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ inc_key,
+                            const int32_t* __restrict__ inc_ptr, int32_t n_nodes, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col_idx, PosT* __restrict__ pos) {
+  // one thread per node; each incidence of the node gets the positions of its element's nodes in the row
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+    for (int32_t k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) {
+      int64_t e = inc_key[k] >> 4;
+      for (int b = 0; b < ref; ++b) {
+        int32_t c = conn[e * ref + b];
+        int64_t lo = rb, hi = re;
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (col_idx[mid] < c) lo = mid + 1;
+          else hi = mid;
+        }
+        pos[(int64_t)k * ref + b] = (PosT)(lo - rb);
+      }
+    }
+  }
+}
+
+// Per-tile element lists: sort + unique the elements of the tile's incidences;
+// local index of every incidence; count.
+__global__ void k_tile_elements(const int32_t* __restrict__ tile_row0, const int32_t* __restrict__ inc_ptr,
+                                const int32_t* __restrict__ inc_key, int32_t* __restrict__ tmp,
+                                int32_t* __restrict__ counts, uint16_t* __restrict__ inc_local) {
+  __shared__ int32_t s[kMaxTileIncidences];
+  __shared__ int32_t wsum[32];
+  const int t = blockIdx.x;
+  const int32_t i0 = inc_ptr[tile_row0[t]], i1 = inc_ptr[tile_row0[t + 1]];
+  const int n = i1 - i0;
+  if (n == 0) {
+    if (threadIdx.x == 0) counts[t] = 0;
+    return;
+  }
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) s[i] = i < n ? (inc_key[i0 + i] >> 4) : INT_MAX;
+  __syncthreads();
+  bitonic_smem<true>(s, np2, threadIdx.x, blockDim.x);
+  // unique: flags -> block scan (sequential per thread chunk)
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int beg = threadIdx.x * per, end = min(n, beg + per);
+  int cnt = 0;
+  for (int i = beg; i < end; ++i) cnt += (i == 0 || s[i] != s[i - 1]);
+  // block exclusive scan of cnt
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    wsum[lane] = v;
+  }
+  __syncthreads();
+  int excl = x - cnt + (wid > 0 ? wsum[wid - 1] : 0);
+  const int total = wsum[(blockDim.x >> 5) - 1];
+  // unique values in place: write to tmp at offset i0
+  for (int i = beg; i < end; ++i) {
+    if (i == 0 || s[i] != s[i - 1]) tmp[i0 + excl++] = s[i];
+  }
+  __syncthreads();
+  // local index of each incidence: binary search in tmp (unique, ascending)
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    int32_t key = inc_key[i0 + k];
+    int32_t e = key >> 4;
+    int lo = 0, hi = total;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (tmp[i0 + mid] < e) lo = mid + 1;
+      else hi = mid;
+    }
+    inc_local[i0 + k] = (uint16_t)((lo << 4) | (key & 15));
+  }
+  if (threadIdx.x == 0) counts[t] = total;
+}
+
+__global__ void k_tile_compact(const int32_t* __restrict__ tile_row0, const int32_t* __restrict__ inc_ptr,
+                               const int32_t* __restrict__ tmp, const int32_t* __restrict__ tile_elem_ptr,
+                               int32_t* __restrict__ tile_elem) {
+  const int t = blockIdx.x;
+  const int32_t i0 = inc_ptr[tile_row0[t]];
+  const int32_t o = tile_elem_ptr[t], n = tile_elem_ptr[t + 1] - o;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tile_elem[o + i] = tmp[i0 + i];
+}
+
+// ----------------------------------------------------------------------------
+// Host orchestration
+// ----------------------------------------------------------------------------
+static unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 64) g = 152 * 64;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+template <typename T>
+static lfem_status dalloc(T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(LFEM_E_NOMEM, "device allocation failed");
+  }
+  return LFEM_OK;
+}
+
+#define TRY(x)                          \
+  do {                                  \
+    lfem_status _s = (x);               \
+    if (_s != LFEM_OK) return _s;       \
+  } while (0)
+
+lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st) {
+  PatternDev& d = p->d;
+  const int32_t N = p->n_nodes;
+  if (tile_slots < 256 || tile_slots > 16384) return fail(LFEM_E_ARG, "tile_slots outside [256, 16384]");
+  if (p->max_row > tile_slots) return fail(LFEM_E_TOO_LARGE, "a CSR row is longer than the tile capacity");
+  // greedy contiguous packing of rows under the slot and incidence budgets
+  std::vector<int64_t> rp(N + 1);
+  std::vector<int32_t> ip(N + 1);
+  LFEM_CUDA(cudaMemcpyAsync(rp.data(), d.row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaMemcpyAsync(ip.data(), d.inc_ptr, sizeof(int32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  std::vector<int32_t> rows;
+  rows.push_back(0);
+  int32_t r0 = 0;
+  for (int32_t i = 0; i < N; ++i) {
+    bool over = (rp[i + 1] - rp[r0] > tile_slots) || (ip[i + 1] - ip[r0] > kMaxTileIncidences);
+    if (over && i > r0) {
+      rows.push_back(i);
+      r0 = i;
+    }
+  }
+  if (N > 0 && rows.back() != N) rows.push_back(N);
+  const int64_t T = (int64_t)rows.size() - 1;
+  if (d.tile_row0) cudaFree(d.tile_row0);
+  if (d.tile_elem_ptr) cudaFree(d.tile_elem_ptr);
+  if (d.tile_elem) cudaFree(d.tile_elem);
+  d.tile_row0 = d.tile_elem_ptr = d.tile_elem = nullptr;
+  TRY(dalloc(&d.tile_row0, T + 1));
+  TRY(dalloc(&d.tile_elem_ptr, T + 1));
+  LFEM_CUDA(cudaMemcpyAsync(d.tile_row0, rows.data(), sizeof(int32_t) * (T + 1), cudaMemcpyHostToDevice, st));
+  int32_t *tmp = nullptr, *counts = nullptr, *scr = nullptr;
+  TRY(dalloc(&tmp, p->n_inc));
+  TRY(dalloc(&counts, T + 1));
+  TRY(dalloc(&scr, scan_scratch_bytes(T, sizeof(int32_t)) / 4));
+  if (T > 0) {
+    k_tile_elements<<<(unsigned)T, 512, 0, st>>>(d.tile_row0, d.inc_ptr, d.inc_key, tmp, counts, d.inc_local);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  scan_exclusive<int32_t, int32_t>(counts, d.tile_elem_ptr, T, scr, st);
+  int32_t total = 0;
+  LFEM_CUDA(cudaMemcpyAsync(&total, d.tile_elem_ptr + T, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  TRY(dalloc(&d.tile_elem, total));
+  if (T > 0) {
+    k_tile_compact<<<(unsigned)T, 256, 0, st>>>(d.tile_row0, d.inc_ptr, tmp, d.tile_elem_ptr, d.tile_elem);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  cudaFree(tmp);
+  cudaFree(counts);
+  cudaFree(scr);
+  p->n_tiles = T;
+  p->tile_slots = tile_slots;
+  p->tile_elems_total = total;
+  return LFEM_OK;
+}
+
+lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_t st) {
+  PatternDev& d = p->d;
+  const int ref = p->ref;
+  const int64_t nE = p->n_elem;
+  const int32_t N = p->n_nodes;
+  const int64_t n_inc = nE * ref;
+  p->n_inc = n_inc;
+  TRY(dalloc(&d.status, 4));
+  LFEM_CUDA(cudaMemsetAsync(d.status, 0, 4 * sizeof(int32_t), st));
+  TRY(dalloc(&d.conn, n_inc));
+  if (n_inc > 0)
+    LFEM_CUDA(cudaMemcpyAsync(d.conn, conn_in, sizeof(int32_t) * n_inc, cudaMemcpyDeviceToDevice, st));
+  int32_t *deg = nullptr, *scr = nullptr, *maxv = nullptr;
+  TRY(dalloc(&deg, (int64_t)N + 1));
+  TRY(dalloc(&d.inc_ptr, (int64_t)N + 1));
+  TRY(dalloc(&scr, scan_scratch_bytes((int64_t)N + n_inc, sizeof(int64_t)) / 4 + (int64_t)N + 2));
+  TRY(dalloc(&maxv, 2));
+  LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((int64_t)N + 1), st));
+  LFEM_CUDA(cudaMemsetAsync(maxv, 0, 2 * sizeof(int32_t), st));
+  if (n_inc > 0) k_count_degree<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, n_inc, N, deg, d.status);
+  LFEM_CUDA(cudaGetLastError());
+  if (N > 0) k_max_i32<<<grid_for(N, 256), 256, 0, st>>>(deg, N, maxv);
+  int32_t hst[2] = {0, 0};
+  LFEM_CUDA(cudaMemcpyAsync(&hst[0], d.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaMemcpyAsync(&hst[1], maxv, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (hst[0] & ST_INDEX) {
+    cudaFree(deg);
+    cudaFree(scr);
+    cudaFree(maxv);
+    return fail(LFEM_E_INDEX, "connectivity holds a node index outside [0, n_nodes)");
+  }
+  p->max_deg = hst[1];
+  if (p->max_deg > kMaxDegree || (int64_t)p->max_deg * ref > kMaxSegSort) {
+    cudaFree(deg);
+    cudaFree(scr);
+    cudaFree(maxv);
+    return fail(LFEM_E_TOO_LARGE, "too many elements meet at one node");
+  }
+  scan_exclusive<int32_t, int32_t>(deg, d.inc_ptr, N, scr, st);
+  TRY(dalloc(&d.inc_key, n_inc));
+  LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((int64_t)N + 1), st));
+  if (n_inc > 0) k_fill_incidence<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, nE, ref, d.inc_ptr, deg, d.inc_key);
+  LFEM_CUDA(cudaGetLastError());
+  int32_t* sort_scr = nullptr;
+  TRY(dalloc(&sort_scr, (int64_t)N + 2));
+  TRY(segsort(d.inc_key, d.inc_ptr, N, 1, p->max_deg, sort_scr, st));
+  // raw column lists per row and the (e, a) -> incidence map
+  int32_t* raw = nullptr;
+  TRY(dalloc(&raw, n_inc * ref));
+  TRY(dalloc(&d.elem_inc, n_inc));
+  if (n_inc > 0) k_elem_inc_and_raw<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, ref, d.inc_key, n_inc, d.elem_inc, raw);
+  LFEM_CUDA(cudaGetLastError());
+  TRY(segsort(raw, d.inc_ptr, N, ref, p->max_deg * ref, sort_scr, st));
+  int32_t* rowlen = deg;  // reuse
+  if (N > 0) k_row_unique_count<<<grid_for(N, 128), 128, 0, st>>>(raw, d.inc_ptr, ref, N, rowlen);
+  LFEM_CUDA(cudaGetLastError());
+  TRY(dalloc(&d.row_ptr, (int64_t)N + 1));
+  int64_t* scr64 = nullptr;
+  TRY(dalloc(&scr64, scan_scratch_bytes(N, sizeof(int64_t)) / 8));
+  scan_exclusive<int32_t, int64_t>(rowlen, d.row_ptr, N, scr64, st);
+  LFEM_CUDA(cudaMemsetAsync(maxv, 0, 2 * sizeof(int32_t), st));
+  if (N > 0) k_max_i32<<<grid_for(N, 256), 256, 0, st>>>(rowlen, N, maxv);
+  int64_t nnz = 0;
+  LFEM_CUDA(cudaMemcpyAsync(&nnz, d.row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaMemcpyAsync(&hst[1], maxv, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  p->nnz = nnz;
+  p->max_row = hst[1];
+  if (nnz >= INT32_MAX) return fail(LFEM_E_TOO_LARGE, "nnz >= 2^31");
+  TRY(dalloc(&d.col_idx, nnz));
+  if (N > 0) k_row_compact<<<grid_for(N, 128), 128, 0, st>>>(raw, d.inc_ptr, ref, N, d.row_ptr, d.col_idx);
+  LFEM_CUDA(cudaGetLastError());
+  p->pos_bytes = p->max_row <= 256 ? 1 : 2;
+  TRY(dalloc(&d.inc_pos, n_inc * ref * p->pos_bytes));
+  if (N > 0) {
+    if (p->pos_bytes == 1)
+      k_positions<uint8_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, d.inc_key, d.inc_ptr, N, d.row_ptr,
+                                                               d.col_idx, d.inc_pos);
+    else
+      k_positions<uint16_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, d.inc_key, d.inc_ptr, N, d.row_ptr,
+                                                                d.col_idx, (uint16_t*)d.inc_pos);
+  }
+  LFEM_CUDA(cudaGetLastError());
+  TRY(dalloc(&d.inc_local, n_inc));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  cudaFree(raw);
+  cudaFree(deg);
+  cudaFree(scr);
+  cudaFree(scr64);
+  cudaFree(maxv);
+  cudaFree(sort_scr);
+  return build_tiles(p, p->tile_slots, st);
+}
+
+}  // namespace lfem

@@ -1,0 +1,291 @@
+"""Python binding of liblfem.so (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library; torch supplies device memory and
+streams.  If the library cannot be loaded the import of this module raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblfem.so")
+
+MASS, STIFF, CMASS = 1, 2, 4
+FP64, MIXED = 0, 1
+STATUS = {0: "LFEM_OK", 1: "LFEM_E_ARG", 2: "LFEM_E_INDEX", 3: "LFEM_E_UNSUPPORTED", 4: "LFEM_E_TOO_LARGE",
+          5: "LFEM_E_NOMEM", 6: "LFEM_E_CUDA", 7: "LFEM_E_DEGENERATE", 8: "LFEM_E_TIMEOUT"}
+
+# Every entry point declared in include/lfem.h.
+EXPORTS = (
+    "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
+    "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_assemble_adjoint", "lfem_eval_points",
+    "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
+    "lfem_status_string",
+)
+
+
+class LfemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Quad(ctypes.Structure):
+    _fields_ = [("n_pts", ctypes.c_int), ("xi", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run __graft_entry__.build() (the CUDA library is required)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, L, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint
+    sig = {
+        "lfem_pattern": [P, L, ctypes.c_int32, I, I, P, P],
+        "lfem_pattern_csr": [P, P, P, P, P],
+        "lfem_pattern_copy_csr": [P, P, P, P],
+        "lfem_pattern_info": [P, P, P, P, P],
+        "lfem_pattern_retile": [P, ctypes.c_int32, P],
+        "lfem_assemble": [P, P, I, P, P, I, U, I, P, P, P, P],
+        "lfem_set_launch": [P, ctypes.c_int32, ctypes.c_int32],
+        "lfem_assemble_adjoint": [P, P, I, P, P, P, P, P, P, P, P],
+        "lfem_eval_points": [P, L, I, I, P, I, P, P, P],
+        "lfem_geometry": [P, L, I, I, P, I, P, P, P, P, P],
+        "lfem_local": [P, L, I, I, P, I, P, P, P, P, P, P],
+        "lfem_sync_status": [P, P],
+        "lfem_mixed_fallback_count": [P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.lfem_pattern_destroy.argtypes = [P]
+    lib.lfem_pattern_destroy.restype = None
+    lib.lfem_last_error.restype = ctypes.c_char_p
+    lib.lfem_status_string.restype = ctypes.c_char_p
+    lib.lfem_status_string.argtypes = [I]
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise LfemError(code, _lib.lfem_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class QuadRule:
+    """Host copy of a rule in the layout the C ABI takes (keeps the arrays alive)."""
+
+    xi: np.ndarray
+    w: np.ndarray
+
+    def __post_init__(self):
+        self.xi = np.ascontiguousarray(self.xi, dtype=np.float64)
+        self.w = np.ascontiguousarray(self.w, dtype=np.float64)
+        self._c = _Quad(int(self.w.shape[0]), self.xi.ctypes.data, self.w.ctypes.data)
+
+    @property
+    def n_pts(self):
+        return int(self.w.shape[0])
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+def as_rule(rule) -> QuadRule:
+    if isinstance(rule, QuadRule):
+        return rule
+    return QuadRule(np.asarray(rule.xi), np.asarray(rule.w))
+
+
+def _dev_i32(t):
+    if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+        raise TypeError("conn must be a contiguous int32 CUDA tensor")
+    return t
+
+
+def _dev_f64(t, name):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return t
+
+
+class Pattern:
+    """CSR pattern + assembly maps of one topology (lfem_pattern)."""
+
+    def __init__(self, conn: torch.Tensor, n_nodes: int, dim: int, order: int, stream=None):
+        conn = _dev_i32(conn)
+        self.dim, self.order, self.n_nodes = int(dim), int(order), int(n_nodes)
+        self.n_elem = int(conn.shape[0])
+        self.ref = int(conn.shape[1]) if conn.dim() == 2 else 0
+        h = ctypes.c_void_p()
+        _check(_lib.lfem_pattern(_ptr(conn), self.n_elem, self.n_nodes, self.dim, self.order, _stream(stream),
+                                 ctypes.byref(h)))
+        self._h = h
+        nr, nnz = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.lfem_pattern_csr(self._h, ctypes.byref(nr), ctypes.byref(nnz), None, None))
+        self.nnz = int(nnz.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def csr(self, stream=None):
+        dev = torch.cuda.current_device()
+        rp = torch.empty(self.n_nodes + 1, dtype=torch.int64, device=dev)
+        ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=dev)
+        _check(_lib.lfem_pattern_copy_csr(self._h, _ptr(rp), _ptr(ci), _stream(stream)))
+        return rp, ci[: self.nnz]
+
+    def info(self):
+        nt, rc, mr, ts = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.lfem_pattern_info(self._h, ctypes.byref(nt), ctypes.byref(rc), ctypes.byref(mr),
+                                      ctypes.byref(ts)))
+        return {"tiles": nt.value, "recompute": rc.value / 1000.0, "max_row": mr.value, "tile_slots": ts.value}
+
+    def retile(self, tile_slots: int, stream=None):
+        _check(_lib.lfem_pattern_retile(self._h, int(tile_slots), _stream(stream)))
+
+    def set_launch(self, elems_per_chunk: int = 0, threads: int = 0):
+        _check(_lib.lfem_set_launch(self._h, int(elems_per_chunk), int(threads)))
+
+    def sync_status(self, stream=None):
+        _check(_lib.lfem_sync_status(self._h, _stream(stream)))
+
+    def fallback_count(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        _check(_lib.lfem_mixed_fallback_count(self._h, _stream(stream), ctypes.byref(n)))
+        return int(n.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.lfem_pattern_destroy(h)
+            self._h = ctypes.c_void_p()
+
+
+def assemble(pat: Pattern, coords: torch.Tensor, rule, coef: Optional[torch.Tensor] = None,
+             which: int = MASS | STIFF, precision: int = FP64, out=None, stream=None):
+    """lfem_assemble: returns a dict {'M', 'A', 'MC'} of CSR value tensors."""
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    dt = torch.float64 if precision == FP64 else torch.float32
+    out = dict(out or {})
+    for key, bit in (("M", MASS), ("A", STIFF), ("MC", CMASS)):
+        if which & bit and key not in out:
+            out[key] = torch.empty(max(pat.nnz, 1), dtype=dt, device=coords.device)
+    coef_f32 = 0
+    if coef is not None:
+        if not (coef.is_cuda and coef.is_contiguous() and coef.dtype in (torch.float32, torch.float64)):
+            raise TypeError("coef must be a contiguous float32/float64 CUDA tensor")
+        coef_f32 = int(coef.dtype == torch.float32)
+    _check(_lib.lfem_assemble(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref, _ptr(coef), coef_f32,
+                              int(which), int(precision), _ptr(out.get("M")), _ptr(out.get("A")),
+                              _ptr(out.get("MC")), _stream(stream)))
+    return {k: v[: pat.nnz] for k, v in out.items()}
+
+
+def assemble_adjoint(pat: Pattern, coords: torch.Tensor, rule, coef=None, gM=None, gA=None, gMC=None,
+                     want_coef_grad: bool = False, stream=None):
+    """lfem_assemble_adjoint: returns (g_coords, g_coef or None)."""
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    gx = torch.empty_like(coords)
+    gc = None
+    if want_coef_grad:
+        gc = torch.empty(pat.n_elem, rule.n_pts, dtype=torch.float64, device=coords.device)
+    _check(_lib.lfem_assemble_adjoint(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref,
+                                      _ptr(_dev_f64(coef, "coef")), _ptr(_dev_f64(gM, "gM")),
+                                      _ptr(_dev_f64(gA, "gA")), _ptr(_dev_f64(gMC, "gMC")), _ptr(gx), _ptr(gc),
+                                      _stream(stream)))
+    return gx, gc
+
+
+def eval_points(conn, dim, order, coords, rule, stream=None):
+    conn = _dev_i32(conn)
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    n = int(coords.shape[1])
+    out = torch.empty(conn.shape[0], rule.n_pts, n, dtype=torch.float64, device=coords.device)
+    _check(_lib.lfem_eval_points(_ptr(conn), conn.shape[0], dim, order, _ptr(coords), n, rule.ref, _ptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def geometry(conn, dim, order, coords, rule, stream=None):
+    conn = _dev_i32(conn)
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    n = int(coords.shape[1])
+    nE, Q = conn.shape[0], rule.n_pts
+    J = torch.empty(nE, Q, n, dim, dtype=torch.float64, device=coords.device)
+    s = torch.empty(nE, Q, dtype=torch.float64, device=coords.device)
+    Gi = torch.empty(nE, Q, dim, dim, dtype=torch.float64, device=coords.device)
+    _check(_lib.lfem_geometry(_ptr(conn), nE, dim, order, _ptr(coords), n, rule.ref, _ptr(J), _ptr(s), _ptr(Gi),
+                              _stream(stream)))
+    return J, s, Gi
+
+
+def local(conn, dim, order, coords, rule, coef=None, which=MASS | STIFF, stream=None):
+    conn = _dev_i32(conn)
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    n = int(coords.shape[1])
+    ref = int(conn.shape[1])
+    U = ref * (ref + 1) // 2
+    mk = lambda bit: torch.empty(conn.shape[0], U, dtype=torch.float64, device=coords.device) if which & bit else None
+    M, A, C = mk(MASS), mk(STIFF), mk(CMASS)
+    _check(_lib.lfem_local(_ptr(conn), conn.shape[0], dim, order, _ptr(coords), n, rule.ref,
+                           _ptr(_dev_f64(coef, "coef")), _ptr(M), _ptr(A), _ptr(C), _stream(stream)))
+    return M, A, C
+
+
+class AssembleFn(torch.autograd.Function):
+    """(coords, coef) -> (M, A, MC) CSR values in FP64; backward calls the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, coords, coef, pat: Pattern, rule):
+        rule = as_rule(rule)
+        which = MASS | STIFF | (CMASS if coef is not None else 0)
+        out = assemble(pat, coords.detach().contiguous(), rule, None if coef is None else coef.detach().contiguous(),
+                       which=which, precision=FP64)
+        ctx.pat, ctx.rule = pat, rule
+        ctx.save_for_backward(coords, coef if coef is not None else torch.empty(0, device=coords.device))
+        ctx.has_coef = coef is not None
+        mc = out.get("MC", torch.zeros_like(out["M"]))
+        return out["M"], out["A"], mc
+
+    @staticmethod
+    def backward(ctx, gM, gA, gMC):
+        coords, coef = ctx.saved_tensors
+        coef = coef if ctx.has_coef else None
+        c = lambda g: None if g is None else g.contiguous().to(torch.float64)
+        gx, gc = assemble_adjoint(ctx.pat, coords.detach().contiguous(), ctx.rule,
+                                  None if coef is None else coef.detach().contiguous(), c(gM), c(gA),
+                                  c(gMC) if ctx.has_coef else None, want_coef_grad=ctx.has_coef)
+        return gx, gc, None, None

@@ -1,0 +1,80 @@
+"""Seeded parity cases: one small mesh per supported (dim, ambient, order),
+sized so the oracle finishes in well under a second but the pattern spans
+several row tiles (tests retile to the minimum capacity) with a ragged tail."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+
+def coef_field(pts: np.ndarray) -> np.ndarray:
+    """c = 1 + x^2 + y z at physical quadrature points (missing coordinates read as 0.5)."""
+    x = pts[..., 0]
+    y = pts[..., 1] if pts.shape[-1] > 1 else 0.5
+    z = pts[..., 2] if pts.shape[-1] > 2 else 0.5
+    return 1.0 + x * x + y * z
+
+
+def _curve_p1(n, seed):
+    x, e = meshes.closed_curve_p2(n, seed)
+    # vertices are the nodes shared by two segments; keep the P1 segments (ends only)
+    conn = e[:, :2].copy()
+    used = np.unique(conn)
+    new = -np.ones(x.shape[0], dtype=np.int64)
+    new[used] = np.arange(used.size)
+    return np.ascontiguousarray(x[used]), new[conn].astype(np.int32)
+
+
+def _space_curve_p2(n, seed):
+    x, e = meshes.closed_curve_p2(n, seed)
+    phi = np.arctan2(x[:, 1], x[:, 0])
+    z = 0.2 * np.sin(3 * phi)
+    return np.ascontiguousarray(np.column_stack([x, z])), e
+
+
+def _interval_p2(n):
+    # [0, 1] with graded nodes; P2: ends then midpoint
+    t = np.linspace(0, 1, n + 1) ** 1.3
+    mids = 0.5 * (t[:-1] + t[1:])
+    x = np.concatenate([t, mids])[:, None]
+    k = np.arange(n)
+    return x, np.stack([k, k + 1, n + 1 + k], 1).astype(np.int32)
+
+
+def build_cases():
+    """name -> (coords, conn, dim, order, rule)."""
+    c = {}
+    r_tri3, r_tri7 = quadrature.tri_3pt_deg2(), quadrature.tri_7pt_deg5()
+    r_tet14, r_tet4 = quadrature.tet_14pt_deg5(), quadrature.tet_4pt_deg2()
+    r_g3 = quadrature.gauss_interval(3)
+    c["sphere_p1"] = (*meshes.icosphere(3, 1), 2, 1, r_tri3)
+    c["ellipsoid_p2"] = (*meshes.ellipsoid(2, sigma=1e-2, seed=3), 2, 2, r_tri7)
+    x, e = meshes.icosphere(3, 2)
+    c["perturbed_sphere_p2"] = (meshes.radial_perturbation(x), e, 2, 2, r_tri7)
+    c["disk_p1"] = (*meshes.hex_disk(7, 1), 2, 1, r_tri3)
+    c["disk_p2"] = (*meshes.hex_disk(5, 2), 2, 2, r_tri7)
+    c["half_disk_p2"] = (*meshes.half_disk_p2(), 2, 2, r_tri7)
+    c["curve_p2"] = (*meshes.closed_curve_p2(400, seed=9), 1, 2, r_g3)
+    c["curve_p1"] = (*_curve_p1(300, 4), 1, 1, quadrature.gauss_interval(2))
+    c["space_curve_p2"] = (*_space_curve_p2(250, 5), 1, 2, r_g3)
+    c["interval_p2"] = (*_interval_p2(200), 1, 2, r_g3)
+    c["cube_p2"] = (*meshes.kuhn_cube_p2(4), 3, 2, r_tet14)
+    c["cube_p1"] = (*meshes.kuhn_cube_p2(5, order=1), 3, 1, r_tet4)
+    xc, ec = meshes.kuhn_cube_p2(3)
+    c["cube_boundary_p2"] = (xc, meshes.boundary_faces_p2(ec), 2, 2, r_tri7)  # rows of interior nodes empty
+    return c
+
+
+def diag_scaled_error(v, ref, rp, ci):
+    """max_ij |v_ij - ref_ij| / sqrt(|ref_ii| |ref_jj|) (0/0 counts as 0)."""
+    n = rp.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    diag = np.zeros(n)
+    is_d = rows == ci
+    diag[rows[is_d]] = np.abs(ref[is_d])
+    den = np.sqrt(diag[rows] * diag[ci])
+    num = np.abs(v - ref)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = np.where(num == 0, 0.0, num / den)
+    return float(np.max(r)) if r.size else 0.0

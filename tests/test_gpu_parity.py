@@ -1,0 +1,210 @@
+"""CUDA path against the FP64 oracle, element by element, on the same seeded inputs.
+
+Bars: patterns bit-exact; FP64 values within 1e-12 diagonal-scaled relative
+error; mixed values within 1e-6 (the stated tolerances); bit-identical reruns
+and tile-shape independence; adjoint within 1e-10 of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from cases import build_cases, coef_field, diag_scaled_error
+
+pytestmark = pytest.mark.gpu
+
+CASES = build_cases()
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lfem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_14035_gb300 import lfem as m
+
+    return m
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def prepare(name, lfem, tile_slots=256):
+    x, e, d, p, rule = CASES[name]
+    pts = oracle.eval_points(x, e, d, p, rule.xi)
+    coef = coef_field(pts)
+    pat = lfem.Pattern(to_dev(e), x.shape[0], d, p)
+    if tile_slots:
+        pat.retile(tile_slots)
+    return x, e, d, p, rule, coef, pat
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pattern_bit_exact(name, lfem):
+    x, e, d, p, rule, coef, pat = prepare(name, lfem, tile_slots=0)
+    rp, ci = pat.csr()
+    orp, oci = oracle.pattern(e, x.shape[0])
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(ci.cpu().numpy(), oci)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_values(name, lfem):
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    assert pat.info()["tiles"] > 2 or x.shape[0] < 50
+    orp, oci, M, A, C = oracle.assemble(x, e, d, p, rule.xi, rule.w, coef)
+    out = lfem.assemble(pat, to_dev(x), rule, to_dev(coef), which=7, precision=lfem.FP64)
+    torch.cuda.synchronize()
+    for k, ref in (("M", M), ("A", A), ("MC", C)):
+        err = diag_scaled_error(out[k].cpu().numpy(), ref, orp, oci)
+        assert err <= FP64_TOL, (k, err)
+    pat.sync_status()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_values(name, lfem):
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    orp, oci, M, A, C = oracle.assemble(x, e, d, p, rule.xi, rule.w, coef)
+    out = lfem.assemble(pat, to_dev(x), rule, to_dev(coef).float(), which=7, precision=lfem.MIXED)
+    torch.cuda.synchronize()
+    for k, ref in (("M", M), ("A", A), ("MC", C)):
+        v = out[k].double().cpu().numpy()
+        assert out[k].dtype == torch.float32
+        err = diag_scaled_error(v, ref, orp, oci)
+        assert err <= MIXED_TOL, (k, err)
+    assert abs(out["M"].double().sum().item() - M.sum()) <= MIXED_TOL * abs(M.sum())
+
+
+@pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p1"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_deterministic_and_tile_independent(name, prec, lfem):
+    """Bit-identical reruns and identical results for every tile capacity: each
+    slot is summed in ascending element order whatever the tiling."""
+    x, e, d, p, rule, coef, pat = prepare(name, lfem, tile_slots=0)
+    xd, cd = to_dev(x), to_dev(coef)
+    if prec == 1:
+        cd = cd.float()
+    ref = lfem.assemble(pat, xd, rule, cd, which=7, precision=prec)
+    again = lfem.assemble(pat, xd, rule, cd, which=7, precision=prec)
+    for slots in (256, 1024, 8192):
+        pat.retile(slots)
+        for chunk in (32, 96):
+            pat.set_launch(chunk, 0)
+            other = lfem.assemble(pat, xd, rule, cd, which=7, precision=prec)
+            for k in ref:
+                assert torch.equal(ref[k], other[k]), (k, slots, chunk)
+    for k in ref:
+        assert torch.equal(ref[k], again[k])
+
+
+@pytest.mark.parametrize("which", [1, 2, 4, 3, 5, 6])
+def test_subsets_of_matrices(which, lfem):
+    x, e, d, p, rule, coef, pat = prepare("ellipsoid_p2", lfem)
+    full = lfem.assemble(pat, to_dev(x), rule, to_dev(coef), which=7, precision=0)
+    part = lfem.assemble(pat, to_dev(x), rule, to_dev(coef), which=which, precision=0)
+    for k, bit in (("M", 1), ("A", 2), ("MC", 4)):
+        if which & bit:
+            assert torch.equal(full[k], part[k])
+        else:
+            assert k not in part
+
+
+@pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p1", "space_curve_p2"])
+def test_element_stages(name, lfem):
+    x, e, d, p, rule, coef, pat = prepare(name, lfem, tile_slots=0)
+    ed, xd = to_dev(e), to_dev(x)
+    pts = lfem.eval_points(ed, d, p, xd, rule).cpu().numpy()
+    assert np.abs(pts - oracle.eval_points(x, e, d, p, rule.xi)).max() < 1e-14 * max(1, np.abs(x).max())
+    J, s, Gi = (t.cpu().numpy() for t in lfem.geometry(ed, d, p, xd, rule))
+    oJ, os_, oGi = oracle.geometry(x, e, d, p, rule.xi)
+    assert np.abs(J - oJ).max() <= 1e-13 * np.abs(oJ).max()
+    assert np.abs(s - os_).max() <= 1e-13 * np.abs(os_).max()
+    assert np.abs(Gi - oGi).max() <= 1e-11 * np.abs(oGi).max()
+    Ml, Al, Cl = (t.cpu().numpy() for t in lfem.local(ed, d, p, xd, rule, to_dev(coef), which=7))
+    oM, oA, oC = oracle.local_matrices(x, e, d, p, rule.xi, rule.w, coef)
+    ref = e.shape[1]
+    iu = np.triu_indices(ref)
+    for got, want in ((Ml, oM), (Al, oA), (Cl, oC)):
+        w = want[:, iu[0], iu[1]]
+        assert np.abs(got - w).max() <= 1e-12 * np.abs(w).max()
+
+
+@pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p2", "sphere_p1", "space_curve_p2"])
+def test_adjoint_matches_oracle(name, lfem):
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    orp, oci = oracle.pattern(e, x.shape[0])
+    rng = np.random.default_rng(17)
+    gM, gA, gC = rng.normal(size=(3, oci.size))
+    gx, gc = lfem.assemble_adjoint(pat, to_dev(x), rule, to_dev(coef), to_dev(gM), to_dev(gA), to_dev(gC),
+                                   want_coef_grad=True)
+    ogx, ogc = oracle.adjoint(x, e, d, p, rule.xi, rule.w, coef, (orp, oci), gM, gA, gC)
+    assert np.abs(gx.cpu().numpy() - ogx).max() <= 1e-10 * np.abs(ogx).max()
+    assert np.abs(gc.cpu().numpy() - ogc).max() <= 1e-11 * np.abs(ogc).max()
+
+
+def test_autograd_function(lfem):
+    """AssembleFn backward against the oracle adjoint of L = u^T M u + v^T A v + w^T MC w."""
+    x, e, d, p, rule, coef, pat = prepare("ellipsoid_p2", lfem)
+    rng = np.random.default_rng(3)
+    u, v, w = (to_dev(rng.normal(size=x.shape[0])) for _ in range(3))
+    rp, ci = pat.csr()
+    rows = torch.repeat_interleave(torch.arange(x.shape[0], device="cuda"), rp[1:] - rp[:-1])
+    xt = to_dev(x).requires_grad_(True)
+    ct = to_dev(coef).requires_grad_(True)
+    M, A, MC = lfem.AssembleFn.apply(xt, ct, pat, rule)
+    L = (M * u[rows] * u[ci]).sum() + (A * v[rows] * v[ci]).sum() + (MC * w[rows] * w[ci]).sum()
+    L.backward()
+    orp, oci = rp.cpu().numpy(), ci.cpu().numpy()
+    rr = rows.cpu().numpy()
+    un, vn, wn = u.cpu().numpy(), v.cpu().numpy(), w.cpu().numpy()
+    ogx, ogc = oracle.adjoint(x, e, d, p, rule.xi, rule.w, coef, (orp, oci), un[rr] * un[oci], vn[rr] * vn[oci],
+                              wn[rr] * wn[oci])
+    assert np.abs(xt.grad.cpu().numpy() - ogx).max() <= 1e-10 * np.abs(ogx).max()
+    assert np.abs(ct.grad.cpu().numpy() - ogc).max() <= 1e-10 * np.abs(ogc).max()
+
+
+def test_edge_cases(lfem):
+    # empty mesh: every row empty
+    pat = lfem.Pattern(torch.empty(0, 3, dtype=torch.int32, device="cuda"), 5, 2, 1)
+    rp, ci = pat.csr()
+    assert pat.nnz == 0 and rp.cpu().tolist() == [0] * 6
+    out = lfem.assemble(pat, torch.zeros(5, 3, dtype=torch.float64, device="cuda"), CASES["sphere_p1"][4])
+    assert out["M"].numel() == 0
+    # one element, unused nodes, repeated node (degenerate -> status, M still finite)
+    conn = np.array([[0, 2, 5]], dtype=np.int32)
+    x = np.random.default_rng(0).normal(size=(7, 3))
+    pat = lfem.Pattern(to_dev(conn), 7, 2, 1)
+    rp, ci = pat.csr()
+    orp, oci = oracle.pattern(conn, 7)
+    assert np.array_equal(rp.cpu().numpy(), orp) and np.array_equal(ci.cpu().numpy(), oci)
+    rule = CASES["sphere_p1"][4]
+    out = lfem.assemble(pat, to_dev(x), rule, which=3)
+    _, _, M, A, _ = oracle.assemble(x, conn, 2, 1, rule.xi, rule.w)
+    assert np.abs(out["M"].cpu().numpy() - M).max() < 1e-14 and np.abs(out["A"].cpu().numpy() - A).max() < 1e-12
+    pat.sync_status()
+    dup = np.array([[0, 2, 2]], dtype=np.int32)
+    pat = lfem.Pattern(to_dev(dup), 7, 2, 1)
+    assert np.array_equal(pat.csr()[1].cpu().numpy(), oracle.pattern(dup, 7)[1])
+    out = lfem.assemble(pat, to_dev(x), rule, which=1)
+    with pytest.raises(lfem.LfemError) as ei:
+        pat.sync_status()
+    assert ei.value.code == 7
+    assert np.all(out["M"].cpu().numpy() == 0.0)
+    pat.sync_status()  # cleared
+    # index out of range is reported by the pattern build
+    for bad in ([[0, 1, 7]], [[0, -1, 2]]):
+        with pytest.raises(lfem.LfemError) as ei:
+            lfem.Pattern(to_dev(np.array(bad, dtype=np.int32)), 7, 2, 1)
+        assert ei.value.code == 2
+    # invalid arguments
+    with pytest.raises(lfem.LfemError) as ei:
+        lfem.assemble(pat, to_dev(x[:, :1].copy()), rule, which=1)  # ambient 1 < dim 2
+    assert ei.value.code == 3
+    with pytest.raises(lfem.LfemError) as ei:
+        lfem.assemble(pat, to_dev(x), rule, which=4)  # weighted mass without a coefficient
+    assert ei.value.code == 1
+    with pytest.raises(lfem.LfemError) as ei:
+        lfem.Pattern(to_dev(conn), 7, 4, 1)
+    assert ei.value.code == 3
