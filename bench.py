@@ -1,0 +1,322 @@
+"""Throughput of isoparametric P2 surface assembly on one GB300 (or N replicas).
+
+Workload (default): P2 perturbed sphere r(theta, phi) = 1 + 0.2 sin(3 theta) cos(2 phi),
+icosphere refined 8 times (1,310,720 six-node triangles, 2,621,442 nodes,
+nnz 30,146,562 per matrix), mass + stiffness + coefficient-weighted mass
+(c = 1 + x^2 + y z at the physical quadrature points) with the 7-point
+degree-5 rule.  A step is one assembly of the three CSR matrices.
+
+  value      elements/s of the mixed path (float geometry and local matrices,
+             double fallback on ill-conditioned elements, compensated sums)
+  fp64       elements/s of the plain FP64 path on the same inputs
+  e2e        the same step through the public API with host buffers: pinned
+             coordinates and coefficient copied in, the three matrices copied out
+  roofline   k_assemble_tiles (mixed) algorithmic bytes / launch time vs the
+             measured HBM copy bandwidth
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = "p2_perturbed_sphere_r8_M_A_MC"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lfem", choices=["lfem", "reference"])
+    ap.add_argument("--level", type=int, default=8, help="icosphere refinement level")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-elems", type=int, default=0, help="elements in the oracle sample (0 = auto)")
+    ap.add_argument("--skip-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def make_inputs(level):
+    from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+    x, e = meshes.icosphere(level, 2)
+    x = meshes.radial_perturbation(x, 0.2)
+    return x, e, quadrature.tri_7pt_deg5()
+
+
+def coef_from_points(pts):
+    return 1.0 + pts[..., 0] ** 2 + pts[..., 1] * pts[..., 2]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_sample(x, e, rule, n_elem):
+    """Time the oracle on the first n_elem elements (pattern of that sub-mesh built beforehand)."""
+    import oracle
+
+    sub = np.ascontiguousarray(e[:n_elem])
+    pts = oracle.eval_points(x, sub, 2, 2, rule.xi)
+    coef = coef_from_points(pts)
+    pat = oracle.pattern(sub, x.shape[0])
+    t0 = time.perf_counter()
+    oracle.assemble(x, sub, 2, 2, rule.xi, rule.w, coef, pat=pat)
+    dt = time.perf_counter() - t0
+    return dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    x, e, rule = make_inputs(args.level)
+    n = args.cpu_sample_elems or 200000
+    for _ in range(args.warmup):
+        oracle_sample(x, e, rule, min(n, 2000))
+    times = [oracle_sample(x, e, rule, n) for _ in range(args.steps)]
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {
+        "impl": "reference", "metric": "elements/s", "value": value, "unit": "elements/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": int(e.shape[0]), "sample_elements_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} elements of the workload per step, M+A+MC, FP64, 1 thread"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    x, e, rule = make_inputs(args.level)
+    nE, N = e.shape[0], x.shape[0]
+    xd = torch.from_numpy(x).to(dev)
+    ed = torch.from_numpy(e).to(dev)
+    pat = lfem.Pattern(ed, N, 2, 2)
+    pts = lfem.eval_points(ed, 2, 2, xd, rule)
+    coef64 = coef_from_points(pts).contiguous()
+    coef32 = coef64.float()
+    del pts
+    nnz = pat.nnz
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1.0)  # untimed: evict L2 between steps
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        tot = sum(ms)
+        if dist is not None:
+            t = torch.tensor([tot], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return tot, ms
+
+    out_mixed = {k: torch.empty(nnz, dtype=torch.float32, device=dev) for k in ("M", "A", "MC")}
+    out_fp64 = {k: torch.empty(nnz, dtype=torch.float64, device=dev) for k in ("M", "A", "MC")}
+
+    def step_mixed():
+        lfem.assemble(pat, xd, rule, coef32, which=7, precision=lfem.MIXED, out=out_mixed)
+
+    def step_fp64():
+        lfem.assemble(pat, xd, rule, coef64, which=7, precision=lfem.FP64, out=out_fp64)
+
+    sm_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            sm_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    with ClockSampler(sm_index) as clk:
+        tot_ms, per = timed(step_mixed, args.steps, args.warmup)
+    clocks = clk.summary()
+    fallback = pat.fallback_count()
+    pat.sync_status()
+    value = world * nE * args.steps / (tot_ms * 1e-3)
+
+    res = {}
+    if not args.skip_fp64:
+        tot64, per64 = timed(step_fp64, max(3, args.steps // 4), max(1, args.warmup // 2))
+        k64 = max(3, args.steps // 4)
+        res["fp64"] = {"value": world * nE * k64 / (tot64 * 1e-3), "unit": "elements/s",
+                       "ms_per_step": tot64 / k64}
+        # accuracy of the mixed path against the FP64 path on every entry (diagonal-scaled)
+        rp, ci = pat.csr()
+        rows = torch.repeat_interleave(torch.arange(N, device=dev), rp[1:] - rp[:-1])
+        isd = rows == ci.long()
+        errs = {}
+        for k in ("M", "A", "MC"):
+            ref = out_fp64[k]
+            diag = torch.zeros(N, dtype=torch.float64, device=dev)
+            diag[rows[isd]] = ref[isd].abs()
+            den = torch.sqrt(diag[rows] * diag[ci.long()])
+            errs[k] = float(((out_mixed[k].double() - ref).abs() / den).max().item())
+        errs["sum_M"] = abs(float(out_mixed["M"].double().sum()) - float(out_fp64["M"].sum())) / float(out_fp64["M"].sum())
+        res["mixed_vs_fp64_err"] = errs
+        del rows, isd
+
+    # end to end through the public API with host buffers
+    x_h = torch.from_numpy(x).pin_memory()
+    c_h = coef32.cpu().pin_memory()
+    outs_h = {k: torch.empty(nnz, dtype=torch.float32).pin_memory() for k in ("M", "A", "MC")}
+    xd2 = torch.empty_like(xd)
+    cd2 = torch.empty_like(coef32)
+
+    def step_e2e():
+        xd2.copy_(x_h, non_blocking=True)
+        cd2.copy_(c_h, non_blocking=True)
+        lfem.assemble(pat, xd2, rule, cd2, which=7, precision=lfem.MIXED, out=out_mixed)
+        for k in outs_h:
+            outs_h[k].copy_(out_mixed[k], non_blocking=True)
+
+    k_e2e = max(3, args.steps // 4)
+    tot_e2e, _ = timed(step_e2e, k_e2e, 2)
+    h2d = x.nbytes + coef32.numel() * 4
+    d2h = 3 * nnz * 4
+
+    # roofline of k_assemble_tiles (mixed): algorithmic bytes = unique inputs + outputs
+    alg_bytes = nE * 6 * 4 + N * 3 * 8 + nE * rule.n_pts * 4 + 3 * nnz * 4
+    launch_ms = tot_ms / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    info = pat.info()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = args.cpu_sample_elems or nE
+        dt = oracle_sample(x, e, rule, n_s)
+        cpu = {"value": n_s / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n_s} elements of the workload, M+A+MC, FP64, single thread, {dt:.1f} s"}
+
+    line = {
+        "metric": "elements/s", "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": nE, "nodes": N, "nnz_per_matrix": nnz, "matrices": "M,A,MC",
+                   "precision": "mixed", "quadrature": "tri 7-point degree 5", "l2": "flushed between steps",
+                   "tile_slots": info["tile_slots"], "tiles": info["tiles"], "recompute": info["recompute"],
+                   "fp64_fallback_elements": fallback, "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_assemble_tiles<2,3,2,float>", "algorithmic_bytes": alg_bytes,
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * nE * k_e2e / (tot_e2e * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        **res,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -55,7 +55,8 @@ __device__ __forceinline__ void adjoint_element(const AdjArgs& a, int64_t e, con
   for (int ai = 0; ai < REF; ++ai) {
     const int32_t k = __ldg(a.elem_inc + e * REF + ai);
     const int64_t rb = __ldg(a.row_ptr + nodes[ai]);
-    const PosT* pos = reinterpret_cast<const PosT*>(a.inc_pos) + (int64_t)k * REF;
+    int pos[REF];
+    load_pos<PosT, REF>(a.inc_pos, k, pos);
 #pragma unroll
     for (int b = 0; b < REF; ++b) {
       const int64_t s = rb + pos[b];

@@ -87,33 +87,100 @@ __device__ __forceinline__ void element_pass(const ElemData<D, NA, P, R>& ed, co
     if (DA) Ao[u] = 0;
     if (DC) Co[u] = 0;
   }
+#pragma unroll 1
   for (int q = 0; q < tb.q; ++q) {
     const R wq = tb.w[q];
     QpGeom<D, NA, P, R> g;
     qp_geometry<D, NA, P, R>(ed, tb, q, wq, g);
     qual = fmin(qual, g.quality);
-    bad |= !(g.s > (R)0) || !isfinite(g.s);
+    // numerically zero |det DF|: metric quality det G / (tr G / D)^D at rounding level
+    bad |= !(g.s > (R)0) || !isfinite(g.s) || !(g.quality > (sizeof(R) == 8 ? (R)1e-28 : (R)1e-12));
     R cq = 0;
     if (DC) cq = load_coef<R>(coef, coef_f32, e * tb.q + q);
     qp_accumulate<D, NA, P, R, DM, DA, DC>(g, tb, q, wq, cq, Mo, Ao, Co);
   }
 }
 
+// Float pair (hi, lo) with hi + lo = x to ~2^-47 relative, from integer
+// operations on the bits of x (no FP64 instruction: on GB300 the FP64 pipe
+// runs at 1/64 of the FP32 rate).  hi = x truncated to 24 significant bits
+// (so differences of nearby hi values are exact), lo = the next 23 bits.
+// |x| >= 2^128 sets ok = false (the element is redone in double); |x| < 2^-103
+// keeps only hi, |x| < 2^-126 maps to 0.
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo, bool& ok) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hw = (uint32_t)(u >> 32), lw = (uint32_t)u;
+  const uint32_t E = (hw >> 20) & 0x7FFu;
+  const uint32_t sign = hw & 0x80000000u;
+  const uint32_t hadj = (hw & 0x7FFFFFFFu) - (896u << 20);
+  const uint32_t hbits = sign | __funnelshift_l(lw, hadj, 3);
+  const uint32_t ef = (E - 919u) << 23;
+  const float lo_mag = __uint_as_float(ef | ((lw >> 6) & 0x7FFFFFu)) - __uint_as_float(ef);
+  hi = E >= 897u ? __uint_as_float(hbits) : 0.0f;
+  lo = E >= 920u ? __uint_as_float(__float_as_uint(lo_mag) ^ sign) : 0.0f;
+  ok = ok && (E <= 1150u);
+}
+
+// Element data in float from the split coordinates: corner edge vectors and
+// edge-node deviations, each a difference of nearby values done on the hi
+// parts (exact) plus the lo parts.
+template <int D, int NA, int P>
+__device__ __forceinline__ bool load_element_data_split(const double* __restrict__ coords,
+                                                        const int32_t (&nodes)[Ref<D, P>::REF],
+                                                        ElemData<D, NA, P, float>& ed) {
+  constexpr int REF = Ref<D, P>::REF;
+  float xh[REF][NA], xl[REF][NA];
+  bool ok = true;
+#pragma unroll
+  for (int b = 0; b < REF; ++b) {
+    const double* p = coords + (int64_t)nodes[b] * NA;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) split_f64(__ldg(p + i), xh[b][i], xl[b][i], ok);
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m)
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ed.e[m][i] = (xh[m + 1][i] - xh[0][i]) + (xl[m + 1][i] - xl[0][i]);
+#pragma unroll
+  for (int k = 0; k < Ref<D, P>::NE; ++k) {
+    const int I = edge_i<D>(k), J = edge_j<D>(k), Ed = D + 1 + k;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float dh = (xh[Ed][i] - xh[I][i]) - 0.5f * (xh[J][i] - xh[I][i]);
+      const float dlo = (xl[Ed][i] - xl[I][i]) - 0.5f * (xl[J][i] - xl[I][i]);
+      ed.dl[k][i] = dh + dlo;
+    }
+  }
+  return ok;
+}
+
 // Compute the requested local matrices of element e in precision R and store
-// them to dst[m * U + u] (m in accumulator order).
-template <int D, int NA, int P, typename R, typename RS>
-__device__ __forceinline__ void element_store(const double (&X)[Ref<D, P>::REF][NA], const TabView<R>& tb,
-                                              const void* coef, int coef_f32, int64_t e, unsigned which,
-                                              RS* dst, int dst_stride_m, R& qual, bool& bad) {
+// them to dst: FULL = ref x ref per matrix (dst[m * ref^2 + a * ref + b]),
+// otherwise the upper triangle (dst[m * dst_stride_m + u]); m in accumulator order.
+template <int D, int NA, int P, typename R, typename RS, bool FULL>
+__device__ __forceinline__ void element_store_ed(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb,
+                                                 const void* coef, int coef_f32, int64_t e, unsigned which,
+                                                 RS* dst, int dst_stride_m, R& qual, bool& bad) {
   constexpr int U = Ref<D, P>::U;
-  ElemData<D, NA, P, R> ed;
-  load_element_data<D, NA, P, R>(X, ed);
+  constexpr int REF = Ref<D, P>::REF;
   R Mo[U], Ao[U], Co[U];
   const bool wm = which & LFEM_MASS, wa = which & LFEM_STIFF, wc = which & LFEM_CMASS;
   const int im = 0, ia = wm ? 1 : 0, ic = (wm ? 1 : 0) + (wa ? 1 : 0);
   auto put = [&](const R(&v)[U], int slot) {
+    if constexpr (FULL) {
+      RS* d = dst + slot * (REF * REF);
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[slot * dst_stride_m + u] = (RS)v[u];
+      for (int x = 0; x < REF; ++x)
+#pragma unroll
+        for (int y = x; y < REF; ++y) {
+          const RS val = (RS)v[upper_index(REF, x, y)];
+          d[x * REF + y] = val;
+          if (y != x) d[y * REF + x] = val;
+        }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) dst[slot * dst_stride_m + u] = (RS)v[u];
+    }
   };
   if constexpr (D == 3) {
     // two passes keep the register footprint at two matrices
@@ -142,17 +209,103 @@ __device__ __forceinline__ void element_store(const double (&X)[Ref<D, P>::REF][
   }
 }
 
-template <int D, int NA, int P, typename R, typename PosT>
-__global__ void __launch_bounds__(256) k_assemble_tiles(const AsmArgs a) {
+// Double-precision recomputation of one element (upper layout), kept out of
+// line so the float hot path does not carry its registers.
+template <int D, int NA, int P, typename RS, bool FULL>
+__device__ __noinline__ void element_fp64(const double* __restrict__ coords, const int32_t* __restrict__ nodes,
+                                          TabRef tab, const void* coef, int coef_f32, int64_t e, unsigned which,
+                                          RS* dst, int dst_stride_m, bool* bad_out) {
+  constexpr int REF = Ref<D, P>::REF;
+  int32_t nd[REF];
+#pragma unroll
+  for (int b = 0; b < REF; ++b) nd[b] = nodes[b];
+  double X[REF][NA];
+  gather_coords<D, NA, P>(coords, nd, X);
+  ElemData<D, NA, P, double> ed;
+  load_element_data<D, NA, P, double>(X, ed);
+  const TabView<double> tb = tab_view<D, P, double>(tab);
+  double qual = 1.0;
+  bool bad = false;
+  element_store_ed<D, NA, P, double, RS, FULL>(ed, tb, coef, coef_f32, e, which, dst, dst_stride_m, qual, bad);
+  *bad_out = bad;
+}
+
+// Double recomputation of one element, one matrix per pass so the registers
+// needed stay below those of the float hot path (upper layout, stored as RS).
+template <int D, int NA, int P, typename RS>
+__device__ __forceinline__ void element_fp64_lean(const double* __restrict__ coords,
+                                                  const int32_t* __restrict__ cn_e, TabRef tab, const void* coef,
+                                                  int coef_f32, int64_t e, unsigned which, RS* dst, int stride_m,
+                                                  bool& bad) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
+  int32_t nd[REF];
+#pragma unroll
+  for (int b = 0; b < REF; ++b) nd[b] = __ldg(cn_e + b);
+  double X[REF][NA];
+  gather_coords<D, NA, P>(coords, nd, X);
+  ElemData<D, NA, P, double> ed;
+  load_element_data<D, NA, P, double>(X, ed);
+  const TabView<double> tb = tab_view<D, P, double>(tab);
+  double qual = 1.0;
+  double V[U], dummy1[U], dummy2[U];
+  int slot = 0;
+  if (which & LFEM_MASS) {
+    element_pass<D, NA, P, double, true, false, false>(ed, tb, coef, coef_f32, e, V, dummy1, dummy2, qual, bad);
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[slot * stride_m + u] = (RS)V[u];
+    ++slot;
+  }
+  if (which & LFEM_STIFF) {
+    element_pass<D, NA, P, double, false, true, false>(ed, tb, coef, coef_f32, e, dummy1, V, dummy2, qual, bad);
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[slot * stride_m + u] = (RS)V[u];
+    ++slot;
+  }
+  if (which & LFEM_CMASS) {
+    element_pass<D, NA, P, double, false, false, true>(ed, tb, coef, coef_f32, e, dummy1, dummy2, V, qual, bad);
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[slot * stride_m + u] = (RS)V[u];
+  }
+}
+
+// Compute (upper layout) from double coordinates, precision R.
+template <int D, int NA, int P, typename R, typename RS>
+__device__ __forceinline__ void element_store(const double (&X)[Ref<D, P>::REF][NA], const TabView<R>& tb,
+                                              const void* coef, int coef_f32, int64_t e, unsigned which,
+                                              RS* dst, int dst_stride_m, R& qual, bool& bad) {
+  ElemData<D, NA, P, R> ed;
+  load_element_data<D, NA, P, R>(X, ed);
+  element_store_ed<D, NA, P, R, RS, false>(ed, tb, coef, coef_f32, e, which, dst, dst_stride_m, qual, bad);
+}
+
+// Launch shape: the float kernel needs ~160 registers, so 192 threads x 2
+// CTAs per SM; the double kernel runs 256 threads x 1 CTA.
+template <typename R>
+struct TileOcc;
+template <>
+struct TileOcc<float> {
+  static constexpr int THREADS = 192;
+  static constexpr int MIN_BLOCKS = 2;
+};
+template <>
+struct TileOcc<double> {
+  static constexpr int THREADS = 256;
+  static constexpr int MIN_BLOCKS = 1;
+};
+
+template <int D, int NA, int P, typename R, typename PosT>
+__global__ void __launch_bounds__(TileOcc<R>::THREADS, TileOcc<R>::MIN_BLOCKS) k_assemble_tiles(const AsmArgs a) {
+  constexpr int REF = Ref<D, P>::REF;
+  constexpr int RR = Ref<D, P>::U;  // local matrices stored as upper triangles
   using Acc = typename AccOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nm = a.nm;
   const int S = a.slots_cap;
   Acc* acc = reinterpret_cast<Acc*>(smem_raw);
   R* lsm = reinterpret_cast<R*>(smem_raw + sizeof(Acc) * (size_t)nm * S);
-  const int lstride = nm * U;
+  const int lstride = nm * RR;
+  uint8_t* flag = reinterpret_cast<uint8_t*>(lsm + (size_t)a.chunk * lstride);  // [chunk]
 
   const int64_t t = a.tile_begin + blockIdx.x;
   const int32_t r0 = a.tile_row0[t], r1 = a.tile_row0[t + 1];
@@ -162,69 +315,85 @@ __global__ void __launch_bounds__(256) k_assemble_tiles(const AsmArgs a) {
   const int nel = a.tile_elem_ptr[t + 1] - el0;
   const int nrows = r1 - r0;
 
-  for (int i = threadIdx.x; i < nm * ns; i += blockDim.x) acc_zero(acc[(i / ns) * S + (i % ns)]);
+  for (int m = 0; m < nm; ++m)
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) acc_zero(acc[m * S + s]);
 
   const TabView<R> tb = tab_view<D, P, R>(a.tab);
   for (int c0 = 0; c0 < nel; c0 += a.chunk) {
     const int cn = min(a.chunk, nel - c0);
-    // ---- phase 1: local matrices, element per thread
+    // ---- phase 1: local matrices (full ref x ref), element per thread
     for (int j = threadIdx.x; j < cn; j += blockDim.x) {
       const int64_t e = a.tile_elem[el0 + c0 + j];
       const int32_t* cn_e = a.conn + e * REF;
       int32_t nodes[REF];
 #pragma unroll
       for (int b = 0; b < REF; ++b) nodes[b] = __ldg(cn_e + b);
-      double X[REF][NA];
-      gather_coords<D, NA, P>(a.coords, nodes, X);
       R qual = (R)1;
       bool bad = false;
       R* dst = lsm + (size_t)j * lstride;
-      element_store<D, NA, P, R, R>(X, tb, a.coef, a.coef_f32, e, a.which, dst, U, qual, bad);
-      const bool owner = nodes[0] >= r0 && nodes[0] < r1;
       if constexpr (sizeof(R) == 4) {
-        if (D > 1 && (qual < (R)a.qmin || bad)) {
-          // ill-conditioned metric: redo the element in double
-          const TabView<double> tb64 = tab_view<D, P, double>(a.tab);
-          double q64 = 1.0;
-          bool bad64 = false;
-          element_store<D, NA, P, double, R>(X, tb64, a.coef, a.coef_f32, e, a.which, dst, U, q64, bad64);
-          if (owner) atomicAdd(a.fallback, 1ull);
-          bad = bad64;
+        ElemData<D, NA, P, float> ed;
+        const bool ok = load_element_data_split<D, NA, P>(a.coords, nodes, ed);
+        element_store_ed<D, NA, P, float, float, false>(ed, tb, a.coef, a.coef_f32, e, a.which, dst, RR, qual, bad);
+        // ill-conditioned metric or out-of-range coordinates: redone in double below
+        flag[j] = (!ok || (D > 1 && qual < (R)a.qmin) || bad) ? 1 : 0;
+      } else {
+        double X[REF][NA];
+        gather_coords<D, NA, P>(a.coords, nodes, X);
+        ElemData<D, NA, P, double> ed;
+        load_element_data<D, NA, P, double>(X, ed);
+        element_store_ed<D, NA, P, double, double, false>(ed, tb, a.coef, a.coef_f32, e, a.which, dst, RR, qual,
+                                                          bad);
+        if (bad && nodes[0] >= r0 && nodes[0] < r1) atomicOr(a.status, ST_DEGENERATE);
+      }
+    }
+    if constexpr (sizeof(R) == 4) {
+      // rare path: double recomputation of the flagged elements of this chunk
+      for (int j = threadIdx.x; j < cn; j += blockDim.x) {
+        if (!flag[j]) continue;
+        const int64_t e = a.tile_elem[el0 + c0 + j];
+        const int32_t* cn_e = a.conn + e * REF;
+        bool bad = false;
+        element_fp64_lean<D, NA, P, float>(a.coords, cn_e, a.tab, a.coef, a.coef_f32, e, a.which,
+                                           lsm + (size_t)j * lstride, RR, bad);
+        const int32_t n0 = __ldg(cn_e);
+        if (n0 >= r0 && n0 < r1) {
+          atomicAdd(a.fallback, 1ull);
+          if (bad) atomicOr(a.status, ST_DEGENERATE);
         }
       }
-      if (bad && owner) atomicOr(a.status, ST_DEGENERATE);
     }
     __syncthreads();
-    // ---- phase 2: per (row, matrix), incidences in ascending element order
-    for (int w = threadIdx.x; w < nrows * nm; w += blockDim.x) {
-      const int rl = w / nm, m = w - rl * nm;
+    // ---- phase 2: per row (all matrices), incidences in ascending element order
+    for (int rl = threadIdx.x; rl < nrows; rl += blockDim.x) {
       const int32_t r = r0 + rl;
-      const int base = (int)(a.row_ptr[r] - s0);
-      Acc* accm = acc + (size_t)m * S + base;
-      const R* lm = lsm + m * U;
+      Acc* accr = acc + (int)(a.row_ptr[r] - s0);
       const int32_t kb = a.inc_ptr[r], ke = a.inc_ptr[r + 1];
       for (int32_t k = kb; k < ke; ++k) {
         const uint16_t lk = a.inc_local[k];
         const int loc = (lk >> 4) - c0;
         if (loc < 0) continue;
         if (loc >= cn) break;
+        int pos[REF];
+        load_pos<PosT, REF>(a.inc_pos, k, pos);
+        const R* le = lsm + (size_t)loc * lstride;
         const int ai = lk & 15;
-        const PosT* pos = reinterpret_cast<const PosT*>(a.inc_pos) + (int64_t)k * REF;
-        const R* lrow = lm + (size_t)loc * lstride;
+        // upper index of (ai, b): row offset of ai (b >= ai) or of b (b < ai)
+        const int off_a = ai * REF - ai * (ai - 1) / 2 - ai;
 #pragma unroll
         for (int b = 0; b < REF; ++b) {
-          const int u = ai <= b ? upper_index(REF, ai, b) : upper_index(REF, b, ai);
-          acc_add(accm[pos[b]], lrow[u]);
+          const int u = b >= ai ? off_a + b : upper_index(REF, b, 0) + ai;
+          for (int m = 0; m < nm; ++m) acc_add(accr[m * S + pos[b]], le[m * RR + u]);
         }
       }
     }
     __syncthreads();
   }
   // ---- phase 3: coalesced stores of the tile's slot range
-  for (int i = threadIdx.x; i < nm * ns; i += blockDim.x) {
-    const int m = i / ns, s = i - m * ns;
-    R* o = reinterpret_cast<R*>(a.out[m]);
-    o[s0 + s] = (R)acc_final(acc[(size_t)m * S + s]);
+  for (int m = 0; m < nm; ++m) {
+    R* o = reinterpret_cast<R*>(a.out[m]) + s0;
+    const Acc* am = acc + (size_t)m * S;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) o[s] = (R)acc_final(am[s]);
   }
 }
 
@@ -357,7 +526,7 @@ lfem_status launch_stage(int kind, const StageArgs& s, cudaStream_t st) {
 template <int D, int NA, int P, typename R>
 size_t tile_smem_bytes(int nm, int slots, int chunk) {
   using Acc = typename AccOf<R>::T;
-  return sizeof(Acc) * (size_t)nm * slots + sizeof(R) * (size_t)chunk * nm * Ref<D, P>::U;
+  return sizeof(Acc) * (size_t)nm * slots + sizeof(R) * (size_t)chunk * nm * Ref<D, P>::U + (size_t)chunk;
 }
 
 template <int D, int NA, int P, typename R>

@@ -311,13 +311,18 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   a.qmin = 0.25f;
   a.status = p->d.status;
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
-  const int threads = p->threads ? p->threads : 256;
-  int chunk = p->chunk;
-  if (!chunk) {
-    // largest multiple of 32 (<= 256) that fits the shared-memory budget
-    chunk = 256;
-    while (chunk > 32 && tile_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk) > 200 * 1024) chunk -= 32;
-  }
+  // mixed kernel: 192 threads (launch bound), double kernel: up to 256
+  const int max_threads = mixed ? 192 : 256;
+  const int threads = p->threads ? (p->threads < max_threads ? p->threads : max_threads) : max_threads;
+  // elements per chunk: the requested value (default 256) lowered, in steps of
+  // 32, until the tile fits the shared-memory budget
+  // (mixed: two CTAs per SM need <= ~110 KB each)
+  const size_t budget = mixed ? 110 * 1024 : 200 * 1024;
+  int chunk = p->chunk ? p->chunk : (mixed ? threads : 128);
+  while (chunk > 32 && tile_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk) > budget)
+    chunk = chunk > 64 ? ((chunk - 1) / 32) * 32 : 32;
+  while (chunk > 8 && tile_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk) > 227 * 1024)
+    chunk /= 2;
   a.chunk = chunk;
   if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
   return run_tiles(p->dim, ambient, p->order, mixed, a, p->n_tiles, threads, p->pos_bytes, st);

@@ -85,6 +85,40 @@ __host__ __device__ constexpr int edge_j(int k) {
   return D == 1 ? 1 : (D == 2 ? (k == 2 ? 0 : k + 1) : (k < 3 ? (k == 2 ? 0 : k + 1) : 3));
 }
 
+// Column positions of one incidence are stored padded to a power of two so a
+// single vector load fetches them (ref 2 -> 2, 3/4 -> 4, 6 -> 8, 10 -> 16).
+__host__ __device__ constexpr int pos_stride(int ref) { return ref <= 2 ? 2 : (ref <= 4 ? 4 : (ref <= 8 ? 8 : 16)); }
+
+template <typename PosT, int REF>
+__device__ __forceinline__ void load_pos(const uint8_t* __restrict__ base, int64_t k, int (&pos)[REF]) {
+  constexpr int BYTES = pos_stride(REF) * (int)sizeof(PosT);
+  const uint8_t* p = base + k * BYTES;
+  uint32_t w[BYTES >= 4 ? BYTES / 4 : 1];
+  if constexpr (BYTES == 2) {
+    w[0] = __ldg(reinterpret_cast<const unsigned short*>(p));
+  } else if constexpr (BYTES == 4) {
+    w[0] = __ldg(reinterpret_cast<const unsigned int*>(p));
+  } else if constexpr (BYTES == 8) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+  } else {
+#pragma unroll
+    for (int h = 0; h < BYTES / 16; ++h) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + h);
+      w[4 * h + 0] = v.x;
+      w[4 * h + 1] = v.y;
+      w[4 * h + 2] = v.z;
+      w[4 * h + 3] = v.w;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < REF; ++b) {
+    if constexpr (sizeof(PosT) == 1) pos[b] = (w[b >> 2] >> (8 * (b & 3))) & 0xFF;
+    else pos[b] = (w[b >> 1] >> (16 * (b & 1))) & 0xFFFF;
+  }
+}
+
 // Upper-triangle index of local pair (a, b), a <= b.
 __host__ __device__ constexpr int upper_index(int ref, int a, int b) {
   return a * ref - a * (a - 1) / 2 + (b - a);
@@ -333,7 +367,7 @@ struct lfem_pattern_s {
   int64_t n_inc = 0;
   int32_t max_row = 0, max_deg = 0;
   int pos_bytes = 1;
-  int32_t tile_slots = 4096;
+  int32_t tile_slots = 2048;
   int64_t n_tiles = 0;
   int64_t tile_elems_total = 0;
   int32_t chunk = 0;    // elements per chunk (0 = default)

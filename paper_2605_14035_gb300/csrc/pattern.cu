@@ -292,7 +292,7 @@ __global__ void k_positions(const int32_t* __restrict__ conn, int ref, const int
           if (col_idx[mid] < c) lo = mid + 1;
           else hi = mid;
         }
-        pos[(int64_t)k * ref + b] = (PosT)(lo - rb);
+        pos[(int64_t)k * pos_stride(ref) + b] = (PosT)(lo - rb);
       }
     }
   }
@@ -531,7 +531,8 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   if (N > 0) k_row_compact<<<grid_for(N, 128), 128, 0, st>>>(raw, d.inc_ptr, ref, N, d.row_ptr, d.col_idx);
   LFEM_CUDA(cudaGetLastError());
   p->pos_bytes = p->max_row <= 256 ? 1 : 2;
-  TRY(dalloc(&d.inc_pos, n_inc * ref * p->pos_bytes));
+  TRY(dalloc(&d.inc_pos, n_inc * pos_stride(ref) * p->pos_bytes));
+  LFEM_CUDA(cudaMemsetAsync(d.inc_pos, 0, (size_t)n_inc * pos_stride(ref) * p->pos_bytes, st));
   if (N > 0) {
     if (p->pos_bytes == 1)
       k_positions<uint8_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, d.inc_key, d.inc_ptr, N, d.row_ptr,

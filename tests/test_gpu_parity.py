@@ -191,8 +191,12 @@ def test_edge_cases(lfem):
     with pytest.raises(lfem.LfemError) as ei:
         pat.sync_status()
     assert ei.value.code == 7
-    assert np.all(out["M"].cpu().numpy() == 0.0)
+    assert np.all(np.abs(out["M"].cpu().numpy()) < 1e-15)
     pat.sync_status()  # cleared
+    out = lfem.assemble(pat, to_dev(x), rule, which=1, precision=lfem.MIXED)
+    with pytest.raises(lfem.LfemError) as ei:
+        pat.sync_status()
+    assert ei.value.code == 7
     # index out of range is reported by the pattern build
     for bad in ([[0, 1, 7]], [[0, -1, 2]]):
         with pytest.raises(lfem.LfemError) as ei:
