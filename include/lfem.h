@@ -178,6 +178,30 @@ lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64
 const char* lfem_last_error(void);
 const char* lfem_status_string(lfem_status s);
 
+/* ---------------------------------------------------------------------------
+ * CSR pattern without any device allocation.  (The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at
+ * run time -- programs whose memory arena or pool owns the device up front, or
+ * loops that forbid cudaMalloc after start-up.)
+ *
+ * Same pattern as lfem_pattern (rows and columns ascending, duplicates merged,
+ * bit-identical output) but only the CSR arrays, no assembly maps.  The caller
+ * passes row_ptr (device int64 [n_nodes+1]) and col_idx (device int32
+ * [col_capacity]); *nnz receives the pattern size.  Scratch lives in a 16 MiB
+ * array inside the library that every GPU loading the library keeps until the
+ * process exits; the mesh must fit it:
+ *   ~ n_elem*ref*(ref+2) + 4*n_nodes int32 words <= 4 Mi words
+ * (for example about 100k six-node triangles), else LFEM_E_TOO_LARGE and
+ * nothing is written.  If nnz > col_capacity the call writes row_ptr, sets *nnz
+ * and returns LFEM_E_TOO_LARGE.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * The call synchronises the stream.  All calls share the one array: calls that
+ * overlap on the GPU race, so issue them one at a time.
+ */
+lfem_status lfem_pattern_csr_noalloc(const int32_t* conn, int64_t n_elem, int32_t n_nodes, int dim, int order,
+                                     int64_t* row_ptr, int32_t* col_idx, int64_t col_capacity, int64_t* nnz,
+                                     void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

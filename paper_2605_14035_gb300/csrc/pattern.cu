@@ -8,6 +8,7 @@
 // sparsity structure removes it from the assembly).
 #include <climits>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "lfem_internal.cuh"
@@ -553,4 +554,111 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   return build_tiles(p, p->tile_slots, st);
 }
 
+// ----------------------------------------------------------------------------
+// CSR pattern without device allocation (lfem_pattern_csr_noalloc).
+//
+// Some callers cannot allocate device memory while they run: programs whose
+// allocator owns all device memory up front (a fixed arena or pool, a real-time
+// loop that forbids cudaMalloc after start-up), or hosts that hand this library
+// only the buffers they manage.  This path keeps its scratch in one file-scope
+// device array instead.  Every GPU that loads the library holds the array until
+// the process exits; all calls share it, so calls whose work overlaps on the
+// GPU (different streams, threads or processes sharing a context) race.  The
+// array keeps the last call's contents; every region a step needs at zero is
+// cleared on the stream first.
+// ----------------------------------------------------------------------------
+constexpr int64_t kStaticScratchWords = 4ll << 20;  // 16 MiB of int32 words
+static __device__ __align__(256) int32_t g_static_scratch[kStaticScratchWords];
+static std::mutex g_static_mu;
+static void* g_static_ptr[64];
+
+// Device address of the array for the current device.  The first call on a
+// device looks it up (cudaGetSymbolAddress); the host-side symbol itself is
+// only a stand-in and must never be passed to a kernel.
+static lfem_status static_scratch(int32_t** out) {
+  int dev = 0;
+  LFEM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(LFEM_E_ARG, "device ordinal >= 64");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[dev] = ptr;
+  }
+  *out = static_cast<int32_t*>(g_static_ptr[dev]);
+  return LFEM_OK;
+}
+
+lfem_status pattern_csr_noalloc(const int32_t* conn, int64_t nE, int32_t N, int dim, int order, int64_t* row_ptr,
+                                int32_t* col_idx, int64_t col_capacity, int64_t* nnz_out, cudaStream_t st) {
+  const int ref = n_ref(dim, order);
+  const int64_t I = nE * ref;
+  // word budget, each region rounded up to 64 words (256 bytes)
+  auto rnd = [](int64_t w) { return (w + 63) / 64 * 64; };
+  const int64_t w_deg = rnd((int64_t)N + 2), w_ptr = rnd((int64_t)N + 2), w_misc = 64;
+  const int64_t w_key = rnd(I), w_einc = rnd(I), w_raw = rnd(I * ref), w_sort = rnd((int64_t)N + 2);
+  const int64_t w_s32 = rnd(scan_scratch_bytes(N, 4) / 4), w_s64 = rnd(scan_scratch_bytes(N, 8) / 4);
+  const int64_t need = w_deg + w_ptr + w_misc + w_key + w_einc + w_raw + w_sort + w_s32 + w_s64;
+  if (need > kStaticScratchWords)
+    return fail(LFEM_E_TOO_LARGE, "mesh needs more than the 16 MiB static scratch of the no-allocation path");
+  int32_t* base = nullptr;
+  TRY(static_scratch(&base));
+  int32_t* deg = base;
+  int32_t* inc_ptr = deg + w_deg;
+  int32_t* misc = inc_ptr + w_ptr;  // [0] status, [1] max degree, [2] max row length
+  int32_t* key = misc + w_misc;
+  int32_t* einc = key + w_key;
+  int32_t* raw = einc + w_einc;
+  int32_t* sort_scr = raw + w_raw;
+  int32_t* s32 = sort_scr + w_sort;
+  int64_t* s64 = reinterpret_cast<int64_t*>(s32 + w_s32);
+
+  LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((size_t)N + 1), st));
+  LFEM_CUDA(cudaMemsetAsync(misc, 0, sizeof(int32_t) * 4, st));
+  if (I > 0) k_count_degree<<<grid_for(I, 256), 256, 0, st>>>(conn, I, N, deg, misc);
+  LFEM_CUDA(cudaGetLastError());
+  if (N > 0) k_max_i32<<<grid_for(N, 256), 256, 0, st>>>(deg, N, misc + 1);
+  LFEM_CUDA(cudaGetLastError());
+  int32_t h[2] = {0, 0};
+  LFEM_CUDA(cudaMemcpyAsync(h, misc, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (h[0] & ST_INDEX) return fail(LFEM_E_INDEX, "connectivity holds a node index outside [0, n_nodes)");
+  if (h[1] > kMaxDegree || (int64_t)h[1] * ref > kMaxSegSort)
+    return fail(LFEM_E_TOO_LARGE, "too many elements meet at one node");
+  scan_exclusive<int32_t, int32_t>(deg, inc_ptr, N, s32, st);
+  LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((size_t)N + 1), st));
+  if (I > 0) k_fill_incidence<<<grid_for(I, 256), 256, 0, st>>>(conn, nE, ref, inc_ptr, deg, key);
+  LFEM_CUDA(cudaGetLastError());
+  TRY(segsort(key, inc_ptr, N, 1, h[1], sort_scr, st));
+  if (I > 0) k_elem_inc_and_raw<<<grid_for(I, 256), 256, 0, st>>>(conn, ref, key, I, einc, raw);
+  LFEM_CUDA(cudaGetLastError());
+  TRY(segsort(raw, inc_ptr, N, ref, h[1] * ref, sort_scr, st));
+  if (N > 0) k_row_unique_count<<<grid_for(N, 128), 128, 0, st>>>(raw, inc_ptr, ref, N, deg);
+  LFEM_CUDA(cudaGetLastError());
+  scan_exclusive<int32_t, int64_t>(deg, row_ptr, N, s64, st);
+  int64_t nnz = 0;
+  LFEM_CUDA(cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (nnz_out) *nnz_out = nnz;
+  if (nnz > col_capacity) return fail(LFEM_E_TOO_LARGE, "col_idx capacity smaller than nnz (nnz returned)");
+  if (N > 0) k_row_compact<<<grid_for(N, 128), 128, 0, st>>>(raw, inc_ptr, ref, N, row_ptr, col_idx);
+  LFEM_CUDA(cudaGetLastError());
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  return LFEM_OK;
+}
+
 }  // namespace lfem
+
+extern "C" lfem_status lfem_pattern_csr_noalloc(const int32_t* conn, int64_t n_elem, int32_t n_nodes, int dim,
+                                                int order, int64_t* row_ptr, int32_t* col_idx, int64_t col_capacity,
+                                                int64_t* nnz, void* cuda_stream) {
+  if (n_elem < 0 || n_nodes < 0 || col_capacity < 0) return lfem::fail(LFEM_E_ARG, "negative size");
+  if ((n_elem > 0 && !conn) || !row_ptr || (col_capacity > 0 && !col_idx))
+    return lfem::fail(LFEM_E_ARG, "NULL argument");
+  if (dim < 1 || dim > 3 || (order != 1 && order != 2)) return lfem::fail(LFEM_E_UNSUPPORTED, "dim/order");
+  if (n_elem >= (1ll << 27)) return lfem::fail(LFEM_E_TOO_LARGE, "too many elements");
+  return lfem::pattern_csr_noalloc(conn, n_elem, n_nodes, dim, order, row_ptr, col_idx, col_capacity, nnz,
+                                   (cudaStream_t)cuda_stream);
+}
+

@@ -27,7 +27,7 @@ EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
     "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
-    "lfem_status_string",
+    "lfem_status_string", "lfem_pattern_csr_noalloc",
 )
 
 
@@ -60,6 +60,7 @@ def _load():
         "lfem_local": [P, L, I, I, P, I, P, P, P, P, P, P],
         "lfem_sync_status": [P, P],
         "lfem_mixed_fallback_count": [P, P, P],
+        "lfem_pattern_csr_noalloc": [P, L, ctypes.c_int32, I, I, P, P, L, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -263,6 +264,22 @@ def local(conn, dim, order, coords, rule, coef=None, which=MASS | STIFF, stream=
     _check(_lib.lfem_local(_ptr(conn), conn.shape[0], dim, order, _ptr(coords), n, rule.ref,
                            _ptr(_dev_f64(coef, "coef")), _ptr(M), _ptr(A), _ptr(C), _stream(stream)))
     return M, A, C
+
+
+def pattern_csr_noalloc(conn: torch.Tensor, n_nodes: int, dim: int, order: int, row_ptr: torch.Tensor,
+                        col_idx: torch.Tensor, stream=None) -> int:
+    """lfem_pattern_csr_noalloc: CSR pattern into caller buffers with no device
+    allocation inside the library; returns nnz (raises if col_idx is too small)."""
+    conn = _dev_i32(conn)
+    if not (row_ptr.is_cuda and row_ptr.dtype == torch.int64 and row_ptr.numel() >= n_nodes + 1):
+        raise TypeError("row_ptr must be an int64 CUDA tensor of n_nodes + 1 entries")
+    if not (col_idx.is_cuda and col_idx.dtype == torch.int32):
+        raise TypeError("col_idx must be an int32 CUDA tensor")
+    nnz = ctypes.c_int64()
+    _check(_lib.lfem_pattern_csr_noalloc(_ptr(conn), int(conn.shape[0]), int(n_nodes), int(dim), int(order),
+                                         _ptr(row_ptr), _ptr(col_idx), int(col_idx.numel()), ctypes.byref(nnz),
+                                         _stream(stream)))
+    return int(nnz.value)
 
 
 class AssembleFn(torch.autograd.Function):
