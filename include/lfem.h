@@ -130,6 +130,12 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
  * per block); 0 keeps the current value.  Used by the autotuner. */
 lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t threads);
 
+/* Failure-path test knob (not for production use): with starve != 0 the first
+ * CTA of the next assemblies on p skips its first metadata copy, so its bounded
+ * wait (2 s) runs out; lfem_sync_status then returns LFEM_E_TIMEOUT and the
+ * values of that CTA's tiles are left unwritten.  The CUDA context stays usable. */
+lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve);
+
 /* ---------------------------------------------------------------------------
  * Adjoint: for L = gM.M + gA.A + gMC.MC (dot products over the CSR values),
  * g_coords [n_nodes][ambient] = dL/d coords (overwritten) and, when g_coef is
@@ -172,7 +178,7 @@ lfem_status lfem_local(const int32_t* conn, int64_t n_elem, int dim, int order, 
  * of pattern p (LFEM_OK, LFEM_E_DEGENERATE, LFEM_E_INDEX), and reports how
  * many elements the last LFEM_MIXED assembly redid in double.
  */
-lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream);
+lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream);  /* also LFEM_E_TIMEOUT */
 lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64_t* n_fp64_elements);
 
 const char* lfem_last_error(void);

@@ -3,17 +3,6 @@
 
 namespace lfem {
 
-lfem_status run_tiles_d1(int NA, int P, bool mixed, const AsmArgs& a, int64_t T, int threads, int pos_bytes,
-                            cudaStream_t st) {
-  LFEM_DEFINE_CASE_TILES(1, 1, 1)
-  LFEM_DEFINE_CASE_TILES(1, 1, 2)
-  LFEM_DEFINE_CASE_TILES(1, 2, 1)
-  LFEM_DEFINE_CASE_TILES(1, 2, 2)
-  LFEM_DEFINE_CASE_TILES(1, 3, 1)
-  LFEM_DEFINE_CASE_TILES(1, 3, 2)
-  return fail(LFEM_E_UNSUPPORTED, "element type");
-}
-
 lfem_status run_stage_d1(int NA, int P, int kind, const StageArgs& s, cudaStream_t st) {
   LFEM_DEFINE_CASE_STAGE(1, 1, 1)
   LFEM_DEFINE_CASE_STAGE(1, 1, 2)
@@ -34,13 +23,24 @@ lfem_status run_adjoint_d1(int NA, int P, const AdjArgs& a, int64_t T, int pos_b
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }
 
-size_t tile_smem_d1(int NA, int P, bool mixed, int nm, int slots, int chunk) {
-  LFEM_DEFINE_CASE_SMEM(1, 1, 1)
-  LFEM_DEFINE_CASE_SMEM(1, 1, 2)
-  LFEM_DEFINE_CASE_SMEM(1, 2, 1)
-  LFEM_DEFINE_CASE_SMEM(1, 2, 2)
-  LFEM_DEFINE_CASE_SMEM(1, 3, 1)
-  LFEM_DEFINE_CASE_SMEM(1, 3, 2)
+lfem_status run_pipe_d1(int NA, int P, bool mixed, const PipeArgs& a, int pos_bytes, int sms, cudaStream_t st) {
+  LFEM_DEFINE_CASE_PIPE(1, 1, 1)
+  LFEM_DEFINE_CASE_PIPE(1, 1, 2)
+  LFEM_DEFINE_CASE_PIPE(1, 2, 1)
+  LFEM_DEFINE_CASE_PIPE(1, 2, 2)
+  LFEM_DEFINE_CASE_PIPE(1, 3, 1)
+  LFEM_DEFINE_CASE_PIPE(1, 3, 2)
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
+size_t pipe_smem_d1(int NA, int P, bool mixed, int nm, int S, int chunk, int cap_bytes, int cap_nodes, int cap_nel,
+                     int q, int coef_bytes) {
+  LFEM_DEFINE_CASE_PIPE_SMEM(1, 1, 1)
+  LFEM_DEFINE_CASE_PIPE_SMEM(1, 1, 2)
+  LFEM_DEFINE_CASE_PIPE_SMEM(1, 2, 1)
+  LFEM_DEFINE_CASE_PIPE_SMEM(1, 2, 2)
+  LFEM_DEFINE_CASE_PIPE_SMEM(1, 3, 1)
+  LFEM_DEFINE_CASE_PIPE_SMEM(1, 3, 2)
   return 0;
 }
 

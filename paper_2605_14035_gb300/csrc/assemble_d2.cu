@@ -3,15 +3,6 @@
 
 namespace lfem {
 
-lfem_status run_tiles_d2(int NA, int P, bool mixed, const AsmArgs& a, int64_t T, int threads, int pos_bytes,
-                            cudaStream_t st) {
-  LFEM_DEFINE_CASE_TILES(2, 2, 1)
-  LFEM_DEFINE_CASE_TILES(2, 2, 2)
-  LFEM_DEFINE_CASE_TILES(2, 3, 1)
-  LFEM_DEFINE_CASE_TILES(2, 3, 2)
-  return fail(LFEM_E_UNSUPPORTED, "element type");
-}
-
 lfem_status run_stage_d2(int NA, int P, int kind, const StageArgs& s, cudaStream_t st) {
   LFEM_DEFINE_CASE_STAGE(2, 2, 1)
   LFEM_DEFINE_CASE_STAGE(2, 2, 2)
@@ -28,11 +19,20 @@ lfem_status run_adjoint_d2(int NA, int P, const AdjArgs& a, int64_t T, int pos_b
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }
 
-size_t tile_smem_d2(int NA, int P, bool mixed, int nm, int slots, int chunk) {
-  LFEM_DEFINE_CASE_SMEM(2, 2, 1)
-  LFEM_DEFINE_CASE_SMEM(2, 2, 2)
-  LFEM_DEFINE_CASE_SMEM(2, 3, 1)
-  LFEM_DEFINE_CASE_SMEM(2, 3, 2)
+lfem_status run_pipe_d2(int NA, int P, bool mixed, const PipeArgs& a, int pos_bytes, int sms, cudaStream_t st) {
+  LFEM_DEFINE_CASE_PIPE(2, 2, 1)
+  LFEM_DEFINE_CASE_PIPE(2, 2, 2)
+  LFEM_DEFINE_CASE_PIPE(2, 3, 1)
+  LFEM_DEFINE_CASE_PIPE(2, 3, 2)
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
+size_t pipe_smem_d2(int NA, int P, bool mixed, int nm, int S, int chunk, int cap_bytes, int cap_nodes, int cap_nel,
+                     int q, int coef_bytes) {
+  LFEM_DEFINE_CASE_PIPE_SMEM(2, 2, 1)
+  LFEM_DEFINE_CASE_PIPE_SMEM(2, 2, 2)
+  LFEM_DEFINE_CASE_PIPE_SMEM(2, 3, 1)
+  LFEM_DEFINE_CASE_PIPE_SMEM(2, 3, 2)
   return 0;
 }
 

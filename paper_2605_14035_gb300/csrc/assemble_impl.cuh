@@ -1,17 +1,7 @@
-// Assembly kernels, templated on the element type (D, NA, P).
-//
-// Fused tile kernel (one CTA per row tile):
-//   phase 1  element per thread: gather coordinates, geometry per quadrature
-//            point, local upper-triangle matrices in registers -> shared memory
-//            (Sec. 3.2.1-3.2.2; Eqs. reference_quadrature_mass / _stiffness)
-//   phase 2  (row, matrix) per thread: add the tile elements' local rows into
-//            the tile's CSR slots in shared memory, incidences in ascending
-//            element order -> a fixed summation order, no atomics
-//            (Eqs. M matrix, A matrix: sum over elements)
-//   phase 3  write the tile's contiguous slot range [row_ptr[r0], row_ptr[r1])
-//            with coalesced stores
-// Each tile owns whole CSR rows, so no other CTA writes its slots; elements
-// touching several tiles are recomputed by each (halo recompute).
+// Element-level building blocks of the assembly (geometry per quadrature
+// point and local upper-triangle matrices, Sec. 3.2.1-3.2.2; Eqs.
+// reference_quadrature_mass / _stiffness), the compensated accumulator, and
+// the element-stage kernels (physical points, geometry, local matrices).
 #pragma once
 
 #include <cstdio>
@@ -234,14 +224,11 @@ __device__ __noinline__ void element_fp64(const double* __restrict__ coords, con
 // needed stay below those of the float hot path (upper layout, stored as RS).
 template <int D, int NA, int P, typename RS>
 __device__ __forceinline__ void element_fp64_lean(const double* __restrict__ coords,
-                                                  const int32_t* __restrict__ cn_e, TabRef tab, const void* coef,
+                                                  const int32_t (&nd)[Ref<D, P>::REF], TabRef tab, const void* coef,
                                                   int coef_f32, int64_t e, unsigned which, RS* dst, int stride_m,
                                                   bool& bad) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
-  int32_t nd[REF];
-#pragma unroll
-  for (int b = 0; b < REF; ++b) nd[b] = __ldg(cn_e + b);
   double X[REF][NA];
   gather_coords<D, NA, P>(coords, nd, X);
   ElemData<D, NA, P, double> ed;
@@ -281,122 +268,6 @@ __device__ __forceinline__ void element_store(const double (&X)[Ref<D, P>::REF][
 
 // Launch shape: the float kernel needs ~160 registers, so 192 threads x 2
 // CTAs per SM; the double kernel runs 256 threads x 1 CTA.
-template <typename R>
-struct TileOcc;
-template <>
-struct TileOcc<float> {
-  static constexpr int THREADS = 192;
-  static constexpr int MIN_BLOCKS = 2;
-};
-template <>
-struct TileOcc<double> {
-  static constexpr int THREADS = 256;
-  static constexpr int MIN_BLOCKS = 1;
-};
-
-template <int D, int NA, int P, typename R, typename PosT>
-__global__ void __launch_bounds__(TileOcc<R>::THREADS, TileOcc<R>::MIN_BLOCKS) k_assemble_tiles(const AsmArgs a) {
-  constexpr int REF = Ref<D, P>::REF;
-  constexpr int RR = Ref<D, P>::U;  // local matrices stored as upper triangles
-  using Acc = typename AccOf<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nm = a.nm;
-  const int S = a.slots_cap;
-  Acc* acc = reinterpret_cast<Acc*>(smem_raw);
-  R* lsm = reinterpret_cast<R*>(smem_raw + sizeof(Acc) * (size_t)nm * S);
-  const int lstride = nm * RR;
-  uint8_t* flag = reinterpret_cast<uint8_t*>(lsm + (size_t)a.chunk * lstride);  // [chunk]
-
-  const int64_t t = a.tile_begin + blockIdx.x;
-  const int32_t r0 = a.tile_row0[t], r1 = a.tile_row0[t + 1];
-  const int64_t s0 = a.row_ptr[r0];
-  const int ns = (int)(a.row_ptr[r1] - s0);
-  const int32_t el0 = a.tile_elem_ptr[t];
-  const int nel = a.tile_elem_ptr[t + 1] - el0;
-  const int nrows = r1 - r0;
-
-  for (int m = 0; m < nm; ++m)
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) acc_zero(acc[m * S + s]);
-
-  const TabView<R> tb = tab_view<D, P, R>(a.tab);
-  for (int c0 = 0; c0 < nel; c0 += a.chunk) {
-    const int cn = min(a.chunk, nel - c0);
-    // ---- phase 1: local matrices (full ref x ref), element per thread
-    for (int j = threadIdx.x; j < cn; j += blockDim.x) {
-      const int64_t e = a.tile_elem[el0 + c0 + j];
-      const int32_t* cn_e = a.conn + e * REF;
-      int32_t nodes[REF];
-#pragma unroll
-      for (int b = 0; b < REF; ++b) nodes[b] = __ldg(cn_e + b);
-      R qual = (R)1;
-      bool bad = false;
-      R* dst = lsm + (size_t)j * lstride;
-      if constexpr (sizeof(R) == 4) {
-        ElemData<D, NA, P, float> ed;
-        const bool ok = load_element_data_split<D, NA, P>(a.coords, nodes, ed);
-        element_store_ed<D, NA, P, float, float, false>(ed, tb, a.coef, a.coef_f32, e, a.which, dst, RR, qual, bad);
-        // ill-conditioned metric or out-of-range coordinates: redone in double below
-        flag[j] = (!ok || (D > 1 && qual < (R)a.qmin) || bad) ? 1 : 0;
-      } else {
-        double X[REF][NA];
-        gather_coords<D, NA, P>(a.coords, nodes, X);
-        ElemData<D, NA, P, double> ed;
-        load_element_data<D, NA, P, double>(X, ed);
-        element_store_ed<D, NA, P, double, double, false>(ed, tb, a.coef, a.coef_f32, e, a.which, dst, RR, qual,
-                                                          bad);
-        if (bad && nodes[0] >= r0 && nodes[0] < r1) atomicOr(a.status, ST_DEGENERATE);
-      }
-    }
-    if constexpr (sizeof(R) == 4) {
-      // rare path: double recomputation of the flagged elements of this chunk
-      for (int j = threadIdx.x; j < cn; j += blockDim.x) {
-        if (!flag[j]) continue;
-        const int64_t e = a.tile_elem[el0 + c0 + j];
-        const int32_t* cn_e = a.conn + e * REF;
-        bool bad = false;
-        element_fp64_lean<D, NA, P, float>(a.coords, cn_e, a.tab, a.coef, a.coef_f32, e, a.which,
-                                           lsm + (size_t)j * lstride, RR, bad);
-        const int32_t n0 = __ldg(cn_e);
-        if (n0 >= r0 && n0 < r1) {
-          atomicAdd(a.fallback, 1ull);
-          if (bad) atomicOr(a.status, ST_DEGENERATE);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- phase 2: per row (all matrices), incidences in ascending element order
-    for (int rl = threadIdx.x; rl < nrows; rl += blockDim.x) {
-      const int32_t r = r0 + rl;
-      Acc* accr = acc + (int)(a.row_ptr[r] - s0);
-      const int32_t kb = a.inc_ptr[r], ke = a.inc_ptr[r + 1];
-      for (int32_t k = kb; k < ke; ++k) {
-        const uint16_t lk = a.inc_local[k];
-        const int loc = (lk >> 4) - c0;
-        if (loc < 0) continue;
-        if (loc >= cn) break;
-        int pos[REF];
-        load_pos<PosT, REF>(a.inc_pos, k, pos);
-        const R* le = lsm + (size_t)loc * lstride;
-        const int ai = lk & 15;
-        // upper index of (ai, b): row offset of ai (b >= ai) or of b (b < ai)
-        const int off_a = ai * REF - ai * (ai - 1) / 2 - ai;
-#pragma unroll
-        for (int b = 0; b < REF; ++b) {
-          const int u = b >= ai ? off_a + b : upper_index(REF, b, 0) + ai;
-          for (int m = 0; m < nm; ++m) acc_add(accr[m * S + pos[b]], le[m * RR + u]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // ---- phase 3: coalesced stores of the tile's slot range
-  for (int m = 0; m < nm; ++m) {
-    R* o = reinterpret_cast<R*>(a.out[m]) + s0;
-    const Acc* am = acc + (size_t)m * S;
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) o[s] = (R)acc_final(am[s]);
-  }
-}
-
 // ----------------------------------------------------------------------------
 // Element-stage kernels (FP64): physical points, geometry, local matrices.
 // ----------------------------------------------------------------------------
@@ -520,30 +391,6 @@ lfem_status launch_stage(int kind, const StageArgs& s, cudaStream_t st) {
     k_local<D, NA, P><<<stage_grid(s.nE), 128, 0, st>>>(s.conn, s.nE, s.coords, s.tab, s.coef, s.which, s.o0, s.o1,
                                                          s.o2);
   LFEM_CUDA(cudaGetLastError());
-  return LFEM_OK;
-}
-
-template <int D, int NA, int P, typename R>
-size_t tile_smem_bytes(int nm, int slots, int chunk) {
-  using Acc = typename AccOf<R>::T;
-  return sizeof(Acc) * (size_t)nm * slots + sizeof(R) * (size_t)chunk * nm * Ref<D, P>::U + (size_t)chunk;
-}
-
-template <int D, int NA, int P, typename R>
-lfem_status launch_tiles(const AsmArgs& a0, int64_t n_tiles, int threads, int pos_bytes, cudaStream_t st) {
-  if (n_tiles == 0) return LFEM_OK;
-  const size_t smem = tile_smem_bytes<D, NA, P, R>(a0.nm, a0.slots_cap, a0.chunk);
-  if (smem > 227 * 1024) return fail(LFEM_E_ARG, "tile configuration needs more than 227 KB of shared memory");
-  auto kern = pos_bytes == 1 ? k_assemble_tiles<D, NA, P, R, uint8_t> : k_assemble_tiles<D, NA, P, R, uint16_t>;
-  LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  AsmArgs a = a0;
-  const int64_t max_grid = 1ll << 30;
-  for (int64_t t0 = 0; t0 < n_tiles; t0 += max_grid) {
-    a.tile_begin = t0;
-    const int64_t nb = n_tiles - t0 < max_grid ? n_tiles - t0 : max_grid;
-    kern<<<(unsigned)nb, threads, smem, st>>>(a);
-    LFEM_CUDA(cudaGetLastError());
-  }
   return LFEM_OK;
 }
 

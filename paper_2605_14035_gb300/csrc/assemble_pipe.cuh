@@ -1,0 +1,584 @@
+// Persistent, pipelined assembly kernel.
+//
+// Each CTA walks the row tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// For every tile it needs one contiguous metadata block (see TileHdr: element
+// ids, row/incidence offsets, column positions, the tile's node list and the
+// local node indices of its elements), the coordinates of the tile's nodes and
+// the coefficients of its elements.  While tile t is computed, the next tile's
+// block is copied by the tensor memory accelerator (one cp.async.bulk with an
+// mbarrier) into the other buffer, and as soon as it lands the next tile's
+// node coordinates and coefficients are gathered with cp.async into that
+// buffer as well: the global-memory latency of tile t+grid hides behind the
+// arithmetic of tile t.
+//
+// Per tile (Sec. 3.2 / 3.3 of the paper; Eqs. reference_quadrature_mass,
+// reference_quadrature_stiffness, M matrix, A matrix):
+//   split    node coordinates -> float pairs (mixed) once per node
+//   phase 1  two threads per element (quadrature points split between them):
+//            geometry and local upper-triangle matrices of every element of
+//            the tile -> shared memory
+//   phase 2  each thread takes a run of consecutive CSR slots holding about
+//            the same number of contributions and sums each slot's list (in
+//            ascending element order, compensated in registers), then stores
+//            the slot -- one writer per slot, fixed order, no atomics
+//
+// Every mbarrier wait is bounded by the global timer; on timeout the CTA
+// records ST_TIMEOUT in the status word, waits (bounded) for its own copy and
+// returns, leaving the context usable.
+#pragma once
+
+#include "assemble_impl.cuh"
+
+namespace lfem {
+
+constexpr int kPipeTPE = 2;  // threads per element in phase 1
+
+// Launch shape: the float kernel fits 170 registers, so 192 threads and two
+// CTAs per SM; the double kernel needs more registers: 256 threads, one CTA.
+template <typename R>
+struct PipeOcc;
+template <>
+struct PipeOcc<float> {
+  static constexpr int THREADS = 192;
+  static constexpr int MIN_BLOCKS = 2;
+};
+template <>
+struct PipeOcc<double> {
+  static constexpr int THREADS = 256;
+  static constexpr int MIN_BLOCKS = 1;
+};
+
+struct PipeArgs {
+  const double* coords;
+  const void* coef;
+  int coef_f32;
+  const uint8_t* meta;
+  const int64_t* meta_off;
+  int64_t n_tiles;
+  void* out[3];
+  int nm;
+  unsigned which;
+  TabRef tab;
+  int chunk;       // elements per phase-1 round (threads / kPipeTPE)
+  int slots_cap;   // S: tile slot capacity
+  int cap_bytes;   // largest metadata block
+  int cap_nodes;   // most nodes in a tile
+  int cap_nel;     // most elements in a tile
+  float qmin;
+  int32_t* status;
+  unsigned long long* fallback;
+  int starve;              // test knob: CTA 0 skips its first metadata copy
+  long long wait_ns;       // bound of every mbarrier wait
+};
+
+struct PipeSmem {
+  size_t mbar, meta0, meta1, node0, node1, coef0, coef1, lsm, flag, total;
+};
+
+template <typename R>
+__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int u, int nm, int S, int chunk, int cap_bytes,
+                                                     int cap_nodes, int cap_nel, int q, int coef_bytes) {
+  auto al = [](size_t b) { return (b + 127) / 128 * 128; };
+  (void)S;
+  (void)chunk;
+  PipeSmem L;
+  size_t o = 0;
+  L.mbar = o;
+  o += 128;
+  L.meta0 = o;
+  o += al(cap_bytes);
+  L.meta1 = o;
+  o += al(cap_bytes);
+  L.node0 = o;
+  o += al((size_t)cap_nodes * na * 8);
+  L.node1 = o;
+  o += al((size_t)cap_nodes * na * 8);
+  L.coef0 = o;
+  o += al((size_t)cap_nel * q * coef_bytes);
+  L.coef1 = o;
+  o += al((size_t)cap_nel * q * coef_bytes);
+  L.lsm = o;
+  o += al(sizeof(R) * (size_t)cap_nel * nm * u);
+  L.flag = o;  // element flags in phase 1, run starts (<= 1025 ints) in phase 2
+  o += al(cap_nel > 4100 ? (size_t)cap_nel : (size_t)4100);
+  L.total = o;
+  return L;
+}
+
+// ---- PTX helpers (TMA bulk copy, mbarrier, cp.async) -------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_block(void* dst, const void* src, uint32_t bytes, uint64_t* mb) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mb))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mb, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for phase `parity` of mb; true if it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mb, uint32_t parity, long long limit_ns) {
+  if (mbar_try_wait(mb, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(mb, parity)) return true;
+    if ((long long)(global_ns() - t0) > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <typename PosT, int REF>
+__device__ __forceinline__ void load_pos_smem(const uint8_t* base, int k, int (&pos)[REF]) {
+  constexpr int BYTES = pos_stride(REF) * (int)sizeof(PosT);
+  const uint8_t* p = base + (size_t)k * BYTES;
+  uint32_t w[BYTES >= 4 ? BYTES / 4 : 1];
+  if constexpr (BYTES == 2) {
+    w[0] = *reinterpret_cast<const unsigned short*>(p);
+  } else if constexpr (BYTES == 4) {
+    w[0] = *reinterpret_cast<const unsigned int*>(p);
+  } else if constexpr (BYTES == 8) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    w[0] = v.x;
+    w[1] = v.y;
+  } else {
+#pragma unroll
+    for (int h = 0; h < BYTES / 16; ++h) {
+      const uint4 v = reinterpret_cast<const uint4*>(p)[h];
+      w[4 * h + 0] = v.x;
+      w[4 * h + 1] = v.y;
+      w[4 * h + 2] = v.z;
+      w[4 * h + 3] = v.w;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < REF; ++b) {
+    if constexpr (sizeof(PosT) == 1) pos[b] = (w[b >> 2] >> (8 * (b & 3))) & 0xFF;
+    else pos[b] = (w[b >> 1] >> (16 * (b & 1))) & 0xFFFF;
+  }
+}
+
+// Issue the gathers of a tile's node coordinates and element coefficients.
+template <int NA>
+__device__ __forceinline__ void issue_gathers(const PipeArgs& a, const uint8_t* meta, double* nodes_dst,
+                                              void* coef_dst, int q, bool want_coef, int ref, int entb) {
+  const TileHdr h = *reinterpret_cast<const TileHdr*>(meta);
+  const TileLayout L = tile_layout(h.nel, h.ns, h.nent, h.nnodes, ref, entb);
+  const int32_t* nd = reinterpret_cast<const int32_t*>(meta + L.nodes);
+  for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
+    const int v = i / NA, c = i - v * NA;
+    cp_async8(nodes_dst + i, a.coords + (int64_t)nd[v] * NA + c);
+  }
+  if (want_coef) {
+    const int32_t* el = reinterpret_cast<const int32_t*>(meta + L.elem);
+    for (int i = threadIdx.x; i < h.nel * q; i += blockDim.x) {
+      const int j = i / q, qq = i - j * q;
+      const int64_t gi = (int64_t)el[j] * q + qq;
+      if (a.coef_f32) cp_async4(static_cast<float*>(coef_dst) + i, static_cast<const float*>(a.coef) + gi);
+      else cp_async8(static_cast<double*>(coef_dst) + i, static_cast<const double*>(a.coef) + gi);
+    }
+  }
+  cp_async_commit();
+}
+
+// Element data from split node coordinates held in shared memory (hi, lo pairs).
+template <int D, int NA, int P>
+__device__ __forceinline__ void element_data_from_pairs(const float2* __restrict__ xs, const uint16_t* __restrict__ en,
+                                                        ElemData<D, NA, P, float>& ed) {
+  constexpr int REF = Ref<D, P>::REF;
+  float xh[REF][NA], xl[REF][NA];
+#pragma unroll
+  for (int b = 0; b < REF; ++b) {
+    const int v = en[b];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float2 t = xs[v * NA + i];
+      xh[b][i] = t.x;
+      xl[b][i] = t.y;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m)
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ed.e[m][i] = (xh[m + 1][i] - xh[0][i]) + (xl[m + 1][i] - xl[0][i]);
+#pragma unroll
+  for (int k = 0; k < Ref<D, P>::NE; ++k) {
+    const int I = edge_i<D>(k), J = edge_j<D>(k), Ed = D + 1 + k;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float dh = (xh[Ed][i] - xh[I][i]) - 0.5f * (xh[J][i] - xh[I][i]);
+      const float dlo = (xl[Ed][i] - xl[I][i]) - 0.5f * (xl[J][i] - xl[I][i]);
+      ed.dl[k][i] = dh + dlo;
+    }
+  }
+}
+
+// Quadrature loop of one element over the points q = q0, q0 + qs, ... (a lane
+// pair splits the points; the partial sums are combined by the caller).
+template <int D, int NA, int P, typename R, bool DM, bool DA, bool DC>
+__device__ __forceinline__ void element_pass_split(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb,
+                                                   const void* coef, int coef_f32, int q0, int qs,
+                                                   R (&Mo)[Ref<D, P>::U], R (&Ao)[Ref<D, P>::U],
+                                                   R (&Co)[Ref<D, P>::U], R& qual, bool& bad) {
+  constexpr int U = Ref<D, P>::U;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (DM) Mo[u] = 0;
+    if (DA) Ao[u] = 0;
+    if (DC) Co[u] = 0;
+  }
+#pragma unroll 1
+  for (int q = q0; q < tb.q; q += qs) {
+    const R wq = tb.w[q];
+    QpGeom<D, NA, P, R> g;
+    qp_geometry<D, NA, P, R>(ed, tb, q, wq, g);
+    qual = fmin(qual, g.quality);
+    bad |= !(g.s > (R)0) || !isfinite(g.s) || !(g.quality > (sizeof(R) == 8 ? (R)1e-28 : (R)1e-12));
+    R cq = 0;
+    if (DC) cq = coef_f32 ? (R)static_cast<const float*>(coef)[q] : (R)static_cast<const double*>(coef)[q];
+    qp_accumulate<D, NA, P, R, DM, DA, DC>(g, tb, q, wq, cq, Mo, Ao, Co);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R pair_sum(R v) {
+  return v + __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
+// Local matrices of one element by a lane pair; the even lane stores the
+// first half of the entries, the odd lane the second half.
+template <int D, int NA, int P, typename R, bool DM, bool DA, bool DC>
+__device__ __forceinline__ void element_pair(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb, const void* coef,
+                                             int coef_f32, int sub, bool store, R* dst, int stride_m, int im,
+                                             int ia, int ic, R& qual, bool& bad) {
+  constexpr int U = Ref<D, P>::U;
+  R Mo[U], Ao[U], Co[U];
+  element_pass_split<D, NA, P, R, DM, DA, DC>(ed, tb, coef, coef_f32, sub, kPipeTPE, Mo, Ao, Co, qual, bad);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (DM) Mo[u] = pair_sum(Mo[u]);
+    if (DA) Ao[u] = pair_sum(Ao[u]);
+    if (DC) Co[u] = pair_sum(Co[u]);
+  }
+  // the even lane stores the mass-type matrices, the odd lane the stiffness
+  // (when only one kind is computed, the even lane stores it)
+  const bool lane_m = (DM || DC) && (sub == 0);
+  const bool lane_a = DA && (sub == ((DM || DC) ? 1 : 0));
+  if (store && lane_m) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (DM) dst[im * stride_m + u] = Mo[u];
+      if (DC) dst[ic * stride_m + u] = Co[u];
+    }
+  }
+  if (store && lane_a) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[ia * stride_m + u] = Ao[u];
+  }
+}
+
+template <int D, int NA, int P, typename R>
+__device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb,
+                                                      const void* coef, int coef_f32, int sub, bool store, R* dst,
+                                                      unsigned which, R& qual, bool& bad) {
+  constexpr int U = Ref<D, P>::U;
+  const bool wm = which & LFEM_MASS, wa = which & LFEM_STIFF, wc = which & LFEM_CMASS;
+  const int im = 0, ia = wm ? 1 : 0, ic = (wm ? 1 : 0) + (wa ? 1 : 0);
+  if constexpr (D == 3) {
+    if (wm || wc) {
+      if (wm && wc)
+        element_pair<D, NA, P, R, true, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      else if (wm)
+        element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      else
+        element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    }
+    if (wa) element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+  } else {
+    if (wm && wa && wc)
+      element_pair<D, NA, P, R, true, true, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    else if (wm && wa)
+      element_pair<D, NA, P, R, true, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    else if (wm && wc)
+      element_pair<D, NA, P, R, true, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    else if (wa && wc)
+      element_pair<D, NA, P, R, false, true, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    else if (wm)
+      element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    else if (wa)
+      element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    else
+      element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+  }
+}
+
+template <int D, int NA, int P, typename R, typename EntT>
+__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k_assemble_pipe(const PipeArgs a) {
+  constexpr int REF = Ref<D, P>::REF;
+  constexpr int U = Ref<D, P>::U;
+  constexpr int UB = ub_bits(U);
+  constexpr int ENTB = (int)sizeof(EntT);
+  using Acc = typename AccOf<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int nm = a.nm, Q = a.tab.q;
+  const bool want_coef = (a.which & LFEM_CMASS) != 0;
+  const int coef_bytes = want_coef ? (a.coef_f32 ? 4 : 8) : 0;
+  const PipeSmem L =
+      pipe_smem_layout<R>(NA, U, nm, a.slots_cap, a.chunk, a.cap_bytes, a.cap_nodes, a.cap_nel, Q, coef_bytes);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
+  int* s_flag = reinterpret_cast<int*>(smem_raw + L.mbar + 64);
+  uint8_t* meta_buf[2] = {smem_raw + L.meta0, smem_raw + L.meta1};
+  double* node_buf[2] = {reinterpret_cast<double*>(smem_raw + L.node0), reinterpret_cast<double*>(smem_raw + L.node1)};
+  void* coef_buf[2] = {smem_raw + L.coef0, smem_raw + L.coef1};
+  R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
+  uint8_t* flag = smem_raw + L.flag;
+  const int lstride = nm * U;
+  const TabView<R> tb = tab_view<D, P, R>(a.tab);
+
+  int64_t t = blockIdx.x;
+  if (t >= a.n_tiles) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+    *s_flag = 0;
+  }
+  __syncthreads();
+
+  auto block_bytes = [&](int64_t tile) { return (uint32_t)(a.meta_off[tile + 1] - a.meta_off[tile]); };
+  // prologue: tile t into buffer 0
+  if (threadIdx.x == 0 && !(a.starve && blockIdx.x == 0))
+    tma_load_block(meta_buf[0], a.meta + a.meta_off[t], block_bytes(t), &mbar[0]);
+  {
+    const bool ok = mbar_wait_bounded(&mbar[0], 0, a.wait_ns);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
+      return;  // nothing was issued for this barrier, or it never completed within the bound
+    }
+  }
+  issue_gathers<NA>(a, meta_buf[0], node_buf[0], coef_buf[0], Q, want_coef, REF, ENTB);
+
+  for (int it = 0; t < a.n_tiles; t += gridDim.x, ++it) {
+    const int b = it & 1, nb = b ^ 1;
+    const int64_t tn = t + gridDim.x;
+    // next tile's metadata block: one bulk copy into the other buffer
+    if (tn < a.n_tiles && threadIdx.x == 0) {
+      fence_proxy_async();
+      tma_load_block(meta_buf[nb], a.meta + a.meta_off[tn], block_bytes(tn), &mbar[nb]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const uint8_t* mb = meta_buf[b];
+    const TileHdr h = *reinterpret_cast<const TileHdr*>(mb);
+    const TileLayout TL = tile_layout(h.nel, h.ns, h.nent, h.nnodes, REF, ENTB);
+    const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
+    const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
+    const uint16_t* t_en = reinterpret_cast<const uint16_t*>(mb + TL.enodes);
+    const uint16_t* t_soff = reinterpret_cast<const uint16_t*>(mb + TL.soff);
+    const EntT* t_sent = reinterpret_cast<const EntT*>(mb + TL.sent);
+    double* xd = node_buf[b];
+
+    // node coordinates -> (hi, lo) float pairs in place (mixed)
+    if constexpr (sizeof(R) == 4) {
+      for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
+        float hi, lo;
+        bool ok = true;
+        split_f64(xd[i], hi, lo, ok);
+        if (!ok) hi = __int_as_float(0x7fc00000);  // out of float range: NaN forces the double path
+        reinterpret_cast<float2*>(xd)[i] = make_float2(hi, lo);
+      }
+      __syncthreads();
+    }
+
+    bool prefetched = false;
+    auto prefetch_next = [&]() {
+      // all threads: wait for the next block (bounded), then gather its nodes and coefficients
+      if (tn < a.n_tiles) {
+        const bool ok = mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0) *s_flag = 1;
+        } else {
+          issue_gathers<NA>(a, meta_buf[nb], node_buf[nb], coef_buf[nb], Q, want_coef, REF, ENTB);
+        }
+      }
+      prefetched = true;
+    };
+
+    // ---- phase 1: a lane pair per element, every element of the tile
+    for (int c0 = 0; c0 < h.nel; c0 += a.chunk) {
+      const int cn = min(a.chunk, h.nel - c0);
+      const int jj = threadIdx.x / kPipeTPE, sub = threadIdx.x % kPipeTPE;
+      const bool active = jj < cn;
+      const int jt = c0 + (active ? jj : 0);
+      const uint16_t* en = t_en + (size_t)jt * REF;
+      const void* cf = coef_buf[b];
+      if (want_coef) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
+      R qual = (R)1;
+      bool bad = false;
+      R* dst = lsm + (size_t)jt * lstride;
+      if constexpr (sizeof(R) == 4) {
+        ElemData<D, NA, P, float> ed;
+        element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
+        element_pair_dispatch<D, NA, P, float>(ed, tb, cf, a.coef_f32, sub, active, dst, a.which, qual, bad);
+      } else {
+        double X[REF][NA];
+#pragma unroll
+        for (int bb = 0; bb < REF; ++bb)
+#pragma unroll
+          for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
+        ElemData<D, NA, P, double> ed;
+        load_element_data<D, NA, P, double>(X, ed);
+        element_pair_dispatch<D, NA, P, double>(ed, tb, cf, a.coef_f32, sub, active, dst, a.which, qual, bad);
+      }
+      const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
+      const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
+      if (active && sub == 0) {
+        if constexpr (sizeof(R) == 4) {
+          flag[jt] = ((D > 1 && q2 < (R)a.qmin) || bad2) ? 1 : 0;
+        } else {
+          const int32_t n0 = t_nodes[en[0]];
+          if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
+        }
+      }
+      if (!prefetched) prefetch_next();
+    }
+    if constexpr (sizeof(R) == 4) {
+      __syncthreads();
+      // rare path: double recomputation of flagged elements from global coordinates
+      for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
+        if (!flag[j]) continue;
+        const uint16_t* en = t_en + (size_t)j * REF;
+        int32_t nd[REF];
+#pragma unroll
+        for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
+        bool bad = false;
+        element_fp64_lean<D, NA, P, float>(a.coords, nd, a.tab, a.coef, a.coef_f32, (int64_t)t_elem[j], a.which,
+                                           lsm + (size_t)j * lstride, U, bad);
+        if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
+          atomicAdd(a.fallback, 1ull);
+          if (bad) atomicOr(a.status, ST_DEGENERATE);
+        }
+      }
+    }
+    if (!prefetched) prefetch_next();
+    __syncthreads();
+
+    // ---- phase 2: runs of slots balanced by contribution count; each slot's
+    // list summed in order (compensated, in registers) and stored
+    {
+      const int per = (h.nent + (int)blockDim.x - 1) / (int)blockDim.x;
+      auto first_slot = [&](int key) {
+        int lo = 0, hi = h.ns;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((int)t_soff[mid] < key) lo = mid + 1;
+          else hi = mid;
+        }
+        return lo;
+      };
+      // one binary search per thread; the next thread's start ends the run
+      int* run_start = reinterpret_cast<int*>(flag);  // flags are dead here (all fallbacks done)
+      run_start[threadIdx.x] = first_slot((int)threadIdx.x * per);
+      if (threadIdx.x == 0) run_start[blockDim.x] = h.ns;
+      __syncthreads();
+      const int sb = run_start[threadIdx.x], se = run_start[threadIdx.x + 1];
+      R* o0 = reinterpret_cast<R*>(a.out[0]) + h.s0;
+      R* o1 = nm > 1 ? reinterpret_cast<R*>(a.out[1]) + h.s0 : o0;
+      R* o2 = nm > 2 ? reinterpret_cast<R*>(a.out[2]) + h.s0 : o0;
+      if (sb < se) {
+        // one loop over the run's contributions (lanes stay in step); a slot
+        // is stored when its list ends
+        int s = sb;
+        int k = t_soff[sb];
+        const int kend = t_soff[se];
+        int kslot = t_soff[sb + 1];
+        Acc c0, c1, c2;
+        acc_zero(c0);
+        acc_zero(c1);
+        acc_zero(c2);
+        for (; k < kend; ++k) {
+          const uint32_t ent = t_sent[k];
+          const R* l = lsm + (size_t)(ent >> UB) * lstride + (ent & ((1u << UB) - 1));
+          acc_add(c0, l[0]);
+          if (nm > 1) acc_add(c1, l[U]);
+          if (nm > 2) acc_add(c2, l[2 * U]);
+          if (k + 1 == kslot) {
+            o0[s] = (R)acc_final(c0);
+            if (nm > 1) o1[s] = (R)acc_final(c1);
+            if (nm > 2) o2[s] = (R)acc_final(c2);
+            acc_zero(c0);
+            acc_zero(c1);
+            acc_zero(c2);
+            ++s;
+            if (s < se) kslot = t_soff[s + 1];
+          }
+        }
+      }
+    }
+    if (*s_flag) {
+      // the next block never arrived: report, wait (bounded) for the copy, stop
+      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
+      if (tn < a.n_tiles) mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
+      cp_async_wait_all();
+      return;
+    }
+    __syncthreads();
+  }
+  cp_async_wait_all();
+}
+
+template <int D, int NA, int P, typename R>
+size_t pipe_smem_bytes(int nm, int S, int chunk, int cap_bytes, int cap_nodes, int cap_nel, int q, int coef_bytes) {
+  return pipe_smem_layout<R>(NA, Ref<D, P>::U, nm, S, chunk, cap_bytes, cap_nodes, cap_nel, q, coef_bytes).total;
+}
+
+template <int D, int NA, int P, typename R>
+lfem_status launch_pipe(const PipeArgs& a, int pos_bytes, int sm_count, cudaStream_t st) {
+  if (a.n_tiles == 0) return LFEM_OK;
+  const int coef_bytes = (a.which & LFEM_CMASS) ? (a.coef_f32 ? 4 : 8) : 0;
+  const size_t smem =
+      pipe_smem_bytes<D, NA, P, R>(a.nm, a.slots_cap, a.chunk, a.cap_bytes, a.cap_nodes, a.cap_nel, a.tab.q, coef_bytes);
+  if (smem > 227 * 1024) return fail(LFEM_E_TOO_LARGE, "pipelined tile needs more than 227 KB of shared memory");
+  auto kern = pos_bytes == 2 ? k_assemble_pipe<D, NA, P, R, uint16_t> : k_assemble_pipe<D, NA, P, R, uint32_t>;
+  LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  LFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PipeOcc<R>::THREADS, smem));
+  if (per_sm < 1) return fail(LFEM_E_TOO_LARGE, "pipelined kernel does not fit on an SM");
+  int64_t grid = (int64_t)per_sm * sm_count;
+  if (grid > a.n_tiles) grid = a.n_tiles;
+  kern<<<(unsigned)grid, PipeOcc<R>::THREADS, smem, st>>>(a);
+  LFEM_CUDA(cudaGetLastError());
+  return LFEM_OK;
+}
+
+}  // namespace lfem

@@ -140,12 +140,6 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
 
 lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_t st);
 
-static lfem_status run_tiles(int dim, int NA, int P, bool mixed, const AsmArgs& a, int64_t T, int thr, int pb,
-                             cudaStream_t st) {
-  if (dim == 1) return run_tiles_d1(NA, P, mixed, a, T, thr, pb, st);
-  if (dim == 2) return run_tiles_d2(NA, P, mixed, a, T, thr, pb, st);
-  return run_tiles_d3(NA, P, mixed, a, T, thr, pb, st);
-}
 static lfem_status run_stage(int dim, int NA, int P, int kind, const StageArgs& s, cudaStream_t st) {
   if (dim == 1) return run_stage_d1(NA, P, kind, s, st);
   if (dim == 2) return run_stage_d2(NA, P, kind, s, st);
@@ -156,15 +150,21 @@ static lfem_status run_adjoint(int dim, int NA, int P, const AdjArgs& a, int64_t
   if (dim == 2) return run_adjoint_d2(NA, P, a, T, pb, st);
   return run_adjoint_d3(NA, P, a, T, pb, st);
 }
-static size_t tile_smem(int dim, int NA, int P, bool mixed, int nm, int slots, int chunk) {
-  if (dim == 1) return tile_smem_d1(NA, P, mixed, nm, slots, chunk);
-  if (dim == 2) return tile_smem_d2(NA, P, mixed, nm, slots, chunk);
-  return tile_smem_d3(NA, P, mixed, nm, slots, chunk);
+static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& a, int pb, int sms, cudaStream_t st) {
+  if (dim == 1) return run_pipe_d1(NA, P, mixed, a, pb, sms, st);
+  if (dim == 2) return run_pipe_d2(NA, P, mixed, a, pb, sms, st);
+  return run_pipe_d3(NA, P, mixed, a, pb, sms, st);
+}
+static size_t pipe_smem(int dim, int NA, int P, bool mixed, int nm, int S, int chunk, int cb, int cn, int ce, int q,
+                        int coefb) {
+  if (dim == 1) return pipe_smem_d1(NA, P, mixed, nm, S, chunk, cb, cn, ce, q, coefb);
+  if (dim == 2) return pipe_smem_d2(NA, P, mixed, nm, S, chunk, cb, cn, ce, q, coefb);
+  return pipe_smem_d3(NA, P, mixed, nm, S, chunk, cb, cn, ce, q, coefb);
 }
 
 static void destroy_dev(PatternDev& d) {
-  void* ptrs[] = {d.conn, d.row_ptr, d.col_idx, d.inc_ptr, d.inc_key, d.inc_pos, d.elem_inc,
-                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status};
+  void* ptrs[] = {d.conn,      d.row_ptr,       d.col_idx,   d.inc_ptr,   d.inc_key, d.inc_pos,    d.elem_inc,
+                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = PatternDev{};
@@ -211,6 +211,8 @@ lfem_status lfem_pattern(const int32_t* conn, int64_t n_elem, int32_t n_nodes, i
   p->ref = ref;
   p->n_elem = n_elem;
   p->n_nodes = n_nodes;
+  // default tile capacity: all of a tile's local matrices stay in shared memory
+  p->tile_slots = ref >= 10 ? 1024 : 2048;
   lfem_status s = build_pattern(p, conn, st);
   if (s != LFEM_OK) {
     std::string keep = g_err;
@@ -272,6 +274,12 @@ lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t t
   return LFEM_OK;
 }
 
+lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  p->debug_starve = starve ? 1 : 0;
+  return LFEM_OK;
+}
+
 lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                           const void* coef, int coef_is_fp32, unsigned which, lfem_precision prec, void* M, void* A,
                           void* MC, void* cuda_stream) {
@@ -311,21 +319,39 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   a.qmin = 0.25f;
   a.status = p->d.status;
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
-  // mixed kernel: 192 threads (launch bound), double kernel: up to 256
-  const int max_threads = mixed ? 192 : 256;
-  const int threads = p->threads ? (p->threads < max_threads ? p->threads : max_threads) : max_threads;
-  // elements per chunk: the requested value (default 256) lowered, in steps of
-  // 32, until the tile fits the shared-memory budget
-  // (mixed: two CTAs per SM need <= ~110 KB each)
-  const size_t budget = mixed ? 110 * 1024 : 200 * 1024;
-  int chunk = p->chunk ? p->chunk : (mixed ? threads : 128);
-  while (chunk > 32 && tile_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk) > budget)
-    chunk = chunk > 64 ? ((chunk - 1) / 32) * 32 : 32;
-  while (chunk > 8 && tile_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk) > 227 * 1024)
+  // persistent pipelined kernel: a lane pair per element, so 192 (float) or
+  // 128 (double) elements per phase-1 round (fewer only if shared memory runs out)
+  PipeArgs pa{};
+  pa.coords = coords;
+  pa.coef = coef;
+  pa.coef_f32 = a.coef_f32;
+  pa.meta = p->d.tile_meta;
+  pa.meta_off = p->d.tile_meta_off;
+  pa.n_tiles = p->n_tiles;
+  for (int m = 0; m < 3; ++m) pa.out[m] = a.out[m];
+  pa.nm = nm;
+  pa.which = which;
+  pa.tab = tab;
+  pa.slots_cap = p->tile_slots;
+  pa.cap_bytes = p->max_tile_bytes;
+  pa.cap_nodes = p->max_tile_nodes;
+  pa.cap_nel = p->max_tile_nel;
+  pa.qmin = a.qmin;
+  pa.status = p->d.status;
+  pa.fallback = a.fallback;
+  pa.starve = p->debug_starve;
+  pa.wait_ns = 2000000000ll;  // 2 s bound on every mbarrier wait
+  const int coefb = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
+  int chunk = (mixed ? PipeOcc<float>::THREADS : PipeOcc<double>::THREADS) / kPipeTPE;
+  if (p->chunk && p->chunk < chunk) chunk = p->chunk;
+  while (chunk > 8 && pipe_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk, pa.cap_bytes,
+                                pa.cap_nodes, pa.cap_nel, tab.q, coefb) > 227 * 1024)
     chunk /= 2;
-  a.chunk = chunk;
+  pa.chunk = chunk;
+  int sms = 0;
+  LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
-  return run_tiles(p->dim, ambient, p->order, mixed, a, p->n_tiles, threads, p->pos_bytes, st);
+  return run_pipe(p->dim, ambient, p->order, mixed, pa, p->ent_bytes, sms, st);
 }
 
 lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
@@ -411,6 +437,7 @@ lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream) {
   LFEM_CUDA(cudaMemcpyAsync(&h, p->d.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   LFEM_CUDA(cudaMemsetAsync(p->d.status, 0, sizeof(int32_t), st));
   LFEM_CUDA(cudaStreamSynchronize(st));
+  if (h & ST_TIMEOUT) return fail(LFEM_E_TIMEOUT, "a bounded device wait ran out");
   if (h & ST_INDEX) return fail(LFEM_E_INDEX, "node index out of range");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
   return LFEM_OK;

@@ -24,12 +24,14 @@ lfem_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // Device status bits (pattern status word).
-enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2 };
+enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2, ST_TIMEOUT = 4 };
 
 // Tile limits.
 constexpr int kMaxTileIncidences = 4096;  // incidences (e, a) per tile; local index fits 12 bits
 constexpr int kMaxDegree = 2048;          // elements meeting at one node
 constexpr int kMaxSegSort = 16384;        // longest row of raw column entries sorted in one block
+constexpr int kMaxTileRows = 4096;        // rows per tile (row offsets are 16-bit)
+constexpr int kMaxTileEntries = 16384;    // incidences x ref per tile (node-list sort in one block)
 
 // ----------------------------------------------------------------------------
 // Element types
@@ -197,12 +199,19 @@ struct QpGeom {
   R quality;      // det G / (tr G / D)^D in (0, 1]; 1 for D = 1
 };
 
-template <typename R>
-__device__ __forceinline__ R rsqrt_(R x);
-template <>
-__device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
-template <>
-__device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+// s = sqrt(s2) and 1/s.  Float: one hardware reciprocal square root (about
+// 1 ulp), no division sequence; double: IEEE square root and division.
+__device__ __forceinline__ void norm_inv(float s2, float& s, float& inv) {
+  inv = rsqrtf(s2);
+  s = s2 * inv;
+}
+__device__ __forceinline__ void norm_inv(double s2, double& s, double& inv) {
+  s = sqrt(s2);
+  inv = 1.0 / s;
+}
+// 1/x: float hardware reciprocal (about 1 ulp); double IEEE.
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 
 template <int D, int NA, int P, typename R>
 __device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb, int q, R wq,
@@ -221,9 +230,10 @@ __device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, con
     R tt = 0;
 #pragma unroll
     for (int i = 0; i < NA; ++i) tt = fma(g.J[i][0], g.J[i][0], tt);
-    R s = sqrt(tt);
+    R s, inv;
+    norm_inv(tt, s, inv);
     g.s = s;
-    g.H[0][0] = wq / s;
+    g.H[0][0] = wq * inv;
     g.quality = (R)1;
   } else if constexpr (D == 2) {
     R g11 = 0, g12 = 0, g22 = 0;
@@ -233,22 +243,23 @@ __device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, con
       g12 = fma(g.J[i][0], g.J[i][1], g12);
       g22 = fma(g.J[i][1], g.J[i][1], g22);
     }
-    R s;
+    R s, inv;
     if constexpr (NA == 2) {
       s = fabs(g.J[0][0] * g.J[1][1] - g.J[0][1] * g.J[1][0]);
+      inv = rcp_(s);
     } else {
       R n0 = g.J[1][0] * g.J[2][1] - g.J[2][0] * g.J[1][1];
       R n1 = g.J[2][0] * g.J[0][1] - g.J[0][0] * g.J[2][1];
       R n2 = g.J[0][0] * g.J[1][1] - g.J[1][0] * g.J[0][1];
-      s = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+      norm_inv(n0 * n0 + n1 * n1 + n2 * n2, s, inv);
     }
     g.s = s;
-    R ws_inv = wq / s;
+    R ws_inv = wq * inv;
     g.H[0][0] = ws_inv * g22;
     g.H[1][1] = ws_inv * g11;
     g.H[0][1] = g.H[1][0] = -ws_inv * g12;
     R tr = (R)0.5 * (g11 + g22);
-    g.quality = (s * s) / (tr * tr);
+    g.quality = (s * s) * rcp_(tr * tr);
   } else {
     // D = NA = 3: cofactor vectors c_m = t_{m+1} x t_{m+2}; adj(G)_mk = c_m . c_k
     R c[3][3];
@@ -262,7 +273,7 @@ __device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, con
     R det = g.J[0][0] * c[0][0] + g.J[1][0] * c[0][1] + g.J[2][0] * c[0][2];
     R s = fabs(det);
     g.s = s;
-    R ws_inv = wq / s;
+    R ws_inv = wq * rcp_(s);
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
@@ -276,7 +287,7 @@ __device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, con
 #pragma unroll
       for (int m = 0; m < 3; ++m) tr = fma(g.J[i][m], g.J[i][m], tr);
     tr *= (R)(1.0 / 3.0);
-    g.quality = (s * s) / (tr * tr * tr);
+    g.quality = (s * s) * rcp_(tr * tr * tr);
   }
 }
 
@@ -339,6 +350,48 @@ __device__ __forceinline__ void gather_coords(const double* __restrict__ coords,
 }
 
 // ----------------------------------------------------------------------------
+// Per-tile metadata block (built once per topology, staged by one TMA bulk copy):
+//   header   TileHdr (32 B)
+//   elem     int32  [nel]          element ids, ascending
+//   nodes    int32  [nnodes]       distinct nodes of the tile's elements, ascending
+//   enodes   uint16 [nel][ref]     local node index of each element node
+//   soff     uint16 [ns + 1]       start of each slot's contribution list in sent
+//   sent     EntT   [nent]         contributions, (local element << UB) | upper index,
+//                                  per slot in ascending (element, a, b) order
+// every section starts on a 16-byte boundary; the block size is a multiple of 16.
+// A row's contributions are contiguous: ref per incidence of the row.
+// ----------------------------------------------------------------------------
+struct TileHdr {
+  int64_t s0;
+  int32_t r0, nrows, ns, nent, nel, nnodes;
+};
+static_assert(sizeof(TileHdr) == 32, "tile header");
+
+__host__ __device__ constexpr int al16(int64_t b) { return (int)((b + 15) / 16 * 16); }
+// bits of the upper index in a contribution entry
+__host__ __device__ constexpr int ub_bits(int u) { return u <= 1 ? 1 : (u <= 2 ? 1 : (u <= 4 ? 2 : (u <= 8 ? 3 : (u <= 16 ? 4 : (u <= 32 ? 5 : 6))))); }
+
+struct TileLayout {
+  int elem, nodes, enodes, soff, sent, total;
+};
+__host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nent, int nnodes, int ref, int entb) {
+  TileLayout L;
+  int o = 32;
+  L.elem = o;
+  o += al16(4ll * nel);
+  L.nodes = o;
+  o += al16(4ll * nnodes);
+  L.enodes = o;
+  o += al16(2ll * ref * nel);
+  L.soff = o;
+  o += al16(2ll * (ns + 1));
+  L.sent = o;
+  o += al16((int64_t)entb * nent);
+  L.total = o;
+  return L;
+}
+
+// ----------------------------------------------------------------------------
 // Pattern handle
 // ----------------------------------------------------------------------------
 struct PatternDev {
@@ -354,6 +407,8 @@ struct PatternDev {
   int32_t* tile_elem = nullptr;  // [sum] ascending element ids per tile
   uint16_t* inc_local = nullptr; // [nInc] (index of e in its tile's list) << 4 | a
   int32_t* status = nullptr;     // [4]: status bits, pad, fallback count (int64 at [2])
+  uint8_t* tile_meta = nullptr;  // per-tile metadata blocks (see TileHdr)
+  int64_t* tile_meta_off = nullptr;  // [T+1] byte offsets, multiples of 16
 };
 
 }  // namespace lfem
@@ -367,9 +422,12 @@ struct lfem_pattern_s {
   int64_t n_inc = 0;
   int32_t max_row = 0, max_deg = 0;
   int pos_bytes = 1;
-  int32_t tile_slots = 2048;
+  int32_t tile_slots = 3072;
   int64_t n_tiles = 0;
   int64_t tile_elems_total = 0;
+  int32_t max_tile_nel = 0, max_tile_nodes = 0, max_tile_bytes = 0;
+  int ent_bytes = 2;     // 2 or 4: contribution entry width in the tile blocks
+  int debug_starve = 0;  // test knob: the first CTA skips its first metadata copy (bounded wait runs out)
   int32_t chunk = 0;    // elements per chunk (0 = default)
   int32_t threads = 0;  // threads per block (0 = default)
   lfem::PatternDev d;

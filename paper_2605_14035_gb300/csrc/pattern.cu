@@ -6,6 +6,7 @@
 // This replaces the per-assembly sort inside sparse(I, J, V) (Sec. 3.3: the
 // log-linear cost comes from sorting and merging duplicates; precomputing the
 // sparsity structure removes it from the assembly).
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <mutex>
@@ -401,6 +402,220 @@ static lfem_status dalloc(T** p, int64_t n) {
     if (_s != LFEM_OK) return _s;       \
   } while (0)
 
+// Distinct nodes of each tile's elements (sorted), and the tile's block size.
+__global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ tile_row0,
+                             const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ inc_ptr,
+                             const int32_t* __restrict__ tile_elem_ptr, const int32_t* __restrict__ tile_elem,
+                             int entb, int32_t* __restrict__ tmp_nodes, int32_t* __restrict__ n_nodes_out,
+                             int64_t* __restrict__ bytes_out) {
+  extern __shared__ int32_t sn[];
+  __shared__ int32_t wsum[32];
+  const int t = blockIdx.x;
+  const int32_t e0 = tile_elem_ptr[t];
+  const int nel = tile_elem_ptr[t + 1] - e0;
+  const int n = nel * ref;
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x)
+    sn[i] = i < n ? conn[(int64_t)tile_elem[e0 + i / ref] * ref + (i % ref)] : INT_MAX;
+  __syncthreads();
+  if (n > 1) bitonic_smem<true>(sn, np2, threadIdx.x, blockDim.x);
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int beg = threadIdx.x * per, end = min(n, beg + per);
+  int cnt = 0;
+  for (int i = beg; i < end; ++i) cnt += (i == 0 || sn[i] != sn[i - 1]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    wsum[lane] = v;
+  }
+  __syncthreads();
+  int excl = x - cnt + (wid > 0 ? wsum[wid - 1] : 0);
+  const int total = wsum[(blockDim.x >> 5) - 1];
+  int32_t* out = tmp_nodes + (int64_t)e0 * ref;
+  for (int i = beg; i < end; ++i)
+    if (i == 0 || sn[i] != sn[i - 1]) out[excl++] = sn[i];
+  if (threadIdx.x == 0) {
+    const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
+    const int ns = (int)(row_ptr[r1] - row_ptr[r0]);
+    const int nent = (inc_ptr[r1] - inc_ptr[r0]) * ref;
+    n_nodes_out[t] = total;
+    bytes_out[t] = tile_layout(nel, ns, nent, total, ref, entb).total;
+  }
+}
+
+// Fill one tile's block.  The contribution list of a slot holds, in ascending
+// (element, a, b) order, every local pair of the tile's elements that adds into
+// it; a row's lists are contiguous (ref entries per incidence of the row).
+template <typename PosT>
+__global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ tile_row0,
+                            const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ inc_ptr,
+                            const uint16_t* __restrict__ inc_local, const PosT* __restrict__ inc_pos,
+                            const int32_t* __restrict__ tile_elem_ptr, const int32_t* __restrict__ tile_elem,
+                            const int32_t* __restrict__ tmp_nodes, const int32_t* __restrict__ n_nodes,
+                            const int64_t* __restrict__ off, int entb, uint8_t* __restrict__ meta) {
+  const int t = blockIdx.x;
+  const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
+  const int32_t i0 = inc_ptr[r0];
+  const int nrows = r1 - r0;
+  const int nent = (inc_ptr[r1] - i0) * ref;
+  const int32_t e0 = tile_elem_ptr[t];
+  const int nel = tile_elem_ptr[t + 1] - e0;
+  const int nn = n_nodes[t];
+  const int64_t s0 = row_ptr[r0];
+  const int ns = (int)(row_ptr[r1] - s0);
+  const int U = ref * (ref + 1) / 2;
+  const int UB = ub_bits(U);
+  const int ps = pos_stride(ref);
+  uint8_t* blk = meta + off[t];
+  const TileLayout L = tile_layout(nel, ns, nent, nn, ref, entb);
+  for (int i = threadIdx.x; i < L.total / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(blk)[i] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    TileHdr h;
+    h.s0 = s0;
+    h.r0 = r0;
+    h.nrows = nrows;
+    h.ns = ns;
+    h.nent = nent;
+    h.nel = nel;
+    h.nnodes = nn;
+    *reinterpret_cast<TileHdr*>(blk) = h;
+  }
+  int32_t* el = reinterpret_cast<int32_t*>(blk + L.elem);
+  int32_t* nd = reinterpret_cast<int32_t*>(blk + L.nodes);
+  uint16_t* en = reinterpret_cast<uint16_t*>(blk + L.enodes);
+  uint16_t* so = reinterpret_cast<uint16_t*>(blk + L.soff);
+  uint8_t* se = blk + L.sent;
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) el[i] = tile_elem[e0 + i];
+  const int32_t* tn = tmp_nodes + (int64_t)e0 * ref;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) nd[i] = tn[i];
+  for (int i = threadIdx.x; i < nel * ref; i += blockDim.x) {
+    const int32_t v = conn[(int64_t)tile_elem[e0 + i / ref] * ref + (i % ref)];
+    int lo = 0, hi = nn;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (tn[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    en[i] = (uint16_t)lo;
+  }
+  // contribution lists, one thread per row
+  for (int rl = threadIdx.x; rl < nrows; rl += blockDim.x) {
+    const int r = r0 + rl;
+    const int kb = inc_ptr[r], ke = inc_ptr[r + 1];
+    const int slot0 = (int)(row_ptr[r] - s0), len = (int)(row_ptr[r + 1] - row_ptr[r]);
+    int run = (kb - i0) * ref;
+    for (int j = 0; j < len; ++j) {
+      so[slot0 + j] = (uint16_t)run;
+      for (int k = kb; k < ke; ++k) {
+        const int lk = inc_local[k];
+        const int a = lk & 15, loc = lk >> 4;
+        for (int b = 0; b < ref; ++b) {
+          if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
+          const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
+          const uint32_t ent = ((uint32_t)loc << UB) | (uint32_t)u;
+          if (entb == 2) reinterpret_cast<uint16_t*>(se)[run] = (uint16_t)ent;
+          else reinterpret_cast<uint32_t*>(se)[run] = ent;
+          ++run;
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0) so[ns] = (uint16_t)nent;
+}
+
+__global__ void k_max_i64(const int64_t* __restrict__ a, int64_t n, int64_t* __restrict__ out) {
+  long long m = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (long long)a[k]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)out, (unsigned long long)m);
+}
+
+// Build the per-tile metadata blocks from the tile lists.
+static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
+  PatternDev& d = p->d;
+  const int64_t T = p->n_tiles;
+  const int ref = p->ref;
+  if (d.tile_meta) cudaFree(d.tile_meta);
+  if (d.tile_meta_off) cudaFree(d.tile_meta_off);
+  d.tile_meta = nullptr;
+  d.tile_meta_off = nullptr;
+  // largest element count per tile decides the contribution entry width
+  std::vector<int32_t> hep(T + 1);
+  LFEM_CUDA(cudaMemcpyAsync(hep.data(), d.tile_elem_ptr, sizeof(int32_t) * (T + 1), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  int32_t mnel = 0;
+  for (int64_t t = 0; t < T; ++t) mnel = std::max(mnel, hep[t + 1] - hep[t]);
+  const int UB = ub_bits(ref * (ref + 1) / 2);
+  const int entb = ((int64_t)mnel << UB) <= 65536 ? 2 : 4;
+  int32_t *tmp_nodes = nullptr, *nn = nullptr;
+  int64_t *bytes = nullptr, *scr = nullptr, *mx = nullptr;
+  TRY(dalloc(&tmp_nodes, p->tile_elems_total * ref));
+  TRY(dalloc(&nn, T + 1));
+  TRY(dalloc(&bytes, T + 1));
+  TRY(dalloc(&mx, 4));
+  TRY(dalloc(&scr, scan_scratch_bytes(T, 8) / 8));
+  TRY(dalloc(&d.tile_meta_off, T + 1));
+  LFEM_CUDA(cudaMemsetAsync(mx, 0, 4 * sizeof(int64_t), st));
+  if (T > 0) {
+    const size_t smem = sizeof(int32_t) * kMaxTileEntries;
+    LFEM_CUDA(cudaFuncSetAttribute(k_tile_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tile_nodes<<<(unsigned)T, 512, smem, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.tile_elem_ptr,
+                                                 d.tile_elem, entb, tmp_nodes, nn, bytes);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  scan_exclusive<int64_t, int64_t>(bytes, d.tile_meta_off, T, scr, st);
+  if (T > 0) {
+    k_max_i64<<<grid_for(T, 256), 256, 0, st>>>(bytes, T, mx);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  int64_t total = 0, hmax[1] = {0};
+  LFEM_CUDA(cudaMemcpyAsync(&total, d.tile_meta_off + T, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaMemcpyAsync(hmax, mx, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  TRY(dalloc(&d.tile_meta, total));
+  if (T > 0) {
+    if (p->pos_bytes == 1)
+      k_tile_fill<uint8_t><<<(unsigned)T, 128, 0, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.inc_local,
+                                                         d.inc_pos, d.tile_elem_ptr, d.tile_elem, tmp_nodes, nn,
+                                                         d.tile_meta_off, entb, d.tile_meta);
+    else
+      k_tile_fill<uint16_t><<<(unsigned)T, 128, 0, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr,
+                                                          d.inc_local, (const uint16_t*)d.inc_pos, d.tile_elem_ptr,
+                                                          d.tile_elem, tmp_nodes, nn, d.tile_meta_off, entb,
+                                                          d.tile_meta);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  std::vector<int32_t> hnn(T);
+  LFEM_CUDA(cudaMemcpyAsync(hnn.data(), nn, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  int32_t mnn = 0;
+  for (int64_t t = 0; t < T; ++t) mnn = std::max(mnn, hnn[t]);
+  p->max_tile_nel = mnel;
+  p->max_tile_nodes = mnn;
+  p->max_tile_bytes = (int32_t)hmax[0];
+  p->ent_bytes = entb;
+  cudaFree(tmp_nodes);
+  cudaFree(nn);
+  cudaFree(bytes);
+  cudaFree(mx);
+  cudaFree(scr);
+  return LFEM_OK;
+}
+
 lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st) {
   PatternDev& d = p->d;
   const int32_t N = p->n_nodes;
@@ -416,7 +631,9 @@ lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st) 
   rows.push_back(0);
   int32_t r0 = 0;
   for (int32_t i = 0; i < N; ++i) {
-    bool over = (rp[i + 1] - rp[r0] > tile_slots) || (ip[i + 1] - ip[r0] > kMaxTileIncidences);
+    const int64_t ninc = ip[i + 1] - ip[r0];
+    bool over = (rp[i + 1] - rp[r0] > tile_slots) || (ninc > kMaxTileIncidences) ||
+                (ninc * p->ref > kMaxTileEntries) || (i + 1 - r0 > kMaxTileRows);
     if (over && i > r0) {
       rows.push_back(i);
       r0 = i;
@@ -455,7 +672,7 @@ lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st) 
   p->n_tiles = T;
   p->tile_slots = tile_slots;
   p->tile_elems_total = total;
-  return LFEM_OK;
+  return build_tile_blocks(p, st);
 }
 
 lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_t st) {

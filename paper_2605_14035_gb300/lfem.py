@@ -27,7 +27,7 @@ EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
     "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
-    "lfem_status_string", "lfem_pattern_csr_noalloc",
+    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait",
 )
 
 
@@ -61,6 +61,7 @@ def _load():
         "lfem_sync_status": [P, P],
         "lfem_mixed_fallback_count": [P, P, P],
         "lfem_pattern_csr_noalloc": [P, L, ctypes.c_int32, I, I, P, P, L, P, P],
+        "lfem_debug_starve_wait": [P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -174,6 +175,9 @@ class Pattern:
 
     def set_launch(self, elems_per_chunk: int = 0, threads: int = 0):
         _check(_lib.lfem_set_launch(self._h, int(elems_per_chunk), int(threads)))
+
+    def debug_starve_wait(self, starve: bool):
+        _check(_lib.lfem_debug_starve_wait(self._h, int(bool(starve))))
 
     def sync_status(self, stream=None):
         _check(_lib.lfem_sync_status(self._h, _stream(stream)))
