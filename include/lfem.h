@@ -130,11 +130,56 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
  * per block); 0 keeps the current value.  Used by the autotuner. */
 lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t threads);
 
+/* Autotuner: times lfem_assemble (CUDA events, after one warm-up) for each
+ * candidate tile capacity (slots per tile: 512..8192, those whose shared
+ * memory fits), keeps the fastest and retiles p with it.  M/A/MC are scratch
+ * outputs sized as for lfem_assemble (overwritten).  If cache_path is not
+ * NULL, results are read from / appended to that text file, keyed by
+ * (dim, ambient, order, quadrature points, precision, which, element-count
+ * bucket, GPU name).  Synchronises the stream; *best_slots may be NULL. */
+lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad, const void* coef,
+                          int coef_is_fp32, unsigned which, lfem_precision prec, void* M, void* A, void* MC,
+                          const char* cache_path, void* cuda_stream, int32_t* best_slots);
+
 /* Failure-path test knob (not for production use): with starve != 0 the first
  * CTA of the next assemblies on p skips its first metadata copy, so its bounded
  * wait (2 s) runs out; lfem_sync_status then returns LFEM_E_TIMEOUT and the
  * values of that CTA's tiles are left unwritten.  The CUDA context stays usable. */
 lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many meshes of uneven sizes and different element types assembled
+ * by one persistent launch over all their row tiles (mixed precision only;
+ * curves and triangles, P1 and P2: (dim, ambient) in (1,2) (2,2) (2,3)).
+ * Motivated by the paper's batchwise processing of large meshes (Remark
+ * "Batch computations", Sec. 3.3; Sec. 5.1).
+ *
+ * Every pointer of an item is fixed at creation: later calls read the current
+ * contents of coords / coef and overwrite M / A / MC (float [nnz] of the
+ * item's pattern).  The batch keeps its own status word.
+ */
+typedef struct {
+  lfem_pattern_t pattern;  /* topology (not owned) */
+  const double* coords;    /* device [n_nodes][ambient] */
+  int ambient;
+  const lfem_quad* quad;   /* host rule; tables are registered at creation */
+  const void* coef;        /* device [n_elem][n_pts] (float if coef_is_fp32) or NULL */
+  void* M;
+  void* A;
+  void* MC;
+} lfem_batch_item;
+
+lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigned which, int coef_is_fp32,
+                              void* cuda_stream, lfem_batch_t* out);
+/* One persistent launch (asynchronous). */
+lfem_status lfem_batch_assemble(lfem_batch_t b, void* cuda_stream);
+/* The same launch as a CUDA graph: captured on the first call, replayed after. */
+lfem_status lfem_batch_graph_launch(lfem_batch_t b, void* cuda_stream);
+/* Synchronises; returns and clears the batch status (LFEM_E_DEGENERATE, LFEM_E_TIMEOUT). */
+lfem_status lfem_batch_sync_status(lfem_batch_t b, void* cuda_stream);
+/* Work items, elements computed and the largest tile of the batch (host values). */
+lfem_status lfem_batch_info(lfem_batch_t b, int64_t* n_work_items, int64_t* n_elements, int32_t* cap_elements);
+void lfem_batch_destroy(lfem_batch_t b);
 
 /* ---------------------------------------------------------------------------
  * Adjoint: for L = gM.M + gA.A + gMC.MC (dot products over the CSR values),

@@ -23,7 +23,7 @@ lfem_status run_adjoint_d1(int NA, int P, const AdjArgs& a, int64_t T, int pos_b
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }
 
-lfem_status run_pipe_d1(int NA, int P, bool mixed, const PipeArgs& a, int pos_bytes, int sms, cudaStream_t st) {
+lfem_status run_pipe_d1(int NA, int P, bool mixed, const PipeArgs& a, int ent_bytes, int sms, cudaStream_t st) {
   LFEM_DEFINE_CASE_PIPE(1, 1, 1)
   LFEM_DEFINE_CASE_PIPE(1, 1, 2)
   LFEM_DEFINE_CASE_PIPE(1, 2, 1)
@@ -31,17 +31,6 @@ lfem_status run_pipe_d1(int NA, int P, bool mixed, const PipeArgs& a, int pos_by
   LFEM_DEFINE_CASE_PIPE(1, 3, 1)
   LFEM_DEFINE_CASE_PIPE(1, 3, 2)
   return fail(LFEM_E_UNSUPPORTED, "element type");
-}
-
-size_t pipe_smem_d1(int NA, int P, bool mixed, int nm, int S, int chunk, int cap_bytes, int cap_nodes, int cap_nel,
-                     int q, int coef_bytes) {
-  LFEM_DEFINE_CASE_PIPE_SMEM(1, 1, 1)
-  LFEM_DEFINE_CASE_PIPE_SMEM(1, 1, 2)
-  LFEM_DEFINE_CASE_PIPE_SMEM(1, 2, 1)
-  LFEM_DEFINE_CASE_PIPE_SMEM(1, 2, 2)
-  LFEM_DEFINE_CASE_PIPE_SMEM(1, 3, 1)
-  LFEM_DEFINE_CASE_PIPE_SMEM(1, 3, 2)
-  return 0;
 }
 
 lfem_status bank_upload_d1(const void* src, size_t bytes, size_t offset) {

@@ -48,27 +48,41 @@ struct PipeOcc<double> {
   static constexpr int MIN_BLOCKS = 1;
 };
 
-struct PipeArgs {
+// One mesh of a launch: its inputs, outputs, tables and tile blocks.
+struct MeshRec {
   const double* coords;
   const void* coef;
-  int coef_f32;
   const uint8_t* meta;
   const int64_t* meta_off;
-  int64_t n_tiles;
   void* out[3];
+  TabRef tab;
+  int type;  // element type id (elem_type_id)
+  int na, ref, entb, coef_f32, pad;
+};
+
+__host__ __device__ constexpr int elem_type_id(int d, int na, int p) { return d * 100 + na * 10 + p; }
+
+// Arguments of a persistent launch over work items (mesh, tile).  With one
+// mesh and no item list, item i is tile i of mesh 0.
+struct PipeArgs {
+  MeshRec one;              // the mesh when meshes is NULL
+  const MeshRec* meshes;    // device table of a batch, or NULL
+  const int2* items;  // (mesh, tile), or NULL
+  int64_t n_items;
   int nm;
   unsigned which;
-  TabRef tab;
   int chunk;       // elements per phase-1 round (threads / kPipeTPE)
-  int slots_cap;   // S: tile slot capacity
   int cap_bytes;   // largest metadata block
   int cap_nodes;   // most nodes in a tile
   int cap_nel;     // most elements in a tile
+  int max_u;       // largest local upper triangle among the meshes
+  int max_q;       // most quadrature points among the meshes
+  int coef_bytes;  // 4 or 8 if the weighted mass is requested, else 0
   float qmin;
   int32_t* status;
   unsigned long long* fallback;
-  int starve;              // test knob: CTA 0 skips its first metadata copy
-  long long wait_ns;       // bound of every mbarrier wait
+  int starve;         // test knob: CTA 0 skips its first metadata copy
+  long long wait_ns;  // bound of every mbarrier wait
 };
 
 struct PipeSmem {
@@ -76,11 +90,9 @@ struct PipeSmem {
 };
 
 template <typename R>
-__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int u, int nm, int S, int chunk, int cap_bytes,
-                                                     int cap_nodes, int cap_nel, int q, int coef_bytes) {
+__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int u, int nm, int cap_bytes, int cap_nodes, int cap_nel,
+                                                     int q, int coef_bytes) {
   auto al = [](size_t b) { return (b + 127) / 128 * 128; };
-  (void)S;
-  (void)chunk;
   PipeSmem L;
   size_t o = 0;
   L.mbar = o;
@@ -188,23 +200,24 @@ __device__ __forceinline__ void load_pos_smem(const uint8_t* base, int k, int (&
 }
 
 // Issue the gathers of a tile's node coordinates and element coefficients.
-template <int NA>
-__device__ __forceinline__ void issue_gathers(const PipeArgs& a, const uint8_t* meta, double* nodes_dst,
-                                              void* coef_dst, int q, bool want_coef, int ref, int entb) {
+__device__ __forceinline__ void issue_gathers(const MeshRec& mr, bool want_coef, const uint8_t* meta,
+                                              double* nodes_dst, void* coef_dst) {
   const TileHdr h = *reinterpret_cast<const TileHdr*>(meta);
-  const TileLayout L = tile_layout(h.nel, h.ns, h.nent, h.nnodes, ref, entb);
+  const TileLayout L = tile_layout(h.nel, h.ns, h.nent, h.nnodes, mr.ref, mr.entb);
   const int32_t* nd = reinterpret_cast<const int32_t*>(meta + L.nodes);
-  for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
-    const int v = i / NA, c = i - v * NA;
-    cp_async8(nodes_dst + i, a.coords + (int64_t)nd[v] * NA + c);
+  const int na = mr.na;
+  for (int i = threadIdx.x; i < h.nnodes * na; i += blockDim.x) {
+    const int v = i / na, c = i - v * na;
+    cp_async8(nodes_dst + i, mr.coords + (int64_t)nd[v] * na + c);
   }
   if (want_coef) {
+    const int q = mr.tab.q;
     const int32_t* el = reinterpret_cast<const int32_t*>(meta + L.elem);
     for (int i = threadIdx.x; i < h.nel * q; i += blockDim.x) {
       const int j = i / q, qq = i - j * q;
       const int64_t gi = (int64_t)el[j] * q + qq;
-      if (a.coef_f32) cp_async4(static_cast<float*>(coef_dst) + i, static_cast<const float*>(a.coef) + gi);
-      else cp_async8(static_cast<double*>(coef_dst) + i, static_cast<const double*>(a.coef) + gi);
+      if (mr.coef_f32) cp_async4(static_cast<float*>(coef_dst) + i, static_cast<const float*>(mr.coef) + gi);
+      else cp_async8(static_cast<double*>(coef_dst) + i, static_cast<const double*>(mr.coef) + gi);
     }
   }
   cp_async_commit();
@@ -341,19 +354,189 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   }
 }
 
-template <int D, int NA, int P, typename R, typename EntT>
-__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k_assemble_pipe(const PipeArgs a) {
+// Shared-memory views of one CTA.
+template <typename R>
+struct TileEnv {
+  R* lsm;
+  uint8_t* flag;
+  int lstride;  // nm * U of the current element type
+};
+
+// Everything done for one tile whose block, node coordinates and coefficients
+// are in shared memory: split, phase 1 (+ the double fallback), the prefetch
+// hook of the next item after the first phase-1 round, phase 2.
+template <int D, int NA, int P, typename R, typename EntT, typename Prefetch>
+__device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
+                                             const void* coef_s, R* lsm, uint8_t* flag, Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   constexpr int UB = ub_bits(U);
   constexpr int ENTB = (int)sizeof(EntT);
   using Acc = typename AccOf<R>::T;
+  const int nm = a.nm, Q = mr.tab.q;
+  const int coef_bytes = a.coef_bytes;
+  const int lstride = nm * U;
+  const TabView<R> tb = tab_view<D, P, R>(mr.tab);
+  const TileHdr h = *reinterpret_cast<const TileHdr*>(mb);
+  const TileLayout TL = tile_layout(h.nel, h.ns, h.nent, h.nnodes, REF, ENTB);
+  const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
+  const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
+  const uint16_t* t_en = reinterpret_cast<const uint16_t*>(mb + TL.enodes);
+  const uint16_t* t_soff = reinterpret_cast<const uint16_t*>(mb + TL.soff);
+  const EntT* t_sent = reinterpret_cast<const EntT*>(mb + TL.sent);
+
+  // node coordinates -> (hi, lo) float pairs in place (mixed)
+  if constexpr (sizeof(R) == 4) {
+    for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
+      float hi, lo;
+      bool ok = true;
+      split_f64(xd[i], hi, lo, ok);
+      if (!ok) hi = __int_as_float(0x7fc00000);  // out of float range: NaN forces the double path
+      reinterpret_cast<float2*>(xd)[i] = make_float2(hi, lo);
+    }
+    __syncthreads();
+  }
+
+  bool prefetched = false;
+  // ---- phase 1: a lane pair per element, every element of the tile
+  for (int c0 = 0; c0 < h.nel; c0 += a.chunk) {
+    const int cn = min(a.chunk, h.nel - c0);
+    const int jj = threadIdx.x / kPipeTPE, sub = threadIdx.x % kPipeTPE;
+    const bool active = jj < cn;
+    const int jt = c0 + (active ? jj : 0);
+    const uint16_t* en = t_en + (size_t)jt * REF;
+    const void* cf = coef_s;
+    if (coef_bytes) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
+    R qual = (R)1;
+    bool bad = false;
+    R* dst = lsm + (size_t)jt * lstride;
+    if constexpr (sizeof(R) == 4) {
+      ElemData<D, NA, P, float> ed;
+      element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
+      element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, a.which, qual, bad);
+    } else {
+      double X[REF][NA];
+#pragma unroll
+      for (int bb = 0; bb < REF; ++bb)
+#pragma unroll
+        for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
+      ElemData<D, NA, P, double> ed;
+      load_element_data<D, NA, P, double>(X, ed);
+      element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, a.which, qual, bad);
+    }
+    const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
+    const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
+    if (active && sub == 0) {
+      if constexpr (sizeof(R) == 4) {
+        flag[jt] = ((D > 1 && q2 < (R)a.qmin) || bad2) ? 1 : 0;
+      } else {
+        const int32_t n0 = t_nodes[en[0]];
+        if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
+      }
+    }
+    if (!prefetched) {
+      prefetch();
+      prefetched = true;
+    }
+  }
+  if constexpr (sizeof(R) == 4) {
+    __syncthreads();
+    // rare path: double recomputation of flagged elements from global coordinates
+    for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
+      if (!flag[j]) continue;
+      const uint16_t* en = t_en + (size_t)j * REF;
+      int32_t nd[REF];
+#pragma unroll
+      for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
+      bool bad = false;
+      element_fp64_lean<D, NA, P, float>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], a.which,
+                                         lsm + (size_t)j * lstride, U, bad);
+      if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
+        atomicAdd(a.fallback, 1ull);
+        if (bad) atomicOr(a.status, ST_DEGENERATE);
+      }
+    }
+  }
+  if (!prefetched) prefetch();
+  __syncthreads();
+
+  // ---- phase 2: runs of slots balanced by contribution count; each slot's
+  // list summed in order (compensated, in registers) and stored
+  const int per = (h.nent + (int)blockDim.x - 1) / (int)blockDim.x;
+  auto first_slot = [&](int key) {
+    int lo = 0, hi = h.ns;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int)t_soff[mid] < key) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  // one binary search per thread; the next thread's start ends the run
+  int* run_start = reinterpret_cast<int*>(flag);  // flags are dead here (all fallbacks done)
+  run_start[threadIdx.x] = first_slot((int)threadIdx.x * per);
+  if (threadIdx.x == 0) run_start[blockDim.x] = h.ns;
+  __syncthreads();
+  const int sb = run_start[threadIdx.x], se = run_start[threadIdx.x + 1];
+  R* o0 = reinterpret_cast<R*>(mr.out[0]) + h.s0;
+  R* o1 = nm > 1 ? reinterpret_cast<R*>(mr.out[1]) + h.s0 : o0;
+  R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
+  if (sb < se) {
+    // one loop over the run's contributions (lanes stay in step); a slot is
+    // stored when its list ends
+    int s = sb;
+    int k = t_soff[sb];
+    const int kend = t_soff[se];
+    int kslot = t_soff[sb + 1];
+    Acc c0, c1, c2;
+    acc_zero(c0);
+    acc_zero(c1);
+    acc_zero(c2);
+    for (; k < kend; ++k) {
+      const uint32_t ent = t_sent[k];
+      const R* l = lsm + (size_t)(ent >> UB) * lstride + (ent & ((1u << UB) - 1));
+      acc_add(c0, l[0]);
+      if (nm > 1) acc_add(c1, l[U]);
+      if (nm > 2) acc_add(c2, l[2 * U]);
+      if (k + 1 == kslot) {
+        o0[s] = (R)acc_final(c0);
+        if (nm > 1) o1[s] = (R)acc_final(c1);
+        if (nm > 2) o2[s] = (R)acc_final(c2);
+        acc_zero(c0);
+        acc_zero(c1);
+        acc_zero(c2);
+        ++s;
+        if (s < se) kslot = t_soff[s + 1];
+      }
+    }
+  }
+}
+
+template <int D_, int NA_, int P_>
+struct EType {
+  static constexpr int D = D_, NA = NA_, P = P_;
+  static constexpr int id = elem_type_id(D_, NA_, P_);
+};
+
+template <typename R, typename EntT, typename T0, typename... Ts, typename Prefetch>
+__device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* mb,
+                                              double* xd, const void* coef_s, R* lsm, uint8_t* flag,
+                                              Prefetch&& prefetch) {
+  if (type == T0::id) {
+    process_tile<T0::D, T0::NA, T0::P, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, prefetch);
+  } else {
+    if constexpr (sizeof...(Ts) > 0) dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, prefetch);
+  }
+}
+
+// Persistent launch over work items; Types lists the element types the launch
+// may meet (one for a single mesh, several for a batch).
+template <typename R, typename EntT, typename... Types>
+__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k_assemble_pipe(const PipeArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int nm = a.nm, Q = a.tab.q;
-  const bool want_coef = (a.which & LFEM_CMASS) != 0;
-  const int coef_bytes = want_coef ? (a.coef_f32 ? 4 : 8) : 0;
+  const bool want_coef = a.coef_bytes != 0;
   const PipeSmem L =
-      pipe_smem_layout<R>(NA, U, nm, a.slots_cap, a.chunk, a.cap_bytes, a.cap_nodes, a.cap_nel, Q, coef_bytes);
+      pipe_smem_layout<R>(3, a.max_u, a.nm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
   int* s_flag = reinterpret_cast<int*>(smem_raw + L.mbar + 64);
   uint8_t* meta_buf[2] = {smem_raw + L.meta0, smem_raw + L.meta1};
@@ -361,11 +544,9 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
   void* coef_buf[2] = {smem_raw + L.coef0, smem_raw + L.coef1};
   R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
   uint8_t* flag = smem_raw + L.flag;
-  const int lstride = nm * U;
-  const TabView<R> tb = tab_view<D, P, R>(a.tab);
 
-  int64_t t = blockIdx.x;
-  if (t >= a.n_tiles) return;
+  int64_t i = blockIdx.x;
+  if (i >= a.n_items) return;
   if (threadIdx.x == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -374,10 +555,26 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
   }
   __syncthreads();
 
-  auto block_bytes = [&](int64_t tile) { return (uint32_t)(a.meta_off[tile + 1] - a.meta_off[tile]); };
-  // prologue: tile t into buffer 0
-  if (threadIdx.x == 0 && !(a.starve && blockIdx.x == 0))
-    tma_load_block(meta_buf[0], a.meta + a.meta_off[t], block_bytes(t), &mbar[0]);
+  auto item = [&](int64_t k, int& mesh, int64_t& tile) {
+    if (a.items) {
+      const int2 v = a.items[k];
+      mesh = v.x;
+      tile = v.y;
+    } else {
+      mesh = 0;
+      tile = k;
+    }
+  };
+  auto load_block = [&](int64_t k, int buf) {
+    int mesh;
+    int64_t tile;
+    item(k, mesh, tile);
+    const MeshRec& mr = a.meshes ? a.meshes[mesh] : a.one;
+    const uint32_t bytes = (uint32_t)(mr.meta_off[tile + 1] - mr.meta_off[tile]);
+    tma_load_block(meta_buf[buf], mr.meta + mr.meta_off[tile], bytes, &mbar[buf]);
+  };
+  // prologue: item i into buffer 0
+  if (threadIdx.x == 0 && !(a.starve && blockIdx.x == 0)) load_block(i, 0);
   {
     const bool ok = mbar_wait_bounded(&mbar[0], 0, a.wait_ns);
     if (__syncthreads_or(!ok)) {
@@ -385,170 +582,48 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
       return;  // nothing was issued for this barrier, or it never completed within the bound
     }
   }
-  issue_gathers<NA>(a, meta_buf[0], node_buf[0], coef_buf[0], Q, want_coef, REF, ENTB);
+  {
+    int mesh;
+    int64_t tile;
+    item(i, mesh, tile);
+    issue_gathers(a.meshes ? a.meshes[mesh] : a.one, want_coef, meta_buf[0], node_buf[0], coef_buf[0]);
+  }
 
-  for (int it = 0; t < a.n_tiles; t += gridDim.x, ++it) {
+  for (int it = 0; i < a.n_items; i += gridDim.x, ++it) {
     const int b = it & 1, nb = b ^ 1;
-    const int64_t tn = t + gridDim.x;
-    // next tile's metadata block: one bulk copy into the other buffer
-    if (tn < a.n_tiles && threadIdx.x == 0) {
+    const int64_t in = i + gridDim.x;
+    // next item's metadata block: one bulk copy into the other buffer
+    if (in < a.n_items && threadIdx.x == 0) {
       fence_proxy_async();
-      tma_load_block(meta_buf[nb], a.meta + a.meta_off[tn], block_bytes(tn), &mbar[nb]);
+      load_block(in, nb);
     }
     cp_async_wait_all();
     __syncthreads();
 
-    const uint8_t* mb = meta_buf[b];
-    const TileHdr h = *reinterpret_cast<const TileHdr*>(mb);
-    const TileLayout TL = tile_layout(h.nel, h.ns, h.nent, h.nnodes, REF, ENTB);
-    const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
-    const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
-    const uint16_t* t_en = reinterpret_cast<const uint16_t*>(mb + TL.enodes);
-    const uint16_t* t_soff = reinterpret_cast<const uint16_t*>(mb + TL.soff);
-    const EntT* t_sent = reinterpret_cast<const EntT*>(mb + TL.sent);
-    double* xd = node_buf[b];
-
-    // node coordinates -> (hi, lo) float pairs in place (mixed)
-    if constexpr (sizeof(R) == 4) {
-      for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
-        float hi, lo;
-        bool ok = true;
-        split_f64(xd[i], hi, lo, ok);
-        if (!ok) hi = __int_as_float(0x7fc00000);  // out of float range: NaN forces the double path
-        reinterpret_cast<float2*>(xd)[i] = make_float2(hi, lo);
-      }
-      __syncthreads();
-    }
-
-    bool prefetched = false;
     auto prefetch_next = [&]() {
       // all threads: wait for the next block (bounded), then gather its nodes and coefficients
-      if (tn < a.n_tiles) {
+      if (in < a.n_items) {
         const bool ok = mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
         if (__syncthreads_or(!ok)) {
           if (threadIdx.x == 0) *s_flag = 1;
         } else {
-          issue_gathers<NA>(a, meta_buf[nb], node_buf[nb], coef_buf[nb], Q, want_coef, REF, ENTB);
+          int mesh;
+          int64_t tile;
+          item(in, mesh, tile);
+          issue_gathers(a.meshes ? a.meshes[mesh] : a.one, want_coef, meta_buf[nb], node_buf[nb], coef_buf[nb]);
         }
       }
-      prefetched = true;
     };
-
-    // ---- phase 1: a lane pair per element, every element of the tile
-    for (int c0 = 0; c0 < h.nel; c0 += a.chunk) {
-      const int cn = min(a.chunk, h.nel - c0);
-      const int jj = threadIdx.x / kPipeTPE, sub = threadIdx.x % kPipeTPE;
-      const bool active = jj < cn;
-      const int jt = c0 + (active ? jj : 0);
-      const uint16_t* en = t_en + (size_t)jt * REF;
-      const void* cf = coef_buf[b];
-      if (want_coef) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
-      R qual = (R)1;
-      bool bad = false;
-      R* dst = lsm + (size_t)jt * lstride;
-      if constexpr (sizeof(R) == 4) {
-        ElemData<D, NA, P, float> ed;
-        element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
-        element_pair_dispatch<D, NA, P, float>(ed, tb, cf, a.coef_f32, sub, active, dst, a.which, qual, bad);
-      } else {
-        double X[REF][NA];
-#pragma unroll
-        for (int bb = 0; bb < REF; ++bb)
-#pragma unroll
-          for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
-        ElemData<D, NA, P, double> ed;
-        load_element_data<D, NA, P, double>(X, ed);
-        element_pair_dispatch<D, NA, P, double>(ed, tb, cf, a.coef_f32, sub, active, dst, a.which, qual, bad);
-      }
-      const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
-      const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
-      if (active && sub == 0) {
-        if constexpr (sizeof(R) == 4) {
-          flag[jt] = ((D > 1 && q2 < (R)a.qmin) || bad2) ? 1 : 0;
-        } else {
-          const int32_t n0 = t_nodes[en[0]];
-          if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
-        }
-      }
-      if (!prefetched) prefetch_next();
-    }
-    if constexpr (sizeof(R) == 4) {
-      __syncthreads();
-      // rare path: double recomputation of flagged elements from global coordinates
-      for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
-        if (!flag[j]) continue;
-        const uint16_t* en = t_en + (size_t)j * REF;
-        int32_t nd[REF];
-#pragma unroll
-        for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
-        bool bad = false;
-        element_fp64_lean<D, NA, P, float>(a.coords, nd, a.tab, a.coef, a.coef_f32, (int64_t)t_elem[j], a.which,
-                                           lsm + (size_t)j * lstride, U, bad);
-        if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
-          atomicAdd(a.fallback, 1ull);
-          if (bad) atomicOr(a.status, ST_DEGENERATE);
-        }
-      }
-    }
-    if (!prefetched) prefetch_next();
-    __syncthreads();
-
-    // ---- phase 2: runs of slots balanced by contribution count; each slot's
-    // list summed in order (compensated, in registers) and stored
-    {
-      const int per = (h.nent + (int)blockDim.x - 1) / (int)blockDim.x;
-      auto first_slot = [&](int key) {
-        int lo = 0, hi = h.ns;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if ((int)t_soff[mid] < key) lo = mid + 1;
-          else hi = mid;
-        }
-        return lo;
-      };
-      // one binary search per thread; the next thread's start ends the run
-      int* run_start = reinterpret_cast<int*>(flag);  // flags are dead here (all fallbacks done)
-      run_start[threadIdx.x] = first_slot((int)threadIdx.x * per);
-      if (threadIdx.x == 0) run_start[blockDim.x] = h.ns;
-      __syncthreads();
-      const int sb = run_start[threadIdx.x], se = run_start[threadIdx.x + 1];
-      R* o0 = reinterpret_cast<R*>(a.out[0]) + h.s0;
-      R* o1 = nm > 1 ? reinterpret_cast<R*>(a.out[1]) + h.s0 : o0;
-      R* o2 = nm > 2 ? reinterpret_cast<R*>(a.out[2]) + h.s0 : o0;
-      if (sb < se) {
-        // one loop over the run's contributions (lanes stay in step); a slot
-        // is stored when its list ends
-        int s = sb;
-        int k = t_soff[sb];
-        const int kend = t_soff[se];
-        int kslot = t_soff[sb + 1];
-        Acc c0, c1, c2;
-        acc_zero(c0);
-        acc_zero(c1);
-        acc_zero(c2);
-        for (; k < kend; ++k) {
-          const uint32_t ent = t_sent[k];
-          const R* l = lsm + (size_t)(ent >> UB) * lstride + (ent & ((1u << UB) - 1));
-          acc_add(c0, l[0]);
-          if (nm > 1) acc_add(c1, l[U]);
-          if (nm > 2) acc_add(c2, l[2 * U]);
-          if (k + 1 == kslot) {
-            o0[s] = (R)acc_final(c0);
-            if (nm > 1) o1[s] = (R)acc_final(c1);
-            if (nm > 2) o2[s] = (R)acc_final(c2);
-            acc_zero(c0);
-            acc_zero(c1);
-            acc_zero(c2);
-            ++s;
-            if (s < se) kslot = t_soff[s + 1];
-          }
-        }
-      }
-    }
+    int mesh;
+    int64_t tile;
+    item(i, mesh, tile);
+    const MeshRec& mr = a.meshes ? a.meshes[mesh] : a.one;
+    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_buf[b], node_buf[b], coef_buf[b], lsm, flag,
+                                     prefetch_next);
     if (*s_flag) {
       // the next block never arrived: report, wait (bounded) for the copy, stop
       if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
-      if (tn < a.n_tiles) mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
+      if (in < a.n_items) mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
       cp_async_wait_all();
       return;
     }
@@ -557,28 +632,35 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
   cp_async_wait_all();
 }
 
-template <int D, int NA, int P, typename R>
-size_t pipe_smem_bytes(int nm, int S, int chunk, int cap_bytes, int cap_nodes, int cap_nel, int q, int coef_bytes) {
-  return pipe_smem_layout<R>(NA, Ref<D, P>::U, nm, S, chunk, cap_bytes, cap_nodes, cap_nel, q, coef_bytes).total;
-}
-
-template <int D, int NA, int P, typename R>
-lfem_status launch_pipe(const PipeArgs& a, int pos_bytes, int sm_count, cudaStream_t st) {
-  if (a.n_tiles == 0) return LFEM_OK;
-  const int coef_bytes = (a.which & LFEM_CMASS) ? (a.coef_f32 ? 4 : 8) : 0;
+template <typename R, typename EntT, typename... Types>
+lfem_status launch_pipe_types(const PipeArgs& a, int sm_count, cudaStream_t st) {
+  if (a.n_items == 0) return LFEM_OK;
   const size_t smem =
-      pipe_smem_bytes<D, NA, P, R>(a.nm, a.slots_cap, a.chunk, a.cap_bytes, a.cap_nodes, a.cap_nel, a.tab.q, coef_bytes);
+      pipe_smem_layout<R>(3, a.max_u, a.nm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
   if (smem > 227 * 1024) return fail(LFEM_E_TOO_LARGE, "pipelined tile needs more than 227 KB of shared memory");
-  auto kern = pos_bytes == 2 ? k_assemble_pipe<D, NA, P, R, uint16_t> : k_assemble_pipe<D, NA, P, R, uint32_t>;
+  auto kern = k_assemble_pipe<R, EntT, Types...>;
   LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   LFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PipeOcc<R>::THREADS, smem));
   if (per_sm < 1) return fail(LFEM_E_TOO_LARGE, "pipelined kernel does not fit on an SM");
   int64_t grid = (int64_t)per_sm * sm_count;
-  if (grid > a.n_tiles) grid = a.n_tiles;
+  if (grid > a.n_items) grid = a.n_items;
   kern<<<(unsigned)grid, PipeOcc<R>::THREADS, smem, st>>>(a);
   LFEM_CUDA(cudaGetLastError());
   return LFEM_OK;
+}
+
+// Single mesh of type (D, NA, P).
+template <int D, int NA, int P, typename R>
+lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, int sm_count, cudaStream_t st) {
+  using T = EType<D, NA, P>;
+  return ent_bytes == 2 ? launch_pipe_types<R, uint16_t, T>(a, sm_count, st)
+                        : launch_pipe_types<R, uint32_t, T>(a, sm_count, st);
+}
+
+template <typename R>
+size_t pipe_smem_bytes(const PipeArgs& a) {
+  return pipe_smem_layout<R>(3, a.max_u, a.nm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
 }
 
 }  // namespace lfem

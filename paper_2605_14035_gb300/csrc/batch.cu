@@ -1,0 +1,224 @@
+// Batched assembly: one persistent launch over the row tiles of many meshes
+// (the batchwise processing of Sec. 3.3, Remark "Batch computations", done as
+// a single work list on the GPU), optionally captured once into a CUDA graph
+// and replayed.
+#include <algorithm>
+#include <vector>
+
+#include "dispatch.cuh"
+
+namespace lfem {
+
+template <typename EntT>
+static lfem_status launch_batch(const PipeArgs& a, int sms, cudaStream_t st) {
+  return launch_pipe_types<float, EntT, EType<1, 2, 1>, EType<1, 2, 2>, EType<2, 2, 1>, EType<2, 2, 2>,
+                           EType<2, 3, 1>, EType<2, 3, 2>>(a, sms, st);
+}
+
+static bool batch_type_ok(int d, int na) { return (d == 1 && na == 2) || (d == 2 && (na == 2 || na == 3)); }
+
+lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset) {
+  LFEM_CUDA(cudaMemcpyToSymbol(c_bank, src, bytes, offset, cudaMemcpyHostToDevice));
+  return LFEM_OK;
+}
+
+}  // namespace lfem
+
+using namespace lfem;
+
+struct lfem_batch_s {
+  int device = 0;
+  PipeArgs args{};
+  MeshRec* d_meshes = nullptr;
+  int2* d_items = nullptr;
+  int32_t* d_status = nullptr;  // [0] status bits, [2..3] fallback count
+  int ent_bytes = 2;
+  int64_t n_elements = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
+  int sms = 0;
+  LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  LFEM_CUDA(cudaMemsetAsync(b->d_status + 2, 0, sizeof(unsigned long long), st));
+  return b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, sms, st) : launch_batch<uint32_t>(b->args, sms, st);
+}
+
+extern "C" {
+
+lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigned which, int coef_is_fp32,
+                              void* cuda_stream, lfem_batch_t* out) {
+  if (!out || !items || n_items <= 0) return fail(LFEM_E_ARG, "batch arguments");
+  *out = nullptr;
+  if (which == 0 || (which & ~7u)) return fail(LFEM_E_ARG, "which");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::vector<MeshRec> recs(n_items);
+  std::vector<int2> work;
+  int cap_bytes = 0, cap_nodes = 0, cap_nel = 0, max_u = 0, max_q = 0, ent_bytes = 2;
+  int64_t n_el = 0;
+  int nm = 0;
+  for (unsigned bit = 1; bit <= 4; bit <<= 1) nm += (which & bit) ? 1 : 0;
+  for (int i = 0; i < n_items; ++i) {
+    const lfem_batch_item& it = items[i];
+    lfem_pattern_s* p = it.pattern;
+    if (!p) return fail(LFEM_E_ARG, "batch item without pattern");
+    if (!supported(p->dim, it.ambient, p->order) || !batch_type_ok(p->dim, it.ambient))
+      return fail(LFEM_E_UNSUPPORTED, "element type not supported in batches");
+    if ((which & LFEM_MASS) && !it.M) return fail(LFEM_E_ARG, "batch item M is NULL");
+    if ((which & LFEM_STIFF) && !it.A) return fail(LFEM_E_ARG, "batch item A is NULL");
+    if ((which & LFEM_CMASS) && (!it.MC || !it.coef)) return fail(LFEM_E_ARG, "batch item MC or coef is NULL");
+    if (p->n_elem > 0 && !it.coords) return fail(LFEM_E_ARG, "batch item coords is NULL");
+    ent_bytes = std::max(ent_bytes, p->ent_bytes);
+  }
+  // all blocks of a batch are read with one entry width: widen where needed
+  for (int i = 0; i < n_items; ++i) {
+    lfem_pattern_s* p = items[i].pattern;
+    if (p->ent_bytes != ent_bytes) {
+      p->min_ent_bytes = ent_bytes;
+      lfem_status s = build_tiles(p, p->tile_slots, st);
+      if (s != LFEM_OK) return s;
+    }
+  }
+  for (int i = 0; i < n_items; ++i) {
+    const lfem_batch_item& it = items[i];
+    lfem_pattern_s* p = it.pattern;
+    TabRef tab;
+    lfem_status s = get_tables(p->dim, p->order, it.quad, st, &tab);
+    if (s != LFEM_OK) return s;
+    MeshRec& r = recs[i];
+    r.coords = it.coords;
+    r.coef = it.coef;
+    r.meta = p->d.tile_meta;
+    r.meta_off = p->d.tile_meta_off;
+    int m = 0;
+    if (which & LFEM_MASS) r.out[m++] = it.M;
+    if (which & LFEM_STIFF) r.out[m++] = it.A;
+    if (which & LFEM_CMASS) r.out[m++] = it.MC;
+    r.tab = tab;
+    r.type = elem_type_id(p->dim, it.ambient, p->order);
+    r.na = it.ambient;
+    r.ref = p->ref;
+    r.entb = p->ent_bytes;
+    r.coef_f32 = coef_is_fp32 ? 1 : 0;
+    cap_bytes = std::max(cap_bytes, p->max_tile_bytes);
+    cap_nodes = std::max(cap_nodes, p->max_tile_nodes);
+    cap_nel = std::max(cap_nel, p->max_tile_nel);
+    max_u = std::max(max_u, n_upper(p->ref));
+    max_q = std::max(max_q, tab.q);
+    n_el += p->tile_elems_total;
+    for (int64_t t = 0; t < p->n_tiles; ++t) work.push_back(make_int2(i, (int)t));
+  }
+  lfem_batch_s* b = new lfem_batch_s();
+  cudaGetDevice(&b->device);
+  b->ent_bytes = ent_bytes;
+  b->n_elements = n_el;
+  auto cleanup = [&]() {
+    if (b->d_meshes) cudaFree(b->d_meshes);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_status) cudaFree(b->d_status);
+    delete b;
+  };
+  if (cudaMalloc(&b->d_meshes, sizeof(MeshRec) * n_items) != cudaSuccess ||
+      cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, work.size())) != cudaSuccess ||
+      cudaMalloc(&b->d_status, 4 * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(LFEM_E_NOMEM, "batch allocation failed");
+  }
+  cudaMemcpyAsync(b->d_meshes, recs.data(), sizeof(MeshRec) * n_items, cudaMemcpyHostToDevice, st);
+  if (!work.empty()) cudaMemcpyAsync(b->d_items, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(b->d_status, 0, 4 * sizeof(int32_t), st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "batch upload");
+  }
+  PipeArgs& a = b->args;
+  a.meshes = b->d_meshes;
+  a.items = b->d_items;
+  a.n_items = (int64_t)work.size();
+  a.nm = nm;
+  a.which = which;
+  a.chunk = PipeOcc<float>::THREADS / kPipeTPE;
+  a.cap_bytes = cap_bytes;
+  a.cap_nodes = cap_nodes;
+  a.cap_nel = cap_nel;
+  a.max_u = max_u;
+  a.max_q = max_q;
+  a.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
+  a.qmin = 0.25f;
+  a.status = b->d_status;
+  a.fallback = reinterpret_cast<unsigned long long*>(b->d_status + 2);
+  a.starve = 0;
+  a.wait_ns = 2000000000ll;
+  const size_t smem = pipe_smem_bytes<float>(a);
+  if (smem > 227 * 1024) {
+    cleanup();
+    return fail(LFEM_E_TOO_LARGE, "largest tile of the batch needs more than 227 KB of shared memory");
+  }
+  *out = b;
+  return LFEM_OK;
+}
+
+lfem_status lfem_batch_assemble(lfem_batch_t b, void* cuda_stream) {
+  if (!b) return fail(LFEM_E_ARG, "batch is NULL");
+  return batch_launch(b, (cudaStream_t)cuda_stream);
+}
+
+lfem_status lfem_batch_graph_launch(lfem_batch_t b, void* cuda_stream) {
+  if (!b) return fail(LFEM_E_ARG, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!b->exec) {
+    if (!st) return fail(LFEM_E_ARG, "graph capture needs a non-default stream");
+    LFEM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    lfem_status s = batch_launch(b, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != LFEM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    b->graph = g;
+  }
+  LFEM_CUDA(cudaGraphLaunch(b->exec, st));
+  return LFEM_OK;
+}
+
+lfem_status lfem_batch_sync_status(lfem_batch_t b, void* cuda_stream) {
+  if (!b) return fail(LFEM_E_ARG, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int32_t h = 0;
+  LFEM_CUDA(cudaMemcpyAsync(&h, b->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  LFEM_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), st));
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (h & ST_TIMEOUT) return fail(LFEM_E_TIMEOUT, "a bounded device wait ran out");
+  if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
+  return LFEM_OK;
+}
+
+lfem_status lfem_batch_info(lfem_batch_t b, int64_t* n_work_items, int64_t* n_elements, int32_t* cap_elements) {
+  if (!b) return fail(LFEM_E_ARG, "batch is NULL");
+  if (n_work_items) *n_work_items = b->args.n_items;
+  if (n_elements) *n_elements = b->n_elements;
+  if (cap_elements) *cap_elements = b->args.cap_nel;
+  return LFEM_OK;
+}
+
+void lfem_batch_destroy(lfem_batch_t b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_meshes) cudaFree(b->d_meshes);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_status) cudaFree(b->d_status);
+  delete b;
+}
+
+}  // extern "C"

@@ -11,14 +11,13 @@ namespace lfem {
   lfem_status run_stage_d##DD(int NA, int P, int kind, const StageArgs& s, cudaStream_t st);                     \
   lfem_status run_adjoint_d##DD(int NA, int P, const AdjArgs& a, int64_t T, int pos_bytes, cudaStream_t st);     \
   lfem_status bank_upload_d##DD(const void* src, size_t bytes, size_t offset);                                 \
-  lfem_status run_pipe_d##DD(int NA, int P, bool mixed, const PipeArgs& a, int pos_bytes, int sms,              \
-                             cudaStream_t st);                                                                    \
-  size_t pipe_smem_d##DD(int NA, int P, bool mixed, int nm, int S, int chunk, int cap_bytes, int cap_nodes,       \
-                         int cap_nel, int q, int coef_bytes);
+  lfem_status run_pipe_d##DD(int NA, int P, bool mixed, const PipeArgs& a, int ent_bytes, int sms,              \
+                             cudaStream_t st);
 
 LFEM_DECLARE_DIM(1)
 LFEM_DECLARE_DIM(2)
 LFEM_DECLARE_DIM(3)
+lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset);
 
 // Body of one dimension's dispatch functions over (NA, P).
 #define LFEM_DEFINE_CASE_STAGE(DD, NN, PP) \
@@ -28,11 +27,7 @@ LFEM_DECLARE_DIM(3)
 
 #define LFEM_DEFINE_CASE_PIPE(DD, NN, PP)                                                          \
   if (NA == NN && P == PP)                                                                         \
-    return mixed ? launch_pipe<DD, NN, PP, float>(a, pos_bytes, sms, st)                           \
-                 : launch_pipe<DD, NN, PP, double>(a, pos_bytes, sms, st);
-#define LFEM_DEFINE_CASE_PIPE_SMEM(DD, NN, PP)                                                               \
-  if (NA == NN && P == PP)                                                                                   \
-    return mixed ? pipe_smem_bytes<DD, NN, PP, float>(nm, S, chunk, cap_bytes, cap_nodes, cap_nel, q, coef_bytes) \
-                 : pipe_smem_bytes<DD, NN, PP, double>(nm, S, chunk, cap_bytes, cap_nodes, cap_nel, q, coef_bytes);
+    return mixed ? launch_pipe<DD, NN, PP, float>(a, ent_bytes, sms, st)                           \
+                 : launch_pipe<DD, NN, PP, double>(a, ent_bytes, sms, st);
 
 }  // namespace lfem

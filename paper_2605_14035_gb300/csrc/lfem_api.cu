@@ -1,6 +1,9 @@
 // C ABI of the library: argument checks, reference tables, dispatch.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <mutex>
 #include <string>
@@ -124,7 +127,7 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
   std::vector<unsigned char> blob(b64 + b32, 0);
   memcpy(blob.data(), t64.data(), b64);
   memcpy(blob.data() + b64, t32.data(), t32.size() * sizeof(float));
-  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3}) {
+  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch}) {
     lfem_status us = up(blob.data(), blob.size(), used);
     if (us != LFEM_OK) return us;
   }
@@ -154,12 +157,6 @@ static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& 
   if (dim == 1) return run_pipe_d1(NA, P, mixed, a, pb, sms, st);
   if (dim == 2) return run_pipe_d2(NA, P, mixed, a, pb, sms, st);
   return run_pipe_d3(NA, P, mixed, a, pb, sms, st);
-}
-static size_t pipe_smem(int dim, int NA, int P, bool mixed, int nm, int S, int chunk, int cb, int cn, int ce, int q,
-                        int coefb) {
-  if (dim == 1) return pipe_smem_d1(NA, P, mixed, nm, S, chunk, cb, cn, ce, q, coefb);
-  if (dim == 2) return pipe_smem_d2(NA, P, mixed, nm, S, chunk, cb, cn, ce, q, coefb);
-  return pipe_smem_d3(NA, P, mixed, nm, S, chunk, cb, cn, ce, q, coefb);
 }
 
 static void destroy_dev(PatternDev& d) {
@@ -319,35 +316,39 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   a.qmin = 0.25f;
   a.status = p->d.status;
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
-  // persistent pipelined kernel: a lane pair per element, so 192 (float) or
-  // 128 (double) elements per phase-1 round (fewer only if shared memory runs out)
+  // persistent pipelined kernel: a lane pair per element, so 96 (float) or
+  // 128 (double) elements per phase-1 round; all of a tile's local matrices
+  // stay in shared memory
   PipeArgs pa{};
-  pa.coords = coords;
-  pa.coef = coef;
-  pa.coef_f32 = a.coef_f32;
-  pa.meta = p->d.tile_meta;
-  pa.meta_off = p->d.tile_meta_off;
-  pa.n_tiles = p->n_tiles;
-  for (int m = 0; m < 3; ++m) pa.out[m] = a.out[m];
+  MeshRec& mr = pa.one;
+  mr.coords = coords;
+  mr.coef = coef;
+  mr.meta = p->d.tile_meta;
+  mr.meta_off = p->d.tile_meta_off;
+  for (int m = 0; m < 3; ++m) mr.out[m] = a.out[m];
+  mr.tab = tab;
+  mr.type = elem_type_id(p->dim, ambient, p->order);
+  mr.na = ambient;
+  mr.ref = p->ref;
+  mr.entb = p->ent_bytes;
+  mr.coef_f32 = a.coef_f32;
+  pa.meshes = nullptr;
+  pa.items = nullptr;
+  pa.n_items = p->n_tiles;
   pa.nm = nm;
   pa.which = which;
-  pa.tab = tab;
-  pa.slots_cap = p->tile_slots;
+  pa.chunk = (mixed ? PipeOcc<float>::THREADS : PipeOcc<double>::THREADS) / kPipeTPE;
   pa.cap_bytes = p->max_tile_bytes;
   pa.cap_nodes = p->max_tile_nodes;
   pa.cap_nel = p->max_tile_nel;
+  pa.max_u = n_upper(p->ref);
+  pa.max_q = tab.q;
+  pa.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
   pa.qmin = a.qmin;
   pa.status = p->d.status;
   pa.fallback = a.fallback;
   pa.starve = p->debug_starve;
   pa.wait_ns = 2000000000ll;  // 2 s bound on every mbarrier wait
-  const int coefb = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
-  int chunk = (mixed ? PipeOcc<float>::THREADS : PipeOcc<double>::THREADS) / kPipeTPE;
-  if (p->chunk && p->chunk < chunk) chunk = p->chunk;
-  while (chunk > 8 && pipe_smem(p->dim, ambient, p->order, mixed, nm, p->tile_slots, chunk, pa.cap_bytes,
-                                pa.cap_nodes, pa.cap_nel, tab.q, coefb) > 227 * 1024)
-    chunk /= 2;
-  pa.chunk = chunk;
   int sms = 0;
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
@@ -453,4 +454,76 @@ lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64
   return LFEM_OK;
 }
 
+static std::string tune_key(lfem_pattern_t p, int ambient, const lfem_quad* quad, lfem_precision prec, unsigned which) {
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) name = prop.name;
+  for (auto& c : name)
+    if (c == ' ') c = '_';
+  int bucket = 0;
+  for (int64_t n = p->n_elem; n > 1; n >>= 1) ++bucket;
+  std::ostringstream k;
+  k << "d" << p->dim << "_n" << ambient << "_p" << p->order << "_q" << quad->n_pts << "_prec" << (int)prec << "_w"
+    << which << "_e2^" << bucket << "_" << name;
+  return k.str();
+}
+
+lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad, const void* coef,
+                          int coef_is_fp32, unsigned which, lfem_precision prec, void* M, void* A, void* MC,
+                          const char* cache_path, void* cuda_stream, int32_t* best_slots) {
+  if (!p || !quad) return fail(LFEM_E_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const std::string key = tune_key(p, ambient, quad, prec, which);
+  int best = 0;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string k;
+    int v;
+    while (in >> k >> v)
+      if (k == key) best = v;
+  }
+  if (!best) {
+    const int cand[] = {512, 1024, 1536, 2048, 3072, 4096, 6144, 8192};
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    LFEM_CUDA(cudaEventCreate(&e0));
+    LFEM_CUDA(cudaEventCreate(&e1));
+    for (int c : cand) {
+      if (c < p->max_row) continue;
+      if (build_tiles(p, c, st) != LFEM_OK) continue;
+      // one warm-up; configurations whose shared memory does not fit are skipped
+      if (lfem_assemble(p, coords, ambient, quad, coef, coef_is_fp32, which, prec, M, A, MC, st) != LFEM_OK) continue;
+      LFEM_CUDA(cudaEventRecord(e0, st));
+      const int reps = 3;
+      for (int r = 0; r < reps; ++r) {
+        lfem_status s = lfem_assemble(p, coords, ambient, quad, coef, coef_is_fp32, which, prec, M, A, MC, st);
+        if (s != LFEM_OK) return s;
+      }
+      LFEM_CUDA(cudaEventRecord(e1, st));
+      LFEM_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best) return fail(LFEM_E_TOO_LARGE, "no tile capacity fits this configuration");
+    if (cache_path) {
+      std::ofstream out(cache_path, std::ios::app);
+      out << key << " " << best << "\n";
+    }
+  }
+  if (p->tile_slots != best) {
+    lfem_status s = build_tiles(p, best, st);
+    if (s != LFEM_OK) return s;
+  }
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (best_slots) *best_slots = best;
+  return LFEM_OK;
+}
+
 }  // extern "C"
+

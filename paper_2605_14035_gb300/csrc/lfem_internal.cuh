@@ -427,6 +427,7 @@ struct lfem_pattern_s {
   int64_t tile_elems_total = 0;
   int32_t max_tile_nel = 0, max_tile_nodes = 0, max_tile_bytes = 0;
   int ent_bytes = 2;     // 2 or 4: contribution entry width in the tile blocks
+  int min_ent_bytes = 2; // batches may ask for the wider entries
   int debug_starve = 0;  // test knob: the first CTA skips its first metadata copy (bounded wait runs out)
   int32_t chunk = 0;    // elements per chunk (0 = default)
   int32_t threads = 0;  // threads per block (0 = default)

@@ -560,7 +560,7 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   int32_t mnel = 0;
   for (int64_t t = 0; t < T; ++t) mnel = std::max(mnel, hep[t + 1] - hep[t]);
   const int UB = ub_bits(ref * (ref + 1) / 2);
-  const int entb = ((int64_t)mnel << UB) <= 65536 ? 2 : 4;
+  const int entb = std::max(((int64_t)mnel << UB) <= 65536 ? 2 : 4, p->min_ent_bytes);
   int32_t *tmp_nodes = nullptr, *nn = nullptr;
   int64_t *bytes = nullptr, *scr = nullptr, *mx = nullptr;
   TRY(dalloc(&tmp_nodes, p->tile_elems_total * ref));

@@ -27,7 +27,9 @@ EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
     "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
-    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait",
+    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
+    "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
+    "lfem_batch_info", "lfem_batch_destroy",
 )
 
 
@@ -39,6 +41,12 @@ class LfemError(RuntimeError):
 
 class _Quad(ctypes.Structure):
     _fields_ = [("n_pts", ctypes.c_int), ("xi", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("pattern", ctypes.c_void_p), ("coords", ctypes.c_void_p), ("ambient", ctypes.c_int),
+                ("quad", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("M", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("MC", ctypes.c_void_p)]
 
 
 def _load():
@@ -62,6 +70,12 @@ def _load():
         "lfem_mixed_fallback_count": [P, P, P],
         "lfem_pattern_csr_noalloc": [P, L, ctypes.c_int32, I, I, P, P, L, P, P],
         "lfem_debug_starve_wait": [P, I],
+        "lfem_autotune": [P, P, I, P, P, I, U, I, P, P, P, ctypes.c_char_p, P, P],
+        "lfem_batch_create": [P, I, U, I, P, P],
+        "lfem_batch_assemble": [P, P],
+        "lfem_batch_graph_launch": [P, P],
+        "lfem_batch_sync_status": [P, P],
+        "lfem_batch_info": [P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -69,6 +83,8 @@ def _load():
         f.restype = ctypes.c_int
     lib.lfem_pattern_destroy.argtypes = [P]
     lib.lfem_pattern_destroy.restype = None
+    lib.lfem_batch_destroy.argtypes = [P]
+    lib.lfem_batch_destroy.restype = None
     lib.lfem_last_error.restype = ctypes.c_char_p
     lib.lfem_status_string.restype = ctypes.c_char_p
     lib.lfem_status_string.argtypes = [I]
@@ -213,6 +229,84 @@ def assemble(pat: Pattern, coords: torch.Tensor, rule, coef: Optional[torch.Tens
                               int(which), int(precision), _ptr(out.get("M")), _ptr(out.get("A")),
                               _ptr(out.get("MC")), _stream(stream)))
     return {k: v[: pat.nnz] for k, v in out.items()}
+
+
+def autotune(pat: Pattern, coords: torch.Tensor, rule, coef=None, which: int = MASS | STIFF,
+             precision: int = FP64, cache_path: Optional[str] = None, stream=None) -> int:
+    """lfem_autotune: pick and apply the fastest tile capacity; returns it."""
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    dt = torch.float64 if precision == FP64 else torch.float32
+    bufs = {k: (torch.empty(max(pat.nnz, 1), dtype=dt, device=coords.device) if which & bit else None)
+            for k, bit in (("M", MASS), ("A", STIFF), ("MC", CMASS))}
+    best = ctypes.c_int32()
+    coef_f32 = int(coef is not None and coef.dtype == torch.float32)
+    _check(_lib.lfem_autotune(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref, _ptr(coef), coef_f32,
+                              int(which), int(precision), _ptr(bufs["M"]), _ptr(bufs["A"]), _ptr(bufs["MC"]),
+                              None if cache_path is None else cache_path.encode(), _stream(stream),
+                              ctypes.byref(best)))
+    return int(best.value)
+
+
+class Batch:
+    """Many meshes assembled by one persistent launch (lfem_batch_*), mixed precision.
+
+    meshes: list of dicts with keys pattern, coords, rule and optionally coef.
+    Outputs are allocated here (float [nnz] per requested matrix) and stay fixed,
+    so the launch can be captured once as a CUDA graph and replayed while the
+    coordinates change in place."""
+
+    def __init__(self, meshes, which: int = MASS | STIFF, stream=None):
+        self.which = int(which)
+        self.meshes = []
+        items = (_BatchItem * len(meshes))()
+        coef_f32 = 1
+        for i, m in enumerate(meshes):
+            pat, coords, rule = m["pattern"], _dev_f64(m["coords"], "coords"), as_rule(m["rule"])
+            coef = m.get("coef")
+            if coef is not None:
+                coef_f32 = int(coef.dtype == torch.float32)
+            outs = {k: (torch.empty(max(pat.nnz, 1), dtype=torch.float32, device=coords.device) if which & bit
+                        else None) for k, bit in (("M", MASS), ("A", STIFF), ("MC", CMASS))}
+            self.meshes.append({"pattern": pat, "coords": coords, "rule": rule, "coef": coef, "out": outs})
+            it = items[i]
+            it.pattern = pat.handle.value
+            it.coords = coords.data_ptr()
+            it.ambient = int(coords.shape[1])
+            it.quad = ctypes.addressof(rule._c)
+            it.coef = None if coef is None else coef.data_ptr()
+            it.M = None if outs["M"] is None else outs["M"].data_ptr()
+            it.A = None if outs["A"] is None else outs["A"].data_ptr()
+            it.MC = None if outs["MC"] is None else outs["MC"].data_ptr()
+        self._items = items
+        h = ctypes.c_void_p()
+        _check(_lib.lfem_batch_create(items, len(meshes), self.which, coef_f32, _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def assemble(self, stream=None):
+        _check(_lib.lfem_batch_assemble(self._h, _stream(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(_lib.lfem_batch_graph_launch(self._h, _stream(stream)))
+
+    def sync_status(self, stream=None):
+        _check(_lib.lfem_batch_sync_status(self._h, _stream(stream)))
+
+    def info(self):
+        n, e, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.lfem_batch_info(self._h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(c)))
+        return {"work_items": n.value, "elements_computed": e.value, "cap_elements": c.value}
+
+    def outputs(self, i):
+        m = self.meshes[i]
+        nnz = m["pattern"].nnz
+        return {k: v[:nnz] for k, v in m["out"].items() if v is not None}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.lfem_batch_destroy(h)
+            self._h = ctypes.c_void_p()
 
 
 def assemble_adjoint(pat: Pattern, coords: torch.Tensor, rule, coef=None, gM=None, gA=None, gMC=None,
