@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-elems", type=int, default=0, help="elements in the oracle sample (0 = auto)")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default): P2 perturbed sphere; c1 P1 sphere; c3 P2 tets + boundary; "
+                         "c4 512-mesh batch; c5 evolving ellipsoid + adjoint")
+    ap.add_argument("--batch-meshes", type=int, default=512)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -160,6 +166,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        import bench_extra
+
+        return bench_extra.run(args)
 
     import torch
 
@@ -186,6 +196,9 @@ def main():
     coef32 = coef64.float()
     del pts
     nnz = pat.nnz
+    tuned = None
+    if not args.no_autotune:
+        tuned = lfem.autotune(pat, xd, rule, coef32, which=7, precision=lfem.MIXED)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -300,10 +313,11 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": nE, "nodes": N, "nnz_per_matrix": nnz, "matrices": "M,A,MC",
                    "precision": "mixed", "quadrature": "tri 7-point degree 5", "l2": "flushed between steps",
-                   "tile_slots": info["tile_slots"], "tiles": info["tiles"], "recompute": info["recompute"],
+                   "tile_slots": info["tile_slots"], "autotuned": tuned is not None, "tiles": info["tiles"],
+                   "recompute": info["recompute"],
                    "fp64_fallback_elements": fallback, "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_assemble_tiles<2,3,2,float>", "algorithmic_bytes": alg_bytes,
+                     "traffic": None, "kernel": "k_assemble_pipe<float,u16,(2,3,2)>", "algorithmic_bytes": alg_bytes,
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": {"value": world * nE * k_e2e / (tot_e2e * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,

@@ -1,0 +1,267 @@
+"""Further workloads of bench.py (--workload c1 | c3 | c4 | c5).
+
+c1  P1 icosphere, 5 refinements (20,480 triangles): FP64 mass + stiffness,
+    3-point rule; launch-bound, so also the same assembly replayed from a CUDA
+    graph (one-mesh batch, mixed precision).
+c3  P2 Kuhn cube 64^3 (1,572,864 ten-node tets, jittered) mass + stiffness with
+    the 14-point rule, plus the boundary surface mass on its 49,152 P2
+    triangles; FP64 and mixed.
+c4  512 meshes of uneven size (P2 curves, P1/P2 disks, P2 spheres; about 77 M
+    elements), mass + stiffness, mixed precision, one persistent launch per
+    batch replayed from a CUDA graph, tile capacity picked by timing; against
+    the plain FP64 path mesh by mesh.
+c5  evolving P2 ellipsoid (327,680 triangles): 100 steps of reassembly of M(x),
+    A(x) (graph replay) with nodes moved along the discrete normal flow, then
+    the adjoint of L = u^T M u + v^T A v through the autograd function.
+Each prints one JSON line.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+import bench
+
+
+def _line(args, workload, value, unit, ms, extra):
+    d = {"metric": "elements/s", "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": extra.pop("dtype", "f32+f64"), "data": "synthetic",
+         "config": {"workload": workload, **extra.pop("config", {})}}
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def _timer(torch, flush):
+    def timed(fn, steps, warmup, stream=None):
+        st = stream or torch.cuda.current_stream()
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            if flush is not None:
+                flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            ms.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ms) / steps
+
+    return timed
+
+
+def run_c1(args):
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+    x, e = meshes.icosphere(5, 1)
+    rule = quadrature.tri_3pt_deg2()
+    xd, ed = torch.from_numpy(x).cuda(), torch.from_numpy(e).cuda()
+    pat = lfem.Pattern(ed, x.shape[0], 2, 1)
+    timed = _timer(torch, None)
+    out = {k: torch.empty(pat.nnz, dtype=torch.float64, device="cuda") for k in ("M", "A")}
+    ms64 = timed(lambda: lfem.assemble(pat, xd, rule, which=3, precision=lfem.FP64, out=out), args.steps * 10, 10)
+    batch = lfem.Batch([{"pattern": pat, "coords": xd, "rule": rule}], which=3)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ms_graph = timed(lambda: batch.graph_launch(s), args.steps * 10, 10, stream=s)
+    batch.sync_status(s)
+    area = float(out["M"].sum())
+    _line(args, "p1_icosphere_r5_M_A", x.shape[0] and e.shape[0] / (ms64 * 1e-3), "elements/s", ms64,
+          {"dtype": "f64", "config": {"elements": int(e.shape[0]), "nnz_per_matrix": pat.nnz, "l2": "resident"},
+           "mixed_graph": {"value": e.shape[0] / (ms_graph * 1e-3), "ms_per_step": ms_graph},
+           "area_minus_4pi": area - 4 * np.pi})
+
+
+def run_c3(args):
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+    x, e = meshes.kuhn_cube_p2(64)
+    b = meshes.boundary_faces_p2(e)
+    r_tet, r_tri = quadrature.tet_14pt_deg5(), quadrature.tri_7pt_deg5()
+    xd, ed, bd = torch.from_numpy(x).cuda(), torch.from_numpy(e).cuda(), torch.from_numpy(b).cuda()
+    pt = lfem.Pattern(ed, x.shape[0], 3, 2)
+    pb = lfem.Pattern(bd, x.shape[0], 2, 2)
+    flush = torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    timed = _timer(torch, flush)
+    res = {}
+    for prec, dt, name in ((lfem.MIXED, torch.float32, "mixed"), (lfem.FP64, torch.float64, "fp64")):
+        if not args.no_autotune:
+            lfem.autotune(pt, xd, r_tet, which=3, precision=prec)
+        ot = {k: torch.empty(pt.nnz, dtype=dt, device="cuda") for k in ("M", "A")}
+        ob = {"M": torch.empty(pb.nnz, dtype=dt, device="cuda")}
+
+        def step():
+            lfem.assemble(pt, xd, r_tet, which=3, precision=prec, out=ot)
+            lfem.assemble(pb, xd, r_tri, which=1, precision=prec, out=ob)
+
+        ms = timed(step, args.steps, args.warmup)
+        res[name] = {"ms_per_step": ms, "value": (e.shape[0] + b.shape[0]) / (ms * 1e-3),
+                     "volume": float(ot["M"].double().sum()), "boundary_area": float(ob["M"].double().sum()),
+                     "tile_slots": pt.info()["tile_slots"]}
+        pt.sync_status()
+    alg = e.shape[0] * 40 + x.shape[0] * 24 + 2 * pt.nnz * 4 + b.shape[0] * 24 + pb.nnz * 4
+    peak, kind = bench.measured_peaks()
+    ach = alg / (res["mixed"]["ms_per_step"] * 1e-3) / 1e9
+    _line(args, "p2_kuhn_cube_64_tets_M_A_plus_boundary_M", res["mixed"]["value"], "elements/s",
+          res["mixed"]["ms_per_step"],
+          {"config": {"tets": int(e.shape[0]), "boundary_triangles": int(b.shape[0]), "nnz_tets": pt.nnz,
+                      "l2": "flushed between steps"},
+           "fp64": res["fp64"], "mixed": res["mixed"],
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "algorithmic_bytes": alg, "peak_kind": kind}})
+
+
+def _gen_batch(n_meshes, scale):
+    """Generate the batch in a spawn process pool (no GPU is touched before)."""
+    import multiprocessing as mp
+
+    from paper_2605_14035_gb300.inputs import meshes
+
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.starmap(meshes.batch_item, [(i, n_meshes, scale) for i in range(n_meshes)])
+
+
+def run_c4(args):
+    t0 = time.time()
+    items = _gen_batch(args.batch_meshes, args.batch_scale)
+    t_gen = time.time() - t0
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import quadrature
+
+    rules = {1: quadrature.gauss_interval(3), (2, 1): quadrature.tri_3pt_deg2(), (2, 2): quadrature.tri_7pt_deg5()}
+    t0 = time.time()
+    mesh_list = []
+    n_el = 0
+    alg = 0
+    for fam, x, e, d, p in items:
+        xd, ed = torch.from_numpy(x).cuda(), torch.from_numpy(e).cuda()
+        pat = lfem.Pattern(ed, x.shape[0], d, p)
+        rule = rules[1] if d == 1 else rules[(d, p)]
+        mesh_list.append({"pattern": pat, "coords": xd, "rule": rule, "conn": ed})
+        n_el += e.shape[0]
+        alg += e.nbytes + x.nbytes + 2 * pat.nnz * 4
+    t_pat = time.time() - t0
+    s = torch.cuda.Stream()
+    timed = _timer(torch, torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda"))
+    best = None
+    for slots in ((2048, 3072) if not args.no_autotune else (2048,)):
+        for m in mesh_list:
+            m["pattern"].retile(slots)
+        batch = lfem.Batch([{k: m[k] for k in ("pattern", "coords", "rule")} for m in mesh_list], which=3)
+        with torch.cuda.stream(s):
+            ms = timed(lambda: batch.graph_launch(s), args.steps, args.warmup, stream=s)
+        batch.sync_status(s)
+        if best is None or ms < best[0]:
+            best = (ms, slots, batch.info())
+        del batch
+    ms, slots, binfo = best
+    # plain FP64 path, mesh by mesh (same matrices)
+    for m in mesh_list:
+        m["pattern"].retile(2048)
+    outs = [{k: torch.empty(m["pattern"].nnz, dtype=torch.float64, device="cuda") for k in ("M", "A")}
+            for m in mesh_list]
+
+    def fp64_all():
+        for m, o in zip(mesh_list, outs):
+            lfem.assemble(m["pattern"], m["coords"], m["rule"], which=3, precision=lfem.FP64, out=o)
+
+    ms64 = timed(fp64_all, max(2, args.steps // 4), 1)
+    peak, kind = bench.measured_peaks()
+    ach = alg / (ms * 1e-3) / 1e9
+    _line(args, "batch_512_meshes_M_A", n_el / (ms * 1e-3), "elements/s", ms,
+          {"config": {"meshes": len(mesh_list), "elements": int(n_el), "tile_slots": slots,
+                      "work_items": binfo["work_items"], "l2": "flushed between steps",
+                      "generation_s": round(t_gen, 1), "pattern_build_s": round(t_pat, 1)},
+           "fp64_plain_per_mesh": {"value": n_el / (ms64 * 1e-3), "ms_per_step": ms64},
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "algorithmic_bytes": int(alg), "peak_kind": kind}})
+
+
+def run_c5(args):
+    import torch
+
+    import oracle
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+    x, e = meshes.ellipsoid(7)
+    rule = quadrature.tri_7pt_deg5()
+    N = x.shape[0]
+    xd, ed = torch.from_numpy(x).cuda(), torch.from_numpy(e).cuda()
+    pat = lfem.Pattern(ed, N, 2, 2)
+    rp, ci = pat.csr()
+    crow = rp
+    col = ci.long()
+    tau, steps = 1e-6, 100
+    s = torch.cuda.Stream()
+    batch = lfem.Batch([{"pattern": pat, "coords": xd, "rule": rule}], which=3)
+    ev = []
+    with torch.cuda.stream(s):
+        for k in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            batch.graph_launch(s)
+            b.record(s)
+            ev.append((a, b))
+            out = batch.outputs(0)
+            A = torch.sparse_csr_tensor(crow, col, out["A"].double(), size=(N, N))
+            Mabs = torch.sparse_csr_tensor(crow, col, out["M"].double().abs(), size=(N, N))
+            Dm = Mabs @ torch.ones(N, dtype=torch.float64, device="cuda")
+            xd.sub_(tau * (A @ xd) / Dm[:, None])
+    torch.cuda.synchronize()
+    batch.sync_status(s)
+    ms_step = sum(a.elapsed_time(b) for a, b in ev[5:]) / (steps - 5)
+    o32 = {k: torch.empty(pat.nnz, dtype=torch.float32, device="cuda") for k in ("M", "A")}
+    lfem.assemble(pat, xd, rule, which=3, precision=lfem.MIXED, out=o32)
+    fallback = pat.fallback_count()
+    # plain FP64 reassembly of the final surface for comparison
+    timed = _timer(torch, None)
+    o64 = {k: torch.empty(pat.nnz, dtype=torch.float64, device="cuda") for k in ("M", "A")}
+    ms64 = timed(lambda: lfem.assemble(pat, xd, rule, which=3, precision=lfem.FP64, out=o64), 20, 3)
+    # adjoint of L = u^T M u + v^T A v through the autograd function
+    rng = np.random.default_rng(20260519)
+    u = torch.from_numpy(rng.normal(size=N)).cuda()
+    v = torch.from_numpy(rng.normal(size=N)).cuda()
+    rows = torch.repeat_interleave(torch.arange(N, device="cuda"), rp[1:] - rp[:-1])
+    xt = xd.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        xt.grad = None
+        M, A, _ = lfem.AssembleFn.apply(xt, None, pat, rule)
+        L = (M * u[rows] * u[col]).sum() + (A * v[rows] * v[col]).sum()
+        L.backward()
+        return L
+
+    ms_adj = timed(fwd_bwd, 10, 2)
+    L = fwd_bwd()
+    torch.cuda.synchronize()
+    xh = xt.detach().cpu().numpy()
+    un, vn, rr, cn = u.cpu().numpy(), v.cpu().numpy(), rows.cpu().numpy(), ci.cpu().numpy()
+    t0 = time.perf_counter()
+    ogx, _ = oracle.adjoint(xh, e, 2, 2, rule.xi, rule.w, None, (rp.cpu().numpy(), cn), un[rr] * un[cn],
+                            vn[rr] * vn[cn], None)
+    t_orc = time.perf_counter() - t0
+    gerr = float(np.abs(xt.grad.cpu().numpy() - ogx).max() / np.abs(ogx).max())
+    _line(args, "evolving_ellipsoid_r7_100_steps_plus_adjoint", e.shape[0] / (ms_step * 1e-3), "elements/s",
+          ms_step,
+          {"config": {"elements": int(e.shape[0]), "steps": steps, "tau": tau, "precision": "mixed, graph replay"},
+           "fp64_assembly_ms": ms64, "adjoint_fwd_bwd_ms": ms_adj, "fp64_fallback_elements_final": fallback,
+           "adjoint_vs_oracle_max_rel": gerr, "oracle_adjoint_s": t_orc, "L": float(L)})
+
+
+def run(args):
+    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)

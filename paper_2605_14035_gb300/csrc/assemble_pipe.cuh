@@ -76,6 +76,7 @@ struct PipeArgs {
   int cap_nodes;   // most nodes in a tile
   int cap_nel;     // most elements in a tile
   int max_u;       // largest local upper triangle among the meshes
+  int64_t cap_lsm; // largest nel * nm * U over the meshes (local-matrix words)
   int max_q;       // most quadrature points among the meshes
   int coef_bytes;  // 4 or 8 if the weighted mass is requested, else 0
   float qmin;
@@ -90,8 +91,8 @@ struct PipeSmem {
 };
 
 template <typename R>
-__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int u, int nm, int cap_bytes, int cap_nodes, int cap_nel,
-                                                     int q, int coef_bytes) {
+__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, int cap_bytes, int cap_nodes,
+                                                     int cap_nel, int q, int coef_bytes) {
   auto al = [](size_t b) { return (b + 127) / 128 * 128; };
   PipeSmem L;
   size_t o = 0;
@@ -110,7 +111,7 @@ __host__ __device__ inline PipeSmem pipe_smem_layout(int na, int u, int nm, int 
   L.coef1 = o;
   o += al((size_t)cap_nel * q * coef_bytes);
   L.lsm = o;
-  o += al(sizeof(R) * (size_t)cap_nel * nm * u);
+  o += al(sizeof(R) * (size_t)cap_lsm);
   L.flag = o;  // element flags in phase 1, run starts (<= 1025 ints) in phase 2
   o += al(cap_nel > 4100 ? (size_t)cap_nel : (size_t)4100);
   L.total = o;
@@ -327,14 +328,9 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   const bool wm = which & LFEM_MASS, wa = which & LFEM_STIFF, wc = which & LFEM_CMASS;
   const int im = 0, ia = wm ? 1 : 0, ic = (wm ? 1 : 0) + (wa ? 1 : 0);
   if constexpr (D == 3) {
-    if (wm || wc) {
-      if (wm && wc)
-        element_pair<D, NA, P, R, true, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
-      else if (wm)
-        element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
-      else
-        element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
-    }
+    // one matrix per pass: 55 accumulators at most
+    if (wm) element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    if (wc) element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
     if (wa) element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
   } else {
     if (wm && wa && wc)
@@ -536,7 +532,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const bool want_coef = a.coef_bytes != 0;
   const PipeSmem L =
-      pipe_smem_layout<R>(3, a.max_u, a.nm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes);
+      pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
   int* s_flag = reinterpret_cast<int*>(smem_raw + L.mbar + 64);
   uint8_t* meta_buf[2] = {smem_raw + L.meta0, smem_raw + L.meta1};
@@ -636,7 +632,7 @@ template <typename R, typename EntT, typename... Types>
 lfem_status launch_pipe_types(const PipeArgs& a, int sm_count, cudaStream_t st) {
   if (a.n_items == 0) return LFEM_OK;
   const size_t smem =
-      pipe_smem_layout<R>(3, a.max_u, a.nm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
+      pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
   if (smem > 227 * 1024) return fail(LFEM_E_TOO_LARGE, "pipelined tile needs more than 227 KB of shared memory");
   auto kern = k_assemble_pipe<R, EntT, Types...>;
   LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -660,7 +656,7 @@ lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, int sm_count, cudaStre
 
 template <typename R>
 size_t pipe_smem_bytes(const PipeArgs& a) {
-  return pipe_smem_layout<R>(3, a.max_u, a.nm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
+  return pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
 }
 
 }  // namespace lfem

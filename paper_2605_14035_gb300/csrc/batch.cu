@@ -56,6 +56,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigne
   std::vector<MeshRec> recs(n_items);
   std::vector<int2> work;
   int cap_bytes = 0, cap_nodes = 0, cap_nel = 0, max_u = 0, max_q = 0, ent_bytes = 2;
+  int64_t cap_lsm = 0;
   int64_t n_el = 0;
   int nm = 0;
   for (unsigned bit = 1; bit <= 4; bit <<= 1) nm += (which & bit) ? 1 : 0;
@@ -105,6 +106,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigne
     cap_nodes = std::max(cap_nodes, p->max_tile_nodes);
     cap_nel = std::max(cap_nel, p->max_tile_nel);
     max_u = std::max(max_u, n_upper(p->ref));
+    cap_lsm = std::max(cap_lsm, (int64_t)p->max_tile_nel * nm * n_upper(p->ref));
     max_q = std::max(max_q, tab.q);
     n_el += p->tile_elems_total;
     for (int64_t t = 0; t < p->n_tiles; ++t) work.push_back(make_int2(i, (int)t));
@@ -145,6 +147,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigne
   a.cap_nodes = cap_nodes;
   a.cap_nel = cap_nel;
   a.max_u = max_u;
+  a.cap_lsm = cap_lsm;
   a.max_q = max_q;
   a.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
   a.qmin = 0.25f;

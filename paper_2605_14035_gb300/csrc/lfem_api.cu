@@ -342,6 +342,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   pa.cap_nodes = p->max_tile_nodes;
   pa.cap_nel = p->max_tile_nel;
   pa.max_u = n_upper(p->ref);
+  pa.cap_lsm = (int64_t)p->max_tile_nel * nm * n_upper(p->ref);
   pa.max_q = tab.q;
   pa.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
   pa.qmin = a.qmin;

@@ -339,3 +339,35 @@ def half_disk_p2():
     )
     conn = np.array([[1, 2, 3, 4, 5, 6], [2, 7, 3, 8, 9, 5]], dtype=np.int32) - 1
     return coords, conn
+
+
+def batch_item(i: int, n_meshes: int = 512, scale: float = 1.0, seed: int = BASE_SEED + 4):
+    """Mesh i of the uneven batch: family i mod 3 = closed P2 curve
+    (1k..200k segments), planar hexagonal disk (5k..500k triangles, P1 and P2
+    alternating), P2 perturbed geodesic sphere (20k..1.31M triangles); sizes
+    log-uniform, drawn from a generator seeded by (seed, i) so every item can be
+    built on its own; `scale` shrinks every size.  Returns
+    (family, coords, conn, dim, order)."""
+    del n_meshes
+    rng = np.random.default_rng([seed, i])
+    u = rng.random()
+    fam = i % 3
+    if fam == 0:
+        n = int(round(np.exp(np.log(1e3) + u * (np.log(2e5) - np.log(1e3))) * scale))
+        x, e = closed_curve_p2(max(n, 8), seed=seed * 1000 + i)
+        return "curve_p2", x, e, 1, 2
+    if fam == 1:
+        t = np.exp(np.log(5e3) + u * (np.log(5e5) - np.log(5e3))) * scale
+        f = max(2, int(round((t / 6.0) ** 0.5)))
+        order = 2 if (i // 3) % 2 == 0 else 1
+        x, e = hex_disk(f, order)
+        return f"disk_p{order}", x, e, 2, order
+    t = np.exp(np.log(2e4) + u * (np.log(1.31e6) - np.log(2e4))) * scale
+    f = max(2, int(round((t / 20.0) ** 0.5)))
+    x, e = geodesic_sphere(f, 2)
+    return "sphere_p2", x, e, 2, 2
+
+
+def batch_workload(n_meshes: int = 512, scale: float = 1.0, seed: int = BASE_SEED + 4):
+    """The whole uneven batch (see batch_item)."""
+    return [batch_item(i, n_meshes, scale, seed) for i in range(n_meshes)]
