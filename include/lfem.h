@@ -130,6 +130,21 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
  * per block); 0 keeps the current value.  Used by the autotuner. */
 lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t threads);
 
+/* Conditioning threshold of LFEM_MIXED (the precision split of the method's
+ * FP32 geometry, with FP64 kept for thin elements).  An element of dimension
+ * d = 2, 3 is redone in double when, at some quadrature point, its metric
+ * G = J^T J may have condition number above kappa_max.  The test needs no
+ * eigenvalues: with q = det G / (tr G / d)^d, q >= 4 k / (1 + k)^2 implies
+ * cond(G) <= k for d = 2 (equality) and d = 3 (the bound is reached when the
+ * middle eigenvalue is the mean of the outer two), so elements with q below
+ * that bound are redone; the test is conservative for d = 3.  Curves have a
+ * scalar metric and are redone only for the degenerate / non-finite checks,
+ * which apply for every kappa_max.  kappa_max >= 1 (INFINITY: never for
+ * conditioning); default 64 (q = 256/4225).  A batch uses the
+ * strictest threshold of its patterns, read when it is created.
+ * LFEM_E_ARG for kappa_max < 1 or NaN. */
+lfem_status lfem_set_mixed_kappa(lfem_pattern_t p, double kappa_max);
+
 /* Autotuner: times lfem_assemble (CUDA events, after one warm-up) for each
  * candidate tile capacity (slots per tile: 512..8192, those whose shared
  * memory fits), keeps the fastest and retiles p with it.  M/A/MC are scratch

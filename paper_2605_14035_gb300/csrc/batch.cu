@@ -150,7 +150,8 @@ lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigne
   a.cap_lsm = cap_lsm;
   a.max_q = max_q;
   a.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
-  a.qmin = 0.25f;
+  a.qmin = 0.0f;
+  for (int i = 0; i < n_items; ++i) a.qmin = std::max(a.qmin, items[i].pattern->qmin);
   a.status = b->d_status;
   a.fallback = reinterpret_cast<unsigned long long*>(b->d_status + 2);
   a.starve = 0;

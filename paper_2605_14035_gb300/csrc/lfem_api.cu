@@ -161,7 +161,8 @@ static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& 
 
 static void destroy_dev(PatternDev& d) {
   void* ptrs[] = {d.conn,      d.row_ptr,       d.col_idx,   d.inc_ptr,   d.inc_key, d.inc_pos,    d.elem_inc,
-                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off};
+                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off,
+                  d.slot_off,  d.slot_ent,      d.elem_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = PatternDev{};
@@ -271,6 +272,14 @@ lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t t
   return LFEM_OK;
 }
 
+lfem_status lfem_set_mixed_kappa(lfem_pattern_t p, double kappa_max) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (!(kappa_max >= 1.0)) return fail(LFEM_E_ARG, "kappa_max must be >= 1");
+  // q = 4 k / (1 + k)^2, the largest metric quality of a metric with condition number k
+  p->qmin = std::isinf(kappa_max) ? 0.0f : (float)(4.0 * kappa_max / ((1.0 + kappa_max) * (1.0 + kappa_max)));
+  return LFEM_OK;
+}
+
 lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   p->debug_starve = starve ? 1 : 0;
@@ -313,9 +322,44 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   a.nm = nm;
   a.tab = tab;
   a.slots_cap = p->tile_slots;
-  a.qmin = 0.25f;
+  a.qmin = p->qmin;
   a.status = p->d.status;
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
+  if (p->dim == 3) {
+    // bulk tets: element-major two passes (local-matrix buffer owned by the pattern)
+    const size_t need = (size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8);
+    if (need > p->d.elem_buf_bytes) {
+      if (p->d.elem_buf) cudaFree(p->d.elem_buf);
+      p->d.elem_buf = nullptr;
+      p->d.elem_buf_bytes = 0;
+      if (cudaMalloc(&p->d.elem_buf, need ? need : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LFEM_E_NOMEM, "element buffer allocation failed");
+      }
+      p->d.elem_buf_bytes = need;
+    }
+    TwoPassArgs ta{};
+    ta.conn = p->d.conn;
+    ta.coords = coords;
+    ta.coef = coef;
+    ta.coef_f32 = a.coef_f32;
+    ta.n_elem = p->n_elem;
+    ta.nnz = p->nnz;
+    ta.slot_off = p->d.slot_off;
+    ta.slot_ent = p->d.slot_ent;
+    ta.lbuf = p->d.elem_buf;
+    for (int m = 0; m < 3; ++m) ta.out[m] = a.out[m];
+    ta.nm = nm;
+    ta.which = which;
+    ta.tab = tab;
+    ta.qmin = a.qmin;
+    ta.status = p->d.status;
+    ta.fallback = a.fallback;
+    int sms3 = 0;
+    LFEM_CUDA(cudaDeviceGetAttribute(&sms3, cudaDevAttrMultiProcessorCount, p->device));
+    if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
+    return run_twopass_d3(p->order, mixed, ta, sms3, st);
+  }
   // persistent pipelined kernel: a lane pair per element, so 96 (float) or
   // 128 (double) elements per phase-1 round; all of a tile's local matrices
   // stay in shared memory

@@ -407,6 +407,10 @@ struct PatternDev {
   int32_t* tile_elem = nullptr;  // [sum] ascending element ids per tile
   uint16_t* inc_local = nullptr; // [nInc] (index of e in its tile's list) << 4 | a
   int32_t* status = nullptr;     // [4]: status bits, pad, fallback count (int64 at [2])
+  int32_t* slot_off = nullptr;   // [nnz+1] element-major path: start of each slot's contributions
+  int32_t* slot_ent = nullptr;   // [nInc*ref] e * U + u, per slot in ascending (e, a, b)
+  void* elem_buf = nullptr;      // element-major path: local matrices [nE][nm][U] (scratch)
+  size_t elem_buf_bytes = 0;
   uint8_t* tile_meta = nullptr;  // per-tile metadata blocks (see TileHdr)
   int64_t* tile_meta_off = nullptr;  // [T+1] byte offsets, multiples of 16
 };
@@ -431,6 +435,9 @@ struct lfem_pattern_s {
   int debug_starve = 0;  // test knob: the first CTA skips its first metadata copy (bounded wait runs out)
   int32_t chunk = 0;    // elements per chunk (0 = default)
   int32_t threads = 0;  // threads per block (0 = default)
+  // LFEM_MIXED: metric quality below which an element is redone in double;
+  // 4k/(1+k)^2 at k = 64, the largest quality of a metric with cond(G) = 64
+  float qmin = 256.0f / 4225.0f;
   lfem::PatternDev d;
 };
 

@@ -300,6 +300,36 @@ __global__ void k_positions(const int32_t* __restrict__ conn, int ref, const int
   }
 }
 
+// Element-major contribution lists: for every CSR slot, the (element, upper
+// index) pairs that add into it, in ascending (e, a, b) order; a row's lists
+// are contiguous (ref entries per incidence of the row).
+template <typename PosT>
+__global__ void k_slot_lists(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_key,
+                             const PosT* __restrict__ inc_pos, const int64_t* __restrict__ row_ptr, int32_t n_nodes,
+                             int ref, int32_t* __restrict__ slot_off, int32_t* __restrict__ slot_ent) {
+  const int U = ref * (ref + 1) / 2;
+  const int ps = pos_stride(ref);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_nodes; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t kb = inc_ptr[r], ke = inc_ptr[r + 1];
+    const int64_t s0 = row_ptr[r];
+    const int len = (int)(row_ptr[r + 1] - s0);
+    int32_t run = kb * ref;
+    for (int j = 0; j < len; ++j) {
+      slot_off[s0 + j] = run;
+      for (int32_t k = kb; k < ke; ++k) {
+        const int32_t key = inc_key[k];
+        const int32_t e = key >> 4;
+        const int a = key & 15;
+        for (int b = 0; b < ref; ++b) {
+          if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
+          const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
+          slot_ent[run++] = e * U + u;
+        }
+      }
+    }
+  }
+}
+
 // Per-tile element lists: sort + unique the elements of the tile's incidences;
 // local index of every incidence; count.
 __global__ void k_tile_elements(const int32_t* __restrict__ tile_row0, const int32_t* __restrict__ inc_ptr,
@@ -761,6 +791,24 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   }
   LFEM_CUDA(cudaGetLastError());
   TRY(dalloc(&d.inc_local, n_inc));
+  if (p->dim == 3) {
+    // bulk tets: element-major path (row tiles would recompute most elements several times)
+    if (n_inc * ref >= INT32_MAX || p->n_elem * n_upper(ref) >= INT32_MAX)
+      return fail(LFEM_E_TOO_LARGE, "too many contributions for the element-major path");
+    TRY(dalloc(&d.slot_off, nnz + 1));
+    TRY(dalloc(&d.slot_ent, n_inc * ref));
+    if (N > 0) {
+      if (p->pos_bytes == 1)
+        k_slot_lists<uint8_t><<<grid_for(N, 128), 128, 0, st>>>(d.inc_ptr, d.inc_key, d.inc_pos, d.row_ptr, N, ref,
+                                                                 d.slot_off, d.slot_ent);
+      else
+        k_slot_lists<uint16_t><<<grid_for(N, 128), 128, 0, st>>>(d.inc_ptr, d.inc_key, (const uint16_t*)d.inc_pos,
+                                                                  d.row_ptr, N, ref, d.slot_off, d.slot_ent);
+      LFEM_CUDA(cudaGetLastError());
+    }
+    const int32_t tot = (int32_t)(n_inc * ref);
+    LFEM_CUDA(cudaMemcpyAsync(d.slot_off + nnz, &tot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  }
   LFEM_CUDA(cudaStreamSynchronize(st));
   cudaFree(raw);
   cudaFree(deg);

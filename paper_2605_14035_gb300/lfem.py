@@ -25,7 +25,7 @@ STATUS = {0: "LFEM_OK", 1: "LFEM_E_ARG", 2: "LFEM_E_INDEX", 3: "LFEM_E_UNSUPPORT
 # Every entry point declared in include/lfem.h.
 EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
-    "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_assemble_adjoint", "lfem_eval_points",
+    "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_set_mixed_kappa", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
     "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
@@ -62,6 +62,7 @@ def _load():
         "lfem_pattern_retile": [P, ctypes.c_int32, P],
         "lfem_assemble": [P, P, I, P, P, I, U, I, P, P, P, P],
         "lfem_set_launch": [P, ctypes.c_int32, ctypes.c_int32],
+        "lfem_set_mixed_kappa": [P, ctypes.c_double],
         "lfem_assemble_adjoint": [P, P, I, P, P, P, P, P, P, P, P],
         "lfem_eval_points": [P, L, I, I, P, I, P, P, P],
         "lfem_geometry": [P, L, I, I, P, I, P, P, P, P, P],
@@ -191,6 +192,10 @@ class Pattern:
 
     def set_launch(self, elems_per_chunk: int = 0, threads: int = 0):
         _check(_lib.lfem_set_launch(self._h, int(elems_per_chunk), int(threads)))
+
+    def set_mixed_kappa(self, kappa_max: float):
+        """LFEM_MIXED redoes in double the elements whose metric may have cond(G) > kappa_max."""
+        _check(_lib.lfem_set_mixed_kappa(self._h, float(kappa_max)))
 
     def debug_starve_wait(self, starve: bool):
         _check(_lib.lfem_debug_starve_wait(self._h, int(bool(starve))))

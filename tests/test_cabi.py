@@ -53,3 +53,5 @@ def test_host_side_errors_without_gpu(libpath):
     assert lib.lfem_status_string(7) == b"degenerate element"
     lib.lfem_assemble.restype = ctypes.c_int
     assert lib.lfem_assemble(None, None, 3, None, None, 0, 1, 0, None, None, None, None) == 1
+    lib.lfem_set_mixed_kappa.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    assert lib.lfem_set_mixed_kappa(None, 2.0) == 1

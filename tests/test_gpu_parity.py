@@ -77,6 +77,26 @@ def test_mixed_values(name, lfem):
     assert abs(out["M"].double().sum().item() - M.sum()) <= MIXED_TOL * abs(M.sum())
 
 
+@pytest.mark.parametrize("name", ["perturbed_sphere_p2", "cube_p2", "cube_p1"])
+def test_mixed_conditioning_threshold(name, lfem):
+    """kappa_max = 1 sends every element (metric quality < 1) to the double
+    recomputation, INFINITY sends none (no degenerate element here); both
+    stay within the mixed tolerance."""
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    orp, oci, M, A, C = oracle.assemble(x, e, d, p, rule.xi, rule.w, coef)
+    xd, cd = to_dev(x), to_dev(coef).float()
+    for kappa, n_fb in ((1.0, e.shape[0]), (float("inf"), 0)):
+        pat.set_mixed_kappa(kappa)
+        out = lfem.assemble(pat, xd, rule, cd, which=7, precision=lfem.MIXED)
+        assert pat.fallback_count() == n_fb
+        for k, ref in (("M", M), ("A", A), ("MC", C)):
+            err = diag_scaled_error(out[k].double().cpu().numpy(), ref, orp, oci)
+            assert err <= MIXED_TOL, (kappa, k, err)
+    pat.sync_status()
+    with pytest.raises(lfem.LfemError):
+        pat.set_mixed_kappa(0.5)
+
+
 @pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p1"])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_deterministic_and_tile_independent(name, prec, lfem):
