@@ -116,6 +116,44 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
 
 
+def dist_init(backend):
+    """One process per GPU (torchrun env); replicas: no collective on the data path,
+    only the barrier and the max over ranks of the timed region."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world <= 1:
+        return None, 1, 0, 0
+    import torch
+    import torch.distributed as dist
+
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return dist, world, rank, local
+
+
+def rank_barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(ms, dist, device):
+    """Timed-region length of the job: the slowest rank's."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, steps, tot_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / (tot_ms * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -206,15 +244,7 @@ def main():
 
     from paper_2605_14035_gb300 import lfem
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    dist, world, rank, local = dist_init("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
 
     x, e, rule = make_inputs(args.level)
@@ -234,8 +264,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        rank_barrier(dist)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -254,12 +283,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
-        tot = sum(ms)
-        if dist is not None:
-            t = torch.tensor([tot], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot, ms
+        return max_over_ranks(sum(ms), dist, dev), ms
 
     out_mixed = {k: torch.empty(nnz, dtype=torch.float32, device=dev) for k in ("M", "A", "MC")}
     out_fp64 = {k: torch.empty(nnz, dtype=torch.float64, device=dev) for k in ("M", "A", "MC")}
@@ -282,7 +306,7 @@ def main():
     clocks = clk.summary()
     fallback = pat.fallback_count()
     pat.sync_status()
-    value = world * nE * args.steps / (tot_ms * 1e-3)
+    value = job_value(world, nE, args.steps, tot_ms)
 
     res = {}
     if not args.skip_fp64:
