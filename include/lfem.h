@@ -238,7 +238,8 @@ lfem_status lfem_local(const int32_t* conn, int64_t n_elem, int dim, int order, 
  * of pattern p (LFEM_OK, LFEM_E_DEGENERATE, LFEM_E_INDEX), and reports how
  * many elements the last LFEM_MIXED assembly redid in double.
  */
-lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream);  /* also LFEM_E_TIMEOUT */
+lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream);  /* also LFEM_E_TIMEOUT, and
+  LFEM_E_UNSUPPORTED if a tile met a kernel without a variant for its element type */
 lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64_t* n_fp64_elements);
 
 const char* lfem_last_error(void);

@@ -15,7 +15,8 @@ lfem_status run_adjoint_d3(int NA, int P, const AdjArgs& a, int64_t T, int pos_b
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }
 
-lfem_status run_pipe_d3(int NA, int P, bool mixed, const PipeArgs& a, int ent_bytes, int sms, cudaStream_t st) {
+lfem_status run_pipe_d3(int NA, int P, bool mixed, const PipeArgs& a, int ent_bytes, bool fast, const FastBank& fb,
+                        int sms, cudaStream_t st) {
   LFEM_DEFINE_CASE_PIPE(3, 3, 1)
   LFEM_DEFINE_CASE_PIPE(3, 3, 2)
   return fail(LFEM_E_UNSUPPORTED, "element type");

@@ -1,0 +1,201 @@
+// Element kernels with the quadrature fixed at compile time.
+//
+// For the usual rules (curves: 3 Gauss points; triangles: 3 points for P1,
+// 7 points for P2; tetrahedra: 4 points for P1, 14 points for P2) the whole
+// quadrature loop is unrolled and every reference quantity is a compile-time
+// offset into a table that travels as a kernel parameter (constant bank), so
+// the FP32 multiply-adds read it as an immediate operand: no table loads.
+// The tables fold the weight into the basis products (Eqs.
+// reference_quadrature_mass, reference_quadrature_stiffness):
+//   TM[q][u]     = w_q phi_a(xi_q) phi_b(xi_q)                     (u = (a <= b))
+//   TA[q][kk][u] = w_q (d_m phi_a d_n phi_b + d_n phi_a d_m phi_b)  (kk = (m < n))
+//                  w_q  d_m phi_a d_m phi_b                         (kk = (m = n))
+//   DPSI[q][k][m] = d_m (4 l_i l_j)(xi_q)   (edge bubbles, hierarchical Jacobian)
+// so that, with Hh = adj(G) / s (Sec. 3.2, the cofactor form of s G^{-1}),
+//   M_u  += s TM,   MC_u += s c_q TM,   A_u += sum_kk Hh_kk TA[kk].
+#pragma once
+
+#include "lfem_internal.cuh"
+
+namespace lfem {
+
+// Quadrature sizes of the compile-time rules.
+template <int D, int P>
+struct FastQ {
+  static constexpr int Q = D == 1 ? 3 : (D == 2 ? (P == 1 ? 3 : 7) : (P == 1 ? 4 : 14));
+};
+
+template <int D, int P>
+struct FastLayout {
+  static constexpr int Q = FastQ<D, P>::Q;
+  static constexpr int U = Ref<D, P>::U;
+  static constexpr int NE = Ref<D, P>::NE;
+  static constexpr int NK = D * (D + 1) / 2;
+  static constexpr int PER_Q = NE * D + U + NK * U;
+  static constexpr int SIZE = Q * PER_Q;
+  static constexpr int dpsi(int q, int k, int m) { return q * PER_Q + k * D + m; }
+  static constexpr int tm(int q, int u) { return q * PER_Q + NE * D + u; }
+  static constexpr int ta(int q, int kk, int u) { return q * PER_Q + NE * D + U + kk * U + u; }
+};
+
+// One table per (D, P) of curves and triangles, at fixed offsets.
+struct FastBank {
+  static constexpr int OFF11 = 0;
+  static constexpr int OFF12 = OFF11 + FastLayout<1, 1>::SIZE;
+  static constexpr int OFF21 = OFF12 + FastLayout<1, 2>::SIZE;
+  static constexpr int OFF22 = OFF21 + FastLayout<2, 1>::SIZE;
+  static constexpr int SIZE = OFF22 + FastLayout<2, 2>::SIZE;
+  template <int D, int P>
+  static constexpr int off() {
+    return D == 1 ? (P == 1 ? OFF11 : OFF12) : (P == 1 ? OFF21 : OFF22);
+  }
+  float v[SIZE];
+};
+
+// Tetrahedra (P1, P2).
+struct FastBankTet {
+  static constexpr int OFF31 = 0;
+  static constexpr int OFF32 = OFF31 + FastLayout<3, 1>::SIZE;
+  static constexpr int SIZE = OFF32 + FastLayout<3, 2>::SIZE;
+  template <int D, int P>
+  static constexpr int off() {
+    return P == 1 ? OFF31 : OFF32;
+  }
+  float v[SIZE];
+};
+
+// Host: the table of (dim, order) for rule quad into dst (FastLayout order);
+// false if the rule's size is not the compile-time one.
+bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst);
+
+// a b - c d with one explicit rounding order (the same in every kernel that
+// inlines it: implicit multiply-add contraction may differ between contexts)
+__device__ __forceinline__ float dif_prod(float a, float b, float c, float d) { return fmaf(a, b, -__fmul_rn(c, d)); }
+
+// Geometry of one element at every point of the compile-time rule: s_q and
+// Hh_q = adj(G_q) / s_q (the weight sits in the tables).  keep = false when
+// some point fails the conditioning / finiteness test (the element is then
+// redone in double by the caller).
+template <int D, int NA, int P, typename Bank>
+__device__ __forceinline__ void geometry_fast(const ElemData<D, NA, P, float>& ed, const Bank& bank, float qthr,
+                                              float (&sq)[FastLayout<D, P>::Q],
+                                              float (&hq)[FastLayout<D, P>::Q][FastLayout<D, P>::NK], bool& keep) {
+  using L = FastLayout<D, P>;
+  constexpr int NE = L::NE, Q = L::Q;
+  constexpr int OFF = Bank::template off<D, P>();
+  const float* tv = bank.v;
+  const float lim = fmaxf(qthr, 1e-12f);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float J[NA][D];
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        float acc = ed.e[m][i];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) acc = fmaf(ed.dl[k][i], tv[OFF + L::dpsi(q, k, m)], acc);
+        J[i][m] = acc;
+      }
+    if constexpr (D == 1) {
+      float tt = 0.f;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) tt = fmaf(J[i][0], J[i][0], tt);
+      const float inv = rsqrtf(tt);
+      sq[q] = tt * inv;
+      hq[q][0] = inv;
+      keep &= (tt > 0.f) & (tt <= 3.0e38f);
+    } else if constexpr (D == 2) {
+      float g11 = 0.f, g12 = 0.f, g22 = 0.f;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        g11 = fmaf(J[i][0], J[i][0], g11);
+        g12 = fmaf(J[i][0], J[i][1], g12);
+        g22 = fmaf(J[i][1], J[i][1], g22);
+      }
+      float s2, inv;
+      if constexpr (NA == 2) {
+        const float det = dif_prod(J[0][0], J[1][1], J[0][1], J[1][0]);
+        sq[q] = fabsf(det);
+        s2 = __fmul_rn(det, det);
+        inv = __fdividef(1.0f, sq[q]);
+      } else {
+        const float n0 = dif_prod(J[1][0], J[2][1], J[2][0], J[1][1]);
+        const float n1 = dif_prod(J[2][0], J[0][1], J[0][0], J[2][1]);
+        const float n2 = dif_prod(J[0][0], J[1][1], J[1][0], J[0][1]);
+        s2 = fmaf(n2, n2, fmaf(n1, n1, __fmul_rn(n0, n0)));
+        inv = rsqrtf(s2);
+        sq[q] = s2 * inv;
+      }
+      hq[q][0] = g22 * inv;
+      hq[q][1] = -g12 * inv;
+      hq[q][2] = g11 * inv;
+      // metric quality det G / (tr G / 2)^2 against the threshold, without a division
+      const float tr = 0.5f * (g11 + g22);
+      keep &= (s2 > lim * (tr * tr)) & (s2 <= 3.0e38f);
+    } else {
+      float c[3][3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+        c[m][0] = dif_prod(J[1][m1], J[2][m2], J[2][m1], J[1][m2]);
+        c[m][1] = dif_prod(J[2][m1], J[0][m2], J[0][m1], J[2][m2]);
+        c[m][2] = dif_prod(J[0][m1], J[1][m2], J[1][m1], J[0][m2]);
+      }
+      const float det = fmaf(J[2][0], c[0][2], fmaf(J[1][0], c[0][1], __fmul_rn(J[0][0], c[0][0])));
+      sq[q] = fabsf(det);
+      const float inv = __fdividef(1.0f, sq[q]);
+      int kk = 0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = m; n < 3; ++n)
+          hq[q][kk++] = __fmul_rn(fmaf(c[m][2], c[n][2], fmaf(c[m][1], c[n][1], __fmul_rn(c[m][0], c[n][0]))), inv);
+      float tr = 0.f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) tr = fmaf(J[i][m], J[i][m], tr);
+      tr *= (1.0f / 3.0f);
+      const float s2 = __fmul_rn(det, det);
+      keep &= (s2 > lim * (tr * tr * tr)) & (s2 <= 3.0e38f);
+    }
+  }
+}
+
+// Mass-type matrix from per-point factors f_q (s_q, or s_q c_q):
+// V_u = sum_q f_q TM[q][u], written to dst[u].
+template <int D, int P, typename Bank>
+__device__ __forceinline__ void contract_mass(const Bank& bank, const float (&f)[FastLayout<D, P>::Q], float* dst) {
+  using L = FastLayout<D, P>;
+  constexpr int OFF = Bank::template off<D, P>();
+  const float* tv = bank.v;
+#pragma unroll
+  for (int u = 0; u < L::U; ++u) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) acc = fmaf(f[q], tv[OFF + L::tm(q, u)], acc);
+    dst[u] = acc;
+  }
+}
+
+// Stiffness: A_u = sum_q sum_kk Hh_q,kk TA[q][kk][u], written to dst[u].
+template <int D, int P, typename Bank>
+__device__ __forceinline__ void contract_stiff(const Bank& bank,
+                                               const float (&hq)[FastLayout<D, P>::Q][FastLayout<D, P>::NK],
+                                               float* dst) {
+  using L = FastLayout<D, P>;
+  constexpr int OFF = Bank::template off<D, P>();
+  const float* tv = bank.v;
+#pragma unroll
+  for (int u = 0; u < L::U; ++u) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q)
+#pragma unroll
+      for (int kk = 0; kk < L::NK; ++kk) acc = fmaf(hq[q][kk], tv[OFF + L::ta(q, kk, u)], acc);
+    dst[u] = acc;
+  }
+}
+
+}  // namespace lfem

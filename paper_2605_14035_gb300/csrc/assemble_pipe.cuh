@@ -27,6 +27,7 @@
 // returns, leaving the context usable.
 #pragma once
 
+#include "assemble_fast.cuh"
 #include "assemble_impl.cuh"
 
 namespace lfem {
@@ -61,6 +62,7 @@ struct MeshRec {
 };
 
 __host__ __device__ constexpr int elem_type_id(int d, int na, int p) { return d * 100 + na * 10 + p; }
+constexpr int kFastTypeOffset = 1000;
 
 // Arguments of a persistent launch over work items (mesh, tile).  With one
 // mesh and no item list, item i is tile i of mesh 0.
@@ -249,8 +251,9 @@ __device__ __forceinline__ void element_data_from_pairs(const float2* __restrict
     const int I = edge_i<D>(k), J = edge_j<D>(k), Ed = D + 1 + k;
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      const float dh = (xh[Ed][i] - xh[I][i]) - 0.5f * (xh[J][i] - xh[I][i]);
-      const float dlo = (xl[Ed][i] - xl[I][i]) - 0.5f * (xl[J][i] - xl[I][i]);
+      // explicit multiply-add: one rounding order in every kernel
+      const float dh = fmaf(-0.5f, xh[J][i] - xh[I][i], xh[Ed][i] - xh[I][i]);
+      const float dlo = fmaf(-0.5f, xl[J][i] - xl[I][i], xl[Ed][i] - xl[I][i]);
       ed.dl[k][i] = dh + dlo;
     }
   }
@@ -350,6 +353,29 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   }
 }
 
+// Local matrices of one element with the compile-time rule, stored (upper
+// layout, requested matrices in the order M, A, MC): the geometry of every
+// point first (a few values per point), then each output entry as one
+// contraction with the tables.
+template <int D, int NA, int P, typename Bank>
+__device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, float>& ed, const Bank& bank,
+                                                   const float* cs, const double* cd, float qthr, unsigned which,
+                                                   float* dst, bool& keep) {
+  using L = FastLayout<D, P>;
+  constexpr int U = L::U, Q = L::Q;
+  float sq[Q], hq[Q][L::NK];
+  geometry_fast<D, NA, P>(ed, bank, qthr, sq, hq, keep);
+  int slot = 0;
+  if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + U * slot++);
+  if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + U * slot++);
+  if (which & LFEM_CMASS) {
+    float sc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sc[q] = sq[q] * (cs ? cs[q] : (float)cd[q]);
+    contract_mass<D, P>(bank, sc, dst + U * slot);
+  }
+}
+
 // Shared-memory views of one CTA.
 template <typename R>
 struct TileEnv {
@@ -361,9 +387,10 @@ struct TileEnv {
 // Everything done for one tile whose block, node coordinates and coefficients
 // are in shared memory: split, phase 1 (+ the double fallback), the prefetch
 // hook of the next item after the first phase-1 round, phase 2.
-template <int D, int NA, int P, typename R, typename EntT, typename Prefetch>
+template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
 __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
-                                             const void* coef_s, R* lsm, uint8_t* flag, Prefetch&& prefetch) {
+                                             const void* coef_s, R* lsm, uint8_t* flag, const FastBank& fb,
+                                             Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   constexpr int UB = ub_bits(U);
@@ -394,6 +421,26 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   }
 
   bool prefetched = false;
+  if constexpr (FAST && sizeof(R) == 4) {
+    // ---- phase 1, compile-time rule: one thread per element, every element of the tile
+    for (int c0 = 0; c0 < h.nel; c0 += (int)blockDim.x) {
+      const int jt = c0 + (int)threadIdx.x;
+      if (jt < h.nel) {
+        ElemData<D, NA, P, float> ed;
+        element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), t_en + (size_t)jt * REF, ed);
+        const float* cs = coef_bytes == 4 ? static_cast<const float*>(coef_s) + (size_t)jt * Q : nullptr;
+        const double* cd = coef_bytes == 8 ? static_cast<const double*>(coef_s) + (size_t)jt * Q : nullptr;
+        bool keep = true;
+        element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * lstride,
+                                     keep);
+        flag[jt] = keep ? 0 : 1;
+      }
+      if (!prefetched) {
+        prefetch();
+        prefetched = true;
+      }
+    }
+  } else
   // ---- phase 1: a lane pair per element, every element of the tile
   for (int c0 = 0; c0 < h.nel; c0 += a.chunk) {
     const int cn = min(a.chunk, h.nel - c0);
@@ -508,27 +555,37 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   }
 }
 
-template <int D_, int NA_, int P_>
+// Element type of a launch; the compile-time-rule variant has its own id, so a
+// batch can hold meshes of one type with and without the usual rule.
+template <int D_, int NA_, int P_, bool FAST_ = false>
 struct EType {
   static constexpr int D = D_, NA = NA_, P = P_;
-  static constexpr int id = elem_type_id(D_, NA_, P_);
+  static constexpr bool FAST = FAST_;
+  static constexpr int id = elem_type_id(D_, NA_, P_) + (FAST_ ? kFastTypeOffset : 0);
 };
 
 template <typename R, typename EntT, typename T0, typename... Ts, typename Prefetch>
 __device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* mb,
                                               double* xd, const void* coef_s, R* lsm, uint8_t* flag,
-                                              Prefetch&& prefetch) {
+                                              const FastBank& fb, Prefetch&& prefetch) {
   if (type == T0::id) {
-    process_tile<T0::D, T0::NA, T0::P, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, prefetch);
+    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
   } else {
-    if constexpr (sizeof...(Ts) > 0) dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, prefetch);
+    if constexpr (sizeof...(Ts) > 0) {
+      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
+    } else {
+      // no variant for this tile's type: report it, keep the pipeline's steps
+      if (threadIdx.x == 0) atomicOr(a.status, ST_TYPE);
+      prefetch();
+      __syncthreads();
+    }
   }
 }
 
 // Persistent launch over work items; Types lists the element types the launch
 // may meet (one for a single mesh, several for a batch).
 template <typename R, typename EntT, typename... Types>
-__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k_assemble_pipe(const PipeArgs a) {
+__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k_assemble_pipe(const PipeArgs a, const __grid_constant__ FastBank fb) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const bool want_coef = a.coef_bytes != 0;
   const PipeSmem L =
@@ -614,7 +671,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
     int64_t tile;
     item(i, mesh, tile);
     const MeshRec& mr = a.meshes ? a.meshes[mesh] : a.one;
-    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_buf[b], node_buf[b], coef_buf[b], lsm, flag,
+    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_buf[b], node_buf[b], coef_buf[b], lsm, flag, fb,
                                      prefetch_next);
     if (*s_flag) {
       // the next block never arrived: report, wait (bounded) for the copy, stop
@@ -629,7 +686,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
 }
 
 template <typename R, typename EntT, typename... Types>
-lfem_status launch_pipe_types(const PipeArgs& a, int sm_count, cudaStream_t st) {
+lfem_status launch_pipe_types(const PipeArgs& a, const FastBank& fb, int sm_count, cudaStream_t st) {
   if (a.n_items == 0) return LFEM_OK;
   const size_t smem =
       pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
@@ -641,17 +698,28 @@ lfem_status launch_pipe_types(const PipeArgs& a, int sm_count, cudaStream_t st) 
   if (per_sm < 1) return fail(LFEM_E_TOO_LARGE, "pipelined kernel does not fit on an SM");
   int64_t grid = (int64_t)per_sm * sm_count;
   if (grid > a.n_items) grid = a.n_items;
-  kern<<<(unsigned)grid, PipeOcc<R>::THREADS, smem, st>>>(a);
+  kern<<<(unsigned)grid, PipeOcc<R>::THREADS, smem, st>>>(a, fb);
   LFEM_CUDA(cudaGetLastError());
   return LFEM_OK;
 }
 
 // Single mesh of type (D, NA, P).
+// Single mesh of type (D, NA, P); fast: the rule is the compile-time one (float only).
 template <int D, int NA, int P, typename R>
-lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, int sm_count, cudaStream_t st) {
+lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, bool fast, const FastBank& fb, int sm_count,
+                        cudaStream_t st) {
   using T = EType<D, NA, P>;
-  return ent_bytes == 2 ? launch_pipe_types<R, uint16_t, T>(a, sm_count, st)
-                        : launch_pipe_types<R, uint32_t, T>(a, sm_count, st);
+  if constexpr (sizeof(R) == 4 && D <= 2) {
+    using TF = EType<D, NA, P, true>;
+    if (fast) {
+      PipeArgs af = a;
+      af.one.type = TF::id;  // the tile dispatch matches the variant's id
+      return ent_bytes == 2 ? launch_pipe_types<R, uint16_t, TF>(af, fb, sm_count, st)
+                            : launch_pipe_types<R, uint32_t, TF>(af, fb, sm_count, st);
+    }
+  }
+  return ent_bytes == 2 ? launch_pipe_types<R, uint16_t, T>(a, fb, sm_count, st)
+                        : launch_pipe_types<R, uint32_t, T>(a, fb, sm_count, st);
 }
 
 template <typename R>

@@ -3,6 +3,7 @@
 // a single work list on the GPU), optionally captured once into a CUDA graph
 // and replayed.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "dispatch.cuh"
@@ -10,9 +11,11 @@
 namespace lfem {
 
 template <typename EntT>
-static lfem_status launch_batch(const PipeArgs& a, int sms, cudaStream_t st) {
-  return launch_pipe_types<float, EntT, EType<1, 2, 1>, EType<1, 2, 2>, EType<2, 2, 1>, EType<2, 2, 2>,
-                           EType<2, 3, 1>, EType<2, 3, 2>>(a, sms, st);
+static lfem_status launch_batch(const PipeArgs& a, const FastBank& fb, int sms, cudaStream_t st) {
+  return launch_pipe_types<float, EntT, EType<1, 2, 1, true>, EType<1, 2, 2, true>, EType<2, 2, 1, true>,
+                           EType<2, 2, 2, true>, EType<2, 3, 1, true>, EType<2, 3, 2, true>, EType<1, 2, 1>,
+                           EType<1, 2, 2>, EType<2, 2, 1>, EType<2, 2, 2>, EType<2, 3, 1>, EType<2, 3, 2>>(a, fb, sms,
+                                                                                                       st);
 }
 
 static bool batch_type_ok(int d, int na) { return (d == 1 && na == 2) || (d == 2 && (na == 2 || na == 3)); }
@@ -34,6 +37,7 @@ struct lfem_batch_s {
   int32_t* d_status = nullptr;  // [0] status bits, [2..3] fallback count
   int ent_bytes = 2;
   int64_t n_elements = 0;
+  FastBank fb{};  // compile-time-rule tables, one per (dim, order)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -42,7 +46,8 @@ static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
   int sms = 0;
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   LFEM_CUDA(cudaMemsetAsync(b->d_status + 2, 0, sizeof(unsigned long long), st));
-  return b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, sms, st) : launch_batch<uint32_t>(b->args, sms, st);
+  return b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, b->fb, sms, st)
+                           : launch_batch<uint32_t>(b->args, b->fb, sms, st);
 }
 
 extern "C" {
@@ -113,6 +118,29 @@ lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigne
   }
   lfem_batch_s* b = new lfem_batch_s();
   cudaGetDevice(&b->device);
+  // compile-time rules: an item runs the compile-time variant of its type when
+  // its rule has the fixed size and the same points and weights as the first
+  // such item of its (dim, order) (one table per (dim, order) in the launch)
+  {
+    bool seen[2][2] = {{false, false}, {false, false}};
+    std::vector<float> tab;
+    for (int i = 0; i < n_items; ++i) {
+      const lfem_pattern_s* p = items[i].pattern;
+      const int d = p->dim, o = p->order;
+      const int off = d == 1 ? (o == 1 ? FastBank::OFF11 : FastBank::OFF12) : (o == 1 ? FastBank::OFF21 : FastBank::OFF22);
+      const int size = d == 1 ? (o == 1 ? FastLayout<1, 1>::SIZE : FastLayout<1, 2>::SIZE)
+                              : (o == 1 ? FastLayout<2, 1>::SIZE : FastLayout<2, 2>::SIZE);
+      tab.assign(size, 0.f);
+      bool fast = fast_tables_host(d, o, items[i].quad, tab.data());
+      if (fast && seen[d - 1][o - 1]) {
+        fast = memcmp(tab.data(), b->fb.v + off, sizeof(float) * size) == 0;
+      } else if (fast) {
+        memcpy(b->fb.v + off, tab.data(), sizeof(float) * size);
+        seen[d - 1][o - 1] = true;
+      }
+      if (fast) recs[i].type += kFastTypeOffset;
+    }
+  }
   b->ent_bytes = ent_bytes;
   b->n_elements = n_el;
   auto cleanup = [&]() {
@@ -203,6 +231,7 @@ lfem_status lfem_batch_sync_status(lfem_batch_t b, void* cuda_stream) {
   LFEM_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), st));
   LFEM_CUDA(cudaStreamSynchronize(st));
   if (h & ST_TIMEOUT) return fail(LFEM_E_TIMEOUT, "a bounded device wait ran out");
+  if (h & ST_TYPE) return fail(LFEM_E_UNSUPPORTED, "a tile met a kernel without its element type");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
   return LFEM_OK;
 }

@@ -12,8 +12,8 @@ namespace lfem {
   lfem_status run_stage_d##DD(int NA, int P, int kind, const StageArgs& s, cudaStream_t st);                     \
   lfem_status run_adjoint_d##DD(int NA, int P, const AdjArgs& a, int64_t T, int pos_bytes, cudaStream_t st);     \
   lfem_status bank_upload_d##DD(const void* src, size_t bytes, size_t offset);                                 \
-  lfem_status run_pipe_d##DD(int NA, int P, bool mixed, const PipeArgs& a, int ent_bytes, int sms,              \
-                             cudaStream_t st);
+  lfem_status run_pipe_d##DD(int NA, int P, bool mixed, const PipeArgs& a, int ent_bytes, bool fast,             \
+                             const FastBank& fb, int sms, cudaStream_t st);
 
 LFEM_DECLARE_DIM(1)
 LFEM_DECLARE_DIM(2)
@@ -29,7 +29,7 @@ lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset);
 
 #define LFEM_DEFINE_CASE_PIPE(DD, NN, PP)                                                          \
   if (NA == NN && P == PP)                                                                         \
-    return mixed ? launch_pipe<DD, NN, PP, float>(a, ent_bytes, sms, st)                           \
-                 : launch_pipe<DD, NN, PP, double>(a, ent_bytes, sms, st);
+    return mixed ? launch_pipe<DD, NN, PP, float>(a, ent_bytes, fast, fb, sms, st)                 \
+                 : launch_pipe<DD, NN, PP, double>(a, ent_bytes, false, fb, sms, st);
 
 }  // namespace lfem

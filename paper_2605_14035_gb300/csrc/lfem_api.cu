@@ -81,6 +81,42 @@ static void host_tables(int dim, int order, const lfem_quad* quad, std::vector<d
   }
 }
 
+// Compile-time-quadrature tables (layout of FastLayout<dim, order>): edge
+// bubble gradients, weighted basis products and weighted symmetric gradient
+// products per quadrature point.
+bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
+  const int REF = n_ref(dim, order), NE = n_edges(dim, order), U = n_upper(REF), NK = dim * (dim + 1) / 2;
+  const int QF = dim == 1 ? 3 : (dim == 2 ? (order == 1 ? 3 : 7) : (order == 1 ? 4 : 14));
+  if (!quad || quad->n_pts != QF) return false;
+  std::vector<double> t;
+  host_tables(dim, order, quad, t);
+  const int Q = QF;
+  const double* w = t.data();
+  const double* phi = w + Q;
+  const double* dphi = phi + Q * REF;
+  const double* dpsi = dphi + Q * REF * dim;
+  const int per_q = NE * dim + U + NK * U;
+  for (int q = 0; q < Q; ++q) {
+    float* d = dst + (size_t)q * per_q;
+    for (int k = 0; k < NE; ++k)
+      for (int m = 0; m < dim; ++m) d[k * dim + m] = (float)dpsi[(q * NE + k) * dim + m];
+    float* tm = d + NE * dim;
+    float* ta = tm + U;
+    for (int a = 0; a < REF; ++a)
+      for (int b = a; b < REF; ++b) {
+        const int u = upper_index(REF, a, b);
+        tm[u] = (float)(w[q] * phi[q * REF + a] * phi[q * REF + b]);
+        const double* ga = dphi + (q * REF + a) * dim;
+        const double* gb = dphi + (q * REF + b) * dim;
+        int kk = 0;
+        for (int m = 0; m < dim; ++m)
+          for (int n = m; n < dim; ++n, ++kk)
+            ta[kk * U + u] = (float)(m == n ? w[q] * ga[m] * gb[m] : w[q] * (ga[m] * gb[n] + ga[n] * gb[m]));
+      }
+  }
+  return true;
+}
+
 struct TabKey {
   int dev, dim, order, q;
   std::vector<double> data;
@@ -153,10 +189,11 @@ static lfem_status run_adjoint(int dim, int NA, int P, const AdjArgs& a, int64_t
   if (dim == 2) return run_adjoint_d2(NA, P, a, T, pb, st);
   return run_adjoint_d3(NA, P, a, T, pb, st);
 }
-static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& a, int pb, int sms, cudaStream_t st) {
-  if (dim == 1) return run_pipe_d1(NA, P, mixed, a, pb, sms, st);
-  if (dim == 2) return run_pipe_d2(NA, P, mixed, a, pb, sms, st);
-  return run_pipe_d3(NA, P, mixed, a, pb, sms, st);
+static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& a, int pb, bool fast,
+                            const FastBank& fb, int sms, cudaStream_t st) {
+  if (dim == 1) return run_pipe_d1(NA, P, mixed, a, pb, fast, fb, sms, st);
+  if (dim == 2) return run_pipe_d2(NA, P, mixed, a, pb, fast, fb, sms, st);
+  return run_pipe_d3(NA, P, mixed, a, pb, fast, fb, sms, st);
 }
 
 static void destroy_dev(PatternDev& d) {
@@ -397,7 +434,15 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   int sms = 0;
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
-  return run_pipe(p->dim, ambient, p->order, mixed, pa, p->ent_bytes, sms, st);
+  // the usual rules run with compile-time quadrature (tables as kernel parameters)
+  FastBank fb;
+  bool fast = false;
+  if (mixed && p->dim <= 2) {
+    const int off = p->dim == 1 ? (p->order == 1 ? FastBank::OFF11 : FastBank::OFF12)
+                                : (p->order == 1 ? FastBank::OFF21 : FastBank::OFF22);
+    fast = fast_tables_host(p->dim, p->order, quad, fb.v + off);
+  }
+  return run_pipe(p->dim, ambient, p->order, mixed, pa, p->ent_bytes, fast, fb, sms, st);
 }
 
 lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
@@ -485,6 +530,7 @@ lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream) {
   LFEM_CUDA(cudaStreamSynchronize(st));
   if (h & ST_TIMEOUT) return fail(LFEM_E_TIMEOUT, "a bounded device wait ran out");
   if (h & ST_INDEX) return fail(LFEM_E_INDEX, "node index out of range");
+  if (h & ST_TYPE) return fail(LFEM_E_UNSUPPORTED, "a tile met a kernel without its element type");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
   return LFEM_OK;
 }

@@ -24,7 +24,7 @@ lfem_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // Device status bits (pattern status word).
-enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2, ST_TIMEOUT = 4 };
+enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2, ST_TIMEOUT = 4, ST_TYPE = 8 };
 
 // Tile limits.
 constexpr int kMaxTileIncidences = 4096;  // incidences (e, a) per tile; local index fits 12 bits
