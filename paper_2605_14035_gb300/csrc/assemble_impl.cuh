@@ -56,6 +56,8 @@ __device__ __forceinline__ void acc_add(float2& a, float v) {
   a.x = t;
 }
 __device__ __forceinline__ void acc_add(double& a, double v) { a += v; }
+__device__ __forceinline__ void acc_init(float2& a, float v) { a = make_float2(v, 0.f); }
+__device__ __forceinline__ void acc_init(double& a, double v) { a = v; }
 __device__ __forceinline__ float acc_final(const float2& a) { return a.x - a.y; }
 __device__ __forceinline__ double acc_final(const double& a) { return a; }
 

@@ -114,8 +114,8 @@ __host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, in
   o += al((size_t)cap_nel * q * coef_bytes);
   L.lsm = o;
   o += al(sizeof(R) * (size_t)cap_lsm);
-  L.flag = o;  // element flags in phase 1, run starts (<= 1025 ints) in phase 2
-  o += al(cap_nel > 4100 ? (size_t)cap_nel : (size_t)4100);
+  L.flag = o;  // element flags of phase 1
+  o += al((size_t)cap_nel);
   L.total = o;
   return L;
 }
@@ -209,18 +209,23 @@ __device__ __forceinline__ void issue_gathers(const MeshRec& mr, bool want_coef,
   const TileLayout L = tile_layout(h.nel, h.ns, h.nent, h.nnodes, mr.ref, mr.entb);
   const int32_t* nd = reinterpret_cast<const int32_t*>(meta + L.nodes);
   const int na = mr.na;
-  for (int i = threadIdx.x; i < h.nnodes * na; i += blockDim.x) {
-    const int v = i / na, c = i - v * na;
-    cp_async8(nodes_dst + i, mr.coords + (int64_t)nd[v] * na + c);
+  // a thread per node (no division by the runtime sizes)
+  for (int v = threadIdx.x; v < h.nnodes; v += blockDim.x) {
+    const double* src = mr.coords + (int64_t)nd[v] * na;
+    for (int c = 0; c < na; ++c) cp_async8(nodes_dst + v * na + c, src + c);
   }
   if (want_coef) {
     const int q = mr.tab.q;
     const int32_t* el = reinterpret_cast<const int32_t*>(meta + L.elem);
-    for (int i = threadIdx.x; i < h.nel * q; i += blockDim.x) {
-      const int j = i / q, qq = i - j * q;
-      const int64_t gi = (int64_t)el[j] * q + qq;
-      if (mr.coef_f32) cp_async4(static_cast<float*>(coef_dst) + i, static_cast<const float*>(mr.coef) + gi);
-      else cp_async8(static_cast<double*>(coef_dst) + i, static_cast<const double*>(mr.coef) + gi);
+    for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
+      const int64_t g0 = (int64_t)el[j] * q;
+      if (mr.coef_f32) {
+        for (int qq = 0; qq < q; ++qq)
+          cp_async4(static_cast<float*>(coef_dst) + j * q + qq, static_cast<const float*>(mr.coef) + g0 + qq);
+      } else {
+        for (int qq = 0; qq < q; ++qq)
+          cp_async8(static_cast<double*>(coef_dst) + j * q + qq, static_cast<const double*>(mr.coef) + g0 + qq);
+      }
     }
   }
   cp_async_commit();
@@ -326,30 +331,30 @@ __device__ __forceinline__ void element_pair(const ElemData<D, NA, P, R>& ed, co
 template <int D, int NA, int P, typename R>
 __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb,
                                                       const void* coef, int coef_f32, int sub, bool store, R* dst,
-                                                      unsigned which, R& qual, bool& bad) {
+                                                      int mstride, unsigned which, R& qual, bool& bad) {
   constexpr int U = Ref<D, P>::U;
   const bool wm = which & LFEM_MASS, wa = which & LFEM_STIFF, wc = which & LFEM_CMASS;
   const int im = 0, ia = wm ? 1 : 0, ic = (wm ? 1 : 0) + (wa ? 1 : 0);
   if constexpr (D == 3) {
     // one matrix per pass: 55 accumulators at most
-    if (wm) element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
-    if (wc) element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
-    if (wa) element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+    if (wm) element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
+    if (wc) element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
+    if (wa) element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
   } else {
     if (wm && wa && wc)
-      element_pair<D, NA, P, R, true, true, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, true, true, true>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
     else if (wm && wa)
-      element_pair<D, NA, P, R, true, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, true, true, false>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
     else if (wm && wc)
-      element_pair<D, NA, P, R, true, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, true, false, true>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
     else if (wa && wc)
-      element_pair<D, NA, P, R, false, true, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, false, true, true>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
     else if (wm)
-      element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, true, false, false>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
     else if (wa)
-      element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, false, true, false>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
     else
-      element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, U, im, ia, ic, qual, bad);
+      element_pair<D, NA, P, R, false, false, true>(ed, tb, coef, coef_f32, sub, store, dst, mstride, im, ia, ic, qual, bad);
   }
 }
 
@@ -360,29 +365,22 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
 template <int D, int NA, int P, typename Bank>
 __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, float>& ed, const Bank& bank,
                                                    const float* cs, const double* cd, float qthr, unsigned which,
-                                                   float* dst, bool& keep) {
+                                                   float* dst, int mstride, bool& keep) {
   using L = FastLayout<D, P>;
-  constexpr int U = L::U, Q = L::Q;
+  constexpr int Q = L::Q;
   float sq[Q], hq[Q][L::NK];
   geometry_fast<D, NA, P>(ed, bank, qthr, sq, hq, keep);
   int slot = 0;
-  if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + U * slot++);
-  if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + U * slot++);
+  if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
+  if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + mstride * slot++);
   if (which & LFEM_CMASS) {
     float sc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) sc[q] = sq[q] * (cs ? cs[q] : (float)cd[q]);
-    contract_mass<D, P>(bank, sc, dst + U * slot);
+    contract_mass<D, P>(bank, sc, dst + mstride * slot);
   }
 }
 
-// Shared-memory views of one CTA.
-template <typename R>
-struct TileEnv {
-  R* lsm;
-  uint8_t* flag;
-  int lstride;  // nm * U of the current element type
-};
 
 // Everything done for one tile whose block, node coordinates and coefficients
 // are in shared memory: split, phase 1 (+ the double fallback), the prefetch
@@ -393,14 +391,15 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
                                              Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
-  constexpr int UB = ub_bits(U);
   constexpr int ENTB = (int)sizeof(EntT);
   using Acc = typename AccOf<R>::T;
   const int nm = a.nm, Q = mr.tab.q;
   const int coef_bytes = a.coef_bytes;
-  const int lstride = nm * U;
   const TabView<R> tb = tab_view<D, P, R>(mr.tab);
   const TileHdr h = *reinterpret_cast<const TileHdr*>(mb);
+  // local matrices matrix-major: lsm[m * nel * U + e * U + u]; a contribution
+  // entry is the word offset e * U + u
+  const int mstride = h.nel * U;
   const TileLayout TL = tile_layout(h.nel, h.ns, h.nent, h.nnodes, REF, ENTB);
   const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
   const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
@@ -431,8 +430,8 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         const float* cs = coef_bytes == 4 ? static_cast<const float*>(coef_s) + (size_t)jt * Q : nullptr;
         const double* cd = coef_bytes == 8 ? static_cast<const double*>(coef_s) + (size_t)jt * Q : nullptr;
         bool keep = true;
-        element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * lstride,
-                                     keep);
+        element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * U,
+                                     mstride, keep);
         flag[jt] = keep ? 0 : 1;
       }
       if (!prefetched) {
@@ -452,11 +451,11 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     if (coef_bytes) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
     R qual = (R)1;
     bool bad = false;
-    R* dst = lsm + (size_t)jt * lstride;
+    R* dst = lsm + (size_t)jt * U;
     if constexpr (sizeof(R) == 4) {
       ElemData<D, NA, P, float> ed;
       element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
-      element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, a.which, qual, bad);
+      element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, mstride, a.which, qual, bad);
     } else {
       double X[REF][NA];
 #pragma unroll
@@ -465,7 +464,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
       ElemData<D, NA, P, double> ed;
       load_element_data<D, NA, P, double>(X, ed);
-      element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, a.which, qual, bad);
+      element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, mstride, a.which, qual, bad);
     }
     const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
     const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
@@ -493,7 +492,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
       for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
       bool bad = false;
       element_fp64_lean<D, NA, P, float>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], a.which,
-                                         lsm + (size_t)j * lstride, U, bad);
+                                         lsm + (size_t)j * U, mstride, bad);
       if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
         atomicAdd(a.fallback, 1ull);
         if (bad) atomicOr(a.status, ST_DEGENERATE);
@@ -503,54 +502,33 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   if (!prefetched) prefetch();
   __syncthreads();
 
-  // ---- phase 2: runs of slots balanced by contribution count; each slot's
-  // list summed in order (compensated, in registers) and stored
-  const int per = (h.nent + (int)blockDim.x - 1) / (int)blockDim.x;
-  auto first_slot = [&](int key) {
-    int lo = 0, hi = h.ns;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((int)t_soff[mid] < key) lo = mid + 1;
-      else hi = mid;
-    }
-    return lo;
-  };
-  // one binary search per thread; the next thread's start ends the run
-  int* run_start = reinterpret_cast<int*>(flag);  // flags are dead here (all fallbacks done)
-  run_start[threadIdx.x] = first_slot((int)threadIdx.x * per);
-  if (threadIdx.x == 0) run_start[blockDim.x] = h.ns;
-  __syncthreads();
-  const int sb = run_start[threadIdx.x], se = run_start[threadIdx.x + 1];
-  R* o0 = reinterpret_cast<R*>(mr.out[0]) + h.s0;
-  R* o1 = nm > 1 ? reinterpret_cast<R*>(mr.out[1]) + h.s0 : o0;
-  R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
-  if (sb < se) {
-    // one loop over the run's contributions (lanes stay in step); a slot is
-    // stored when its list ends
-    int s = sb;
-    int k = t_soff[sb];
-    const int kend = t_soff[se];
-    int kslot = t_soff[sb + 1];
-    Acc c0, c1, c2;
-    acc_zero(c0);
-    acc_zero(c1);
-    acc_zero(c2);
-    for (; k < kend; ++k) {
-      const uint32_t ent = t_sent[k];
-      const R* l = lsm + (size_t)(ent >> UB) * lstride + (ent & ((1u << UB) - 1));
-      acc_add(c0, l[0]);
-      if (nm > 1) acc_add(c1, l[U]);
-      if (nm > 2) acc_add(c2, l[2 * U]);
-      if (k + 1 == kslot) {
-        o0[s] = (R)acc_final(c0);
-        if (nm > 1) o1[s] = (R)acc_final(c1);
-        if (nm > 2) o2[s] = (R)acc_final(c2);
-        acc_zero(c0);
-        acc_zero(c1);
-        acc_zero(c2);
-        ++s;
-        if (s < se) kslot = t_soff[s + 1];
+  // ---- phase 2: a thread per CSR slot (consecutive threads, consecutive
+  // slots: coalesced stores); each slot's list, in ascending element order,
+  // summed with a compensated pair in registers -- one writer per slot, fixed
+  // order, no atomics.  Every slot has at least one contribution.
+  {
+    R* o0 = reinterpret_cast<R*>(mr.out[0]) + h.s0;
+    R* o1 = nm > 1 ? reinterpret_cast<R*>(mr.out[1]) + h.s0 : o0;
+    R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
+    const R* l1 = lsm + mstride;
+    const R* l2 = lsm + 2 * mstride;
+    for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
+      int k = t_soff[s];
+      const int k1 = t_soff[s + 1];
+      uint32_t ent = t_sent[k];
+      Acc c0, c1, c2;
+      acc_init(c0, lsm[ent]);
+      if (nm > 1) acc_init(c1, l1[ent]);
+      if (nm > 2) acc_init(c2, l2[ent]);
+      for (++k; k < k1; ++k) {
+        ent = t_sent[k];
+        acc_add(c0, lsm[ent]);
+        if (nm > 1) acc_add(c1, l1[ent]);
+        if (nm > 2) acc_add(c2, l2[ent]);
       }
+      o0[s] = (R)acc_final(c0);
+      if (nm > 1) o1[s] = (R)acc_final(c1);
+      if (nm > 2) o2[s] = (R)acc_final(c2);
     }
   }
 }

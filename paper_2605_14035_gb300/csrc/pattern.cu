@@ -487,7 +487,8 @@ __global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const in
 
 // Fill one tile's block.  The contribution list of a slot holds, in ascending
 // (element, a, b) order, every local pair of the tile's elements that adds into
-// it; a row's lists are contiguous (ref entries per incidence of the row).
+// it, as the word offset e_local * U + u of that entry in a local-matrix
+// array; a row's lists are contiguous (ref entries per incidence of the row).
 template <typename PosT>
 __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ tile_row0,
                             const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ inc_ptr,
@@ -506,7 +507,6 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
   const int64_t s0 = row_ptr[r0];
   const int ns = (int)(row_ptr[r1] - s0);
   const int U = ref * (ref + 1) / 2;
-  const int UB = ub_bits(U);
   const int ps = pos_stride(ref);
   uint8_t* blk = meta + off[t];
   const TileLayout L = tile_layout(nel, ns, nent, nn, ref, entb);
@@ -555,7 +555,7 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
         for (int b = 0; b < ref; ++b) {
           if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
           const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
-          const uint32_t ent = ((uint32_t)loc << UB) | (uint32_t)u;
+          const uint32_t ent = (uint32_t)loc * (uint32_t)U + (uint32_t)u;
           if (entb == 2) reinterpret_cast<uint16_t*>(se)[run] = (uint16_t)ent;
           else reinterpret_cast<uint32_t*>(se)[run] = ent;
           ++run;
@@ -589,8 +589,8 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   LFEM_CUDA(cudaStreamSynchronize(st));
   int32_t mnel = 0;
   for (int64_t t = 0; t < T; ++t) mnel = std::max(mnel, hep[t + 1] - hep[t]);
-  const int UB = ub_bits(ref * (ref + 1) / 2);
-  const int entb = std::max(((int64_t)mnel << UB) <= 65536 ? 2 : 4, p->min_ent_bytes);
+  // entries are local-matrix word offsets e * U + u
+  const int entb = std::max((int64_t)mnel * (ref * (ref + 1) / 2) <= 65536 ? 2 : 4, p->min_ent_bytes);
   int32_t *tmp_nodes = nullptr, *nn = nullptr;
   int64_t *bytes = nullptr, *scr = nullptr, *mx = nullptr;
   TRY(dalloc(&tmp_nodes, p->tile_elems_total * ref));
