@@ -33,6 +33,7 @@
 namespace lfem {
 
 constexpr int kPipeTPE = 2;  // threads per element in phase 1
+constexpr int kLongCap = 1024;  // phase 2: slots with long lists deferred to a second pass
 
 // Launch shape: the float kernel fits 170 registers, so 192 threads and two
 // CTAs per SM; the double kernel needs more registers: 256 threads, one CTA.
@@ -89,7 +90,7 @@ struct PipeArgs {
 };
 
 struct PipeSmem {
-  size_t mbar, meta0, meta1, node0, node1, coef0, coef1, lsm, flag, total;
+  size_t mbar, rec, meta0, meta1, node0, node1, coef0, coef1, lsm, flag, longl, total;
 };
 
 template <typename R>
@@ -100,6 +101,8 @@ __host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, in
   size_t o = 0;
   L.mbar = o;
   o += 128;
+  L.rec = o;  // the MeshRec of the current and of the next item
+  o += al(2 * sizeof(MeshRec));
   L.meta0 = o;
   o += al(cap_bytes);
   L.meta1 = o;
@@ -116,6 +119,8 @@ __host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, in
   o += al(sizeof(R) * (size_t)cap_lsm);
   L.flag = o;  // element flags of phase 1
   o += al((size_t)cap_nel);
+  L.longl = o;  // slots with more than two contributions (phase 2)
+  o += al(sizeof(uint16_t) * kLongCap);
   L.total = o;
   return L;
 }
@@ -387,8 +392,8 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
 // hook of the next item after the first phase-1 round, phase 2.
 template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
 __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
-                                             const void* coef_s, R* lsm, uint8_t* flag, const FastBank& fb,
-                                             Prefetch&& prefetch) {
+                                             const void* coef_s, R* lsm, uint8_t* flag, uint16_t* longl, int* nlong,
+                                             const FastBank& fb, Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   constexpr int ENTB = (int)sizeof(EntT);
@@ -407,6 +412,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   const uint16_t* t_soff = reinterpret_cast<const uint16_t*>(mb + TL.soff);
   const EntT* t_sent = reinterpret_cast<const EntT*>(mb + TL.sent);
 
+  if (threadIdx.x == 0) *nlong = 0;  // visible after the next barrier
   // node coordinates -> (hi, lo) float pairs in place (mixed)
   if constexpr (sizeof(R) == 4) {
     for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
@@ -505,16 +511,17 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   // ---- phase 2: a thread per CSR slot (consecutive threads, consecutive
   // slots: coalesced stores); each slot's list, in ascending element order,
   // summed with a compensated pair in registers -- one writer per slot, fixed
-  // order, no atomics.  Every slot has at least one contribution.
+  // order, no atomics on values.  Every slot has at least one contribution.
+  // Slots with more than two contributions (the diagonal of a surface node)
+  // are deferred to a second pass over a compacted list, so a warp does not
+  // wait on one long list in the first pass.
   {
     R* o0 = reinterpret_cast<R*>(mr.out[0]) + h.s0;
     R* o1 = nm > 1 ? reinterpret_cast<R*>(mr.out[1]) + h.s0 : o0;
     R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
     const R* l1 = lsm + mstride;
     const R* l2 = lsm + 2 * mstride;
-    for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
-      int k = t_soff[s];
-      const int k1 = t_soff[s + 1];
+    auto slot_sum = [&](int s, int k, int k1) {
       uint32_t ent = t_sent[k];
       Acc c0, c1, c2;
       acc_init(c0, lsm[ent]);
@@ -529,6 +536,23 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
       o0[s] = (R)acc_final(c0);
       if (nm > 1) o1[s] = (R)acc_final(c1);
       if (nm > 2) o2[s] = (R)acc_final(c2);
+    };
+    for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
+      const int k = t_soff[s], k1 = t_soff[s + 1];
+      if (k1 - k > 2) {
+        const int i = atomicAdd(nlong, 1);
+        if (i < kLongCap) {
+          longl[i] = (uint16_t)s;
+          continue;
+        }
+      }
+      slot_sum(s, k, k1);
+    }
+    __syncthreads();
+    const int nl = min(*nlong, kLongCap);
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+      const int s = longl[i];
+      slot_sum(s, t_soff[s], t_soff[s + 1]);
     }
   }
 }
@@ -544,13 +568,14 @@ struct EType {
 
 template <typename R, typename EntT, typename T0, typename... Ts, typename Prefetch>
 __device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* mb,
-                                              double* xd, const void* coef_s, R* lsm, uint8_t* flag,
-                                              const FastBank& fb, Prefetch&& prefetch) {
+                                              double* xd, const void* coef_s, R* lsm, uint8_t* flag, uint16_t* longl,
+                                              int* nlong, const FastBank& fb, Prefetch&& prefetch) {
   if (type == T0::id) {
-    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
+    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, longl, nlong, fb,
+                                                          prefetch);
   } else {
     if constexpr (sizeof...(Ts) > 0) {
-      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
+      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, longl, nlong, fb, prefetch);
     } else {
       // no variant for this tile's type: report it, keep the pipeline's steps
       if (threadIdx.x == 0) atomicOr(a.status, ST_TYPE);
@@ -570,11 +595,16 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
       pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
   int* s_flag = reinterpret_cast<int*>(smem_raw + L.mbar + 64);
-  uint8_t* meta_buf[2] = {smem_raw + L.meta0, smem_raw + L.meta1};
-  double* node_buf[2] = {reinterpret_cast<double*>(smem_raw + L.node0), reinterpret_cast<double*>(smem_raw + L.node1)};
-  void* coef_buf[2] = {smem_raw + L.coef0, smem_raw + L.coef1};
+  // buffers as shared-memory base + offset (no pointer arrays: a pointer
+  // loaded back from local memory would turn every access generic)
+  MeshRec* s_rec = reinterpret_cast<MeshRec*>(smem_raw + L.rec);
+  auto meta_of = [&](int buf) { return smem_raw + (buf ? L.meta1 : L.meta0); };
+  auto node_of = [&](int buf) { return reinterpret_cast<double*>(smem_raw + (buf ? L.node1 : L.node0)); };
+  auto coef_of = [&](int buf) { return static_cast<void*>(smem_raw + (buf ? L.coef1 : L.coef0)); };
   R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
   uint8_t* flag = smem_raw + L.flag;
+  uint16_t* longl = reinterpret_cast<uint16_t*>(smem_raw + L.longl);
+  int* s_nlong = reinterpret_cast<int*>(smem_raw + L.mbar + 68);
 
   int64_t i = blockIdx.x;
   if (i >= a.n_items) return;
@@ -596,13 +626,17 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
       tile = k;
     }
   };
+  // thread 0: item k's MeshRec into s_rec[buf] (read by all after the next
+  // barrier) and one bulk copy of its metadata block
   auto load_block = [&](int64_t k, int buf) {
     int mesh;
     int64_t tile;
     item(k, mesh, tile);
-    const MeshRec& mr = a.meshes ? a.meshes[mesh] : a.one;
-    const uint32_t bytes = (uint32_t)(mr.meta_off[tile + 1] - mr.meta_off[tile]);
-    tma_load_block(meta_buf[buf], mr.meta + mr.meta_off[tile], bytes, &mbar[buf]);
+    MeshRec& r = s_rec[buf];
+    if (a.meshes) r = a.meshes[mesh];
+    else r = a.one;
+    const uint32_t bytes = (uint32_t)(r.meta_off[tile + 1] - r.meta_off[tile]);
+    tma_load_block(meta_of(buf), r.meta + r.meta_off[tile], bytes, &mbar[buf]);
   };
   // prologue: item i into buffer 0
   if (threadIdx.x == 0 && !(a.starve && blockIdx.x == 0)) load_block(i, 0);
@@ -613,12 +647,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
       return;  // nothing was issued for this barrier, or it never completed within the bound
     }
   }
-  {
-    int mesh;
-    int64_t tile;
-    item(i, mesh, tile);
-    issue_gathers(a.meshes ? a.meshes[mesh] : a.one, want_coef, meta_buf[0], node_buf[0], coef_buf[0]);
-  }
+  issue_gathers(s_rec[0], want_coef, meta_of(0), node_of(0), coef_of(0));
 
   for (int it = 0; i < a.n_items; i += gridDim.x, ++it) {
     const int b = it & 1, nb = b ^ 1;
@@ -638,19 +667,13 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
         if (__syncthreads_or(!ok)) {
           if (threadIdx.x == 0) *s_flag = 1;
         } else {
-          int mesh;
-          int64_t tile;
-          item(in, mesh, tile);
-          issue_gathers(a.meshes ? a.meshes[mesh] : a.one, want_coef, meta_buf[nb], node_buf[nb], coef_buf[nb]);
+          issue_gathers(s_rec[nb], want_coef, meta_of(nb), node_of(nb), coef_of(nb));
         }
       }
     };
-    int mesh;
-    int64_t tile;
-    item(i, mesh, tile);
-    const MeshRec& mr = a.meshes ? a.meshes[mesh] : a.one;
-    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_buf[b], node_buf[b], coef_buf[b], lsm, flag, fb,
-                                     prefetch_next);
+    const MeshRec& mr = s_rec[b];
+    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_of(b), node_of(b), coef_of(b), lsm, flag, longl, s_nlong,
+                                     fb, prefetch_next);
     if (*s_flag) {
       // the next block never arrived: report, wait (bounded) for the copy, stop
       if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
