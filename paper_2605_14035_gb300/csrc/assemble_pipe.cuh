@@ -17,10 +17,10 @@
 //   phase 1  two threads per element (quadrature points split between them):
 //            geometry and local upper-triangle matrices of every element of
 //            the tile -> shared memory
-//   phase 2  each thread takes a run of consecutive CSR slots holding about
-//            the same number of contributions and sums each slot's list (in
-//            ascending element order, compensated in registers), then stores
-//            the slot -- one writer per slot, fixed order, no atomics
+//   phase 2  one writer per CSR slot: slots with one or two contributions
+//            take a thread each (plain sum, coalesced stores); longer lists
+//            are summed in ascending element order with a compensated pair --
+//            fixed order, no atomics
 //
 // Every mbarrier wait is bounded by the global timer; on timeout the CTA
 // records ST_TIMEOUT in the status word, waits (bounded) for its own copy and
@@ -33,7 +33,6 @@
 namespace lfem {
 
 constexpr int kPipeTPE = 2;  // threads per element in phase 1
-constexpr int kLongCap = 1024;  // phase 2: slots with long lists deferred to a second pass
 
 // Launch shape: the float kernel fits 170 registers, so 192 threads and two
 // CTAs per SM; the double kernel needs more registers: 256 threads, one CTA.
@@ -90,7 +89,7 @@ struct PipeArgs {
 };
 
 struct PipeSmem {
-  size_t mbar, rec, meta0, meta1, node0, node1, coef0, coef1, lsm, flag, longl, total;
+  size_t mbar, rec, meta0, meta1, node0, node1, coef0, coef1, lsm, flag, total;
 };
 
 template <typename R>
@@ -119,8 +118,6 @@ __host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, in
   o += al(sizeof(R) * (size_t)cap_lsm);
   L.flag = o;  // element flags of phase 1
   o += al((size_t)cap_nel);
-  L.longl = o;  // slots with more than two contributions (phase 2)
-  o += al(sizeof(uint16_t) * kLongCap);
   L.total = o;
   return L;
 }
@@ -211,7 +208,7 @@ __device__ __forceinline__ void load_pos_smem(const uint8_t* base, int k, int (&
 __device__ __forceinline__ void issue_gathers(const MeshRec& mr, bool want_coef, const uint8_t* meta,
                                               double* nodes_dst, void* coef_dst) {
   const TileHdr h = *reinterpret_cast<const TileHdr*>(meta);
-  const TileLayout L = tile_layout(h.nel, h.ns, h.nent, h.nnodes, mr.ref, mr.entb);
+  const TileLayout L = tile_layout(h.nel, h.ns, h.nl, h.nle, h.nnodes, mr.ref, mr.entb);
   const int32_t* nd = reinterpret_cast<const int32_t*>(meta + L.nodes);
   const int na = mr.na;
   // a thread per node (no division by the runtime sizes)
@@ -392,8 +389,8 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
 // hook of the next item after the first phase-1 round, phase 2.
 template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
 __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
-                                             const void* coef_s, R* lsm, uint8_t* flag, uint16_t* longl, int* nlong,
-                                             const FastBank& fb, Prefetch&& prefetch) {
+                                             const void* coef_s, R* lsm, uint8_t* flag, const FastBank& fb,
+                                             Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   constexpr int ENTB = (int)sizeof(EntT);
@@ -405,14 +402,14 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   // local matrices matrix-major: lsm[m * nel * U + e * U + u]; a contribution
   // entry is the word offset e * U + u
   const int mstride = h.nel * U;
-  const TileLayout TL = tile_layout(h.nel, h.ns, h.nent, h.nnodes, REF, ENTB);
+  const TileLayout TL = tile_layout(h.nel, h.ns, h.nl, h.nle, h.nnodes, REF, ENTB);
   const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
   const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
   const uint16_t* t_en = reinterpret_cast<const uint16_t*>(mb + TL.enodes);
-  const uint16_t* t_soff = reinterpret_cast<const uint16_t*>(mb + TL.soff);
-  const EntT* t_sent = reinterpret_cast<const EntT*>(mb + TL.sent);
+  const EntT* t_pair = reinterpret_cast<const EntT*>(mb + TL.pair);
+  const int4* t_lrec = reinterpret_cast<const int4*>(mb + TL.lrec);
+  const EntT* t_lent = reinterpret_cast<const EntT*>(mb + TL.lent);
 
-  if (threadIdx.x == 0) *nlong = 0;  // visible after the next barrier
   // node coordinates -> (hi, lo) float pairs in place (mixed)
   if constexpr (sizeof(R) == 4) {
     for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
@@ -508,51 +505,48 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   if (!prefetched) prefetch();
   __syncthreads();
 
-  // ---- phase 2: a thread per CSR slot (consecutive threads, consecutive
-  // slots: coalesced stores); each slot's list, in ascending element order,
-  // summed with a compensated pair in registers -- one writer per slot, fixed
-  // order, no atomics on values.  Every slot has at least one contribution.
-  // Slots with more than two contributions (the diagonal of a surface node)
-  // are deferred to a second pass over a compacted list, so a warp does not
-  // wait on one long list in the first pass.
+  // ---- phase 2: one writer per CSR slot, each slot's contributions summed
+  // in ascending (element, a, b) order -- fixed order, no atomics.  Slots with
+  // one or two contributions (nearly all of them on surfaces) take a thread
+  // each, consecutive slots on consecutive threads (coalesced stores, no
+  // loop); the few longer lists (the diagonal of a node of high valence) are
+  // summed with a compensated pair from the long list.
   {
+    constexpr EntT NONE = (EntT)~(EntT)0;
     R* o0 = reinterpret_cast<R*>(mr.out[0]) + h.s0;
     R* o1 = nm > 1 ? reinterpret_cast<R*>(mr.out[1]) + h.s0 : o0;
     R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
     const R* l1 = lsm + mstride;
     const R* l2 = lsm + 2 * mstride;
-    auto slot_sum = [&](int s, int k, int k1) {
-      uint32_t ent = t_sent[k];
+    for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
+      const EntT x = t_pair[2 * s], y = t_pair[2 * s + 1];
+      if (x == NONE) continue;
+      R v0 = lsm[x], v1 = nm > 1 ? l1[x] : (R)0, v2 = nm > 2 ? l2[x] : (R)0;
+      if (y != NONE) {
+        v0 += lsm[y];
+        if (nm > 1) v1 += l1[y];
+        if (nm > 2) v2 += l2[y];
+      }
+      o0[s] = v0;
+      if (nm > 1) o1[s] = v1;
+      if (nm > 2) o2[s] = v2;
+    }
+    for (int j = threadIdx.x; j < h.nl; j += blockDim.x) {
+      const int4 r = t_lrec[j];
+      uint32_t ent = t_lent[r.y];
       Acc c0, c1, c2;
       acc_init(c0, lsm[ent]);
       if (nm > 1) acc_init(c1, l1[ent]);
       if (nm > 2) acc_init(c2, l2[ent]);
-      for (++k; k < k1; ++k) {
-        ent = t_sent[k];
+      for (int k = r.y + 1; k < r.z; ++k) {
+        ent = t_lent[k];
         acc_add(c0, lsm[ent]);
         if (nm > 1) acc_add(c1, l1[ent]);
         if (nm > 2) acc_add(c2, l2[ent]);
       }
-      o0[s] = (R)acc_final(c0);
-      if (nm > 1) o1[s] = (R)acc_final(c1);
-      if (nm > 2) o2[s] = (R)acc_final(c2);
-    };
-    for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
-      const int k = t_soff[s], k1 = t_soff[s + 1];
-      if (k1 - k > 2) {
-        const int i = atomicAdd(nlong, 1);
-        if (i < kLongCap) {
-          longl[i] = (uint16_t)s;
-          continue;
-        }
-      }
-      slot_sum(s, k, k1);
-    }
-    __syncthreads();
-    const int nl = min(*nlong, kLongCap);
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-      const int s = longl[i];
-      slot_sum(s, t_soff[s], t_soff[s + 1]);
+      o0[r.x] = (R)acc_final(c0);
+      if (nm > 1) o1[r.x] = (R)acc_final(c1);
+      if (nm > 2) o2[r.x] = (R)acc_final(c2);
     }
   }
 }
@@ -568,14 +562,13 @@ struct EType {
 
 template <typename R, typename EntT, typename T0, typename... Ts, typename Prefetch>
 __device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* mb,
-                                              double* xd, const void* coef_s, R* lsm, uint8_t* flag, uint16_t* longl,
-                                              int* nlong, const FastBank& fb, Prefetch&& prefetch) {
+                                              double* xd, const void* coef_s, R* lsm, uint8_t* flag,
+                                              const FastBank& fb, Prefetch&& prefetch) {
   if (type == T0::id) {
-    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, longl, nlong, fb,
-                                                          prefetch);
+    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
   } else {
     if constexpr (sizeof...(Ts) > 0) {
-      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, longl, nlong, fb, prefetch);
+      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
     } else {
       // no variant for this tile's type: report it, keep the pipeline's steps
       if (threadIdx.x == 0) atomicOr(a.status, ST_TYPE);
@@ -603,8 +596,6 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
   auto coef_of = [&](int buf) { return static_cast<void*>(smem_raw + (buf ? L.coef1 : L.coef0)); };
   R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
   uint8_t* flag = smem_raw + L.flag;
-  uint16_t* longl = reinterpret_cast<uint16_t*>(smem_raw + L.longl);
-  int* s_nlong = reinterpret_cast<int*>(smem_raw + L.mbar + 68);
 
   int64_t i = blockIdx.x;
   if (i >= a.n_items) return;
@@ -672,8 +663,8 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
       }
     };
     const MeshRec& mr = s_rec[b];
-    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_of(b), node_of(b), coef_of(b), lsm, flag, longl, s_nlong,
-                                     fb, prefetch_next);
+    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_of(b), node_of(b), coef_of(b), lsm, flag, fb,
+                                     prefetch_next);
     if (*s_flag) {
       // the next block never arrived: report, wait (bounded) for the copy, stop
       if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);

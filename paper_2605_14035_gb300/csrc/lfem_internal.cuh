@@ -364,29 +364,42 @@ __device__ __forceinline__ void gather_coords(const double* __restrict__ coords,
 struct TileHdr {
   int64_t s0;
   int32_t r0, nrows, ns, nent, nel, nnodes;
+  int32_t nl, nle;  // slots with more than two contributions, and their entries
+  int32_t pad[2];
 };
-static_assert(sizeof(TileHdr) == 32, "tile header");
+static_assert(sizeof(TileHdr) == 48, "tile header");
 
 __host__ __device__ constexpr int al16(int64_t b) { return (int)((b + 15) / 16 * 16); }
-// bits of the upper index in a contribution entry
-__host__ __device__ constexpr int ub_bits(int u) { return u <= 1 ? 1 : (u <= 2 ? 1 : (u <= 4 ? 2 : (u <= 8 ? 3 : (u <= 16 ? 4 : (u <= 32 ? 5 : 6))))); }
 
+// Tile block after the header:
+//   elem[nel] (int32)   global element ids
+//   nodes[nnodes]       global node ids (sorted)
+//   enodes[nel][ref]    (u16) tile-local node index of each element node
+//   pair[ns][2]         (EntT) slots with one or two contributions: their
+//                       entries (the second all ones for one); all ones in
+//                       both for a slot on the long list
+//   lrec[nl]            (int4) long slots: {slot, first, end, 0} into lent
+//   lent[nle]           (EntT) entries of the long slots, each slot's run in
+//                       ascending (element, a, b) order
+// An entry is the word offset e_local * U + u of a local upper-triangle entry.
 struct TileLayout {
-  int elem, nodes, enodes, soff, sent, total;
+  int elem, nodes, enodes, pair, lrec, lent, total;
 };
-__host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nent, int nnodes, int ref, int entb) {
+__host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nl, int nle, int nnodes, int ref, int entb) {
   TileLayout L;
-  int o = 32;
+  int o = (int)sizeof(TileHdr);
   L.elem = o;
   o += al16(4ll * nel);
   L.nodes = o;
   o += al16(4ll * nnodes);
   L.enodes = o;
   o += al16(2ll * ref * nel);
-  L.soff = o;
-  o += al16(2ll * (ns + 1));
-  L.sent = o;
-  o += al16((int64_t)entb * nent);
+  L.pair = o;
+  o += al16(2ll * entb * ns);
+  L.lrec = o;
+  o += al16(16ll * nl);
+  L.lent = o;
+  o += al16((int64_t)entb * nle);
   L.total = o;
   return L;
 }

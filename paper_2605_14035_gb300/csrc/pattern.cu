@@ -1,7 +1,10 @@
 // Pattern builder (once per topology): integer sort / unique of the element
 // index pairs (E[e,a], E[e,b]) into CSR, plus the maps the assembly kernels
-// use.  All integer work; the result is bit-exact and independent of thread
-// scheduling (atomics only count, every list is sorted before use).
+// use.  All integer work; the CSR pattern and every contribution list are
+// bit-exact and independent of thread scheduling (atomics only count, every
+// list is sorted before use).  The one exception is the order of a tile's
+// long-slot work list, which atomics hand out; it decides which thread sums a
+// slot, never how.
 //
 // This replaces the per-assembly sort inside sparse(I, J, V) (Sec. 3.3: the
 // log-linear cost comes from sorting and merging duplicates; precomputing the
@@ -436,7 +439,8 @@ static lfem_status dalloc(T** p, int64_t n) {
 __global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ tile_row0,
                              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ inc_ptr,
                              const int32_t* __restrict__ tile_elem_ptr, const int32_t* __restrict__ tile_elem,
-                             int entb, int32_t* __restrict__ tmp_nodes, int32_t* __restrict__ n_nodes_out,
+                             int entb, const int32_t* __restrict__ nl_in, const int32_t* __restrict__ nle_in,
+                             int32_t* __restrict__ tmp_nodes, int32_t* __restrict__ n_nodes_out,
                              int64_t* __restrict__ bytes_out) {
   extern __shared__ int32_t sn[];
   __shared__ int32_t wsum[32];
@@ -479,9 +483,50 @@ __global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const in
   if (threadIdx.x == 0) {
     const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
     const int ns = (int)(row_ptr[r1] - row_ptr[r0]);
-    const int nent = (inc_ptr[r1] - inc_ptr[r0]) * ref;
     n_nodes_out[t] = total;
-    bytes_out[t] = tile_layout(nel, ns, nent, total, ref, entb).total;
+    bytes_out[t] = tile_layout(nel, ns, nl_in[t], nle_in[t], total, ref, entb).total;
+  }
+}
+
+// Contributions of slot j of a row: local pairs (incidence k, node b) of the
+// row's incidences kb..ke whose column position is j.
+template <typename PosT>
+__device__ __forceinline__ int slot_count(const PosT* __restrict__ inc_pos, int ps, int ref, int kb, int ke, int j) {
+  int c = 0;
+  for (int k = kb; k < ke; ++k)
+    for (int b = 0; b < ref; ++b) c += ((int)inc_pos[(int64_t)k * ps + b] == j);
+  return c;
+}
+
+// Per tile: number of slots with more than two contributions and their entries.
+template <typename PosT>
+__global__ void k_tile_long(int ref, const int32_t* __restrict__ tile_row0, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ inc_ptr, const PosT* __restrict__ inc_pos,
+                            int32_t* __restrict__ nl_out, int32_t* __restrict__ nle_out) {
+  __shared__ int s_nl, s_nle;
+  const int t = blockIdx.x;
+  if (threadIdx.x == 0) s_nl = s_nle = 0;
+  __syncthreads();
+  const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
+  const int ps = pos_stride(ref);
+  int nl = 0, nle = 0;
+  for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) {
+    const int kb = inc_ptr[r], ke = inc_ptr[r + 1];
+    const int len = (int)(row_ptr[r + 1] - row_ptr[r]);
+    for (int j = 0; j < len; ++j) {
+      const int c = slot_count(inc_pos, ps, ref, kb, ke, j);
+      if (c > 2) {
+        ++nl;
+        nle += c;
+      }
+    }
+  }
+  atomicAdd(&s_nl, nl);
+  atomicAdd(&s_nle, nle);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    nl_out[t] = s_nl;
+    nle_out[t] = s_nle;
   }
 }
 
@@ -495,7 +540,9 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
                             const uint16_t* __restrict__ inc_local, const PosT* __restrict__ inc_pos,
                             const int32_t* __restrict__ tile_elem_ptr, const int32_t* __restrict__ tile_elem,
                             const int32_t* __restrict__ tmp_nodes, const int32_t* __restrict__ n_nodes,
+                            const int32_t* __restrict__ nl_in, const int32_t* __restrict__ nle_in,
                             const int64_t* __restrict__ off, int entb, uint8_t* __restrict__ meta) {
+  __shared__ int s_nl, s_nle;
   const int t = blockIdx.x;
   const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
   const int32_t i0 = inc_ptr[r0];
@@ -509,8 +556,10 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
   const int U = ref * (ref + 1) / 2;
   const int ps = pos_stride(ref);
   uint8_t* blk = meta + off[t];
-  const TileLayout L = tile_layout(nel, ns, nent, nn, ref, entb);
+  const int nl_t = nl_in[t], nle_t = nle_in[t];
+  const TileLayout L = tile_layout(nel, ns, nl_t, nle_t, nn, ref, entb);
   for (int i = threadIdx.x; i < L.total / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(blk)[i] = 0u;
+  if (threadIdx.x == 0) s_nl = s_nle = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     TileHdr h;
@@ -521,13 +570,17 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
     h.nent = nent;
     h.nel = nel;
     h.nnodes = nn;
+    h.nl = nl_t;
+    h.nle = nle_t;
+    h.pad[0] = h.pad[1] = 0;
     *reinterpret_cast<TileHdr*>(blk) = h;
   }
   int32_t* el = reinterpret_cast<int32_t*>(blk + L.elem);
   int32_t* nd = reinterpret_cast<int32_t*>(blk + L.nodes);
   uint16_t* en = reinterpret_cast<uint16_t*>(blk + L.enodes);
-  uint16_t* so = reinterpret_cast<uint16_t*>(blk + L.soff);
-  uint8_t* se = blk + L.sent;
+  uint8_t* pr = blk + L.pair;
+  int4* lrec = reinterpret_cast<int4*>(blk + L.lrec);
+  uint8_t* lent = blk + L.lent;
   for (int i = threadIdx.x; i < nel; i += blockDim.x) el[i] = tile_elem[e0 + i];
   const int32_t* tn = tmp_nodes + (int64_t)e0 * ref;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nd[i] = tn[i];
@@ -541,14 +594,31 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
     }
     en[i] = (uint16_t)lo;
   }
-  // contribution lists, one thread per row
+  const uint32_t NONE = entb == 2 ? 0xFFFFu : 0xFFFFFFFFu;
+  auto put = [&](uint8_t* base, int64_t i, uint32_t v) {
+    if (entb == 2) reinterpret_cast<uint16_t*>(base)[i] = (uint16_t)v;
+    else reinterpret_cast<uint32_t*>(base)[i] = v;
+  };
+  // contribution lists, one thread per row; slots with one or two entries go
+  // to the pair array, longer lists to the long list (its order is the order
+  // the threads claim places in it; each run keeps ascending (e, a, b))
   for (int rl = threadIdx.x; rl < nrows; rl += blockDim.x) {
     const int r = r0 + rl;
     const int kb = inc_ptr[r], ke = inc_ptr[r + 1];
     const int slot0 = (int)(row_ptr[r] - s0), len = (int)(row_ptr[r + 1] - row_ptr[r]);
-    int run = (kb - i0) * ref;
     for (int j = 0; j < len; ++j) {
-      so[slot0 + j] = (uint16_t)run;
+      const int c = slot_count(inc_pos, ps, ref, kb, ke, j);
+      const int slot = slot0 + j;
+      int w = 0, lbeg = 0;
+      if (c > 2) {
+        const int li = atomicAdd(&s_nl, 1);
+        lbeg = atomicAdd(&s_nle, c);
+        if (li < nl_t && lbeg + c <= nle_t) lrec[li] = make_int4(slot, lbeg, lbeg + c, 0);
+        put(pr, 2ll * slot, NONE);
+        put(pr, 2ll * slot + 1, NONE);
+      } else {
+        put(pr, 2ll * slot + 1, NONE);
+      }
       for (int k = kb; k < ke; ++k) {
         const int lk = inc_local[k];
         const int a = lk & 15, loc = lk >> 4;
@@ -556,14 +626,16 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
           if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
           const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
           const uint32_t ent = (uint32_t)loc * (uint32_t)U + (uint32_t)u;
-          if (entb == 2) reinterpret_cast<uint16_t*>(se)[run] = (uint16_t)ent;
-          else reinterpret_cast<uint32_t*>(se)[run] = ent;
-          ++run;
+          if (c > 2) {
+            if (lbeg + w < nle_t) put(lent, lbeg + w, ent);
+          } else {
+            put(pr, 2ll * slot + w, ent);
+          }
+          ++w;
         }
       }
     }
   }
-  if (threadIdx.x == 0) so[ns] = (uint16_t)nent;
 }
 
 __global__ void k_max_i64(const int64_t* __restrict__ a, int64_t n, int64_t* __restrict__ out) {
@@ -590,21 +662,30 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   int32_t mnel = 0;
   for (int64_t t = 0; t < T; ++t) mnel = std::max(mnel, hep[t + 1] - hep[t]);
   // entries are local-matrix word offsets e * U + u
-  const int entb = std::max((int64_t)mnel * (ref * (ref + 1) / 2) <= 65536 ? 2 : 4, p->min_ent_bytes);
-  int32_t *tmp_nodes = nullptr, *nn = nullptr;
+  // (all ones marks an absent entry, so two-byte entries stay below 0xFFFF)
+  const int entb = std::max((int64_t)mnel * (ref * (ref + 1) / 2) < 65535 ? 2 : 4, p->min_ent_bytes);
+  int32_t *tmp_nodes = nullptr, *nn = nullptr, *nl = nullptr, *nle = nullptr;
   int64_t *bytes = nullptr, *scr = nullptr, *mx = nullptr;
   TRY(dalloc(&tmp_nodes, p->tile_elems_total * ref));
   TRY(dalloc(&nn, T + 1));
+  TRY(dalloc(&nl, T + 1));
+  TRY(dalloc(&nle, T + 1));
   TRY(dalloc(&bytes, T + 1));
   TRY(dalloc(&mx, 4));
   TRY(dalloc(&scr, scan_scratch_bytes(T, 8) / 8));
   TRY(dalloc(&d.tile_meta_off, T + 1));
   LFEM_CUDA(cudaMemsetAsync(mx, 0, 4 * sizeof(int64_t), st));
   if (T > 0) {
+    if (p->pos_bytes == 1)
+      k_tile_long<uint8_t><<<(unsigned)T, 128, 0, st>>>(ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.inc_pos, nl, nle);
+    else
+      k_tile_long<uint16_t><<<(unsigned)T, 128, 0, st>>>(ref, d.tile_row0, d.row_ptr, d.inc_ptr,
+                                                          (const uint16_t*)d.inc_pos, nl, nle);
+    LFEM_CUDA(cudaGetLastError());
     const size_t smem = sizeof(int32_t) * kMaxTileEntries;
     LFEM_CUDA(cudaFuncSetAttribute(k_tile_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_tile_nodes<<<(unsigned)T, 512, smem, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.tile_elem_ptr,
-                                                 d.tile_elem, entb, tmp_nodes, nn, bytes);
+                                                 d.tile_elem, entb, nl, nle, tmp_nodes, nn, bytes);
     LFEM_CUDA(cudaGetLastError());
   }
   scan_exclusive<int64_t, int64_t>(bytes, d.tile_meta_off, T, scr, st);
@@ -621,11 +702,11 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
     if (p->pos_bytes == 1)
       k_tile_fill<uint8_t><<<(unsigned)T, 128, 0, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.inc_local,
                                                          d.inc_pos, d.tile_elem_ptr, d.tile_elem, tmp_nodes, nn,
-                                                         d.tile_meta_off, entb, d.tile_meta);
+                                                         nl, nle, d.tile_meta_off, entb, d.tile_meta);
     else
       k_tile_fill<uint16_t><<<(unsigned)T, 128, 0, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr,
                                                           d.inc_local, (const uint16_t*)d.inc_pos, d.tile_elem_ptr,
-                                                          d.tile_elem, tmp_nodes, nn, d.tile_meta_off, entb,
+                                                          d.tile_elem, tmp_nodes, nn, nl, nle, d.tile_meta_off, entb,
                                                           d.tile_meta);
     LFEM_CUDA(cudaGetLastError());
   }
@@ -640,6 +721,8 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   p->ent_bytes = entb;
   cudaFree(tmp_nodes);
   cudaFree(nn);
+  cudaFree(nl);
+  cudaFree(nle);
   cudaFree(bytes);
   cudaFree(mx);
   cudaFree(scr);
