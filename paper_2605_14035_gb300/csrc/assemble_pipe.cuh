@@ -204,6 +204,11 @@ __device__ __forceinline__ void load_pos_smem(const uint8_t* base, int k, int (&
   }
 }
 
+// Store to global memory by an explicitly global address (a generic store
+// could alias shared memory and would pin later shared loads behind it).
+__device__ __forceinline__ void st_global(float* p, float v) { __stcg(p, v); }
+__device__ __forceinline__ void st_global(double* p, double v) { __stcg(p, v); }
+
 // Issue the gathers of a tile's node coordinates and element coefficients.
 __device__ __forceinline__ void issue_gathers(const MeshRec& mr, bool want_coef, const uint8_t* meta,
                                               double* nodes_dst, void* coef_dst) {
@@ -216,7 +221,8 @@ __device__ __forceinline__ void issue_gathers(const MeshRec& mr, bool want_coef,
     const double* src = mr.coords + (int64_t)nd[v] * na;
     for (int c = 0; c < na; ++c) cp_async8(nodes_dst + v * na + c, src + c);
   }
-  if (want_coef) {
+  // compile-time-rule tiles read their coefficients straight from global memory
+  if (want_coef && mr.type < kFastTypeOffset) {
     const int q = mr.tab.q;
     const int32_t* el = reinterpret_cast<const int32_t*>(meta + L.elem);
     for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
@@ -370,6 +376,11 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
                                                    float* dst, int mstride, bool& keep) {
   using L = FastLayout<D, P>;
   constexpr int Q = L::Q;
+  float cq[Q];
+  if (which & LFEM_CMASS) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cq[q] = cs ? __ldg(cs + q) : (float)__ldg(cd + q);
+  }
   float sq[Q], hq[Q][L::NK];
   geometry_fast<D, NA, P>(ed, bank, qthr, sq, hq, keep);
   int slot = 0;
@@ -378,7 +389,7 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
   if (which & LFEM_CMASS) {
     float sc[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sc[q] = sq[q] * (cs ? cs[q] : (float)cd[q]);
+    for (int q = 0; q < Q; ++q) sc[q] = sq[q] * cq[q];
     contract_mass<D, P>(bank, sc, dst + mstride * slot);
   }
 }
@@ -430,8 +441,10 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
       if (jt < h.nel) {
         ElemData<D, NA, P, float> ed;
         element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), t_en + (size_t)jt * REF, ed);
-        const float* cs = coef_bytes == 4 ? static_cast<const float*>(coef_s) + (size_t)jt * Q : nullptr;
-        const double* cd = coef_bytes == 8 ? static_cast<const double*>(coef_s) + (size_t)jt * Q : nullptr;
+        // coefficients of the element from global memory (loaded first, used last)
+        const int64_t cg = (int64_t)t_elem[jt] * Q;
+        const float* cs = coef_bytes == 4 ? static_cast<const float*>(mr.coef) + cg : nullptr;
+        const double* cd = coef_bytes == 8 ? static_cast<const double*>(mr.coef) + cg : nullptr;
         bool keep = true;
         element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * U,
                                      mstride, keep);
@@ -518,6 +531,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
     const R* l1 = lsm + mstride;
     const R* l2 = lsm + 2 * mstride;
+#pragma unroll 2
     for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
       const EntT x = t_pair[2 * s], y = t_pair[2 * s + 1];
       if (x == NONE) continue;
@@ -527,9 +541,9 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         if (nm > 1) v1 += l1[y];
         if (nm > 2) v2 += l2[y];
       }
-      o0[s] = v0;
-      if (nm > 1) o1[s] = v1;
-      if (nm > 2) o2[s] = v2;
+      st_global(o0 + s, v0);
+      if (nm > 1) st_global(o1 + s, v1);
+      if (nm > 2) st_global(o2 + s, v2);
     }
     for (int j = threadIdx.x; j < h.nl; j += blockDim.x) {
       const int4 r = t_lrec[j];
@@ -544,9 +558,9 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         if (nm > 1) acc_add(c1, l1[ent]);
         if (nm > 2) acc_add(c2, l2[ent]);
       }
-      o0[r.x] = (R)acc_final(c0);
-      if (nm > 1) o1[r.x] = (R)acc_final(c1);
-      if (nm > 2) o2[r.x] = (R)acc_final(c2);
+      st_global(o0 + r.x, (R)acc_final(c0));
+      if (nm > 1) st_global(o1 + r.x, (R)acc_final(c1));
+      if (nm > 2) st_global(o2 + r.x, (R)acc_final(c2));
     }
   }
 }
