@@ -22,9 +22,12 @@ lfem_status run_pipe_d3(int NA, int P, bool mixed, const PipeArgs& a, int ent_by
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }
 
-lfem_status run_twopass_d3(int P, bool mixed, const TwoPassArgs& a, int sms, cudaStream_t st) {
-  if (P == 1) return mixed ? launch_twopass<3, 3, 1, float>(a, sms, st) : launch_twopass<3, 3, 1, double>(a, sms, st);
-  if (P == 2) return mixed ? launch_twopass<3, 3, 2, float>(a, sms, st) : launch_twopass<3, 3, 2, double>(a, sms, st);
+lfem_status run_twopass_d3(int P, bool mixed, bool fast, const FastBankTet& fb, const TwoPassArgs& a, int sms,
+                           cudaStream_t st) {
+  if (P == 1)
+    return mixed ? launch_twopass<3, 3, 1, float>(a, fast, fb, sms, st) : launch_twopass<3, 3, 1, double>(a, false, fb, sms, st);
+  if (P == 2)
+    return mixed ? launch_twopass<3, 3, 2, float>(a, fast, fb, sms, st) : launch_twopass<3, 3, 2, double>(a, false, fb, sms, st);
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }
 

@@ -15,6 +15,7 @@
 //   M_u  += s TM,   MC_u += s c_q TM,   A_u += sum_kk Hh_kk TA[kk].
 #pragma once
 
+#include "lfem.h"
 #include "lfem_internal.cuh"
 
 namespace lfem {
@@ -25,17 +26,24 @@ struct FastQ {
   static constexpr int Q = D == 1 ? 3 : (D == 2 ? (P == 1 ? 3 : 7) : (P == 1 ? 4 : 14));
 };
 
+// Per point: DPSI, TM, then for curves and triangles TA; for tetrahedra the
+// stiffness table would outgrow the constant cache (55 x 6 per point), so they
+// keep the reference gradients DPHI[q][b][m] and the weight w_q instead and
+// accumulate point by point.
 template <int D, int P>
 struct FastLayout {
   static constexpr int Q = FastQ<D, P>::Q;
+  static constexpr int REF = Ref<D, P>::REF;
   static constexpr int U = Ref<D, P>::U;
   static constexpr int NE = Ref<D, P>::NE;
   static constexpr int NK = D * (D + 1) / 2;
-  static constexpr int PER_Q = NE * D + U + NK * U;
+  static constexpr int PER_Q = NE * D + U + (D == 3 ? REF * D + 1 : NK * U);
   static constexpr int SIZE = Q * PER_Q;
   static constexpr int dpsi(int q, int k, int m) { return q * PER_Q + k * D + m; }
   static constexpr int tm(int q, int u) { return q * PER_Q + NE * D + u; }
   static constexpr int ta(int q, int kk, int u) { return q * PER_Q + NE * D + U + kk * U + u; }
+  static constexpr int dphi(int q, int b, int m) { return q * PER_Q + NE * D + U + b * D + m; }
+  static constexpr int w(int q) { return q * PER_Q + NE * D + U + REF * D; }
 };
 
 // One table per (D, P) of curves and triangles, at fixed offsets.
@@ -198,4 +206,155 @@ __device__ __forceinline__ void contract_stiff(const Bank& bank,
   }
 }
 
+// Tetrahedra, stiffness point by point: Hw = w_q adj(G) / s from the
+// cofactors of J, y_b = Hw grad phi_b, A_ab += grad phi_a . y_b; also the
+// conditioning test of every point.
+template <int NA, int P, typename Bank>
+__device__ __forceinline__ void stiff_tet_fast(const ElemData<3, NA, P, float>& ed, const Bank& bank, float qthr,
+                                               float* dst, bool& keep) {
+  using L = FastLayout<3, P>;
+  constexpr int REF = L::REF, U = L::U, NE = L::NE, Q = L::Q;
+  constexpr int OFF = Bank::template off<3, P>();
+  const float* tv = bank.v;
+  const float lim = fmaxf(qthr, 1e-12f);
+  float Ao[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) Ao[u] = 0.f;
+  // the point loop stays rolled: unrolled, 14 points of 10 x 10 gradient
+  // products outgrow the instruction cache (the table reads are then uniform
+  // constant-cache loads)
+#pragma unroll 1
+  for (int q = 0; q < Q; ++q) {
+    float J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float acc = ed.e[m][i];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) acc = fmaf(ed.dl[k][i], tv[OFF + L::dpsi(q, k, m)], acc);
+        J[i][m] = acc;
+      }
+    float c[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+      c[m][0] = dif_prod(J[1][m1], J[2][m2], J[2][m1], J[1][m2]);
+      c[m][1] = dif_prod(J[2][m1], J[0][m2], J[0][m1], J[2][m2]);
+      c[m][2] = dif_prod(J[0][m1], J[1][m2], J[1][m1], J[0][m2]);
+    }
+    const float det = fmaf(J[2][0], c[0][2], fmaf(J[1][0], c[0][1], __fmul_rn(J[0][0], c[0][0])));
+    const float winv = __fdividef(tv[OFF + L::w(q)], fabsf(det));
+    float H[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = m; n < 3; ++n)
+        H[m][n] = H[n][m] =
+            __fmul_rn(fmaf(c[m][2], c[n][2], fmaf(c[m][1], c[n][1], __fmul_rn(c[m][0], c[n][0]))), winv);
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) tr = fmaf(J[i][m], J[i][m], tr);
+    tr *= (1.0f / 3.0f);
+    const float s2 = __fmul_rn(det, det);
+    keep &= (s2 > lim * (tr * tr * tr)) & (s2 <= 3.0e38f);
+#pragma unroll
+    for (int b = 0; b < REF; ++b) {
+      float y[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+        y[m] = fmaf(H[m][2], tv[OFF + L::dphi(q, b, 2)],
+                    fmaf(H[m][1], tv[OFF + L::dphi(q, b, 1)], __fmul_rn(H[m][0], tv[OFF + L::dphi(q, b, 0)])));
+#pragma unroll
+      for (int a = 0; a <= b; ++a) {
+        const int u = upper_index(REF, a, b);
+        float acc = Ao[u];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc = fmaf(tv[OFF + L::dphi(q, a, m)], y[m], acc);
+        Ao[u] = acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) dst[u] = Ao[u];
+}
+
+// Tetrahedra, |det J| at every point (mass-type matrices) and the test.
+template <int NA, int P, typename Bank>
+__device__ __forceinline__ void jac_tet_fast(const ElemData<3, NA, P, float>& ed, const Bank& bank, float qthr,
+                                             float (&sq)[FastLayout<3, P>::Q], bool& keep) {
+  using L = FastLayout<3, P>;
+  constexpr int NE = L::NE, Q = L::Q;
+  constexpr int OFF = Bank::template off<3, P>();
+  const float* tv = bank.v;
+  const float lim = fmaxf(qthr, 1e-12f);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float acc = ed.e[m][i];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) acc = fmaf(ed.dl[k][i], tv[OFF + L::dpsi(q, k, m)], acc);
+        J[i][m] = acc;
+      }
+    const float c0 = dif_prod(J[1][1], J[2][2], J[2][1], J[1][2]);
+    const float c1 = dif_prod(J[2][1], J[0][2], J[0][1], J[2][2]);
+    const float c2 = dif_prod(J[0][1], J[1][2], J[1][1], J[0][2]);
+    const float det = fmaf(J[2][0], c2, fmaf(J[1][0], c1, __fmul_rn(J[0][0], c0)));
+    sq[q] = fabsf(det);
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) tr = fmaf(J[i][m], J[i][m], tr);
+    tr *= (1.0f / 3.0f);
+    const float s2 = __fmul_rn(det, det);
+    keep &= (s2 > lim * (tr * tr * tr)) & (s2 <= 3.0e38f);
+  }
+}
+
+// Local matrices of one element with the compile-time rule, stored (upper
+// layout, requested matrices in the order M, A, MC): the geometry of every
+// point first (a few values per point), then each output entry as one
+// contraction with the tables.
+template <int D, int NA, int P, typename Bank>
+__device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, float>& ed, const Bank& bank,
+                                                   const float* cs, const double* cd, float qthr, unsigned which,
+                                                   float* dst, int mstride, bool& keep) {
+  using L = FastLayout<D, P>;
+  constexpr int Q = L::Q;
+  float cq[Q];
+  if (which & LFEM_CMASS) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cq[q] = cs ? __ldg(cs + q) : (float)__ldg(cd + q);
+  }
+  float sq[Q];
+  int slot = 0;
+  if constexpr (D == 3) {
+    if (which & (LFEM_MASS | LFEM_CMASS)) jac_tet_fast<NA, P>(ed, bank, qthr, sq, keep);
+    if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
+    if (which & LFEM_STIFF) stiff_tet_fast<NA, P>(ed, bank, qthr, dst + mstride * slot++, keep);
+  } else {
+    float hq[Q][L::NK];
+    geometry_fast<D, NA, P>(ed, bank, qthr, sq, hq, keep);
+    if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
+    if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + mstride * slot++);
+  }
+  if (which & LFEM_CMASS) {
+    float sc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sc[q] = sq[q] * cq[q];
+    contract_mass<D, P>(bank, sc, dst + mstride * slot);
+  }
+}
+
+
+// Everything done for one tile whose block, node coordinates and coefficients
+// are in shared memory: split, phase 1 (+ the double fallback), the prefetch
+// hook of the next item after the first phase-1 round, phase 2.
 }  // namespace lfem

@@ -366,38 +366,6 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   }
 }
 
-// Local matrices of one element with the compile-time rule, stored (upper
-// layout, requested matrices in the order M, A, MC): the geometry of every
-// point first (a few values per point), then each output entry as one
-// contraction with the tables.
-template <int D, int NA, int P, typename Bank>
-__device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, float>& ed, const Bank& bank,
-                                                   const float* cs, const double* cd, float qthr, unsigned which,
-                                                   float* dst, int mstride, bool& keep) {
-  using L = FastLayout<D, P>;
-  constexpr int Q = L::Q;
-  float cq[Q];
-  if (which & LFEM_CMASS) {
-#pragma unroll
-    for (int q = 0; q < Q; ++q) cq[q] = cs ? __ldg(cs + q) : (float)__ldg(cd + q);
-  }
-  float sq[Q], hq[Q][L::NK];
-  geometry_fast<D, NA, P>(ed, bank, qthr, sq, hq, keep);
-  int slot = 0;
-  if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
-  if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + mstride * slot++);
-  if (which & LFEM_CMASS) {
-    float sc[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) sc[q] = sq[q] * cq[q];
-    contract_mass<D, P>(bank, sc, dst + mstride * slot);
-  }
-}
-
-
-// Everything done for one tile whose block, node coordinates and coefficients
-// are in shared memory: split, phase 1 (+ the double fallback), the prefetch
-// hook of the next item after the first phase-1 round, phase 2.
 template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
 __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
                                              const void* coef_s, R* lsm, uint8_t* flag, const FastBank& fb,

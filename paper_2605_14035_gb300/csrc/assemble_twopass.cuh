@@ -12,6 +12,7 @@
 // Deterministic and atomic-free like the tiled path.
 #pragma once
 
+#include "assemble_fast.cuh"
 #include "assemble_impl.cuh"
 
 namespace lfem {
@@ -62,8 +63,9 @@ __device__ __forceinline__ void element_lean(const ElemData<D, NA, P, R>& ed, co
   }
 }
 
-template <int D, int NA, int P, typename R>
-__global__ void __launch_bounds__(128) k_elem_local(const TwoPassArgs a) {
+// FAST: the rule is the compile-time one (float only; tables in fb).
+template <int D, int NA, int P, typename R, bool FAST>
+__global__ void __launch_bounds__(128) k_elem_local(const TwoPassArgs a, const __grid_constant__ FastBankTet fb) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   const TabView<R> tb = tab_view<D, P, R>(a.tab);
@@ -76,7 +78,19 @@ __global__ void __launch_bounds__(128) k_elem_local(const TwoPassArgs a) {
     R* dst = lb + (size_t)e * a.nm * U;
     R qual = (R)1;
     bool bad = false;
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (FAST && sizeof(R) == 4) {
+      ElemData<D, NA, P, float> ed;
+      const bool ok = load_element_data_split<D, NA, P>(a.coords, nodes, ed);
+      constexpr int Q = FastLayout<D, P>::Q;
+      const float* cs = (a.which & LFEM_CMASS) && a.coef_f32 ? static_cast<const float*>(a.coef) + e * Q : nullptr;
+      const double* cd = (a.which & LFEM_CMASS) && !a.coef_f32 ? static_cast<const double*>(a.coef) + e * Q : nullptr;
+      bool keep = true;
+      element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, dst, U, keep);
+      if (!ok || !keep) {
+        element_fp64_lean<D, NA, P, float>(a.coords, nodes, a.tab, a.coef, a.coef_f32, e, a.which, dst, U, bad);
+        atomicAdd(a.fallback, 1ull);
+      }
+    } else if constexpr (sizeof(R) == 4) {
       ElemData<D, NA, P, float> ed;
       const bool ok = load_element_data_split<D, NA, P>(a.coords, nodes, ed);
       element_lean<D, NA, P, float, float>(ed, tb, a.coef, a.coef_f32, e, a.which, dst, qual, bad);
@@ -122,12 +136,19 @@ __global__ void __launch_bounds__(256) k_slot_gather(const TwoPassArgs a) {
 }
 
 template <int D, int NA, int P, typename R>
-lfem_status launch_twopass(const TwoPassArgs& a, int sm_count, cudaStream_t st) {
+lfem_status launch_twopass(const TwoPassArgs& a, bool fast, const FastBankTet& fb, int sm_count, cudaStream_t st) {
   constexpr int U = Ref<D, P>::U;
   if (a.n_elem > 0) {
     int64_t g = (a.n_elem + 127) / 128;
     if (g > (int64_t)sm_count * 32) g = (int64_t)sm_count * 32;
-    k_elem_local<D, NA, P, R><<<(unsigned)g, 128, 0, st>>>(a);
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+      if (fast) {
+        k_elem_local<D, NA, P, R, true><<<(unsigned)g, 128, 0, st>>>(a, fb);
+        done = true;
+      }
+    }
+    if (!done) k_elem_local<D, NA, P, R, false><<<(unsigned)g, 128, 0, st>>>(a, fb);
     LFEM_CUDA(cudaGetLastError());
   }
   if (a.nnz > 0) {

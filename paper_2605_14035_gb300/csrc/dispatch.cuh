@@ -18,7 +18,8 @@ namespace lfem {
 LFEM_DECLARE_DIM(1)
 LFEM_DECLARE_DIM(2)
 LFEM_DECLARE_DIM(3)
-lfem_status run_twopass_d3(int P, bool mixed, const TwoPassArgs& a, int sms, cudaStream_t st);
+lfem_status run_twopass_d3(int P, bool mixed, bool fast, const FastBankTet& fb, const TwoPassArgs& a, int sms,
+                           cudaStream_t st);
 lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset);
 
 // Body of one dimension's dispatch functions over (NA, P).

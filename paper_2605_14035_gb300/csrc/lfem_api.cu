@@ -95,7 +95,7 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
   const double* phi = w + Q;
   const double* dphi = phi + Q * REF;
   const double* dpsi = dphi + Q * REF * dim;
-  const int per_q = NE * dim + U + NK * U;
+  const int per_q = NE * dim + U + (dim == 3 ? REF * dim + 1 : NK * U);
   for (int q = 0; q < Q; ++q) {
     float* d = dst + (size_t)q * per_q;
     for (int k = 0; k < NE; ++k)
@@ -106,6 +106,7 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
       for (int b = a; b < REF; ++b) {
         const int u = upper_index(REF, a, b);
         tm[u] = (float)(w[q] * phi[q * REF + a] * phi[q * REF + b]);
+        if (dim == 3) continue;
         const double* ga = dphi + (q * REF + a) * dim;
         const double* gb = dphi + (q * REF + b) * dim;
         int kk = 0;
@@ -113,6 +114,12 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
           for (int n = m; n < dim; ++n, ++kk)
             ta[kk * U + u] = (float)(m == n ? w[q] * ga[m] * gb[m] : w[q] * (ga[m] * gb[n] + ga[n] * gb[m]));
       }
+    if (dim == 3) {
+      // tetrahedra: reference gradients and the weight (point-by-point stiffness)
+      for (int b = 0; b < REF; ++b)
+        for (int m = 0; m < dim; ++m) ta[b * dim + m] = (float)dphi[(q * REF + b) * dim + m];
+      ta[REF * dim] = (float)w[q];
+    }
   }
   return true;
 }
@@ -395,7 +402,10 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
     int sms3 = 0;
     LFEM_CUDA(cudaDeviceGetAttribute(&sms3, cudaDevAttrMultiProcessorCount, p->device));
     if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
-    return run_twopass_d3(p->order, mixed, ta, sms3, st);
+    FastBankTet fbt;
+    const bool fast3 = mixed && fast_tables_host(3, p->order, quad, fbt.v + (p->order == 1 ? FastBankTet::OFF31
+                                                                                          : FastBankTet::OFF32));
+    return run_twopass_d3(p->order, mixed, fast3, fbt, ta, sms3, st);
   }
   // persistent pipelined kernel: a lane pair per element, so 96 (float) or
   // 128 (double) elements per phase-1 round; all of a tile's local matrices
