@@ -26,10 +26,11 @@ struct FastQ {
   static constexpr int Q = D == 1 ? 3 : (D == 2 ? (P == 1 ? 3 : 7) : (P == 1 ? 4 : 14));
 };
 
-// Per point: DPSI, TM, then for curves and triangles TA; for tetrahedra the
-// stiffness table would outgrow the constant cache (55 x 6 per point), so they
-// keep the reference gradients DPHI[q][b][m] and the weight w_q instead and
-// accumulate point by point.
+// Per point: DPSI, TM, then for curves TA; triangles and tetrahedra keep the
+// reference gradients DPHI[q][b][m] and the weight w_q instead and accumulate
+// the stiffness point by point (triangles in a form whose rounding grows with
+// sqrt(cond G) rather than cond G; for tetrahedra a product table would also
+// outgrow the constant cache).
 template <int D, int P>
 struct FastLayout {
   static constexpr int Q = FastQ<D, P>::Q;
@@ -37,7 +38,7 @@ struct FastLayout {
   static constexpr int U = Ref<D, P>::U;
   static constexpr int NE = Ref<D, P>::NE;
   static constexpr int NK = D * (D + 1) / 2;
-  static constexpr int PER_Q = NE * D + U + (D == 3 ? REF * D + 1 : NK * U);
+  static constexpr int PER_Q = NE * D + U + (D >= 2 ? REF * D + 1 : NK * U);
   static constexpr int SIZE = Q * PER_Q;
   static constexpr int dpsi(int q, int k, int m) { return q * PER_Q + k * D + m; }
   static constexpr int tm(int q, int u) { return q * PER_Q + NE * D + u; }
@@ -80,93 +81,111 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst);
 // inlines it: implicit multiply-add contraction may differ between contexts)
 __device__ __forceinline__ float dif_prod(float a, float b, float c, float d) { return fmaf(a, b, -__fmul_rn(c, d)); }
 
-// Geometry of one element at every point of the compile-time rule: s_q and
-// Hh_q = adj(G_q) / s_q (the weight sits in the tables).  keep = false when
-// some point fails the conditioning / finiteness test (the element is then
-// redone in double by the caller).
-template <int D, int NA, int P, typename Bank>
-__device__ __forceinline__ void geometry_fast(const ElemData<D, NA, P, float>& ed, const Bank& bank, float qthr,
-                                              float (&sq)[FastLayout<D, P>::Q],
-                                              float (&hq)[FastLayout<D, P>::Q][FastLayout<D, P>::NK], bool& keep) {
-  using L = FastLayout<D, P>;
+// Curves: s_q = |t| and Hh_q = 1 / s_q at every point of the compile-time rule
+// (the weight sits in the tables); keep = false on a zero or non-finite
+// length (the element is then redone in double by the caller).
+template <int NA, int P, typename Bank>
+__device__ __forceinline__ void curve_fast(const ElemData<1, NA, P, float>& ed, const Bank& bank,
+                                           float (&sq)[FastLayout<1, P>::Q], float (&hq)[FastLayout<1, P>::Q][1],
+                                           bool& keep) {
+  using L = FastLayout<1, P>;
   constexpr int NE = L::NE, Q = L::Q;
-  constexpr int OFF = Bank::template off<D, P>();
+  constexpr int OFF = Bank::template off<1, P>();
+  const float* tv = bank.v;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float t[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      float acc = ed.e[0][i];
+#pragma unroll
+      for (int k = 0; k < NE; ++k) acc = fmaf(ed.dl[k][i], tv[OFF + L::dpsi(q, k, 0)], acc);
+      t[i] = acc;
+    }
+    float tt = 0.f;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) tt = fmaf(t[i], t[i], tt);
+    const float inv = rsqrtf(tt);
+    sq[q] = tt * inv;
+    hq[q][0] = inv;
+    keep &= (tt > 0.f) & (tt <= 3.0e38f);
+  }
+}
+
+// Triangles (surface or plane): s_q at every point and, when asked, the
+// stiffness accumulated point by point.  With J = Q R (R upper triangular:
+// r11 = |t1|, r12 = t1.t2 / r11, r22 = s / r11), grad^T G^{-1} grad =
+// |R^{-T} grad|^2, so A_ab += y_a . y_b with
+//   y_b = sqrt(w s) R^{-T} grad phi_b = (c1 g_b1, c2 g_b2 - c3 g_b1),
+//   c1 = sqrt(w s) / r11, c2 = sqrt(w s) r11 / s, c3 = sqrt(w s) g12 / (r11 s):
+// every term of the sum is a product of two well-scaled factors, so rounding
+// grows with cond(R) = sqrt(cond G) (the adj(G) form grows with cond G).
+template <int NA, int P, typename Bank>
+__device__ __forceinline__ void tri_fast(const ElemData<2, NA, P, float>& ed, const Bank& bank, float qthr,
+                                         bool do_a, float (&sq)[FastLayout<2, P>::Q], float (&Ao)[Ref<2, P>::U],
+                                         bool& keep) {
+  using L = FastLayout<2, P>;
+  constexpr int REF = L::REF, NE = L::NE, Q = L::Q, U = L::U;
+  constexpr int OFF = Bank::template off<2, P>();
   const float* tv = bank.v;
   const float lim = fmaxf(qthr, 1e-12f);
 #pragma unroll
+  for (int u = 0; u < U; ++u) Ao[u] = 0.f;
+#pragma unroll
   for (int q = 0; q < Q; ++q) {
-    float J[NA][D];
+    float J[NA][2];
 #pragma unroll
     for (int i = 0; i < NA; ++i)
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
+      for (int m = 0; m < 2; ++m) {
         float acc = ed.e[m][i];
 #pragma unroll
         for (int k = 0; k < NE; ++k) acc = fmaf(ed.dl[k][i], tv[OFF + L::dpsi(q, k, m)], acc);
         J[i][m] = acc;
       }
-    if constexpr (D == 1) {
-      float tt = 0.f;
+    float g11 = 0.f, g12 = 0.f, g22 = 0.f;
 #pragma unroll
-      for (int i = 0; i < NA; ++i) tt = fmaf(J[i][0], J[i][0], tt);
-      const float inv = rsqrtf(tt);
-      sq[q] = tt * inv;
-      hq[q][0] = inv;
-      keep &= (tt > 0.f) & (tt <= 3.0e38f);
-    } else if constexpr (D == 2) {
-      float g11 = 0.f, g12 = 0.f, g22 = 0.f;
-#pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        g11 = fmaf(J[i][0], J[i][0], g11);
-        g12 = fmaf(J[i][0], J[i][1], g12);
-        g22 = fmaf(J[i][1], J[i][1], g22);
-      }
-      float s2, inv;
-      if constexpr (NA == 2) {
-        const float det = dif_prod(J[0][0], J[1][1], J[0][1], J[1][0]);
-        sq[q] = fabsf(det);
-        s2 = __fmul_rn(det, det);
-        inv = __fdividef(1.0f, sq[q]);
-      } else {
-        const float n0 = dif_prod(J[1][0], J[2][1], J[2][0], J[1][1]);
-        const float n1 = dif_prod(J[2][0], J[0][1], J[0][0], J[2][1]);
-        const float n2 = dif_prod(J[0][0], J[1][1], J[1][0], J[0][1]);
-        s2 = fmaf(n2, n2, fmaf(n1, n1, __fmul_rn(n0, n0)));
-        inv = rsqrtf(s2);
-        sq[q] = s2 * inv;
-      }
-      hq[q][0] = g22 * inv;
-      hq[q][1] = -g12 * inv;
-      hq[q][2] = g11 * inv;
-      // metric quality det G / (tr G / 2)^2 against the threshold, without a division
-      const float tr = 0.5f * (g11 + g22);
-      keep &= (s2 > lim * (tr * tr)) & (s2 <= 3.0e38f);
+    for (int i = 0; i < NA; ++i) {
+      g11 = fmaf(J[i][0], J[i][0], g11);
+      g12 = fmaf(J[i][0], J[i][1], g12);
+      g22 = fmaf(J[i][1], J[i][1], g22);
+    }
+    float s, s2;
+    if constexpr (NA == 2) {
+      const float det = dif_prod(J[0][0], J[1][1], J[0][1], J[1][0]);
+      s = fabsf(det);
+      s2 = __fmul_rn(det, det);
     } else {
-      float c[3][3];
+      const float n0 = dif_prod(J[1][0], J[2][1], J[2][0], J[1][1]);
+      const float n1 = dif_prod(J[2][0], J[0][1], J[0][0], J[2][1]);
+      const float n2 = dif_prod(J[0][0], J[1][1], J[1][0], J[0][1]);
+      s2 = fmaf(n2, n2, fmaf(n1, n1, __fmul_rn(n0, n0)));
+      s = s2 * rsqrtf(s2);
+    }
+    sq[q] = s;
+    // metric quality det G / (tr G / 2)^2 against the threshold, without a division
+    const float tr = 0.5f * (g11 + g22);
+    keep &= (s2 > lim * (tr * tr)) & (s2 <= 3.0e38f);
+    if (do_a) {
+      const float ir11 = rsqrtf(g11);
+      const float ws = tv[OFF + L::w(q)] * s;
+      const float sws = ws * rsqrtf(ws);
+      const float k = __fdividef(sws * ir11, s);
+      const float c1 = sws * ir11, c2 = k * g11, c3 = k * g12;
+      float y[REF][2];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
-        c[m][0] = dif_prod(J[1][m1], J[2][m2], J[2][m1], J[1][m2]);
-        c[m][1] = dif_prod(J[2][m1], J[0][m2], J[0][m1], J[2][m2]);
-        c[m][2] = dif_prod(J[0][m1], J[1][m2], J[1][m1], J[0][m2]);
+      for (int b = 0; b < REF; ++b) {
+        const float gb1 = tv[OFF + L::dphi(q, b, 0)], gb2 = tv[OFF + L::dphi(q, b, 1)];
+        y[b][0] = c1 * gb1;
+        y[b][1] = fmaf(c2, gb2, -__fmul_rn(c3, gb1));
       }
-      const float det = fmaf(J[2][0], c[0][2], fmaf(J[1][0], c[0][1], __fmul_rn(J[0][0], c[0][0])));
-      sq[q] = fabsf(det);
-      const float inv = __fdividef(1.0f, sq[q]);
-      int kk = 0;
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
+      for (int a = 0; a < REF; ++a)
 #pragma unroll
-        for (int n = m; n < 3; ++n)
-          hq[q][kk++] = __fmul_rn(fmaf(c[m][2], c[n][2], fmaf(c[m][1], c[n][1], __fmul_rn(c[m][0], c[n][0]))), inv);
-      float tr = 0.f;
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) tr = fmaf(J[i][m], J[i][m], tr);
-      tr *= (1.0f / 3.0f);
-      const float s2 = __fmul_rn(det, det);
-      keep &= (s2 > lim * (tr * tr * tr)) & (s2 <= 3.0e38f);
+        for (int b = a; b < REF; ++b) {
+          const int u = upper_index(REF, a, b);
+          Ao[u] = fmaf(y[a][1], y[b][1], fmaf(y[a][0], y[b][0], Ao[u]));
+        }
     }
   }
 }
@@ -339,9 +358,19 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
     if (which & (LFEM_MASS | LFEM_CMASS)) jac_tet_fast<NA, P>(ed, bank, qthr, sq, keep);
     if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
     if (which & LFEM_STIFF) stiff_tet_fast<NA, P>(ed, bank, qthr, dst + mstride * slot++, keep);
+  } else if constexpr (D == 2) {
+    float Ao[Ref<D, P>::U];
+    const bool do_a = which & LFEM_STIFF;
+    tri_fast<NA, P>(ed, bank, qthr, do_a, sq, Ao, keep);
+    if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
+    if (do_a) {
+      float* d = dst + mstride * slot++;
+#pragma unroll
+      for (int u = 0; u < Ref<D, P>::U; ++u) d[u] = Ao[u];
+    }
   } else {
     float hq[Q][L::NK];
-    geometry_fast<D, NA, P>(ed, bank, qthr, sq, hq, keep);
+    curve_fast<NA, P>(ed, bank, sq, hq, keep);
     if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
     if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + mstride * slot++);
   }
@@ -353,8 +382,4 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
   }
 }
 
-
-// Everything done for one tile whose block, node coordinates and coefficients
-// are in shared memory: split, phase 1 (+ the double fallback), the prefetch
-// hook of the next item after the first phase-1 round, phase 2.
 }  // namespace lfem

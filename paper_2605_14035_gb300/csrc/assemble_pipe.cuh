@@ -366,6 +366,9 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   }
 }
 
+// Everything done for one tile whose block, node coordinates and coefficients
+// are in shared memory: split, phase 1 (+ the double fallback), the prefetch
+// hook of the next item after the first phase-1 round, phase 2.
 template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
 __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
                                              const void* coef_s, R* lsm, uint8_t* flag, const FastBank& fb,

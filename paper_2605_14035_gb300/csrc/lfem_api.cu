@@ -95,7 +95,7 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
   const double* phi = w + Q;
   const double* dphi = phi + Q * REF;
   const double* dpsi = dphi + Q * REF * dim;
-  const int per_q = NE * dim + U + (dim == 3 ? REF * dim + 1 : NK * U);
+  const int per_q = NE * dim + U + (dim >= 2 ? REF * dim + 1 : NK * U);
   for (int q = 0; q < Q; ++q) {
     float* d = dst + (size_t)q * per_q;
     for (int k = 0; k < NE; ++k)
@@ -106,7 +106,7 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
       for (int b = a; b < REF; ++b) {
         const int u = upper_index(REF, a, b);
         tm[u] = (float)(w[q] * phi[q * REF + a] * phi[q * REF + b]);
-        if (dim == 3) continue;
+        if (dim >= 2) continue;
         const double* ga = dphi + (q * REF + a) * dim;
         const double* gb = dphi + (q * REF + b) * dim;
         int kk = 0;
@@ -114,8 +114,8 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
           for (int n = m; n < dim; ++n, ++kk)
             ta[kk * U + u] = (float)(m == n ? w[q] * ga[m] * gb[m] : w[q] * (ga[m] * gb[n] + ga[n] * gb[m]));
       }
-    if (dim == 3) {
-      // tetrahedra: reference gradients and the weight (point-by-point stiffness)
+    if (dim >= 2) {
+      // triangles, tetrahedra: reference gradients and the weight (stiffness point by point)
       for (int b = 0; b < REF; ++b)
         for (int m = 0; m < dim; ++m) ta[b * dim + m] = (float)dphi[(q * REF + b) * dim + m];
       ta[REF * dim] = (float)w[q];
