@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = "p2_perturbed_sphere_r8_M_A_MC"
-KERNEL = "k_assemble_pipe<float,u16,(2,3,2)>"
+KERNEL = "k_assemble_pipe<float,u16,EType<2,3,2,fast>>"
 
 
 def parse():
@@ -165,7 +165,8 @@ def measured_peaks():
 
 # Sources that define the timed kernel; a DRAM traffic figure taken with ncu is
 # reported only while these files are byte-identical to the captured build.
-KERNEL_SOURCES = ("assemble_pipe.cuh", "assemble_impl.cuh", "lfem_internal.cuh", "dispatch.cuh", "assemble_d2.cu")
+KERNEL_SOURCES = ("assemble_pipe.cuh", "assemble_fast.cuh", "assemble_impl.cuh", "lfem_internal.cuh", "dispatch.cuh",
+                  "assemble_d2.cu", "lfem_api.cu", "pattern.cu")
 
 
 def kernel_source_hash():
