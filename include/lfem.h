@@ -131,9 +131,10 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
 lfem_status lfem_set_launch(lfem_pattern_t p, int32_t elems_per_chunk, int32_t threads);
 
 /* Conditioning threshold of LFEM_MIXED (the precision split of the method's
- * FP32 geometry, with FP64 kept for thin elements).  An element of dimension
- * d = 2, 3 is redone in double when, at some quadrature point, its metric
- * G = J^T J may have condition number above kappa_max.  The test needs no
+ * FP32 geometry, with FP64 kept for thin elements).  The stiffness of an
+ * element of dimension d = 2, 3 is redone in double when, at some quadrature
+ * point, its metric G = J^T J may have condition number above kappa_max (the
+ * mass-type matrices need |det DF| only and stay in FP32).  The test needs no
  * eigenvalues: with q = det G / (tr G / d)^d, q >= 4 k / (1 + k)^2 implies
  * cond(G) <= k for d = 2 (equality) and d = 3 (the bound is reached when the
  * middle eigenvalue is the mean of the outer two), so elements with q below

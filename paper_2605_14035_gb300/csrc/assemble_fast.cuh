@@ -81,13 +81,21 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst);
 // inlines it: implicit multiply-add contraction may differ between contexts)
 __device__ __forceinline__ float dif_prod(float a, float b, float c, float d) { return fmaf(a, b, -__fmul_rn(c, d)); }
 
+// Outcome of the per-point tests of one element: good = every |det DF| is
+// finite and not numerically zero; cond = the metric passed the conditioning
+// threshold (only the stiffness depends on it: mass-type matrices need s only).
+struct Checks {
+  bool good = true;
+  bool cond = true;
+};
+
 // Curves: s_q = |t| and Hh_q = 1 / s_q at every point of the compile-time rule
-// (the weight sits in the tables); keep = false on a zero or non-finite
+// (the weight sits in the tables); ck.good = false on a zero or non-finite
 // length (the element is then redone in double by the caller).
 template <int NA, int P, typename Bank>
 __device__ __forceinline__ void curve_fast(const ElemData<1, NA, P, float>& ed, const Bank& bank,
                                            float (&sq)[FastLayout<1, P>::Q], float (&hq)[FastLayout<1, P>::Q][1],
-                                           bool& keep) {
+                                           Checks& ck) {
   using L = FastLayout<1, P>;
   constexpr int NE = L::NE, Q = L::Q;
   constexpr int OFF = Bank::template off<1, P>();
@@ -108,7 +116,7 @@ __device__ __forceinline__ void curve_fast(const ElemData<1, NA, P, float>& ed, 
     const float inv = rsqrtf(tt);
     sq[q] = tt * inv;
     hq[q][0] = inv;
-    keep &= (tt > 0.f) & (tt <= 3.0e38f);
+    ck.good &= (tt > 0.f) & (tt <= 3.0e38f);
   }
 }
 
@@ -123,12 +131,11 @@ __device__ __forceinline__ void curve_fast(const ElemData<1, NA, P, float>& ed, 
 template <int NA, int P, typename Bank>
 __device__ __forceinline__ void tri_fast(const ElemData<2, NA, P, float>& ed, const Bank& bank, float qthr,
                                          bool do_a, float (&sq)[FastLayout<2, P>::Q], float (&Ao)[Ref<2, P>::U],
-                                         bool& keep) {
+                                         Checks& ck) {
   using L = FastLayout<2, P>;
   constexpr int REF = L::REF, NE = L::NE, Q = L::Q, U = L::U;
   constexpr int OFF = Bank::template off<2, P>();
   const float* tv = bank.v;
-  const float lim = fmaxf(qthr, 1e-12f);
 #pragma unroll
   for (int u = 0; u < U; ++u) Ao[u] = 0.f;
 #pragma unroll
@@ -165,7 +172,8 @@ __device__ __forceinline__ void tri_fast(const ElemData<2, NA, P, float>& ed, co
     sq[q] = s;
     // metric quality det G / (tr G / 2)^2 against the threshold, without a division
     const float tr = 0.5f * (g11 + g22);
-    keep &= (s2 > lim * (tr * tr)) & (s2 <= 3.0e38f);
+    ck.good &= (s2 > 1e-12f * (tr * tr)) & (s2 <= 3.0e38f);
+    ck.cond &= s2 >= qthr * (tr * tr);
     if (do_a) {
       const float ir11 = rsqrtf(g11);
       const float ws = tv[OFF + L::w(q)] * s;
@@ -230,12 +238,11 @@ __device__ __forceinline__ void contract_stiff(const Bank& bank,
 // conditioning test of every point.
 template <int NA, int P, typename Bank>
 __device__ __forceinline__ void stiff_tet_fast(const ElemData<3, NA, P, float>& ed, const Bank& bank, float qthr,
-                                               float* dst, bool& keep) {
+                                               float* dst, Checks& ck) {
   using L = FastLayout<3, P>;
   constexpr int REF = L::REF, U = L::U, NE = L::NE, Q = L::Q;
   constexpr int OFF = Bank::template off<3, P>();
   const float* tv = bank.v;
-  const float lim = fmaxf(qthr, 1e-12f);
   float Ao[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) Ao[u] = 0.f;
@@ -278,7 +285,8 @@ __device__ __forceinline__ void stiff_tet_fast(const ElemData<3, NA, P, float>& 
       for (int m = 0; m < 3; ++m) tr = fmaf(J[i][m], J[i][m], tr);
     tr *= (1.0f / 3.0f);
     const float s2 = __fmul_rn(det, det);
-    keep &= (s2 > lim * (tr * tr * tr)) & (s2 <= 3.0e38f);
+    ck.good &= (s2 > 1e-12f * (tr * tr * tr)) & (s2 <= 3.0e38f);
+    ck.cond &= s2 >= qthr * (tr * tr * tr);
 #pragma unroll
     for (int b = 0; b < REF; ++b) {
       float y[3];
@@ -303,12 +311,11 @@ __device__ __forceinline__ void stiff_tet_fast(const ElemData<3, NA, P, float>& 
 // Tetrahedra, |det J| at every point (mass-type matrices) and the test.
 template <int NA, int P, typename Bank>
 __device__ __forceinline__ void jac_tet_fast(const ElemData<3, NA, P, float>& ed, const Bank& bank, float qthr,
-                                             float (&sq)[FastLayout<3, P>::Q], bool& keep) {
+                                             float (&sq)[FastLayout<3, P>::Q], Checks& ck) {
   using L = FastLayout<3, P>;
   constexpr int NE = L::NE, Q = L::Q;
   constexpr int OFF = Bank::template off<3, P>();
   const float* tv = bank.v;
-  const float lim = fmaxf(qthr, 1e-12f);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     float J[3][3];
@@ -333,7 +340,8 @@ __device__ __forceinline__ void jac_tet_fast(const ElemData<3, NA, P, float>& ed
       for (int m = 0; m < 3; ++m) tr = fmaf(J[i][m], J[i][m], tr);
     tr *= (1.0f / 3.0f);
     const float s2 = __fmul_rn(det, det);
-    keep &= (s2 > lim * (tr * tr * tr)) & (s2 <= 3.0e38f);
+    ck.good &= (s2 > 1e-12f * (tr * tr * tr)) & (s2 <= 3.0e38f);
+    ck.cond &= s2 >= qthr * (tr * tr * tr);
   }
 }
 
@@ -344,7 +352,7 @@ __device__ __forceinline__ void jac_tet_fast(const ElemData<3, NA, P, float>& ed
 template <int D, int NA, int P, typename Bank>
 __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, float>& ed, const Bank& bank,
                                                    const float* cs, const double* cd, float qthr, unsigned which,
-                                                   float* dst, int mstride, bool& keep) {
+                                                   float* dst, int mstride, Checks& ck) {
   using L = FastLayout<D, P>;
   constexpr int Q = L::Q;
   float cq[Q];
@@ -355,13 +363,13 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
   float sq[Q];
   int slot = 0;
   if constexpr (D == 3) {
-    if (which & (LFEM_MASS | LFEM_CMASS)) jac_tet_fast<NA, P>(ed, bank, qthr, sq, keep);
+    if (which & (LFEM_MASS | LFEM_CMASS)) jac_tet_fast<NA, P>(ed, bank, qthr, sq, ck);
     if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
-    if (which & LFEM_STIFF) stiff_tet_fast<NA, P>(ed, bank, qthr, dst + mstride * slot++, keep);
+    if (which & LFEM_STIFF) stiff_tet_fast<NA, P>(ed, bank, qthr, dst + mstride * slot++, ck);
   } else if constexpr (D == 2) {
     float Ao[Ref<D, P>::U];
     const bool do_a = which & LFEM_STIFF;
-    tri_fast<NA, P>(ed, bank, qthr, do_a, sq, Ao, keep);
+    tri_fast<NA, P>(ed, bank, qthr, do_a, sq, Ao, ck);
     if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
     if (do_a) {
       float* d = dst + mstride * slot++;
@@ -370,7 +378,7 @@ __device__ __forceinline__ void element_fast_store(const ElemData<D, NA, P, floa
     }
   } else {
     float hq[Q][L::NK];
-    curve_fast<NA, P>(ed, bank, sq, hq, keep);
+    curve_fast<NA, P>(ed, bank, sq, hq, ck);
     if (which & LFEM_MASS) contract_mass<D, P>(bank, sq, dst + mstride * slot++);
     if (which & LFEM_STIFF) contract_stiff<D, P>(bank, hq, dst + mstride * slot++);
   }

@@ -416,10 +416,10 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         const int64_t cg = (int64_t)t_elem[jt] * Q;
         const float* cs = coef_bytes == 4 ? static_cast<const float*>(mr.coef) + cg : nullptr;
         const double* cd = coef_bytes == 8 ? static_cast<const double*>(mr.coef) + cg : nullptr;
-        bool keep = true;
+        Checks ck;
         element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * U,
-                                     mstride, keep);
-        flag[jt] = keep ? 0 : 1;
+                                     mstride, ck);
+        flag[jt] = !ck.good ? 2 : (ck.cond ? 0 : 1);
       }
       if (!prefetched) {
         prefetch();
@@ -457,7 +457,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
     if (active && sub == 0) {
       if constexpr (sizeof(R) == 4) {
-        flag[jt] = ((D > 1 && q2 < (R)a.qmin) || bad2) ? 1 : 0;
+        flag[jt] = bad2 ? 2 : ((D > 1 && q2 < (R)a.qmin) ? 1 : 0);
       } else {
         const int32_t n0 = t_nodes[en[0]];
         if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
@@ -470,16 +470,24 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   }
   if constexpr (sizeof(R) == 4) {
     __syncthreads();
-    // rare path: double recomputation of flagged elements from global coordinates
+    // rare path: double recomputation of flagged elements from global
+    // coordinates -- every requested matrix for an element that failed the
+    // finiteness test (2), the stiffness alone for one that failed only the
+    // conditioning test (1): mass-type matrices need s, not G^{-1}
+    const int ia = (a.which & LFEM_MASS) ? 1 : 0;
     for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
-      if (!flag[j]) continue;
+      const int fl = flag[j];
+      if (!fl) continue;
+      const unsigned fw = fl == 2 ? a.which : (a.which & LFEM_STIFF);
+      if (!fw) continue;
       const uint16_t* en = t_en + (size_t)j * REF;
       int32_t nd[REF];
 #pragma unroll
       for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
       bool bad = false;
-      element_fp64_lean<D, NA, P, float>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], a.which,
-                                         lsm + (size_t)j * U, mstride, bad);
+      R* d = lsm + (size_t)j * U + (fl == 2 ? 0 : ia * mstride);
+      element_fp64_lean<D, NA, P, float>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw, d,
+                                         mstride, bad);
       if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
         atomicAdd(a.fallback, 1ull);
         if (bad) atomicOr(a.status, ST_DEGENERATE);

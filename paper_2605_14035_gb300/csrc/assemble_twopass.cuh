@@ -84,10 +84,15 @@ __global__ void __launch_bounds__(128) k_elem_local(const TwoPassArgs a, const _
       constexpr int Q = FastLayout<D, P>::Q;
       const float* cs = (a.which & LFEM_CMASS) && a.coef_f32 ? static_cast<const float*>(a.coef) + e * Q : nullptr;
       const double* cd = (a.which & LFEM_CMASS) && !a.coef_f32 ? static_cast<const double*>(a.coef) + e * Q : nullptr;
-      bool keep = true;
-      element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, dst, U, keep);
-      if (!ok || !keep) {
-        element_fp64_lean<D, NA, P, float>(a.coords, nodes, a.tab, a.coef, a.coef_f32, e, a.which, dst, U, bad);
+      Checks ck;
+      element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, dst, U, ck);
+      // double recomputation: every matrix after a failed finiteness test,
+      // the stiffness alone after a failed conditioning test
+      const bool full = !ok || !ck.good;
+      const unsigned fw = full ? a.which : (ck.cond ? 0u : (a.which & LFEM_STIFF));
+      if (fw) {
+        float* d = dst + (full ? 0 : ((a.which & LFEM_MASS) ? U : 0));
+        element_fp64_lean<D, NA, P, float>(a.coords, nodes, a.tab, a.coef, a.coef_f32, e, fw, d, U, bad);
         atomicAdd(a.fallback, 1ull);
       }
     } else if constexpr (sizeof(R) == 4) {
