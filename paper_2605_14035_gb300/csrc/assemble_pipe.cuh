@@ -116,8 +116,8 @@ __host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, in
   o += al((size_t)cap_nel * q * coef_bytes);
   L.lsm = o;
   o += al(sizeof(R) * (size_t)cap_lsm);
-  L.flag = o;  // element flags of phase 1
-  o += al((size_t)cap_nel);
+  L.flag = o;  // phase 1: compacted list of the elements to redo in double
+  o += al(sizeof(uint32_t) * (size_t)cap_nel);
   L.total = o;
   return L;
 }
@@ -371,7 +371,8 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
 // hook of the next item after the first phase-1 round, phase 2.
 template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
 __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
-                                             const void* coef_s, R* lsm, uint8_t* flag, const FastBank& fb,
+                                             const void* coef_s, R* lsm, uint32_t* flist, int* nflag,
+                                             const FastBank& fb,
                                              Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
@@ -392,6 +393,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
   const int4* t_lrec = reinterpret_cast<const int4*>(mb + TL.lrec);
   const EntT* t_lent = reinterpret_cast<const EntT*>(mb + TL.lent);
 
+  if (threadIdx.x == 0) *nflag = 0;  // visible after the next barrier (split, or the one after phase 1)
   // node coordinates -> (hi, lo) float pairs in place (mixed)
   if constexpr (sizeof(R) == 4) {
     for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
@@ -419,7 +421,8 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         Checks ck;
         element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * U,
                                      mstride, ck);
-        flag[jt] = !ck.good ? 2 : (ck.cond ? 0 : 1);
+        const uint32_t fl = !ck.good ? 2u : (ck.cond ? 0u : 1u);
+        if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
       }
       if (!prefetched) {
         prefetch();
@@ -457,7 +460,8 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
     if (active && sub == 0) {
       if constexpr (sizeof(R) == 4) {
-        flag[jt] = bad2 ? 2 : ((D > 1 && q2 < (R)a.qmin) ? 1 : 0);
+        const uint32_t fl = bad2 ? 2u : ((D > 1 && q2 < (R)a.qmin) ? 1u : 0u);
+        if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
       } else {
         const int32_t n0 = t_nodes[en[0]];
         if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
@@ -474,10 +478,13 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     // coordinates -- every requested matrix for an element that failed the
     // finiteness test (2), the stiffness alone for one that failed only the
     // conditioning test (1): mass-type matrices need s, not G^{-1}
+    // (a compacted list, so that whole warps work on it: the FP64 pipe costs
+    // the same for a warp instruction with few active lanes)
     const int ia = (a.which & LFEM_MASS) ? 1 : 0;
-    for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
-      const int fl = flag[j];
-      if (!fl) continue;
+    const int nf = *nflag;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+      const uint32_t v = flist[i];
+      const int j = (int)(v & 0x3FFFFFFFu), fl = (int)(v >> 30);
       const unsigned fw = fl == 2 ? a.which : (a.which & LFEM_STIFF);
       if (!fw) continue;
       const uint16_t* en = t_en + (size_t)j * REF;
@@ -555,13 +562,13 @@ struct EType {
 
 template <typename R, typename EntT, typename T0, typename... Ts, typename Prefetch>
 __device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* mb,
-                                              double* xd, const void* coef_s, R* lsm, uint8_t* flag,
+                                              double* xd, const void* coef_s, R* lsm, uint32_t* flist, int* nflag,
                                               const FastBank& fb, Prefetch&& prefetch) {
   if (type == T0::id) {
-    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
+    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flist, nflag, fb, prefetch);
   } else {
     if constexpr (sizeof...(Ts) > 0) {
-      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flag, fb, prefetch);
+      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flist, nflag, fb, prefetch);
     } else {
       // no variant for this tile's type: report it, keep the pipeline's steps
       if (threadIdx.x == 0) atomicOr(a.status, ST_TYPE);
@@ -588,7 +595,8 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
   auto node_of = [&](int buf) { return reinterpret_cast<double*>(smem_raw + (buf ? L.node1 : L.node0)); };
   auto coef_of = [&](int buf) { return static_cast<void*>(smem_raw + (buf ? L.coef1 : L.coef0)); };
   R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
-  uint8_t* flag = smem_raw + L.flag;
+  uint32_t* flist = reinterpret_cast<uint32_t*>(smem_raw + L.flag);
+  int* s_nflag = reinterpret_cast<int*>(smem_raw + L.mbar + 68);
 
   int64_t i = blockIdx.x;
   if (i >= a.n_items) return;
@@ -656,7 +664,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
       }
     };
     const MeshRec& mr = s_rec[b];
-    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_of(b), node_of(b), coef_of(b), lsm, flag, fb,
+    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_of(b), node_of(b), coef_of(b), lsm, flist, s_nflag, fb,
                                      prefetch_next);
     if (*s_flag) {
       // the next block never arrived: report, wait (bounded) for the copy, stop
