@@ -63,6 +63,11 @@ def build_cases():
     c["cube_p1"] = (*meshes.kuhn_cube_p2(5, order=1), 3, 1, r_tet4)
     xc, ec = meshes.kuhn_cube_p2(3)
     c["cube_boundary_p2"] = (xc, meshes.boundary_faces_p2(ec), 2, 2, r_tri7)  # rows of interior nodes empty
+    # rules other than the compile-time ones take the general (lane-pair) path
+    x, e = meshes.icosphere(2, 2)
+    c["sphere_p2_gauss9"] = (meshes.radial_perturbation(x), e, 2, 2, quadrature.collapsed_gauss(2, 3))
+    c["disk_p1_gauss4"] = (*meshes.hex_disk(4, 1), 2, 1, quadrature.collapsed_gauss(2, 2))
+    c["cube_p2_gauss8"] = (*meshes.kuhn_cube_p2(3), 3, 2, quadrature.collapsed_gauss(3, 2))
     return c
 
 
