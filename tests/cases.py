@@ -66,7 +66,7 @@ def build_cases():
     # rules other than the compile-time ones take the general (lane-pair) path
     x, e = meshes.icosphere(2, 2)
     c["sphere_p2_gauss9"] = (meshes.radial_perturbation(x), e, 2, 2, quadrature.collapsed_gauss(2, 3))
-    c["disk_p1_gauss4"] = (*meshes.hex_disk(4, 1), 2, 1, quadrature.collapsed_gauss(2, 2))
+    c["disk_p1_gauss4"] = (*meshes.hex_disk(8, 1), 2, 1, quadrature.collapsed_gauss(2, 2))
     c["cube_p2_gauss8"] = (*meshes.kuhn_cube_p2(3), 3, 2, quadrature.collapsed_gauss(3, 2))
     return c
 
