@@ -112,13 +112,23 @@ def run_c3(args):
     alg = e.shape[0] * 40 + x.shape[0] * 24 + 2 * pt.nnz * 4 + b.shape[0] * 24 + pb.nnz * 4
     peak, kind = bench.measured_peaks()
     ach = alg / (res["mixed"]["ms_per_step"] * 1e-3) / 1e9
+    tflops = e.shape[0] * TET_P2_FLOPS / (res["mixed"]["ms_per_step"] * 1e-3) / 1e12
     _line(args, "p2_kuhn_cube_64_tets_M_A_plus_boundary_M", res["mixed"]["value"], "elements/s",
           res["mixed"]["ms_per_step"],
           {"config": {"tets": int(e.shape[0]), "boundary_triangles": int(b.shape[0]), "nnz_tets": pt.nnz,
                       "l2": "flushed between steps"},
            "fp64": res["fp64"], "mixed": res["mixed"],
-           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                        "traffic": None, "algorithmic_bytes": alg, "peak_kind": kind}})
+           # tets are bound by FP32 arithmetic: about 6.1k multiply-adds + 0.8k multiplies per P2 tet
+           # (M + A, 14 points; counted from the element code) against the FP32 pipe peak
+           "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": tflops / FP32_PEAK_TFLOPS, "traffic": None, "flops_per_tet": TET_P2_FLOPS,
+                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
+           "roofline_hbm": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                            "algorithmic_bytes": alg, "peak_kind": kind}})
+
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+TET_P2_FLOPS = 12950
 
 
 def _gen_batch(n_meshes, scale):

@@ -14,4 +14,6 @@ from .oracle import (  # noqa: F401
     local_matrices,
     assemble,
     adjoint,
+    load,
+    kll,
 )

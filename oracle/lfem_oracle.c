@@ -506,4 +506,99 @@ int oracle_adjoint(const double* coords, int n, const int32_t* conn, int64_t nE,
   return rc;
 }
 
+/*
+ * Load vector (Sec. 2, the load vector of the Poisson problem): b_j =
+ * integral over Gamma_h of f_h phi_j, with f_h = sum_i f_i phi_i the
+ * interpolant of the nodal values f (so b = M f).  Per element and quadrature
+ * point: f_q = sum_b f_{E[b]} phi_b, local b_a += w_q s_q f_q phi_a; the local
+ * vectors are added into b in increasing (e, a) with Neumaier sums.
+ * b [n_nodes] is overwritten.
+ */
+int oracle_load(const double* coords, int n, const int32_t* conn, int64_t nE, int64_t n_nodes, int dim, int order,
+                int nq, const double* xi, const double* w, const double* f, double* b) {
+  int ref = n_ref(dim, order);
+  if (check_combo(dim, order, n)) return 1;
+  double* acc = (double*)calloc((size_t)n_nodes * 2, sizeof(double));
+  if (!acc) return 3;
+  double X[MAXREF * MAXD];
+  for (int64_t e = 0; e < nE; ++e) {
+    gather(coords, n, conn, ref, e, X);
+    double loc[MAXREF] = {0};
+    for (int q = 0; q < nq; ++q) {
+      qp_geom g;
+      element_qp(dim, order, n, X, xi + q * dim, &g);
+      double fq = 0.0;
+      for (int a = 0; a < ref; ++a) fq += f[conn[e * ref + a]] * g.phi[a];
+      double sq = g.s;
+#if ORACLE_MUTATION == 7
+      sq = 1.0; /* planted: surface element dropped */
+#endif
+      for (int a = 0; a < ref; ++a) loc[a] += w[q] * sq * fq * g.phi[a];
+    }
+    for (int a = 0; a < ref; ++a) {
+      int64_t v = conn[e * ref + a];
+      neumaier_add(&acc[2 * v], &acc[2 * v + 1], loc[a]);
+    }
+  }
+  for (int64_t v = 0; v < n_nodes; ++v) b[v] = acc[2 * v] + acc[2 * v + 1];
+  free(acc);
+  return 0;
+}
+
+/*
+ * Non-linear vectors of the mean curvature flow system (Sec. 5.1, after
+ * Kovacs-Li-Lubich): with u = (nu, H) given at the nodes ([n_nodes][4]),
+ * nu_h and H_h their interpolants and alpha^2 = |grad_Gamma_h nu_h|^2 (the
+ * Frobenius norm of the tangential gradient of the normal field),
+ *   f1[k][j] = integral of alpha^2 (nu_h)_k phi_j   (k = 0, 1, 2)
+ *   f2[j]    = integral of alpha^2 H_h phi_j,
+ * written to out[k * n_nodes + j] (k = 0..2) and out[3 * n_nodes + j].  The
+ * tangential gradient is the oracle's C_E^T grad^ phi (as for the stiffness).
+ * Surfaces (dim 2 in R^3) only.
+ */
+int oracle_kll(const double* coords, const int32_t* conn, int64_t nE, int64_t n_nodes, int order, int nq,
+               const double* xi, const double* w, const double* u, double* out) {
+  const int dim = 2, n = 3;
+  int ref = n_ref(dim, order);
+  if (check_combo(dim, order, n)) return 1;
+  double* acc = (double*)calloc((size_t)n_nodes * 8, sizeof(double));
+  if (!acc) return 3;
+  double X[MAXREF * MAXD];
+  for (int64_t e = 0; e < nE; ++e) {
+    gather(coords, n, conn, ref, e, X);
+    double loc[MAXREF][4];
+    memset(loc, 0, sizeof(loc));
+    for (int q = 0; q < nq; ++q) {
+      qp_geom g;
+      element_qp(dim, order, n, X, xi + q * dim, &g);
+      double val[4] = {0, 0, 0, 0};     /* nu_h (3), H_h at the point */
+      double gnu[3][3] = {{0}};         /* gnu[k][i] = i-th component of grad_Gamma (nu_h)_k */
+      for (int b = 0; b < ref; ++b) {
+        const double* ub = u + (int64_t)conn[e * ref + b] * 4;
+        for (int k = 0; k < 4; ++k) val[k] += ub[k] * g.phi[b];
+        for (int k = 0; k < 3; ++k)
+          for (int i = 0; i < 3; ++i) {
+#if ORACLE_MUTATION == 8
+            gnu[k][i] += ub[k] * (i < dim ? g.dphi[b][i] : 0.0); /* planted: reference gradient */
+#else
+            gnu[k][i] += ub[k] * g.grad[b][i];
+#endif
+          }
+      }
+      double alpha2 = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i) alpha2 += gnu[k][i] * gnu[k][i];
+      for (int a = 0; a < ref; ++a)
+        for (int k = 0; k < 4; ++k) loc[a][k] += w[q] * g.s * alpha2 * val[k] * g.phi[a];
+    }
+    for (int a = 0; a < ref; ++a) {
+      int64_t v = conn[e * ref + a];
+      for (int k = 0; k < 4; ++k) neumaier_add(&acc[(k * n_nodes + v) * 2], &acc[(k * n_nodes + v) * 2 + 1], loc[a][k]);
+    }
+  }
+  for (int64_t i = 0; i < 4 * n_nodes; ++i) out[i] = acc[2 * i] + acc[2 * i + 1];
+  free(acc);
+  return 0;
+}
+
 int oracle_mutation_id(void) { return ORACLE_MUTATION; }

@@ -52,8 +52,10 @@ def _lib(mutation: int = 0):
         lib.oracle_local.argtypes = [P, I, P, L, I, I, I, P, P, P, P, P, P]
         lib.oracle_assemble.argtypes = [P, I, P, L, I, I, I, P, P, P, P, P, L, P, P, P]
         lib.oracle_adjoint.argtypes = [P, I, P, L, L, I, I, I, P, P, P, P, P, P, P, P, P, P]
+        lib.oracle_load.argtypes = [P, I, P, L, L, I, I, I, P, P, P, P]
+        lib.oracle_kll.argtypes = [P, P, L, L, I, I, P, P, P, P]
         for f in ("oracle_tabulate", "oracle_eval_points", "oracle_geometry", "oracle_local",
-                  "oracle_assemble", "oracle_adjoint", "oracle_mutation_id"):
+                  "oracle_assemble", "oracle_adjoint", "oracle_load", "oracle_kll", "oracle_mutation_id"):
             getattr(lib, f).restype = ctypes.c_int
         _libs[mutation] = lib
         return lib
@@ -180,6 +182,37 @@ def assemble(coords, conn, dim, order, xi, w, coef=None, pat=None, mutation=0):
     if rc:
         raise ValueError(f"oracle_assemble failed ({rc})")
     return row_ptr, col_idx, M, A, C
+
+
+def load(coords, conn, dim, order, xi, w, f, mutation=0):
+    """Load vector b_j = int f_h phi_j with f_h the interpolant of nodal f (Sec. 2; b = M f)."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    w = _f64(w)
+    f = _f64(f)
+    b = np.zeros(coords.shape[0])
+    rc = _lib(mutation).oracle_load(_p(coords), coords.shape[1], _p(conn), conn.shape[0], coords.shape[0], dim, order,
+                                    xi.shape[0], _p(xi), _p(w), _p(f), _p(b))
+    if rc:
+        raise ValueError(f"oracle_load failed ({rc})")
+    return b
+
+
+def kll(coords, conn, order, xi, w, u, mutation=0):
+    """Non-linear vectors of the mean curvature flow system (Sec. 5.1): u = (nu, H) nodal [N][4];
+    returns [4][N]: rows 0..2 = int alpha^2 (nu_h)_k phi_j, row 3 = int alpha^2 H_h phi_j."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, 2)
+    w = _f64(w)
+    u = _f64(u).reshape(-1, 4)
+    out = np.zeros((4, coords.shape[0]))
+    rc = _lib(mutation).oracle_kll(_p(coords), _p(conn), conn.shape[0], coords.shape[0], order, xi.shape[0], _p(xi),
+                                   _p(w), _p(u), _p(out))
+    if rc:
+        raise ValueError(f"oracle_kll failed ({rc})")
+    return out
 
 
 def adjoint(coords, conn, dim, order, xi, w, coef, pat, gM=None, gA=None, gMC=None, mutation=0):

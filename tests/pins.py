@@ -209,6 +209,44 @@ def check_fd(mutation=0, n_coords=12, seed=7):
     return worst
 
 
+def check_load_is_mass_times_f(mutation=0):
+    """The load vector of the interpolant f_h = sum f_i phi_i is b = M f (Sec. 2),
+    on curved P2 surfaces, a P1 sphere, a P2 curve and P2 tets; relative to max |b|."""
+    worst = 0.0
+    rng = np.random.default_rng(21)
+    for (x, e), d, p in ((meshes.icosphere(2, 2), 2, 2), (meshes.icosphere(2, 1), 2, 1),
+                         (meshes.closed_curve_p2(60, seed=4), 1, 2), (meshes.kuhn_cube_p2(2), 3, 2)):
+        r = quadrature.default_rule(d, p)
+        f = rng.standard_normal(x.shape[0])
+        rp, ci, M, _, _ = oracle.assemble(x, e, d, p, r.xi, r.w, mutation=mutation)
+        b = oracle.load(x, e, d, p, r.xi, r.w, f, mutation=mutation)
+        Mf = csr(M, (rp, ci), x.shape[0]) @ f
+        worst = max(worst, np.abs(b - Mf).max() / np.abs(Mf).max())
+    return worst
+
+
+def check_kll_identity_normal(mutation=0):
+    """Non-linear vectors of Sec. 5.1 with the nodal 'normal' set to the node
+    positions: nu_h is then the identity on Gamma_h, its tangential gradient is
+    the tangential projector (Frobenius norm^2 = 2 exactly on a surface), so
+    f1_k = 2 M x_k and f2 = 2 M H for any nodal H; a constant field gives 0."""
+    worst = 0.0
+    rng = np.random.default_rng(22)
+    for order in (1, 2):
+        x, e = meshes.ellipsoid(2, sigma=1e-2, seed=5) if order == 2 else meshes.icosphere(2, 1)
+        r = quadrature.default_rule(2, order)
+        H = rng.standard_normal(x.shape[0])
+        u = np.column_stack([x, H])
+        out = oracle.kll(x, e, order, r.xi, r.w, u, mutation=mutation)
+        rp, ci, M, _, _ = oracle.assemble(x, e, 2, order, r.xi, r.w, mutation=mutation)
+        Mm = csr(M, (rp, ci), x.shape[0])
+        ref = np.vstack([2 * (Mm @ x[:, k]) for k in range(3)] + [2 * (Mm @ H)])
+        worst = max(worst, np.abs(out - ref).max() / np.abs(ref).max())
+        const = np.column_stack([np.tile([0.3, -0.2, 0.9], (x.shape[0], 1)), H])
+        worst = max(worst, np.abs(oracle.kll(x, e, order, r.xi, r.w, const, mutation=mutation)).max())
+    return worst
+
+
 ALL_CHECKS = {
     "lagrange": (check_lagrange, 1e-8),
     "affine_exact": (check_affine_exact, 1e-12),
@@ -216,6 +254,8 @@ ALL_CHECKS = {
     "half_disk": (check_half_disk, 1e-14),
     "area_gradient": (check_area_gradient, 1e-12),
     "fd": (check_fd, 1e-6),
+    "load_is_mass_times_f": (check_load_is_mass_times_f, 1e-13),
+    "kll_identity_normal": (check_kll_identity_normal, 1e-12),
 }
 
 

@@ -27,10 +27,12 @@ def test_pin(name):
     assert fn() < tol
 
 
-@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_planted_mistake_is_caught(mutation):
     """Each planted mistake (wrong bubble scale, swapped edge nodes, wrong surface
-    element, J^-1 for J^-T, dropped weight, dropped factor in the adjoint) fails a pin."""
+    element, J^-1 for J^-T, dropped weight, dropped factor in the adjoint, load
+    vector without the surface element, reference instead of tangential
+    gradient of the normal field) fails a pin."""
     assert pins.failing_checks(mutation), f"mutation {mutation} passed every pin"
 
 
