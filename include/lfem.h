@@ -198,6 +198,32 @@ lfem_status lfem_batch_info(lfem_batch_t b, int64_t* n_work_items, int64_t* n_el
 void lfem_batch_destroy(lfem_batch_t b);
 
 /* ---------------------------------------------------------------------------
+ * Vector assembly on the pattern's node incidences, FP64, deterministic (each
+ * element's local vector once, then every node sums its incidences in
+ * ascending element order; no atomics).  coords as for lfem_assemble; the
+ * local-vector scratch ([n_elem][ref][nc] doubles) is allocated by the
+ * pattern on first use and kept.
+ *
+ * Load vector of the Poisson problem (Sec. 2): b_j = integral over Gamma_h of
+ * f_h phi_j, f_h = sum_i f_i phi_i the interpolant of the nodal values, so
+ * b = M f.  f: [n_nodes] doubles; b: [n_nodes] doubles, overwritten.  Every
+ * (dim, ambient, order) lfem_assemble supports.
+ */
+lfem_status lfem_assemble_load(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                               const double* f, double* b, void* cuda_stream);
+
+/* Non-linear vectors of the mean curvature flow system (Sec. 5.1): with
+ * u = (nu, H) at the nodes ([n_nodes][4] doubles: normal components, then
+ * mean curvature), nu_h, H_h their interpolants and alpha^2 =
+ * |grad_Gamma_h nu_h|^2 (Frobenius norm of the tangential gradient),
+ *   out[k * n_nodes + j]     = integral of alpha^2 (nu_h)_k phi_j  (k = 0, 1, 2)
+ *   out[3 * n_nodes + j]     = integral of alpha^2 H_h phi_j.
+ * out: [4][n_nodes] doubles, overwritten.  Surfaces only (dim 2, ambient 3):
+ * LFEM_E_UNSUPPORTED otherwise. */
+lfem_status lfem_assemble_mcf_nonlinear(lfem_pattern_t p, const double* coords, const lfem_quad* quad,
+                                        const double* u, double* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint: for L = gM.M + gA.A + gMC.MC (dot products over the CSR values),
  * g_coords [n_nodes][ambient] = dL/d coords (overwritten) and, when g_coef is
  * not NULL, g_coef [n_elem][n_pts] = dL/d coef.  FP64 throughout.  gM, gA,

@@ -21,6 +21,8 @@ LFEM_DECLARE_DIM(3)
 lfem_status run_twopass_d3(int P, bool mixed, bool fast, const FastBankTet& fb, const TwoPassArgs& a, int sms,
                            cudaStream_t st);
 lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset);
+lfem_status bank_upload_vec(const void* src, size_t bytes, size_t offset);
+lfem_status run_vectors(int D, int NA, int P, int kind, const VecArgs& a, cudaStream_t st);
 
 // Body of one dimension's dispatch functions over (NA, P).
 #define LFEM_DEFINE_CASE_STAGE(DD, NN, PP) \

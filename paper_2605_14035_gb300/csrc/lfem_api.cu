@@ -170,7 +170,7 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
   std::vector<unsigned char> blob(b64 + b32, 0);
   memcpy(blob.data(), t64.data(), b64);
   memcpy(blob.data() + b64, t32.data(), t32.size() * sizeof(float));
-  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch}) {
+  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch, bank_upload_vec}) {
     lfem_status us = up(blob.data(), blob.size(), used);
     if (us != LFEM_OK) return us;
   }
@@ -206,7 +206,7 @@ static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& 
 static void destroy_dev(PatternDev& d) {
   void* ptrs[] = {d.conn,      d.row_ptr,       d.col_idx,   d.inc_ptr,   d.inc_key, d.inc_pos,    d.elem_inc,
                   d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off,
-                  d.slot_off,  d.slot_ent,      d.elem_buf};
+                  d.slot_off,  d.slot_ent,      d.elem_buf,  d.vec_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = PatternDev{};
@@ -543,6 +543,57 @@ lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream) {
   if (h & ST_TYPE) return fail(LFEM_E_UNSUPPORTED, "a tile met a kernel without its element type");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
   return LFEM_OK;
+}
+
+}  // extern "C"
+
+static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                                  const double* u, double* out, int kind, cudaStream_t st) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
+  if (kind == 1 && !(p->dim == 2 && ambient == 3))
+    return fail(LFEM_E_UNSUPPORTED, "the non-linear vectors need a surface (dim 2 in R^3)");
+  if (p->n_elem > 0 && (!coords || !u)) return fail(LFEM_E_ARG, "coords or nodal values are NULL");
+  if (p->n_nodes > 0 && !out) return fail(LFEM_E_ARG, "output is NULL");
+  TabRef tab;
+  lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
+  if (s != LFEM_OK) return s;
+  const int nc = kind == 0 ? 1 : 4;
+  const size_t need = (size_t)p->n_elem * p->ref * nc * sizeof(double);
+  if (need > p->d.vec_buf_bytes) {
+    if (p->d.vec_buf) cudaFree(p->d.vec_buf);
+    p->d.vec_buf = nullptr;
+    p->d.vec_buf_bytes = 0;
+    if (cudaMalloc(&p->d.vec_buf, need ? need : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LFEM_E_NOMEM, "local-vector buffer allocation failed");
+    }
+    p->d.vec_buf_bytes = need;
+  }
+  VecArgs a{};
+  a.conn = p->d.conn;
+  a.coords = coords;
+  a.u = u;
+  a.loc = p->d.vec_buf;
+  a.inc_ptr = p->d.inc_ptr;
+  a.inc_key = p->d.inc_key;
+  a.out = out;
+  a.n_elem = p->n_elem;
+  a.n_nodes = p->n_nodes;
+  a.tab = tab;
+  return run_vectors(p->dim, ambient, p->order, kind, a, st);
+}
+
+extern "C" {
+
+lfem_status lfem_assemble_load(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                               const double* f, double* b, void* cuda_stream) {
+  return vectors_common(p, coords, ambient, quad, f, b, 0, (cudaStream_t)cuda_stream);
+}
+
+lfem_status lfem_assemble_mcf_nonlinear(lfem_pattern_t p, const double* coords, const lfem_quad* quad,
+                                        const double* u, double* out, void* cuda_stream) {
+  return vectors_common(p, coords, 3, quad, u, out, 1, (cudaStream_t)cuda_stream);
 }
 
 lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64_t* n_fp64_elements) {

@@ -407,6 +407,20 @@ __host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nl, int n
 // ----------------------------------------------------------------------------
 // Pattern handle
 // ----------------------------------------------------------------------------
+// Vector assembly (load vector, mean-curvature-flow non-linear vectors).
+struct VecArgs {
+  const int32_t* conn;
+  const double* coords;
+  const double* u;  // nodal [N][nc]: f (nc = 1) or (nu, H) (nc = 4)
+  double* loc;      // [nE][ref][nc]
+  const int32_t* inc_ptr;
+  const int32_t* inc_key;
+  double* out;      // [nc][N]
+  int64_t n_elem;
+  int32_t n_nodes;
+  TabRef tab;
+};
+
 struct PatternDev {
   int32_t* conn = nullptr;       // [nE][ref] device copy
   int64_t* row_ptr = nullptr;    // [N+1]
@@ -424,6 +438,8 @@ struct PatternDev {
   int32_t* slot_ent = nullptr;   // [nInc*ref] e * U + u, per slot in ascending (e, a, b)
   void* elem_buf = nullptr;      // element-major path: local matrices [nE][nm][U] (scratch)
   size_t elem_buf_bytes = 0;
+  double* vec_buf = nullptr;     // vector assembly: local vectors [nE][ref][nc] (scratch)
+  size_t vec_buf_bytes = 0;
   uint8_t* tile_meta = nullptr;  // per-tile metadata blocks (see TileHdr)
   int64_t* tile_meta_off = nullptr;  // [T+1] byte offsets, multiples of 16
 };

@@ -25,7 +25,8 @@ STATUS = {0: "LFEM_OK", 1: "LFEM_E_ARG", 2: "LFEM_E_INDEX", 3: "LFEM_E_UNSUPPORT
 # Every entry point declared in include/lfem.h.
 EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
-    "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_set_mixed_kappa", "lfem_assemble_adjoint", "lfem_eval_points",
+    "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_set_mixed_kappa", "lfem_assemble_load",
+    "lfem_assemble_mcf_nonlinear", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
     "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
@@ -63,6 +64,8 @@ def _load():
         "lfem_assemble": [P, P, I, P, P, I, U, I, P, P, P, P],
         "lfem_set_launch": [P, ctypes.c_int32, ctypes.c_int32],
         "lfem_set_mixed_kappa": [P, ctypes.c_double],
+        "lfem_assemble_load": [P, P, I, P, P, P, P],
+        "lfem_assemble_mcf_nonlinear": [P, P, P, P, P, P],
         "lfem_assemble_adjoint": [P, P, I, P, P, P, P, P, P, P, P],
         "lfem_eval_points": [P, L, I, I, P, I, P, P, P],
         "lfem_geometry": [P, L, I, I, P, I, P, P, P, P, P],
@@ -328,6 +331,27 @@ def assemble_adjoint(pat: Pattern, coords: torch.Tensor, rule, coef=None, gM=Non
                                       _ptr(_dev_f64(gA, "gA")), _ptr(_dev_f64(gMC, "gMC")), _ptr(gx), _ptr(gc),
                                       _stream(stream)))
     return gx, gc
+
+
+def assemble_load(pat: Pattern, coords: torch.Tensor, rule, f: torch.Tensor, stream=None) -> torch.Tensor:
+    """lfem_assemble_load: b_j = integral of f_h phi_j for nodal f ([n_nodes]); returns b (b = M f)."""
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    f = _dev_f64(f, "f")
+    b = torch.empty(pat.n_nodes, dtype=torch.float64, device=coords.device)
+    _check(_lib.lfem_assemble_load(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref, _ptr(f), _ptr(b),
+                                   _stream(stream)))
+    return b
+
+
+def assemble_mcf_nonlinear(pat: Pattern, coords: torch.Tensor, rule, u: torch.Tensor, stream=None) -> torch.Tensor:
+    """lfem_assemble_mcf_nonlinear: u = (nu, H) at the nodes ([n_nodes][4]); returns [4][n_nodes]."""
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    u = _dev_f64(u, "u")
+    out = torch.empty(4, pat.n_nodes, dtype=torch.float64, device=coords.device)
+    _check(_lib.lfem_assemble_mcf_nonlinear(pat.handle, _ptr(coords), rule.ref, _ptr(u), _ptr(out), _stream(stream)))
+    return out
 
 
 def eval_points(conn, dim, order, coords, rule, stream=None):

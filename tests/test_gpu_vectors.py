@@ -1,0 +1,68 @@
+"""Load vector (Sec. 2) and the non-linear vectors of the mean curvature flow
+system (Sec. 5.1) on the GPU against the FP64 oracle, on the same seeded inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from cases import build_cases
+
+pytestmark = pytest.mark.gpu
+
+CASES = build_cases()
+TOL = 1e-12  # relative to max |reference|
+SURFACES = ["sphere_p1", "ellipsoid_p2", "perturbed_sphere_p2", "cube_boundary_p2", "sphere_p2_gauss9"]
+
+
+@pytest.fixture(scope="module")
+def lfem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_14035_gb300 import lfem as m
+
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_load_vector(name, lfem):
+    x, e, d, p, rule = CASES[name]
+    f = np.random.default_rng(31).standard_normal(x.shape[0])
+    ref = oracle.load(x, e, d, p, rule.xi, rule.w, f)
+    pat = lfem.Pattern(dev(e), x.shape[0], d, p)
+    b = lfem.assemble_load(pat, dev(x), rule, dev(f))
+    again = lfem.assemble_load(pat, dev(x), rule, dev(f))
+    got = b.cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+    assert torch.equal(b, again)
+
+
+@pytest.mark.parametrize("name", SURFACES)
+def test_mcf_nonlinear_vectors(name, lfem):
+    x, e, d, p, rule = CASES[name]
+    rng = np.random.default_rng(32)
+    # a smooth field plus noise (any nodal field is a valid input; unit length is not required)
+    nu = np.column_stack([np.sin(3 * x[:, 1]), np.cos(2 * x[:, 2]), x[:, 0] * x[:, 1]]) + 0.05 * rng.standard_normal(
+        x.shape)
+    u = np.column_stack([nu, rng.standard_normal(x.shape[0])])
+    ref = oracle.kll(x, e, p, rule.xi, rule.w, u)
+    pat = lfem.Pattern(dev(e), x.shape[0], d, p)
+    out = lfem.assemble_mcf_nonlinear(pat, dev(x), rule, dev(u)).cpu().numpy()
+    assert np.abs(out - ref).max() <= TOL * np.abs(ref).max()
+
+
+def test_vectors_edge_cases(lfem):
+    x, e, d, p, rule = CASES["curve_p2"]
+    pat = lfem.Pattern(dev(e), x.shape[0], d, p)
+    with pytest.raises(lfem.LfemError):
+        lfem.assemble_mcf_nonlinear(pat, dev(x), rule, dev(np.zeros((x.shape[0], 4))))
+    # an unreferenced node gets b = 0
+    xs, es, ds, ps, rs = CASES["sphere_p1"]
+    xs = np.vstack([xs, [[5.0, 5.0, 5.0]]])
+    pat = lfem.Pattern(dev(es), xs.shape[0], ds, ps)
+    b = lfem.assemble_load(pat, dev(xs), rs, dev(np.ones(xs.shape[0]))).cpu().numpy()
+    assert b[-1] == 0.0
+    assert abs(b[:-1].sum() - oracle.load(xs, es, ds, ps, rs.xi, rs.w, np.ones(xs.shape[0])).sum()) < 1e-12
