@@ -264,11 +264,23 @@ def run_c5(args):
                             vn[rr] * vn[cn], None)
     t_orc = time.perf_counter() - t0
     gerr = float(np.abs(xt.grad.cpu().numpy() - ogx).max() / np.abs(ogx).max())
+    # the right-hand sides of the flow on the final surface (Sec. 5.1): load
+    # vector of the nodal mean curvature field and the non-linear vectors,
+    # FP64, against the oracle
+    H = torch.from_numpy(rng.normal(size=N)).cuda()
+    nrm = xd / xd.norm(dim=1, keepdim=True)
+    uf = torch.cat([nrm, H[:, None]], dim=1).contiguous()
+    ms_load = timed(lambda: lfem.assemble_load(pat, xd, rule, H), 20, 3)
+    ms_nl = timed(lambda: lfem.assemble_mcf_nonlinear(pat, xd, rule, uf), 20, 3)
+    nl = lfem.assemble_mcf_nonlinear(pat, xd, rule, uf).cpu().numpy()
+    onl = oracle.kll(xh, e, 2, rule.xi, rule.w, uf.cpu().numpy())
+    nl_err = float(np.abs(nl - onl).max() / np.abs(onl).max())
     _line(args, "evolving_ellipsoid_r7_100_steps_plus_adjoint", e.shape[0] / (ms_step * 1e-3), "elements/s",
           ms_step,
           {"config": {"elements": int(e.shape[0]), "steps": steps, "tau": tau, "precision": "mixed, graph replay"},
            "fp64_assembly_ms": ms64, "adjoint_fwd_bwd_ms": ms_adj, "fp64_fallback_elements_final": fallback,
-           "adjoint_vs_oracle_max_rel": gerr, "oracle_adjoint_s": t_orc, "L": float(L)})
+           "adjoint_vs_oracle_max_rel": gerr, "oracle_adjoint_s": t_orc, "L": float(L),
+           "load_vector_ms": ms_load, "mcf_nonlinear_ms": ms_nl, "mcf_nonlinear_vs_oracle_max_rel": nl_err})
 
 
 def run(args):
