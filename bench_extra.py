@@ -283,5 +283,42 @@ def run_c5(args):
            "load_vector_ms": ms_load, "mcf_nonlinear_ms": ms_nl, "mcf_nonlinear_vs_oracle_max_rel": nl_err})
 
 
+def run_c2q16(args):
+    """The C2 surface with the rule size the paper uses for P2 triangles (16 points,
+    degree 8): the general element path (any rule) in mixed precision and FP64."""
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import quadrature
+
+    x, e, _ = bench.make_inputs(args.level)
+    rule = quadrature.paper_rule(2)
+    xd, ed = torch.from_numpy(x).cuda(), torch.from_numpy(e).cuda()
+    pat = lfem.Pattern(ed, x.shape[0], 2, 2)
+    flush = torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    timed = _timer(torch, flush)
+    res = {}
+    for prec, dt, name in ((lfem.MIXED, torch.float32, "mixed"), (lfem.FP64, torch.float64, "fp64")):
+        if not args.no_autotune:
+            lfem.autotune(pat, xd, rule, which=3, precision=prec)
+        out = {k: torch.empty(pat.nnz, dtype=dt, device="cuda") for k in ("M", "A")}
+        ms = timed(lambda: lfem.assemble(pat, xd, rule, which=3, precision=prec, out=out), args.steps, args.warmup)
+        res[name] = {"ms_per_step": ms, "value": e.shape[0] / (ms * 1e-3), "tile_slots": pat.info()["tile_slots"],
+                     "M_sum": float(out["M"].double().sum())}
+        if prec == lfem.MIXED:
+            res[name]["fp64_fallback_elements"] = pat.fallback_count()
+        pat.sync_status()
+    alg = e.shape[0] * 24 + x.shape[0] * 24 + 2 * pat.nnz * 4
+    peak, kind = bench.measured_peaks()
+    ach = alg / (res["mixed"]["ms_per_step"] * 1e-3) / 1e9
+    _line(args, "p2_perturbed_sphere_r8_M_A_rule16_deg8", res["mixed"]["value"], "elements/s",
+          res["mixed"]["ms_per_step"],
+          {"config": {"elements": int(e.shape[0]), "quadrature": "tri 16-point degree 8 (general path)",
+                      "l2": "flushed between steps"},
+           "fp64": res["fp64"], "mixed": res["mixed"],
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "algorithmic_bytes": alg, "peak_kind": kind}})
+
+
 def run(args):
-    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
+    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "c2q16": run_c2q16}[args.workload](args)

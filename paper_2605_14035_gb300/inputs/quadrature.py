@@ -33,6 +33,8 @@ __all__ = [
     "tri_7pt_deg5",
     "tet_14pt_deg5",
     "tet_4pt_deg2",
+    "tri_16pt_deg8",
+    "paper_rule",
     "collapsed_gauss",
     "monomial_exponents",
     "exact_monomial_integral",
@@ -234,6 +236,61 @@ def tet_4pt_deg2() -> Rule:
     _check_exact(rule)
     _check_interior(rule)
     return rule
+
+
+def _tri_orbit_s111(a: float, b: float) -> np.ndarray:
+    """Barycentric orbit of (a, b, 1-a-b): its six permutations."""
+    c = 1.0 - a - b
+    lam = np.array([[a, b, c], [a, c, b], [b, a, c], [b, c, a], [c, a, b], [c, b, a]])
+    return lam[:, 1:]
+
+
+@lru_cache(maxsize=None)
+def tri_16pt_deg8() -> Rule:
+    """Fully symmetric 16-point degree-8 triangle rule (the size and degree the
+    paper uses for P2 surfaces, Sec. 4.2): centroid + three S21 orbits + one
+    S111 orbit.  Unknowns (w0, a1, w1, a2, w2, a3, w3, b1, b2, w4); equations:
+    every monomial of degree <= 8.  Solved by Gauss-Newton from a few coarse
+    starts; the first root with all points interior and positive weights is
+    kept (checked, with exactness to 1e-14)."""
+    exps = monomial_exponents(2, 8)
+
+    def build(p):
+        w0, a1, w1, a2, w2, a3, w3, b1, b2, w4 = p
+        pts = np.vstack([[[1 / 3, 1 / 3]], _tri_orbit_s21(a1), _tri_orbit_s21(a2), _tri_orbit_s21(a3),
+                         _tri_orbit_s111(b1, b2)])
+        wts = np.concatenate([[w0], np.full(3, w1), np.full(3, w2), np.full(3, w3), np.full(6, w4)])
+        return pts, wts
+
+    starts = [[0.07, 0.45, 0.05, 0.17, 0.05, 0.05, 0.015, 0.26, 0.01, 0.014],
+              [0.07, 0.46, 0.045, 0.17, 0.05, 0.06, 0.015, 0.30, 0.02, 0.01],
+              [0.06, 0.44, 0.04, 0.2, 0.04, 0.05, 0.02, 0.25, 0.03, 0.012]]
+    for st in starts:
+        p = _gauss_newton(build, st, exps, iters=400)
+        pts, wts = build(p)
+        rule = Rule(2, pts, wts, 8, "tri16_deg8")
+        try:
+            _check_exact(rule)
+            _check_interior(rule)
+        except RuntimeError:
+            continue
+        return rule
+    raise RuntimeError("no admissible 16-point degree-8 root from the starts")
+
+
+def paper_rule(dim: int) -> Rule:
+    """Rules of the sizes and degrees the paper names for P2 (Sec. 4.2: order
+    10, 8 and 7 in one, two and three dimensions), derived here: 6-point Gauss
+    (degree 11 >= 10) on the interval, the 16-point degree-8 symmetric triangle
+    rule, and for the tetrahedron a degree-7 conical product rule (64 points;
+    the paper's symmetric tet rule is not transcribed)."""
+    if dim == 1:
+        return gauss_interval(6)
+    if dim == 2:
+        return tri_16pt_deg8()
+    if dim == 3:
+        return collapsed_gauss(3, 4)
+    raise ValueError(dim)
 
 
 def _check_interior(rule: Rule) -> None:

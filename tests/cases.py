@@ -68,6 +68,10 @@ def build_cases():
     c["sphere_p2_gauss9"] = (meshes.radial_perturbation(x), e, 2, 2, quadrature.collapsed_gauss(2, 3))
     c["disk_p1_gauss4"] = (*meshes.hex_disk(8, 1), 2, 1, quadrature.collapsed_gauss(2, 2))
     c["cube_p2_gauss8"] = (*meshes.kuhn_cube_p2(3), 3, 2, quadrature.collapsed_gauss(3, 2))
+    # the rule sizes the paper uses for P2 (order 10 / 8 / 7 in 1-D / 2-D / 3-D)
+    c["ellipsoid_p2_paper16"] = (*meshes.ellipsoid(2, sigma=1e-2, seed=6), 2, 2, quadrature.paper_rule(2))
+    c["curve_p2_paper6"] = (*meshes.closed_curve_p2(120, seed=10), 1, 2, quadrature.paper_rule(1))
+    c["cube_p2_paper64"] = (*meshes.kuhn_cube_p2(2), 3, 2, quadrature.paper_rule(3))
     return c
 
 

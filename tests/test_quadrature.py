@@ -36,6 +36,9 @@ RULES = [
     (Q.tri_7pt_deg5(), 0.5),
     (Q.tet_4pt_deg2(), 1.0 / 6.0),
     (Q.tet_14pt_deg5(), 1.0 / 6.0),
+    (Q.tri_16pt_deg8(), 0.5),
+    (Q.paper_rule(1), 1.0),
+    (Q.paper_rule(3), 1.0 / 6.0),
     (Q.collapsed_gauss(2, 6), 0.5),
     (Q.collapsed_gauss(3, 5), 1.0 / 6.0),
 ]
@@ -86,3 +89,16 @@ def test_tri7_orbit_parameters_closed_form():
     s15 = 15 ** 0.5
     assert sorted(reps) == sorted([round((6 - s15) / 21, 12), round((6 + s15) / 21, 12)])
     assert abs(r.w[0] - 9 / 80) < 1e-14
+
+
+def test_sixteen_point_rule_is_symmetric_and_interior():
+    """The derived degree-8 rule: 16 points, positive weights, every point inside
+    the triangle, and invariant under the permutations of the barycentrics."""
+    r = Q.tri_16pt_deg8()
+    assert r.w.size == 16 and r.degree == 8 and np.all(r.w > 0)
+    lam = np.column_stack([1.0 - r.xi.sum(axis=1), r.xi])
+    assert np.all(lam > 0)
+    key = sorted(zip(np.round(np.sort(lam, axis=1), 12).tolist(), np.round(r.w, 14)))
+    for perm in ([1, 0, 2], [2, 1, 0], [0, 2, 1]):
+        lp = lam[:, perm]
+        assert sorted(zip(np.round(np.sort(lp, axis=1), 12).tolist(), np.round(r.w, 14))) == key
