@@ -275,12 +275,27 @@ def run_c5(args):
     nl = lfem.assemble_mcf_nonlinear(pat, xd, rule, uf).cpu().numpy()
     onl = oracle.kll(xh, e, 2, rule.xi, rule.w, uf.cpu().numpy())
     nl_err = float(np.abs(nl - onl).max() / np.abs(onl).max())
+    # one step of Dziuk's scheme on the final surface: FP64 assembly + PCG on the GPU,
+    # against the oracle's direct solve
+    xs = xd.clone()
+    x1, cg_it = lfem.mcf_step(pat, xs, rule, 1e-4, rtol=1e-12, max_iter=5000)
+    t_mcf = []
+    for _ in range(3):
+        a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        lfem.mcf_step(pat, xs, rule, 1e-4, rtol=1e-12, max_iter=5000, out=x1)
+        b0.record()
+        torch.cuda.synchronize()
+        t_mcf.append(a0.elapsed_time(b0))
+    ox1 = oracle.mcf_step(xh, e, 2, 2, rule.xi, rule.w, 1e-4)
+    mcf_err = float(np.abs(x1.cpu().numpy() - ox1).max() / np.abs(ox1).max())
     _line(args, "evolving_ellipsoid_r7_100_steps_plus_adjoint", e.shape[0] / (ms_step * 1e-3), "elements/s",
           ms_step,
           {"config": {"elements": int(e.shape[0]), "steps": steps, "tau": tau, "precision": "mixed, graph replay"},
            "fp64_assembly_ms": ms64, "adjoint_fwd_bwd_ms": ms_adj, "fp64_fallback_elements_final": fallback,
            "adjoint_vs_oracle_max_rel": gerr, "oracle_adjoint_s": t_orc, "L": float(L),
-           "load_vector_ms": ms_load, "mcf_nonlinear_ms": ms_nl, "mcf_nonlinear_vs_oracle_max_rel": nl_err})
+           "load_vector_ms": ms_load, "mcf_nonlinear_ms": ms_nl, "mcf_nonlinear_vs_oracle_max_rel": nl_err,
+           "dziuk_step_ms": min(t_mcf), "dziuk_step_cg_iterations": cg_it, "dziuk_step_vs_oracle_max_rel": mcf_err})
 
 
 def run_c2q16(args):

@@ -223,6 +223,23 @@ lfem_status lfem_assemble_load(lfem_pattern_t p, const double* coords, int ambie
 lfem_status lfem_assemble_mcf_nonlinear(lfem_pattern_t p, const double* coords, const lfem_quad* quad,
                                         const double* u, double* out, void* cuda_stream);
 
+/* One step of Dziuk's scheme for mean curvature flow, the classical method the
+ * paper's flow example builds on (Sec. 5.1):
+ *   (M(x0) + tau A(x0)) x1 = M(x0) x0      (one system per coordinate),
+ * M and A assembled in FP64 on the pattern, the systems solved together by a
+ * Jacobi-preconditioned conjugate gradient (hand-written kernels, reductions
+ * in a fixed order: bit-reproducible), started from x0, stopped when every
+ * column's residual satisfies |r| <= rtol |M x0| (checked every 8
+ * iterations) or after max_iter iterations.  Curves in R^2 and surfaces in R^3
+ * (ambient = dim + 1), else LFEM_E_UNSUPPORTED.
+ *   coords:     x0 [n_nodes][ambient] device doubles.
+ *   coords_out: x1 [n_nodes][ambient] device doubles (may equal coords).
+ *   iterations: host int, the CG iterations done (== max_iter: not converged).
+ * Synchronises the stream (convergence checks); scratch (3 nnz + 6 n_nodes x
+ * ambient doubles) is allocated by the pattern on first use and kept. */
+lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad, double tau,
+                          double rtol, int max_iter, double* coords_out, int* iterations, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Adjoint: for L = gM.M + gA.A + gMC.MC (dot products over the CSR values),
  * g_coords [n_nodes][ambient] = dL/d coords (overwritten) and, when g_coef is

@@ -16,4 +16,5 @@ from .oracle import (  # noqa: F401
     adjoint,
     load,
     kll,
+    mcf_step,
 )

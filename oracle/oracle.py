@@ -215,6 +215,28 @@ def kll(coords, conn, order, xi, w, u, mutation=0):
     return out
 
 
+def mcf_step(coords, conn, dim, order, xi, w, tau, mutation=0):
+    """One step of Dziuk's scheme (the starting point of the flow example, Sec. 5.1):
+    (M(x0) + tau A(x0)) x1 = M(x0) x0, per coordinate, with the oracle's FP64 M and A
+    and a sparse direct solve (library primitive).  Returns x1 [N][n]."""
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spl
+
+    coords = _f64(coords)
+    rp, ci, M, A, _ = assemble(coords, conn, dim, order, xi, w, mutation=mutation)
+    n = coords.shape[0]
+    Mm = sps.csr_matrix((M, ci, rp), shape=(n, n))
+    Km = sps.csr_matrix((M + tau * A, ci, rp), shape=(n, n))
+    rhs = Mm @ coords
+    out = np.empty_like(coords)
+    used = np.diff(rp) > 0
+    K_used = Km[used][:, used].tocsc()
+    sol = spl.spsolve(K_used, rhs[used])
+    out[used] = sol.reshape(-1, coords.shape[1])
+    out[~used] = coords[~used]
+    return out
+
+
 def adjoint(coords, conn, dim, order, xi, w, coef, pat, gM=None, gA=None, gMC=None, mutation=0):
     """dL/dx [N][n] and dL/dc [nE][Q] for L = gM.M + gA.A + gMC.MC (closed forms in
     lfem_oracle.c; derived from Eqs. reference_quadrature_mass / _stiffness)."""

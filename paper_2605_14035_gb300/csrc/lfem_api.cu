@@ -206,7 +206,7 @@ static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& 
 static void destroy_dev(PatternDev& d) {
   void* ptrs[] = {d.conn,      d.row_ptr,       d.col_idx,   d.inc_ptr,   d.inc_key, d.inc_pos,    d.elem_inc,
                   d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off,
-                  d.slot_off,  d.slot_ent,      d.elem_buf,  d.vec_buf};
+                  d.slot_off,  d.slot_ent,      d.elem_buf,  d.vec_buf,   d.mcf_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = PatternDev{};
@@ -589,6 +589,65 @@ extern "C" {
 lfem_status lfem_assemble_load(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                                const double* f, double* b, void* cuda_stream) {
   return vectors_common(p, coords, ambient, quad, f, b, 0, (cudaStream_t)cuda_stream);
+}
+
+lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad, double tau,
+                          double rtol, int max_iter, double* coords_out, int* iterations, void* cuda_stream) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  if (!supported(p->dim, ambient, p->order) || ambient != p->dim + 1)
+    return fail(LFEM_E_UNSUPPORTED, "mean curvature flow needs a curve in R^2 or a surface in R^3");
+  if (!(tau >= 0.0) || !(rtol > 0.0) || max_iter <= 0) return fail(LFEM_E_ARG, "tau, rtol or max_iter");
+  if (!iterations || (p->n_nodes > 0 && (!coords || !coords_out))) return fail(LFEM_E_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int nc = ambient;
+  const size_t nnz = (size_t)p->nnz, n = (size_t)p->n_nodes;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_mat = al(sizeof(double) * nnz), b_vec = al(sizeof(double) * n * nc), b_dg = al(sizeof(double) * n);
+  const size_t b_part = al(sizeof(double) * 256 * 3), b_sc = al(sizeof(McfScalars));
+  const size_t need = 3 * b_mat + b_dg + 6 * b_vec + b_part + b_sc;
+  if (need > p->d.mcf_buf_bytes) {
+    if (p->d.mcf_buf) cudaFree(p->d.mcf_buf);
+    p->d.mcf_buf = nullptr;
+    p->d.mcf_buf_bytes = 0;
+    if (cudaMalloc(&p->d.mcf_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LFEM_E_NOMEM, "flow-step scratch allocation failed");
+    }
+    p->d.mcf_buf_bytes = need;
+  }
+  char* base = static_cast<char*>(p->d.mcf_buf);
+  auto take = [&](size_t b) {
+    char* r = base;
+    base += b;
+    return r;
+  };
+  McfSolveArgs s{};
+  double* M = reinterpret_cast<double*>(take(b_mat));
+  double* A = reinterpret_cast<double*>(take(b_mat));
+  s.K = reinterpret_cast<double*>(take(b_mat));
+  s.dinv = reinterpret_cast<double*>(take(b_dg));
+  s.X = reinterpret_cast<double*>(take(b_vec));
+  s.B = reinterpret_cast<double*>(take(b_vec));
+  s.Q = reinterpret_cast<double*>(take(b_vec));
+  s.R = reinterpret_cast<double*>(take(b_vec));
+  s.Z = reinterpret_cast<double*>(take(b_vec));
+  s.P = reinterpret_cast<double*>(take(b_vec));
+  s.part = reinterpret_cast<double*>(take(b_part));
+  s.scalars = reinterpret_cast<McfScalars*>(take(b_sc));
+  lfem_status e = lfem_assemble(p, coords, ambient, quad, nullptr, 0, LFEM_MASS | LFEM_STIFF, LFEM_FP64, M, A,
+                                nullptr, cuda_stream);
+  if (e != LFEM_OK) return e;
+  s.row_ptr = p->d.row_ptr;
+  s.col_idx = p->d.col_idx;
+  s.M = M;
+  s.A = A;
+  s.tau = tau;
+  s.n = p->n_nodes;
+  s.X0 = coords;
+  s.X_out = coords_out;
+  s.rtol = rtol;
+  s.max_iter = max_iter;
+  return run_mcf_solve(nc, s, st, iterations);
 }
 
 lfem_status lfem_assemble_mcf_nonlinear(lfem_pattern_t p, const double* coords, const lfem_quad* quad,

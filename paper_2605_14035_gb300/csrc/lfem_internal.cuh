@@ -421,6 +421,36 @@ struct VecArgs {
   TabRef tab;
 };
 
+// Device scalars of the solve, per column.
+struct McfScalars {
+  double rz[3], pq[3], rz_new[3], rr[3], bb[3];
+};
+
+// One mean-curvature-flow step (mcf.cu): the pattern's CSR arrays, the
+// assembled M and A, and the solver's work vectors ([n][nc], nc = ambient).
+struct McfSolveArgs {
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* M;
+  const double* A;
+  double tau;
+  int32_t n;
+  double* K;
+  double* dinv;
+  const double* X0;
+  double* X;
+  double* B;
+  double* Q;
+  double* R;
+  double* Z;
+  double* P;
+  double* part;
+  McfScalars* scalars;
+  double* X_out;
+  double rtol;
+  int max_iter;
+};
+
 struct PatternDev {
   int32_t* conn = nullptr;       // [nE][ref] device copy
   int64_t* row_ptr = nullptr;    // [N+1]
@@ -440,6 +470,8 @@ struct PatternDev {
   size_t elem_buf_bytes = 0;
   double* vec_buf = nullptr;     // vector assembly: local vectors [nE][ref][nc] (scratch)
   size_t vec_buf_bytes = 0;
+  void* mcf_buf = nullptr;       // mean-curvature-flow step: matrices and solver vectors (scratch)
+  size_t mcf_buf_bytes = 0;
   uint8_t* tile_meta = nullptr;  // per-tile metadata blocks (see TileHdr)
   int64_t* tile_meta_off = nullptr;  // [T+1] byte offsets, multiples of 16
 };

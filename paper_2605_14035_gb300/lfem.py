@@ -26,7 +26,7 @@ STATUS = {0: "LFEM_OK", 1: "LFEM_E_ARG", 2: "LFEM_E_INDEX", 3: "LFEM_E_UNSUPPORT
 EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
     "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_set_mixed_kappa", "lfem_assemble_load",
-    "lfem_assemble_mcf_nonlinear", "lfem_assemble_adjoint", "lfem_eval_points",
+    "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
     "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
@@ -66,6 +66,7 @@ def _load():
         "lfem_set_mixed_kappa": [P, ctypes.c_double],
         "lfem_assemble_load": [P, P, I, P, P, P, P],
         "lfem_assemble_mcf_nonlinear": [P, P, P, P, P, P],
+        "lfem_mcf_step": [P, P, I, P, ctypes.c_double, ctypes.c_double, I, P, P, P],
         "lfem_assemble_adjoint": [P, P, I, P, P, P, P, P, P, P, P],
         "lfem_eval_points": [P, L, I, I, P, I, P, P, P],
         "lfem_geometry": [P, L, I, I, P, I, P, P, P, P, P],
@@ -352,6 +353,18 @@ def assemble_mcf_nonlinear(pat: Pattern, coords: torch.Tensor, rule, u: torch.Te
     out = torch.empty(4, pat.n_nodes, dtype=torch.float64, device=coords.device)
     _check(_lib.lfem_assemble_mcf_nonlinear(pat.handle, _ptr(coords), rule.ref, _ptr(u), _ptr(out), _stream(stream)))
     return out
+
+
+def mcf_step(pat: Pattern, coords: torch.Tensor, rule, tau: float, rtol: float = 1e-12, max_iter: int = 2000,
+             out=None, stream=None):
+    """lfem_mcf_step: one step of Dziuk's scheme; returns (x1, cg_iterations)."""
+    coords = _dev_f64(coords, "coords")
+    rule = as_rule(rule)
+    x1 = torch.empty_like(coords) if out is None else _dev_f64(out, "out")
+    it = ctypes.c_int()
+    _check(_lib.lfem_mcf_step(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref, float(tau), float(rtol),
+                              int(max_iter), _ptr(x1), ctypes.byref(it), _stream(stream)))
+    return x1, int(it.value)
 
 
 def eval_points(conn, dim, order, coords, rule, stream=None):

@@ -247,6 +247,19 @@ def check_kll_identity_normal(mutation=0):
     return worst
 
 
+def check_mcf_sphere_step(mutation=0):
+    """One step of Dziuk's scheme on the unit sphere shrinks it by the factor
+    1 / (1 + 2 tau): with A x = M (2 x / r^2) for the sphere (H = 2 / r),
+    (M + tau A) c x0 = M x0 gives c = 1 / (1 + 2 tau).  P2 icosphere level 3,
+    tau = 1e-3: every node's radius against that factor."""
+    x, e = meshes.icosphere(3, 2)
+    r = quadrature.default_rule(2, 2)
+    tau = 1e-3
+    x1 = oracle.mcf_step(x, e, 2, 2, r.xi, r.w, tau, mutation=mutation)
+    rad = np.linalg.norm(x1, axis=1)
+    return float(np.abs(rad - 1.0 / (1.0 + 2.0 * tau)).max())
+
+
 ALL_CHECKS = {
     "lagrange": (check_lagrange, 1e-8),
     "affine_exact": (check_affine_exact, 1e-12),
@@ -256,6 +269,7 @@ ALL_CHECKS = {
     "fd": (check_fd, 1e-6),
     "load_is_mass_times_f": (check_load_is_mass_times_f, 1e-13),
     "kll_identity_normal": (check_kll_identity_normal, 1e-12),
+    "mcf_sphere_step": (check_mcf_sphere_step, 2e-5),
 }
 
 

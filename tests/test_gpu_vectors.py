@@ -1,5 +1,6 @@
-"""Load vector (Sec. 2) and the non-linear vectors of the mean curvature flow
-system (Sec. 5.1) on the GPU against the FP64 oracle, on the same seeded inputs."""
+"""Load vector (Sec. 2), the non-linear vectors of the mean curvature flow
+system (Sec. 5.1) and one step of Dziuk's scheme on the GPU against the FP64
+oracle, on the same seeded inputs."""
 import numpy as np
 import pytest
 import torch
@@ -66,3 +67,22 @@ def test_vectors_edge_cases(lfem):
     b = lfem.assemble_load(pat, dev(xs), rs, dev(np.ones(xs.shape[0]))).cpu().numpy()
     assert b[-1] == 0.0
     assert abs(b[:-1].sum() - oracle.load(xs, es, ds, ps, rs.xi, rs.w, np.ones(xs.shape[0])).sum()) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["ellipsoid_p2", "perturbed_sphere_p2", "sphere_p1", "curve_p2", "cube_boundary_p2"])
+def test_mcf_step(name, lfem):
+    x, e, d, p, rule = CASES[name]
+    tau = 1e-3
+    ref = oracle.mcf_step(x, e, d, p, rule.xi, rule.w, tau)
+    pat = lfem.Pattern(dev(e), x.shape[0], d, p)
+    xd = dev(x)
+    x1, it = lfem.mcf_step(pat, xd, rule, tau, rtol=1e-13, max_iter=5000)
+    again, it2 = lfem.mcf_step(pat, xd, rule, tau, rtol=1e-13, max_iter=5000)
+    assert it < 5000 and it == it2
+    got = x1.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert torch.equal(x1, again)
+    # in place
+    xin = xd.clone()
+    lfem.mcf_step(pat, xin, rule, tau, rtol=1e-13, max_iter=5000, out=xin)
+    assert torch.equal(xin, x1)
