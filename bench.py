@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--batch-slots", default="2048,3072", help="tile capacities the batch workload tries")
     return ap.parse_args()
 
 

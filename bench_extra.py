@@ -166,13 +166,15 @@ def run_c4(args):
     s = torch.cuda.Stream()
     timed = _timer(torch, torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda"))
     best = None
-    for slots in ((2048, 3072) if not args.no_autotune else (2048,)):
+    cands = {}
+    for slots in (tuple(int(v) for v in args.batch_slots.split(",")) if not args.no_autotune else (2048,)):
         for m in mesh_list:
             m["pattern"].retile(slots)
         batch = lfem.Batch([{k: m[k] for k in ("pattern", "coords", "rule")} for m in mesh_list], which=3)
         with torch.cuda.stream(s):
             ms = timed(lambda: batch.graph_launch(s), args.steps, args.warmup, stream=s)
         batch.sync_status(s)
+        cands[slots] = ms
         if best is None or ms < best[0]:
             best = (ms, slots, batch.info())
         del batch
@@ -191,7 +193,7 @@ def run_c4(args):
     peak, kind = bench.measured_peaks()
     ach = alg / (ms * 1e-3) / 1e9
     _line(args, "batch_512_meshes_M_A", n_el / (ms * 1e-3), "elements/s", ms,
-          {"config": {"meshes": len(mesh_list), "elements": int(n_el), "tile_slots": slots,
+          {"config": {"meshes": len(mesh_list), "elements": int(n_el), "tile_slots": slots, "candidates_ms": cands,
                       "work_items": binfo["work_items"], "l2": "flushed between steps",
                       "generation_s": round(t_gen, 1), "pattern_build_s": round(t_pat, 1)},
            "fp64_plain_per_mesh": {"value": n_el / (ms64 * 1e-3), "ms_per_step": ms64},
