@@ -42,12 +42,14 @@
 #define ORACLE_MUTATION 0 /* >0 only in tests that plant a known mistake */
 #endif
 
-#define MAXREF 10
+#define MAXREF 15
 #define MAXD 3
 
 static int n_ref(int dim, int order) {
   if (order == 1) return dim + 1;
   if (order == 2) return (dim + 1) * (dim + 2) / 2;
+  /* orders 3, 4 on curves and triangles: C(p + d, d) */
+  if ((order == 3 || order == 4) && dim <= 2) return dim == 1 ? order + 1 : (order + 1) * (order + 2) / 2;
   return -1;
 }
 
@@ -58,6 +60,76 @@ static const int EDGES3[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}}
 
 static const int (*edge_list(int dim))[2] {
   return dim == 1 ? EDGES1 : (dim == 2 ? EDGES2 : EDGES3);
+}
+
+/*
+ * Orders p = 3, 4 (curves and triangles): the Lagrange basis of the nodes
+ * lambda = alpha / p, |alpha| = p, written in barycentric coordinates as
+ *   phi_alpha = prod_i l_{alpha_i}(lambda_i),  l_k(t) = prod_{j<k} (p t - j) / (j + 1),
+ * which is 1 at its own node and 0 at every other (l_k vanishes at t = j/p,
+ * j < k).  Node order: corners; then, edge by edge in the P2 edge order
+ * (i, j), the p - 1 nodes alpha = (p - k) e_i + k e_j, k = 1..p-1 (from corner
+ * i towards j); then the triangle's interior nodes (every alpha_i >= 1) in
+ * increasing (alpha_1, alpha_2).
+ */
+static int node_multi_indices(int dim, int p, int (*al)[MAXD + 1]) {
+  int cnt = 0;
+  for (int i = 0; i <= dim; ++i) {
+    for (int c = 0; c <= dim; ++c) al[cnt][c] = 0;
+    al[cnt++][i] = p;
+  }
+  const int(*ed)[2] = edge_list(dim);
+  const int ne = dim == 1 ? 1 : 3;
+  for (int k = 0; k < ne; ++k)
+    for (int t = 1; t < p; ++t) {
+      for (int c = 0; c <= dim; ++c) al[cnt][c] = 0;
+      al[cnt][ed[k][0]] = p - t;
+      al[cnt][ed[k][1]] = t;
+      ++cnt;
+    }
+  if (dim == 2)
+    for (int a1 = 1; a1 < p; ++a1)
+      for (int a2 = 1; a1 + a2 < p; ++a2) {
+        al[cnt][0] = p - a1 - a2;
+        al[cnt][1] = a1;
+        al[cnt][2] = a2;
+        ++cnt;
+      }
+  return cnt;
+}
+
+/* l_k(t) and its derivative for the order-p Lagrange factors. */
+static void lag_factor(int p, int k, double t, double* v, double* dv) {
+  double val = 1.0, der = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double f = (p * t - j) / (j + 1), df = (double)p / (j + 1);
+    der = der * f + val * df;
+    val *= f;
+  }
+  *v = val;
+  *dv = der;
+}
+
+static void basis_high(int dim, int p, const double* lam, double dlam[][MAXD], double* phi, double dphi[][MAXD]) {
+  int al[MAXREF][MAXD + 1];
+  const int ref = node_multi_indices(dim, p, al);
+  for (int a = 0; a < ref; ++a) {
+    double v[MAXD + 1], dv[MAXD + 1];
+    for (int i = 0; i <= dim; ++i) lag_factor(p, al[a][i], lam[i], &v[i], &dv[i]);
+    double prod = 1.0;
+    for (int i = 0; i <= dim; ++i) prod *= v[i];
+    phi[a] = prod;
+    for (int m = 0; m < dim; ++m) {
+      double g = 0.0;
+      for (int i = 0; i <= dim; ++i) {
+        double rest = dv[i] * dlam[i][m];
+        for (int l = 0; l <= dim; ++l)
+          if (l != i) rest *= v[l];
+        g += rest;
+      }
+      dphi[a][m] = g;
+    }
+  }
 }
 
 /* Basis values phi[a] and reference gradients dphi[a][m] at reference point xi. */
@@ -75,6 +147,10 @@ static void basis(int dim, int order, const double* xi, double* phi, double dphi
       phi[a] = lam[a];
       for (int m = 0; m < dim; ++m) dphi[a][m] = dlam[a][m];
     }
+    return;
+  }
+  if (order >= 3) {
+    basis_high(dim, order, lam, dlam, phi, dphi);
     return;
   }
   for (int a = 0; a <= dim; ++a) {
@@ -222,7 +298,7 @@ static void element_qp(int dim, int order, int n, const double* X /*[ref][n]*/, 
 
 static int check_combo(int dim, int order, int n) {
   if (dim < 1 || dim > 3 || n < dim || n > 3) return 1;
-  if (order != 1 && order != 2) return 1;
+  if (order < 1 || order > 4 || (order > 2 && dim > 2)) return 1;
   if (dim == 2 && n == 3) return 0;
   if (dim == n) return 0;
   if (dim == 1) return 0;

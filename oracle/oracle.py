@@ -75,7 +75,11 @@ def _i32(a):
 
 def n_ref(dim: int, order: int) -> int:
     """Local nodes per element, C(p+d, d) (Sec. 4, dim(E))."""
-    return {1: dim + 1, 2: (dim + 1) * (dim + 2) // 2}[order]
+    from math import comb
+
+    if order in (1, 2) or (order in (3, 4) and dim <= 2):
+        return comb(order + dim, dim)
+    raise ValueError((dim, order))
 
 
 def tabulate(dim, order, xi, mutation=0):

@@ -139,6 +139,57 @@ def icosphere(level: int, order: int = 1):
     return renumber_first_touch(v, f)
 
 
+def to_order(v: np.ndarray, f: np.ndarray, order: int, project=None):
+    """Order-p nodes (p = 3, 4) from a P1 curve or triangle mesh (the node
+    generation of the paper's preprocessing, Sec. 4): corners keep their
+    numbers; each edge gets p - 1 nodes at lambda = k/p, numbered along the
+    edge from its lower to its higher vertex number and shared by the elements
+    that meet there; each triangle gets its (p-1)(p-2)/2 interior nodes.  Local
+    order: corners, then per local edge (0,1) [, (1,2), (2,0)] the nodes from the
+    edge's first corner to its second, then the interior nodes in increasing
+    (alpha_1, alpha_2) for barycentric alpha / p.  Positions are the straight
+    ones (sum lambda_i x_i), then `project` if given."""
+    if order not in (3, 4):
+        raise ValueError(order)
+    dim = f.shape[1] - 1
+    local_edges = [(0, 1)] if dim == 1 else TRI_EDGES
+    nv = v.shape[0]
+    edges, eid = _edge_ids(f, nv, local_edges)          # edges[k] = (low, high)
+    n_e = edges.shape[0]
+    cols, pos = [f], [v]
+    ts = np.arange(1, order) / order
+    # edge nodes along low -> high
+    epos = v[edges[:, 0]][:, None, :] * (1 - ts)[None, :, None] + v[edges[:, 1]][:, None, :] * ts[None, :, None]
+    pos.append(epos.reshape(-1, v.shape[1]))
+    for le, (i, j) in enumerate(local_edges):
+        forward = f[:, i] < f[:, j]
+        for k in range(1, order):
+            kk = np.where(forward, k, order - k)
+            cols.append((nv + eid[:, le] * (order - 1) + (kk - 1))[:, None])
+    if dim == 2:
+        alphas = [(order - a1 - a2, a1, a2) for a1 in range(1, order) for a2 in range(1, order - a1)]
+        base = nv + n_e * (order - 1)
+        n_int = len(alphas)
+        for t, al in enumerate(alphas):
+            lam = np.array(al, float) / order
+            pos.append(lam[0] * v[f[:, 0]] + lam[1] * v[f[:, 1]] + lam[2] * v[f[:, 2]])
+            cols.append((base + np.arange(f.shape[0]) * n_int + t)[:, None])
+        # interior positions were appended per t; reorder to element-major numbering
+        ints = np.stack(pos[2:], axis=1).reshape(-1, v.shape[1])
+        pos = [pos[0], pos[1], ints]
+    x = np.vstack(pos)
+    if project is not None:
+        x[nv:] = project(x[nv:])
+    conn = np.concatenate(cols, axis=1).astype(np.int32)
+    return x, conn
+
+
+def icosphere_high(level: int, order: int):
+    """Unit icosphere with order-3/4 nodes: every generated node projected to S^2."""
+    v, f = _subdivide_sphere(level)
+    return to_order(v, f, order, project=_unit)
+
+
 def radial_perturbation(coords: np.ndarray, amp: float = 0.2):
     """Map every node radially to r(theta, phi) = 1 + amp sin(3 theta) cos(2 phi)
     (theta polar angle from +z, phi = atan2(y, x)); nodes assumed on S^2 first."""

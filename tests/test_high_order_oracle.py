@@ -1,0 +1,155 @@
+"""Orders 3 and 4 (curves and triangles) in the oracle, pinned independently
+of its product formula: the Lagrange basis obtained by inverting the
+Vandermonde matrix of the nodes (exact rationals), exact reference mass and
+stiffness matrices, the Lagrange property, partition of unity and finite
+differences of the gradients."""
+from fractions import Fraction
+from itertools import product
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_14035_gb300.inputs import quadrature
+
+sympy = pytest.importorskip("sympy")
+
+
+def node_alphas(dim, p):
+    """The documented node order: corners, then edge by edge ((0,1) for curves;
+    (0,1), (1,2), (2,0) for triangles) the nodes (p-k) e_i + k e_j, k = 1..p-1,
+    then interior nodes in increasing (alpha_1, alpha_2)."""
+    al = []
+    for i in range(dim + 1):
+        a = [0] * (dim + 1)
+        a[i] = p
+        al.append(a)
+    edges = [(0, 1)] if dim == 1 else [(0, 1), (1, 2), (2, 0)]
+    for i, j in edges:
+        for k in range(1, p):
+            a = [0] * (dim + 1)
+            a[i], a[j] = p - k, k
+            al.append(a)
+    if dim == 2:
+        for a1 in range(1, p):
+            for a2 in range(1, p - a1):
+                al.append([p - a1 - a2, a1, a2])
+    return al
+
+
+def ref_nodes(dim, p):
+    """Reference coordinates (x, y) = (lambda_1, lambda_2) of the nodes, exact."""
+    return [[Fraction(a[m + 1], p) for m in range(dim)] for a in node_alphas(dim, p)]
+
+
+def vandermonde_basis(dim, p):
+    """Lagrange basis as sympy polynomials from the Vandermonde inverse."""
+    xs = sympy.symbols("x0:%d" % dim)
+    monos = [m for m in product(range(p + 1), repeat=dim) if sum(m) <= p]
+    nodes = ref_nodes(dim, p)
+    V = sympy.Matrix([[sympy.prod([sympy.Rational(n[k].numerator, n[k].denominator) ** m[k] for k in range(dim)])
+                       for m in monos] for n in nodes])
+    C = V.inv()  # column a holds the coefficients of phi_a
+    basis = [sum(C[r, a] * sympy.prod([xs[k] ** monos[r][k] for k in range(dim)]) for r in range(len(monos)))
+             for a in range(len(nodes))]
+    return xs, basis
+
+
+def integrate_ref(expr, xs):
+    """Exact integral over the reference interval / triangle, monomial by monomial:
+    int_0^1 x^a = 1/(a+1); over the triangle x^a y^b -> a! b! / (a+b+2)!."""
+    from math import factorial
+
+    total = sympy.Rational(0)
+    for mono, coef in sympy.Poly(sympy.expand(expr), *xs).terms():
+        if len(xs) == 1:
+            total += coef * sympy.Rational(1, mono[0] + 1)
+        else:
+            a, b = mono
+            total += coef * sympy.Rational(factorial(a) * factorial(b), factorial(a + b + 2))
+    return total
+
+
+@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4)])
+def test_lagrange_property_and_partition_of_unity(dim, p):
+    nodes = np.array([[float(c) for c in n] for n in ref_nodes(dim, p)])
+    phi, dphi = oracle.tabulate(dim, p, nodes)
+    assert np.abs(phi - np.eye(len(nodes))).max() < 1e-13
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(0, 1, (20, dim))
+    if dim == 2:
+        pts = pts[pts.sum(1) < 1]
+    phi, dphi = oracle.tabulate(dim, p, pts)
+    assert np.abs(phi.sum(1) - 1).max() < 1e-13
+    assert np.abs(dphi.sum(1)).max() < 1e-12
+    h = 1e-6
+    for m in range(dim):
+        e = np.zeros(dim)
+        e[m] = h
+        fd = (oracle.tabulate(dim, p, pts + e)[0] - oracle.tabulate(dim, p, pts - e)[0]) / (2 * h)
+        assert np.abs(fd - dphi[:, :, m]).max() < 1e-7
+
+
+@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4)])
+def test_reference_matrices_against_vandermonde_basis(dim, p):
+    """Affine reference element (the identity map): oracle M and A against the
+    exact integrals of the Vandermonde-built basis."""
+    xs, basis = vandermonde_basis(dim, p)
+    n = len(basis)
+    Mx = np.array([[float(integrate_ref(basis[a] * basis[b], xs)) for b in range(n)] for a in range(n)])
+    grads = [[sympy.diff(f, x) for x in xs] for f in basis]
+    Ax = np.array([[float(integrate_ref(sum(grads[a][k] * grads[b][k] for k in range(dim)), xs)) for b in range(n)]
+                   for a in range(n)])
+    rule = quadrature.gauss_interval(6) if dim == 1 else quadrature.tri_16pt_deg8()
+    x = np.array([[float(c) for c in nd] for nd in ref_nodes(dim, p)])
+    conn = np.arange(n, dtype=np.int32)[None, :]
+    M, A, _ = oracle.local_matrices(x, conn, dim, p, rule.xi, rule.w)
+    assert np.abs(M[0] - Mx).max() < 1e-14 * 100
+    assert np.abs(A[0] - Ax).max() < 1e-12 * np.abs(Ax).max()
+
+
+def _circle_p1(n):
+    t = 2 * np.pi * np.arange(n) / n
+    x = np.stack([np.cos(t), np.sin(t)], axis=1)
+    conn = np.stack([np.arange(n), (np.arange(n) + 1) % n], axis=1).astype(np.int32)
+    return x, conn
+
+
+@pytest.mark.parametrize("p,rate", [(3, 3.8), (4, 4.8)])
+def test_sphere_and_circle_measures_converge(p, rate):
+    """1^T M 1 -> 4 pi on the projected order-p icosphere and -> 2 pi on the
+    projected order-p circle, at the rate of the geometric error O(h^{p+1})
+    (observed: 4 for p = 3, 6 for p = 4 on the sphere); A.1 = 0."""
+    from paper_2605_14035_gb300.inputs import meshes
+
+    errs = []
+    for lvl in (1, 2, 3):
+        x, e = meshes.icosphere_high(lvl, p)
+        r = quadrature.tri_16pt_deg8()
+        rp, ci, M, A, _ = oracle.assemble(x, e, 2, p, r.xi, r.w)
+        errs.append(abs(M.sum() - 4 * np.pi))
+        rows = np.repeat(np.arange(x.shape[0]), np.diff(rp))
+        assert np.abs(np.bincount(rows, A, x.shape[0])).max() < 1e-12
+    assert np.log2(errs[1] / errs[2]) > rate
+    cerrs = []
+    for n in (16, 32, 64):
+        x1, c1 = _circle_p1(n)
+        x, e = meshes.to_order(x1, c1, p, project=lambda y: y / np.linalg.norm(y, axis=1, keepdims=True))
+        r = quadrature.gauss_interval(6)
+        _, _, M, _, _ = oracle.assemble(x, e, 1, p, r.xi, r.w)
+        cerrs.append(abs(M.sum() - 2 * np.pi))
+    assert np.log2(cerrs[1] / cerrs[2]) > rate
+
+
+def test_order_lifting_shares_edge_nodes():
+    """Generated order-p meshes: every edge node is shared by the two triangles
+    meeting at the edge, and the closed surface has V + (p-1) E + (p-1)(p-2)/2 F nodes."""
+    from paper_2605_14035_gb300.inputs import meshes
+
+    for p in (3, 4):
+        x, e = meshes.icosphere_high(1, p)
+        F = e.shape[0]
+        V, E = F // 2 + 2, 3 * F // 2
+        assert x.shape[0] == V + (p - 1) * E + (p - 1) * (p - 2) // 2 * F
+        counts = np.bincount(e[:, 3:3 + 3 * (p - 1)].ravel(), minlength=x.shape[0])
+        assert set(np.unique(counts[V:V + (p - 1) * E])) == {2}
