@@ -143,6 +143,12 @@ __device__ __forceinline__ bool load_element_data_split(const double* __restrict
       ed.dl[k][i] = dh + dlo;
     }
   }
+  if constexpr (P >= 3) {
+#pragma unroll
+    for (int a = 1; a < REF; ++a)
+#pragma unroll
+      for (int d = 0; d < NA; ++d) ed.rel[a][d] = (xh[a][d] - xh[0][d]) + (xl[a][d] - xl[0][d]);
+  }
   return ok;
 }
 

@@ -147,7 +147,7 @@ lfem_status launch_twopass(const TwoPassArgs& a, bool fast, const FastBankTet& f
     int64_t g = (a.n_elem + 127) / 128;
     if (g > (int64_t)sm_count * 32) g = (int64_t)sm_count * 32;
     bool done = false;
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && D == 3 && P <= 2) {
       if (fast) {
         k_elem_local<D, NA, P, R, true><<<(unsigned)g, 128, 0, st>>>(a, fb);
         done = true;

@@ -69,7 +69,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigne
     const lfem_batch_item& it = items[i];
     lfem_pattern_s* p = it.pattern;
     if (!p) return fail(LFEM_E_ARG, "batch item without pattern");
-    if (!supported(p->dim, it.ambient, p->order) || !batch_type_ok(p->dim, it.ambient))
+    if (!supported(p->dim, it.ambient, p->order) || !batch_type_ok(p->dim, it.ambient) || p->order > 2)
       return fail(LFEM_E_UNSUPPORTED, "element type not supported in batches");
     if ((which & LFEM_MASS) && !it.M) return fail(LFEM_E_ARG, "batch item M is NULL");
     if ((which & LFEM_STIFF) && !it.A) return fail(LFEM_E_ARG, "batch item A is NULL");

@@ -22,6 +22,8 @@ lfem_status run_twopass_d3(int P, bool mixed, bool fast, const FastBankTet& fb, 
                            cudaStream_t st);
 lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset);
 lfem_status bank_upload_vec(const void* src, size_t bytes, size_t offset);
+lfem_status bank_upload_high(const void* src, size_t bytes, size_t offset);
+lfem_status run_twopass_high(int D, int NA, int P, bool mixed, const TwoPassArgs& a, int sms, cudaStream_t st);
 lfem_status run_vectors(int D, int NA, int P, int kind, const VecArgs& a, cudaStream_t st);
 lfem_status run_mcf_solve(int nc, const McfSolveArgs& s, cudaStream_t st, int* iterations);
 

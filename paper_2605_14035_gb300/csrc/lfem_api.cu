@@ -27,7 +27,7 @@ lfem_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool supported(int dim, int ambient, int order) {
-  if (order != 1 && order != 2) return false;
+  if (order < 1 || order > 4 || (order > 2 && dim > 2)) return false;
   if (dim < 1 || dim > 3 || ambient < dim || ambient > 3) return false;
   if (dim == 2 && ambient == 3) return true;
   if (dim == ambient) return true;
@@ -48,6 +48,50 @@ static void edge_nodes(int dim, int k, int& i, int& j) {
   j = E[k][1];
 }
 
+// Orders 3, 4 (curves, triangles): barycentric multi-indices of the nodes in
+// the library's order -- corners; per edge (i, j) of the P2 edge order the
+// nodes (p-k) e_i + k e_j, k = 1..p-1; interior nodes by increasing
+// (alpha_1, alpha_2) -- and the Lagrange basis prod_i l_{alpha_i}(lambda_i),
+// l_k(t) = prod_{j<k} (p t - j) / (j + 1).
+static int high_order_nodes(int dim, int p, int al[][4]) {
+  int n = 0;
+  for (int i = 0; i <= dim; ++i) {
+    for (int c = 0; c < 4; ++c) al[n][c] = c == i ? p : 0;
+    ++n;
+  }
+  const int ne = dim == 1 ? 1 : 3;
+  for (int k = 0; k < ne; ++k) {
+    int i, j;
+    edge_nodes(dim, k, i, j);
+    for (int t = 1; t < p; ++t) {
+      for (int c = 0; c < 4; ++c) al[n][c] = 0;
+      al[n][i] = p - t;
+      al[n][j] = t;
+      ++n;
+    }
+  }
+  if (dim == 2)
+    for (int a1 = 1; a1 < p; ++a1)
+      for (int a2 = 1; a1 + a2 < p; ++a2) {
+        al[n][0] = p - a1 - a2;
+        al[n][1] = a1;
+        al[n][2] = a2;
+        al[n][3] = 0;
+        ++n;
+      }
+  return n;
+}
+
+static void lagrange_factor(int p, int k, double t, double& v, double& dv) {
+  v = 1.0;
+  dv = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double f = (p * t - j) / (j + 1);
+    dv = dv * f + v * ((double)p / (j + 1));
+    v *= f;
+  }
+}
+
 static void host_tables(int dim, int order, const lfem_quad* quad, std::vector<double>& out) {
   const int Q = quad->n_pts, REF = n_ref(dim, order), NE = n_edges(dim, order);
   out.assign((size_t)Q * (1 + REF + REF * dim + NE * dim), 0.0);
@@ -64,6 +108,28 @@ static void host_tables(int dim, int order, const lfem_quad* quad, std::vector<d
     for (int m = 0; m < dim; ++m) lam[m + 1] = quad->xi[q * dim + m];
     for (int i = 0; i <= dim; ++i)
       for (int m = 0; m < dim; ++m) dlam[i][m] = (i == 0) ? -1.0 : (i == m + 1 ? 1.0 : 0.0);
+    if (order >= 3) {
+      int al[16][4];
+      const int n = high_order_nodes(dim, order, al);
+      for (int a = 0; a < n; ++a) {
+        double v[4], dv[4];
+        for (int i = 0; i <= dim; ++i) lagrange_factor(order, al[a][i], lam[i], v[i], dv[i]);
+        double prod = 1.0;
+        for (int i = 0; i <= dim; ++i) prod *= v[i];
+        phi[q * REF + a] = prod;
+        for (int m = 0; m < dim; ++m) {
+          double g = 0.0;
+          for (int i = 0; i <= dim; ++i) {
+            double t = dv[i] * dlam[i][m];
+            for (int l = 0; l <= dim; ++l)
+              if (l != i) t *= v[l];
+            g += t;
+          }
+          dphi[(q * REF + a) * dim + m] = g;
+        }
+      }
+      continue;
+    }
     for (int a = 0; a <= dim; ++a) {
       phi[q * REF + a] = order == 1 ? lam[a] : lam[a] * (2.0 * lam[a] - 1.0);
       for (int m = 0; m < dim; ++m) dphi[(q * REF + a) * dim + m] = order == 1 ? dlam[a][m] : (4.0 * lam[a] - 1.0) * dlam[a][m];
@@ -170,7 +236,8 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
   std::vector<unsigned char> blob(b64 + b32, 0);
   memcpy(blob.data(), t64.data(), b64);
   memcpy(blob.data() + b64, t32.data(), t32.size() * sizeof(float));
-  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch, bank_upload_vec}) {
+  for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch, bank_upload_vec,
+                  bank_upload_high}) {
     lfem_status us = up(blob.data(), blob.size(), used);
     if (us != LFEM_OK) return us;
   }
@@ -369,8 +436,8 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   a.qmin = p->qmin;
   a.status = p->d.status;
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
-  if (p->dim == 3) {
-    // bulk tets: element-major two passes (local-matrix buffer owned by the pattern)
+  if (p->dim == 3 || p->order >= 3) {
+    // bulk tets and orders 3, 4: element-major two passes (local-matrix buffer owned by the pattern)
     const size_t need = (size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8);
     if (need > p->d.elem_buf_bytes) {
       if (p->d.elem_buf) cudaFree(p->d.elem_buf);
@@ -402,6 +469,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
     int sms3 = 0;
     LFEM_CUDA(cudaDeviceGetAttribute(&sms3, cudaDevAttrMultiProcessorCount, p->device));
     if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
+    if (p->dim != 3) return run_twopass_high(p->dim, ambient, p->order, mixed, ta, sms3, st);
     FastBankTet fbt;
     const bool fast3 = mixed && fast_tables_host(3, p->order, quad, fbt.v + (p->order == 1 ? FastBankTet::OFF31
                                                                                           : FastBankTet::OFF32));

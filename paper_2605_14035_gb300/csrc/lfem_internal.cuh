@@ -36,7 +36,10 @@ constexpr int kMaxTileEntries = 16384;    // incidences x ref per tile (node-lis
 // ----------------------------------------------------------------------------
 // Element types
 // ----------------------------------------------------------------------------
-__host__ __device__ constexpr int n_ref(int d, int p) { return p == 1 ? d + 1 : (d + 1) * (d + 2) / 2; }
+// C(p + d, d) local nodes: P1, P2 on every simplex; orders 3 and 4 on curves and triangles.
+__host__ __device__ constexpr int n_ref(int d, int p) {
+  return p == 1 ? d + 1 : (p == 2 ? (d + 1) * (d + 2) / 2 : (d == 1 ? p + 1 : (p + 1) * (p + 2) / 2));
+}
 __host__ __device__ constexpr int n_upper(int ref) { return ref * (ref + 1) / 2; }
 __host__ __device__ constexpr int n_edges(int d, int p) { return p == 2 ? n_ref(d, 2) - (d + 1) : 0; }
 
@@ -175,6 +178,7 @@ struct ElemData {
   static constexpr int NE = Ref<D, P>::NE;
   R e[D][NA];                      // corner edge vectors x_{m+1} - x_0
   R dl[NE > 0 ? NE : 1][NA];       // edge-node deviations
+  R rel[P >= 3 ? REF : 1][NA];     // orders 3, 4: every node relative to node 0
 };
 
 template <int D, int NA, int P, typename R>
@@ -183,6 +187,12 @@ __device__ __forceinline__ void load_element_data(const double (&X)[Ref<D, P>::R
   for (int m = 0; m < D; ++m)
 #pragma unroll
     for (int i = 0; i < NA; ++i) ed.e[m][i] = (R)(X[m + 1][i] - X[0][i]);
+  if constexpr (P >= 3) {
+#pragma unroll
+    for (int a = 1; a < Ref<D, P>::REF; ++a)
+#pragma unroll
+      for (int i = 0; i < NA; ++i) ed.rel[a][i] = (R)(X[a][i] - X[0][i]);
+  }
 #pragma unroll
   for (int k = 0; k < Ref<D, P>::NE; ++k)
 #pragma unroll
@@ -217,15 +227,29 @@ template <int D, int NA, int P, typename R>
 __device__ __forceinline__ void qp_geometry(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb, int q, R wq,
                                             QpGeom<D, NA, P, R>& g) {
   constexpr int NE = Ref<D, P>::NE;
+  if constexpr (P >= 3) {
+    // orders 3, 4: J = sum_a (x_a - x_0) grad^phi_a^T (Eq. F_map differentiated)
+    constexpr int REF = Ref<D, P>::REF;
 #pragma unroll
-  for (int i = 0; i < NA; ++i)
+    for (int i = 0; i < NA; ++i)
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
-      R acc = ed.e[m][i];
+      for (int m = 0; m < D; ++m) {
+        R acc = 0;
 #pragma unroll
-      for (int k = 0; k < NE; ++k) acc = fma(ed.dl[k][i], tb.dpsi[(q * NE + k) * D + m], acc);
-      g.J[i][m] = acc;
-    }
+        for (int a = 1; a < REF; ++a) acc = fma(ed.rel[a][i], tb.dphi[(q * REF + a) * D + m], acc);
+        g.J[i][m] = acc;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        R acc = ed.e[m][i];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) acc = fma(ed.dl[k][i], tb.dpsi[(q * NE + k) * D + m], acc);
+        g.J[i][m] = acc;
+      }
+  }
   if constexpr (D == 1) {
     R tt = 0;
 #pragma unroll

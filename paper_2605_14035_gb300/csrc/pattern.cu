@@ -874,8 +874,9 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   }
   LFEM_CUDA(cudaGetLastError());
   TRY(dalloc(&d.inc_local, n_inc));
-  if (p->dim == 3) {
-    // bulk tets: element-major path (row tiles would recompute most elements several times)
+  if (p->dim == 3 || p->order >= 3) {
+    // bulk tets and orders 3, 4: element-major path (row tiles would recompute
+    // most tets several times; high orders have large local matrices)
     if (n_inc * ref >= INT32_MAX || p->n_elem * n_upper(ref) >= INT32_MAX)
       return fail(LFEM_E_TOO_LARGE, "too many contributions for the element-major path");
     TRY(dalloc(&d.slot_off, nnz + 1));

@@ -150,6 +150,12 @@ lfem_status run_vectors(int D, int NA, int P, int kind, const VecArgs& a, cudaSt
   LFEM_VEC_CASE(2, 3, 2)
   LFEM_VEC_CASE(3, 3, 1)
   LFEM_VEC_CASE(3, 3, 2)
+  LFEM_VEC_CASE(1, 2, 3)
+  LFEM_VEC_CASE(1, 2, 4)
+  LFEM_VEC_CASE(2, 2, 3)
+  LFEM_VEC_CASE(2, 2, 4)
+  LFEM_VEC_CASE(2, 3, 3)
+  LFEM_VEC_CASE(2, 3, 4)
 #undef LFEM_VEC_CASE
   return fail(LFEM_E_UNSUPPORTED, "element type");
 }

@@ -72,6 +72,17 @@ def build_cases():
     c["ellipsoid_p2_paper16"] = (*meshes.ellipsoid(2, sigma=1e-2, seed=6), 2, 2, quadrature.paper_rule(2))
     c["curve_p2_paper6"] = (*meshes.closed_curve_p2(120, seed=10), 1, 2, quadrature.paper_rule(1))
     c["cube_p2_paper64"] = (*meshes.kuhn_cube_p2(2), 3, 2, quadrature.paper_rule(3))
+    # orders 3 and 4 (curves and triangles): element-major path, general Jacobian
+    r16 = quadrature.tri_16pt_deg8()
+    c["sphere_p3"] = (*meshes.icosphere_high(1, 3), 2, 3, r16)
+    c["sphere_p4"] = (*meshes.icosphere_high(1, 4), 2, 4, r16)
+    xd, ed = meshes.hex_disk(4, 1)
+    c["disk_p3"] = (*meshes.to_order(xd, ed, 3), 2, 3, r16)
+    t = 2 * np.pi * np.arange(40) / 40
+    xc = np.stack([np.cos(t), np.sin(t)], axis=1)
+    ec = np.stack([np.arange(40), (np.arange(40) + 1) % 40], axis=1).astype(np.int32)
+    unit = lambda y: y / np.linalg.norm(y, axis=1, keepdims=True)  # noqa: E731
+    c["circle_p4"] = (*meshes.to_order(xc, ec, 4, project=unit), 1, 4, quadrature.gauss_interval(6))
     return c
 
 
