@@ -19,7 +19,13 @@
  *                              Edge-node order: segment (0,1); triangle (0,1),(1,2),(2,0);
  *                              tetrahedron (0,1),(1,2),(2,0),(0,3),(1,3),(2,3).
  *  - Supported (dim, ambient): (1,1) (1,2) (1,3) (2,2) (2,3) (3,3); order 1 or 2
- *    (Table ellFEM_overview).  Anything else: LFEM_E_UNSUPPORTED.
+ *    (Table ellFEM_overview); orders 3 and 4 on curves and triangles (dim <= 2),
+ *    for lfem_pattern, lfem_assemble and the vector assemblies (not for the
+ *    adjoint, the stage entry points, batches or lfem_pattern_csr_noalloc).
+ *    Order-p node order (p = 3, 4): corners; then per edge (i, j) in the order
+ *    above the p - 1 nodes at barycentric ((p-k) e_i + k e_j) / p, k = 1..p-1;
+ *    then the triangle's interior nodes alpha / p (every alpha_i >= 1) in
+ *    increasing (alpha_1, alpha_2).  Anything else: LFEM_E_UNSUPPORTED.
  *  - Quadrature rules are host arrays on the reference simplex (interval [0,1],
  *    triangle conv{0,e1,e2}, tetrahedron conv{0,e1,e2,e3}); weights sum to its
  *    measure.  n_pts <= LFEM_MAX_QPTS.

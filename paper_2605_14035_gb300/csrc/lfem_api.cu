@@ -309,7 +309,8 @@ lfem_status lfem_pattern(const int32_t* conn, int64_t n_elem, int32_t n_nodes, i
   *out = nullptr;
   if (n_elem < 0 || n_nodes < 0) return fail(LFEM_E_ARG, "negative size");
   if (n_elem > 0 && !conn) return fail(LFEM_E_ARG, "conn is NULL");
-  if (dim < 1 || dim > 3 || (order != 1 && order != 2)) return fail(LFEM_E_UNSUPPORTED, "dim/order");
+  if (dim < 1 || dim > 3 || order < 1 || order > 4 || (order > 2 && dim > 2))
+    return fail(LFEM_E_UNSUPPORTED, "dim/order");
   const int ref = n_ref(dim, order);
   if (n_elem >= (1ll << 27) || n_elem * ref >= (1ll << 31)) return fail(LFEM_E_TOO_LARGE, "too many elements");
   cudaStream_t st = (cudaStream_t)cuda_stream;
