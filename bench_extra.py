@@ -337,5 +337,42 @@ def run_c2q16(args):
                         "traffic": None, "algorithmic_bytes": alg, "peak_kind": kind}})
 
 
+def run_p4(args):
+    """Order 4 on the sphere: the P1 icosphere (level 6) lifted to order 4 on the GPU
+    (lfem_lift_order), nodes projected to S^2, then M + A with the 16-point rule."""
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+    x1, e1 = meshes.icosphere(6, 1)
+    xd1, ed1 = torch.from_numpy(x1).cuda(), torch.from_numpy(e1).cuda()
+    p1 = lfem.Pattern(ed1, x1.shape[0], 2, 1)
+    t_lift = []
+    for _ in range(3):
+        a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        xp, ep = lfem.lift_order(p1, xd1, 4)
+        b0.record()
+        torch.cuda.synchronize()
+        t_lift.append(a0.elapsed_time(b0))
+    xp = xp / xp.norm(dim=1, keepdim=True)
+    rule = quadrature.tri_16pt_deg8()
+    pat = lfem.Pattern(ep, xp.shape[0], 2, 4)
+    flush = torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    timed = _timer(torch, flush)
+    res = {}
+    for prec, dt, name in ((lfem.MIXED, torch.float32, "mixed"), (lfem.FP64, torch.float64, "fp64")):
+        out = {k: torch.empty(pat.nnz, dtype=dt, device="cuda") for k in ("M", "A")}
+        ms = timed(lambda: lfem.assemble(pat, xp, rule, which=3, precision=prec, out=out), args.steps, args.warmup)
+        res[name] = {"ms_per_step": ms, "value": ep.shape[0] / (ms * 1e-3),
+                     "area_minus_4pi": float(out["M"].double().sum()) - 4 * np.pi}
+        pat.sync_status()
+    _line(args, "p4_icosphere_r6_M_A_rule16", res["mixed"]["value"], "elements/s", res["mixed"]["ms_per_step"],
+          {"config": {"elements": int(ep.shape[0]), "nodes": int(xp.shape[0]), "nnz_per_matrix": pat.nnz,
+                      "quadrature": "tri 16-point degree 8", "l2": "flushed between steps"},
+           "fp64": res["fp64"], "mixed": res["mixed"], "lift_order_ms": min(t_lift)})
+
+
 def run(args):
-    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "c2q16": run_c2q16}[args.workload](args)
+    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "c2q16": run_c2q16, "p4": run_p4}[args.workload](args)

@@ -295,6 +295,25 @@ lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64
 const char* lfem_last_error(void);
 const char* lfem_status_string(lfem_status s);
 
+/* Order-p nodes from an order-1 curve or triangle mesh (the node generation of
+ * the paper's preprocessing, Sec. 4; orders 2..4).  p1 is the order-1
+ * pattern of the mesh; its edges are the upper slots (i < j) of the pattern's
+ * rows, numbered in CSR order.  Output numbering: the P1 vertices keep their
+ * numbers; then p - 1 nodes per edge, from its lower to its higher vertex
+ * number, at the straight positions x_lo (1 - k/p) + x_hi k/p; then each
+ * triangle's interior nodes at alpha / p in barycentrics (the order-p node
+ * order of the conventions above).  Positions are rounded in a fixed order
+ * (products, then sums left to right), so any implementation that evaluates
+ * the same expressions that way gets the same bits.
+ *   coords:      [n_vertices][ambient] device doubles (the P1 nodes).
+ *   conn_out:    [n_elem][C(order+dim, dim)] device int32, or NULL.
+ *   coords_out:  [n_nodes_out][ambient] device doubles, or NULL.
+ *   n_nodes_out: host; always written.  With both outputs NULL only the size
+ *                is computed.  Synchronises the stream.
+ * Curved geometry: move the generated nodes afterwards (e.g. project them). */
+lfem_status lfem_lift_order(lfem_pattern_t p1, const double* coords, int ambient, int order, int32_t* conn_out,
+                            double* coords_out, int64_t* n_nodes_out, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * CSR pattern without any device allocation.  (The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory at

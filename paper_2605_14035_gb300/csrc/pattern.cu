@@ -997,7 +997,160 @@ lfem_status pattern_csr_noalloc(const int32_t* conn, int64_t nE, int32_t N, int 
   return LFEM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Order-p nodes from an order-1 mesh (the node generation of the paper's
+// preprocessing, Sec. 4).  Edges are the upper slots (i < j) of the P1
+// pattern's rows, numbered in CSR order (row i ascending, then column j), so
+// edge (i, j)'s number is up_start[i] + (position of j in row i) - (entries of
+// row i with column <= i).  Node numbers: vertices, then p - 1 nodes per edge
+// from its lower to its higher vertex, then each triangle's interior nodes.
+// Positions are the straight ones, rounded in a fixed order (products, then
+// sums left to right; no multiply-add contraction).
+// ---------------------------------------------------------------------------
+__global__ void k_lift_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n,
+                             int32_t* __restrict__ up_cnt, int32_t* __restrict__ c_le) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
+    const int64_t b = lo, e = hi;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (col_idx[mid] <= i) lo = mid + 1;
+      else hi = mid;
+    }
+    c_le[i] = (int32_t)(lo - b);
+    up_cnt[i] = (int32_t)(e - lo);
+  }
+}
+
+__global__ void k_lift_corners(const double* __restrict__ x, int64_t n_values, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_values; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = x[i];
+}
+
+__global__ void k_lift_elements(const int32_t* __restrict__ conn, int64_t n_elem, int dim, int na, int order,
+                                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                const int64_t* __restrict__ up_start, const int32_t* __restrict__ c_le,
+                                int32_t n_vert, int64_t n_edges, const double* __restrict__ x, int32_t* conn_out,
+                                double* coords_out) {
+  const int ref1 = dim + 1;
+  const int n_le = dim == 1 ? 1 : 3;
+  const int n_int = dim == 2 ? (order - 1) * (order - 2) / 2 : 0;
+  const int refp = ref1 + n_le * (order - 1) + n_int;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[3];
+    for (int a = 0; a < ref1; ++a) v[a] = conn[e * ref1 + a];
+    int32_t* row = conn_out ? conn_out + e * refp : nullptr;
+    if (row)
+      for (int a = 0; a < ref1; ++a) row[a] = v[a];
+    int slot = ref1;
+    for (int le = 0; le < n_le; ++le) {
+      const int ia = le, ib = (le + 1) % (dim + 1);  // (0,1) | (0,1),(1,2),(2,0)
+      const int32_t i = v[ia], j = v[ib];
+      const int32_t lo_v = i < j ? i : j, hi_v = i < j ? j : i;
+      int64_t lo = row_ptr[lo_v], hi = row_ptr[lo_v + 1];
+      const int64_t rb = lo;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col_idx[mid] < hi_v) lo = mid + 1;
+        else hi = mid;
+      }
+      const int64_t eid = up_start[lo_v] + (lo - rb) - c_le[lo_v];
+      const int64_t first = (int64_t)n_vert + eid * (order - 1);
+      for (int k = 1; k < order; ++k) {
+        if (row) row[slot + k - 1] = (int32_t)(first + (i < j ? k : order - k) - 1);
+        if (coords_out) {
+          const double t = (double)k / (double)order, s = 1.0 - t;
+          for (int c = 0; c < na; ++c)
+            coords_out[(first + k - 1) * na + c] =
+                __dadd_rn(__dmul_rn(x[(int64_t)lo_v * na + c], s), __dmul_rn(x[(int64_t)hi_v * na + c], t));
+        }
+      }
+      slot += order - 1;
+    }
+    if (dim == 2) {
+      const int64_t base = (int64_t)n_vert + n_edges * (order - 1) + e * n_int;
+      int t = 0;
+      for (int a1 = 1; a1 < order; ++a1)
+        for (int a2 = 1; a1 + a2 < order; ++a2, ++t) {
+          if (row) row[slot + t] = (int32_t)(base + t);
+          if (coords_out) {
+            const double l0 = (double)(order - a1 - a2) / order, l1 = (double)a1 / order, l2 = (double)a2 / order;
+            for (int c = 0; c < na; ++c) {
+              const double s01 = __dadd_rn(__dmul_rn(l0, x[(int64_t)v[0] * na + c]), __dmul_rn(l1, x[(int64_t)v[1] * na + c]));
+              coords_out[(base + t) * na + c] = __dadd_rn(s01, __dmul_rn(l2, x[(int64_t)v[2] * na + c]));
+            }
+          }
+        }
+    }
+  }
+}
+
+lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int order, int32_t* conn_out,
+                       double* coords_out, int64_t* n_nodes_out, cudaStream_t st) {
+  PatternDev& d = p->d;
+  const int32_t N = p->n_nodes;
+  int32_t *cnt = nullptr, *cle = nullptr;
+  int64_t *up = nullptr, *scr = nullptr;
+  auto cleanup = [&]() {
+    if (cnt) cudaFree(cnt);
+    if (cle) cudaFree(cle);
+    if (up) cudaFree(up);
+    if (scr) cudaFree(scr);
+  };
+  lfem_status s = LFEM_OK;
+  if ((s = dalloc(&cnt, (int64_t)N + 1)) != LFEM_OK || (s = dalloc(&cle, (int64_t)N + 1)) != LFEM_OK ||
+      (s = dalloc(&up, (int64_t)N + 1)) != LFEM_OK ||
+      (s = dalloc(&scr, scan_scratch_bytes((int64_t)N + 1, 8) / 8)) != LFEM_OK) {
+    cleanup();
+    return s;
+  }
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)N + 1), st);
+  if (N > 0) k_lift_count<<<grid_for(N, 256), 256, 0, st>>>(d.row_ptr, d.col_idx, N, cnt, cle);
+  scan_exclusive<int32_t, int64_t>(cnt, up, (int64_t)N + 1, scr, st);
+  int64_t n_edges = 0;
+  cudaMemcpyAsync(&n_edges, up + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    cleanup();
+    return cuda_fail(ce, "order lifting");
+  }
+  const int n_int = p->dim == 2 ? (order - 1) * (order - 2) / 2 : 0;
+  const int64_t n_out = (int64_t)N + n_edges * (order - 1) + p->n_elem * n_int;
+  *n_nodes_out = n_out;
+  if (n_out >= INT32_MAX) {
+    cleanup();
+    return fail(LFEM_E_TOO_LARGE, "order-p mesh has too many nodes for int32 indices");
+  }
+  if (conn_out || coords_out) {
+    if (coords_out && N > 0)
+      k_lift_corners<<<grid_for((int64_t)N * na, 256), 256, 0, st>>>(coords, (int64_t)N * na, coords_out);
+    if (p->n_elem > 0)
+      k_lift_elements<<<grid_for(p->n_elem, 128), 128, 0, st>>>(d.conn, p->n_elem, p->dim, na, order, d.row_ptr,
+                                                                d.col_idx, up, cle, N, n_edges, coords, conn_out,
+                                                                coords_out);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // scratch is freed below
+    if (ce != cudaSuccess) {
+      cleanup();
+      return cuda_fail(ce, "order lifting");
+    }
+  }
+  cleanup();
+  return LFEM_OK;
+}
+
 }  // namespace lfem
+
+extern "C" lfem_status lfem_lift_order(lfem_pattern_t p, const double* coords, int ambient, int order,
+                                       int32_t* conn_out, double* coords_out, int64_t* n_nodes_out,
+                                       void* cuda_stream) {
+  if (!p || !n_nodes_out) return lfem::fail(LFEM_E_ARG, "NULL argument");
+  if (p->order != 1 || p->dim > 2 || order < 2 || order > 4)
+    return lfem::fail(LFEM_E_UNSUPPORTED, "lifting needs an order-1 curve or triangle pattern and order 2..4");
+  if (ambient < p->dim || ambient > 3) return lfem::fail(LFEM_E_ARG, "ambient");
+  if (coords_out && p->n_nodes > 0 && !coords) return lfem::fail(LFEM_E_ARG, "coords is NULL");
+  return lfem::lift_order(p, coords, ambient, order, conn_out, coords_out, n_nodes_out, (cudaStream_t)cuda_stream);
+}
 
 extern "C" lfem_status lfem_pattern_csr_noalloc(const int32_t* conn, int64_t n_elem, int32_t n_nodes, int dim,
                                                 int order, int64_t* row_ptr, int32_t* col_idx, int64_t col_capacity,

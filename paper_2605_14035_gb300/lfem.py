@@ -26,7 +26,7 @@ STATUS = {0: "LFEM_OK", 1: "LFEM_E_ARG", 2: "LFEM_E_INDEX", 3: "LFEM_E_UNSUPPORT
 EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
     "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_set_mixed_kappa", "lfem_assemble_load",
-    "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_assemble_adjoint", "lfem_eval_points",
+    "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_lift_order", "lfem_assemble_adjoint", "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
     "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
@@ -67,6 +67,7 @@ def _load():
         "lfem_assemble_load": [P, P, I, P, P, P, P],
         "lfem_assemble_mcf_nonlinear": [P, P, P, P, P, P],
         "lfem_mcf_step": [P, P, I, P, ctypes.c_double, ctypes.c_double, I, P, P, P],
+        "lfem_lift_order": [P, P, I, I, P, P, P, P],
         "lfem_assemble_adjoint": [P, P, I, P, P, P, P, P, P, P, P],
         "lfem_eval_points": [P, L, I, I, P, I, P, P, P],
         "lfem_geometry": [P, L, I, I, P, I, P, P, P, P, P],
@@ -365,6 +366,20 @@ def mcf_step(pat: Pattern, coords: torch.Tensor, rule, tau: float, rtol: float =
     _check(_lib.lfem_mcf_step(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref, float(tau), float(rtol),
                               int(max_iter), _ptr(x1), ctypes.byref(it), _stream(stream)))
     return x1, int(it.value)
+
+
+def lift_order(pat1: Pattern, coords: torch.Tensor, order: int, stream=None):
+    """lfem_lift_order: order-p nodes of an order-1 mesh; returns (coords_p, conn_p)."""
+    coords = _dev_f64(coords, "coords")
+    n = ctypes.c_int64()
+    _check(_lib.lfem_lift_order(pat1.handle, _ptr(coords), int(coords.shape[1]), int(order), None, None,
+                                ctypes.byref(n), _stream(stream)))
+    ref = (order + 1) if pat1.dim == 1 else (order + 1) * (order + 2) // 2
+    conn = torch.empty(pat1.n_elem, ref, dtype=torch.int32, device=coords.device)
+    out = torch.empty(n.value, coords.shape[1], dtype=torch.float64, device=coords.device)
+    _check(_lib.lfem_lift_order(pat1.handle, _ptr(coords), int(coords.shape[1]), int(order), _ptr(conn), _ptr(out),
+                                ctypes.byref(n), _stream(stream)))
+    return out, conn
 
 
 def eval_points(conn, dim, order, coords, rule, stream=None):
