@@ -1031,7 +1031,7 @@ __global__ void k_lift_elements(const int32_t* __restrict__ conn, int64_t n_elem
                                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                                 const int64_t* __restrict__ up_start, const int32_t* __restrict__ c_le,
                                 int32_t n_vert, int64_t n_edges, const double* __restrict__ x, int32_t* conn_out,
-                                double* coords_out) {
+                                double* coords_out, int32_t* status) {
   const int ref1 = dim + 1;
   const int n_le = dim == 1 ? 1 : 3;
   const int n_int = dim == 2 ? (order - 1) * (order - 2) / 2 : 0;
@@ -1055,6 +1055,11 @@ __global__ void k_lift_elements(const int32_t* __restrict__ conn, int64_t n_elem
         else hi = mid;
       }
       const int64_t eid = up_start[lo_v] + (lo - rb) - c_le[lo_v];
+      if (lo >= row_ptr[lo_v + 1] || col_idx[lo] != hi_v || eid < 0 || eid >= n_edges) {
+        atomicOr(status, ST_INDEX);  // the pattern does not hold this edge: skip its nodes
+        slot += order - 1;
+        continue;
+      }
       const int64_t first = (int64_t)n_vert + eid * (order - 1);
       for (int k = 1; k < order; ++k) {
         if (row) row[slot + k - 1] = (int32_t)(first + (i < j ? k : order - k) - 1);
@@ -1106,7 +1111,8 @@ lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int orde
   }
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)N + 1), st);
   if (N > 0) k_lift_count<<<grid_for(N, 256), 256, 0, st>>>(d.row_ptr, d.col_idx, N, cnt, cle);
-  scan_exclusive<int32_t, int64_t>(cnt, up, (int64_t)N + 1, scr, st);
+  // up[0..N]: exclusive scan of the N row counts, up[N] = number of edges
+  scan_exclusive<int32_t, int64_t>(cnt, up, (int64_t)N, scr, st);
   int64_t n_edges = 0;
   cudaMemcpyAsync(&n_edges, up + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   cudaError_t ce = cudaStreamSynchronize(st);
@@ -1127,7 +1133,7 @@ lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int orde
     if (p->n_elem > 0)
       k_lift_elements<<<grid_for(p->n_elem, 128), 128, 0, st>>>(d.conn, p->n_elem, p->dim, na, order, d.row_ptr,
                                                                 d.col_idx, up, cle, N, n_edges, coords, conn_out,
-                                                                coords_out);
+                                                                coords_out, d.status);
     ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // scratch is freed below
     if (ce != cudaSuccess) {
