@@ -11,8 +11,9 @@ degree-5 rule.  A step is one assembly of the three CSR matrices.
   fp64       elements/s of the plain FP64 path on the same inputs
   e2e        the same step through the public API with host buffers: pinned
              coordinates and coefficient copied in, the three matrices copied out
-  roofline   k_assemble_tiles (mixed) algorithmic bytes / launch time vs the
-             measured HBM copy bandwidth
+  roofline   k_assemble_pipe (mixed) algorithmic bytes / launch time vs the
+             measured HBM copy bandwidth; traffic = DRAM bytes per launch from
+             the committed ncu capture while the kernel's sources match it
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """

@@ -1,4 +1,4 @@
-"""Further workloads of bench.py (--workload c1 | c3 | c4 | c5).
+"""Further workloads of bench.py (--workload c1 | c3 | c4 | c5 | c2q16 | p4).
 
 c1  P1 icosphere, 5 refinements (20,480 triangles): FP64 mass + stiffness,
     3-point rule; launch-bound, so also the same assembly replayed from a CUDA
@@ -12,7 +12,14 @@ c4  512 meshes of uneven size (P2 curves, P1/P2 disks, P2 spheres; about 77 M
     the plain FP64 path mesh by mesh.
 c5  evolving P2 ellipsoid (327,680 triangles): 100 steps of reassembly of M(x),
     A(x) (graph replay) with nodes moved along the discrete normal flow, then
-    the adjoint of L = u^T M u + v^T A v through the autograd function.
+    the adjoint of L = u^T M u + v^T A v through the autograd function; on the
+    final surface also the load vector, the flow's non-linear vectors and one
+    step of Dziuk's scheme (FP64 assembly + hand-written PCG), each against the
+    oracle.
+c2q16  the C2 surface with the 16-point degree-8 rule (the rule size the paper
+    uses for P2), mass + stiffness through the general element path.
+p4  order 4 on the sphere: the level-6 P1 icosphere lifted to order 4 on the GPU,
+    projected, mass + stiffness with the 16-point rule.
 Each prints one JSON line.
 """
 from __future__ import annotations

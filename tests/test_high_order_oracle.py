@@ -153,3 +153,25 @@ def test_order_lifting_shares_edge_nodes():
         assert x.shape[0] == V + (p - 1) * E + (p - 1) * (p - 2) // 2 * F
         counts = np.bincount(e[:, 3:3 + 3 * (p - 1)].ravel(), minlength=x.shape[0])
         assert set(np.unique(counts[V:V + (p - 1) * E])) == {2}
+
+
+def test_edge_numbering_of_the_lifting_is_the_upper_csr_slots():
+    """The GPU lifting numbers edges by the upper slots (i < j) of the order-1
+    pattern in CSR order; on the CPU that is the lexicographic order of (low,
+    high) vertex pairs the generator uses -- checked by rebuilding the generated
+    edge-node numbers from the oracle's pattern."""
+    from paper_2605_14035_gb300.inputs import meshes
+
+    for x, e in (meshes.icosphere(2, 1), meshes.hex_disk(4, 1)):
+        N = x.shape[0]
+        rp, ci = oracle.pattern(e, N)
+        upper = [(i, int(j)) for i in range(N) for j in ci[rp[i]:rp[i + 1]] if j > i]
+        eid = {edge: k for k, edge in enumerate(upper)}
+        for p in (3, 4):
+            _, conn = meshes.to_order(x, e, p)
+            for le, (a, b) in enumerate([(0, 1), (1, 2), (2, 0)]):
+                i, j = e[:, a], e[:, b]
+                lo, hi = np.minimum(i, j), np.maximum(i, j)
+                ids = np.array([eid[(int(u), int(v))] for u, v in zip(lo, hi)])
+                k1 = np.where(i < j, 1, p - 1)  # the node next to the edge's first corner
+                assert np.array_equal(conn[:, 3 + le * (p - 1)], N + ids * (p - 1) + k1 - 1)
