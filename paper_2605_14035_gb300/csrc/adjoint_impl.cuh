@@ -1,4 +1,6 @@
-// Adjoint of the assembly: dL/d(CSR values) -> dL/d(node coordinates), FP64.
+// Adjoint of the assembly: dL/d(CSR values) -> dL/d(node coordinates), FP64
+// (and a mixed variant: FP32 geometry, double recomputation of the elements
+// that fail the conditioning test, double per-node sums).
 //
 // For L = sum_s gM[s] M[s] + gA[s] A[s] + gMC[s] MC[s] and one element, with
 // Gb the element's gathered gradients and s = |det DF|, G = J^T J:
@@ -13,6 +15,7 @@
 // adds the incidences in ascending element order (deterministic, no atomics).
 #pragma once
 
+#include "assemble_impl.cuh"
 #include "lfem_internal.cuh"
 
 namespace lfem {
@@ -37,20 +40,24 @@ struct AdjArgs {
   TabRef tab;
   int chunk;
   int64_t tile_begin;
+  int mixed;                     // FP32 geometry with a double recomputation of flagged elements
+  float qmin;                    // conditioning threshold of the mixed path (metric quality)
+  unsigned long long* fallback;  // elements recomputed in double (mixed)
 };
 
-template <int D, int NA, int P, typename PosT>
+// R = double: the reference computation; R = float: the mixed path, which
+// reports (redo) an element whose coordinates leave the float range or whose
+// metric fails the conditioning or finiteness test, for a double recomputation.
+template <int D, int NA, int P, typename PosT, typename R>
 __device__ __forceinline__ void adjoint_element(const AdjArgs& a, int64_t e, const int32_t (&nodes)[Ref<D, P>::REF],
-                                                const TabView<double>& tb, bool write_coef,
-                                                double (&ge)[Ref<D, P>::REF][NA]) {
+                                                const TabView<R>& tb, bool write_coef,
+                                                double (&ge_out)[Ref<D, P>::REF][NA], bool& redo) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
-  double X[REF][NA];
-  gather_coords<D, NA, P>(a.coords, nodes, X);
   // symmetric gathered gradients per upper pair: Gb_ab + Gb_ba (a < b), Gb_aa
-  double GM[U], GA[U], GC[U];
+  double GMd[U], GAd[U], GCd[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) GM[u] = GA[u] = GC[u] = 0.0;
+  for (int u = 0; u < U; ++u) GMd[u] = GAd[u] = GCd[u] = 0.0;
 #pragma unroll
   for (int ai = 0; ai < REF; ++ai) {
     const int32_t k = __ldg(a.elem_inc + e * REF + ai);
@@ -61,62 +68,81 @@ __device__ __forceinline__ void adjoint_element(const AdjArgs& a, int64_t e, con
     for (int b = 0; b < REF; ++b) {
       const int64_t s = rb + pos[b];
       const int u = sym_index(REF, ai, b);
-      if (a.gM) GM[u] += __ldg(a.gM + s);
-      if (a.gA) GA[u] += __ldg(a.gA + s);
-      if (a.gC) GC[u] += __ldg(a.gC + s);
+      if (a.gM) GMd[u] += __ldg(a.gM + s);
+      if (a.gA) GAd[u] += __ldg(a.gA + s);
+      if (a.gC) GCd[u] += __ldg(a.gC + s);
     }
   }
+  R GM[U], GA[U], GC[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    GM[u] = (R)GMd[u];
+    GA[u] = (R)GAd[u];
+    GC[u] = (R)GCd[u];
+  }
+  R ge[REF][NA];
 #pragma unroll
   for (int ai = 0; ai < REF; ++ai)
 #pragma unroll
-    for (int i = 0; i < NA; ++i) ge[ai][i] = 0.0;
-  ElemData<D, NA, P, double> ed;
-  load_element_data<D, NA, P, double>(X, ed);
+    for (int i = 0; i < NA; ++i) ge[ai][i] = (R)0;
+  ElemData<D, NA, P, R> ed;
+  bool ok = true;
+  if constexpr (sizeof(R) == 4) {
+    ok = load_element_data_split<D, NA, P>(a.coords, nodes, ed);
+  } else {
+    double X[REF][NA];
+    gather_coords<D, NA, P>(a.coords, nodes, X);
+    load_element_data<D, NA, P, double>(X, ed);
+  }
+  R qual = (R)1;
+  bool bad = false;
   for (int q = 0; q < tb.q; ++q) {
-    const double wq = tb.w[q];
-    QpGeom<D, NA, P, double> g;
-    qp_geometry<D, NA, P, double>(ed, tb, q, 1.0, g);  // H = s G^-1
-    const double s = g.s;
-    double Gi[D][D];
+    const R wq = tb.w[q];
+    QpGeom<D, NA, P, R> g;
+    qp_geometry<D, NA, P, R>(ed, tb, q, (R)1, g);  // H = s G^-1
+    qual = fmin(qual, g.quality);
+    bad |= !(g.s > (R)0) || !isfinite(g.s);
+    const R s = g.s;
+    R Gi[D][D];
 #pragma unroll
     for (int m = 0; m < D; ++m)
 #pragma unroll
       for (int k = 0; k < D; ++k) Gi[m][k] = g.H[m][k] / s;
-    const double* ph = tb.phi + q * REF;
-    const double* dph = tb.dphi + q * REF * D;
-    const double cq = (a.coef && a.gC) ? __ldg(a.coef + e * tb.q + q) : 0.0;
-    double mq = 0.0, mc = 0.0;
-    double K[D][D];
+    const R* ph = tb.phi + q * REF;
+    const R* dph = tb.dphi + q * REF * D;
+    const R cq = (a.coef && a.gC) ? (R)__ldg(a.coef + e * tb.q + q) : (R)0;
+    R mq = 0, mc = 0;
+    R K[D][D];
 #pragma unroll
     for (int m = 0; m < D; ++m)
 #pragma unroll
-      for (int k = 0; k < D; ++k) K[m][k] = 0.0;
+      for (int k = 0; k < D; ++k) K[m][k] = 0;
 #pragma unroll
     for (int ai = 0; ai < REF; ++ai)
 #pragma unroll
       for (int b = ai; b < REF; ++b) {
         const int u = upper_index(REF, ai, b);
-        const double pp = ph[ai] * ph[b];
+        const R pp = ph[ai] * ph[b];
         mq += (GM[u] + cq * GC[u]) * pp;
         mc += GC[u] * pp;
         // symmetric part of GA_u grad phi_a grad phi_b^T (halved for a < b since GA sums both orders)
-        const double f = (ai == b) ? GA[u] : 0.5 * GA[u];
+        const R f = (ai == b) ? GA[u] : (R)0.5 * GA[u];
 #pragma unroll
         for (int m = 0; m < D; ++m)
 #pragma unroll
-          for (int k = 0; k < D; ++k) K[m][k] += f * (dph[ai * D + m] * dph[b * D + k] + (ai == b ? 0.0 : dph[b * D + m] * dph[ai * D + k]));
+          for (int k = 0; k < D; ++k) K[m][k] += f * (dph[ai * D + m] * dph[b * D + k] + (ai == b ? (R)0 : dph[b * D + m] * dph[ai * D + k]));
       }
-    double KG = 0.0;
+    R KG = 0;
 #pragma unroll
     for (int m = 0; m < D; ++m)
 #pragma unroll
       for (int k = 0; k < D; ++k) KG += K[m][k] * Gi[m][k];
-    double T[D][D], B[D][D];
+    R T[D][D], B[D][D];
 #pragma unroll
     for (int m = 0; m < D; ++m)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        double t = 0.0;
+        R t = 0;
 #pragma unroll
         for (int l = 0; l < D; ++l) t += Gi[m][l] * K[l][k];
         T[m][k] = t;
@@ -125,39 +151,44 @@ __device__ __forceinline__ void adjoint_element(const AdjArgs& a, int64_t e, con
     for (int m = 0; m < D; ++m)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        double t = 0.0;
+        R t = 0;
 #pragma unroll
         for (int l = 0; l < D; ++l) t += T[m][l] * Gi[l][k];
         B[m][k] = t;
       }
-    double dLdJ[NA][D];
-    const double ws = wq * s;
+    R dLdJ[NA][D];
+    const R ws = wq * s;
 #pragma unroll
     for (int i = 0; i < NA; ++i)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        double jg = 0.0, jb = 0.0;
+        R jg = 0, jb = 0;
 #pragma unroll
         for (int m = 0; m < D; ++m) {
           jg += g.J[i][m] * Gi[m][k];
           jb += g.J[i][m] * B[m][k];
         }
-        dLdJ[i][k] = ws * ((mq + KG) * jg - 2.0 * jb);
+        dLdJ[i][k] = ws * ((mq + KG) * jg - (R)2 * jb);
       }
 #pragma unroll
     for (int ai = 0; ai < REF; ++ai)
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
-        double t = 0.0;
+        R t = 0;
 #pragma unroll
         for (int k = 0; k < D; ++k) t += dLdJ[i][k] * dph[ai * D + k];
         ge[ai][i] += t;
       }
-    if (write_coef) a.g_coef[e * tb.q + q] = ws * mc;
+    if (write_coef) a.g_coef[e * tb.q + q] = (double)(ws * mc);
   }
+#pragma unroll
+  for (int ai = 0; ai < REF; ++ai)
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ge_out[ai][i] = (double)ge[ai][i];
+  if constexpr (sizeof(R) == 4) redo = !ok || bad || (D > 1 && qual < (R)a.qmin) || !(qual > (R)1e-12);
 }
 
-template <int D, int NA, int P, typename PosT>
+template <int D, int NA, int P, typename PosT, bool MIXED>
 __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
   constexpr int REF = Ref<D, P>::REF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,6 +199,7 @@ __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
   const int nel = a.tile_elem_ptr[t + 1] - el0;
   const int nrows = r1 - r0;
   const TabView<double> tb = tab_view<D, P, double>(a.tab);
+  const TabView<float> tbf = tab_view<D, P, float>(a.tab);
   const int nchunks = nel == 0 ? 1 : (nel + a.chunk - 1) / a.chunk;
   for (int ci = 0; ci < nchunks; ++ci) {
     const int c0 = ci * a.chunk;
@@ -179,7 +211,12 @@ __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
       for (int b = 0; b < REF; ++b) nodes[b] = __ldg(a.conn + e * REF + b);
       const bool owner = nodes[0] >= r0 && nodes[0] < r1;
       double ge[REF][NA];
-      adjoint_element<D, NA, P, PosT>(a, e, nodes, tb, owner && a.g_coef != nullptr, ge);
+      bool redo = false;
+      if constexpr (MIXED) adjoint_element<D, NA, P, PosT, float>(a, e, nodes, tbf, owner && a.g_coef != nullptr, ge, redo);
+      if (!MIXED || redo) {
+        adjoint_element<D, NA, P, PosT, double>(a, e, nodes, tb, owner && a.g_coef != nullptr, ge, redo);
+        if (MIXED && owner) atomicAdd(a.fallback, 1ull);
+      }
 #pragma unroll
       for (int ai = 0; ai < REF; ++ai)
 #pragma unroll
@@ -210,7 +247,8 @@ lfem_status launch_adjoint(const AdjArgs& a0, int64_t n_tiles, int pos_bytes, cu
   if (n_tiles == 0) return LFEM_OK;
   constexpr int REF = Ref<D, P>::REF;
   const size_t smem = sizeof(double) * (size_t)a0.chunk * REF * NA;
-  auto kern = pos_bytes == 1 ? k_adjoint_tiles<D, NA, P, uint8_t> : k_adjoint_tiles<D, NA, P, uint16_t>;
+  auto kern = a0.mixed ? (pos_bytes == 1 ? k_adjoint_tiles<D, NA, P, uint8_t, true> : k_adjoint_tiles<D, NA, P, uint16_t, true>)
+                       : (pos_bytes == 1 ? k_adjoint_tiles<D, NA, P, uint8_t, false> : k_adjoint_tiles<D, NA, P, uint16_t, false>);
   LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   AdjArgs a = a0;
   const int64_t max_grid = 1ll << 30;

@@ -524,9 +524,27 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   return run_pipe(p->dim, ambient, p->order, mixed, pa, p->ent_bytes, fast, fb, sms, st);
 }
 
+static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                                  const double* coef, const double* gM, const double* gA, const double* gMC,
+                                  double* g_coords, double* g_coef, bool mixed, void* cuda_stream);
+
 lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                                   const double* coef, const double* gM, const double* gA, const double* gMC,
                                   double* g_coords, double* g_coef, void* cuda_stream) {
+  return adjoint_common(p, coords, ambient, quad, coef, gM, gA, gMC, g_coords, g_coef, false, cuda_stream);
+}
+
+lfem_status lfem_assemble_adjoint_mixed(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                                        const double* coef, const double* gM, const double* gA, const double* gMC,
+                                        double* g_coords, double* g_coef, void* cuda_stream) {
+  return adjoint_common(p, coords, ambient, quad, coef, gM, gA, gMC, g_coords, g_coef, true, cuda_stream);
+}
+
+}  // extern "C"
+
+static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
+                                  const double* coef, const double* gM, const double* gA, const double* gMC,
+                                  double* g_coords, double* g_coef, bool mixed, void* cuda_stream) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
   if (!g_coords && p->n_nodes > 0) return fail(LFEM_E_ARG, "g_coords is NULL");
@@ -555,6 +573,10 @@ lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int am
   a.tile_elem = p->d.tile_elem;
   a.tab = tab;
   a.chunk = 128;
+  a.mixed = mixed ? 1 : 0;
+  a.qmin = p->qmin;
+  a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
+  if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
   if (g_coef && !gMC && p->n_elem > 0) {
     // dL/dc is zero without gMC
     LFEM_CUDA(cudaMemsetAsync(g_coef, 0, sizeof(double) * p->n_elem * quad->n_pts, st));
@@ -562,6 +584,8 @@ lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int am
   }
   return run_adjoint(p->dim, ambient, p->order, a, p->n_tiles, p->pos_bytes, st);
 }
+
+extern "C" {
 
 static lfem_status stage_common(int kind, const int32_t* conn, int64_t n_elem, int dim, int order,
                                 const double* coords, int ambient, const lfem_quad* quad, const double* coef,

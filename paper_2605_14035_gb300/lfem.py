@@ -26,7 +26,8 @@ STATUS = {0: "LFEM_OK", 1: "LFEM_E_ARG", 2: "LFEM_E_INDEX", 3: "LFEM_E_UNSUPPORT
 EXPORTS = (
     "lfem_pattern", "lfem_pattern_csr", "lfem_pattern_copy_csr", "lfem_pattern_info", "lfem_pattern_retile",
     "lfem_pattern_destroy", "lfem_assemble", "lfem_set_launch", "lfem_set_mixed_kappa", "lfem_assemble_load",
-    "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_lift_order", "lfem_assemble_adjoint", "lfem_eval_points",
+    "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_lift_order", "lfem_assemble_adjoint", "lfem_assemble_adjoint_mixed",
+    "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
     "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
@@ -69,6 +70,7 @@ def _load():
         "lfem_mcf_step": [P, P, I, P, ctypes.c_double, ctypes.c_double, I, P, P, P],
         "lfem_lift_order": [P, P, I, I, P, P, P, P],
         "lfem_assemble_adjoint": [P, P, I, P, P, P, P, P, P, P, P],
+        "lfem_assemble_adjoint_mixed": [P, P, I, P, P, P, P, P, P, P, P],
         "lfem_eval_points": [P, L, I, I, P, I, P, P, P],
         "lfem_geometry": [P, L, I, I, P, I, P, P, P, P, P],
         "lfem_local": [P, L, I, I, P, I, P, P, P, P, P, P],
@@ -320,15 +322,16 @@ class Batch:
 
 
 def assemble_adjoint(pat: Pattern, coords: torch.Tensor, rule, coef=None, gM=None, gA=None, gMC=None,
-                     want_coef_grad: bool = False, stream=None):
-    """lfem_assemble_adjoint: returns (g_coords, g_coef or None)."""
+                     want_coef_grad: bool = False, stream=None, precision: int = FP64):
+    """lfem_assemble_adjoint (FP64) or lfem_assemble_adjoint_mixed: returns (g_coords, g_coef or None)."""
     coords = _dev_f64(coords, "coords")
     rule = as_rule(rule)
     gx = torch.empty_like(coords)
     gc = None
     if want_coef_grad:
         gc = torch.empty(pat.n_elem, rule.n_pts, dtype=torch.float64, device=coords.device)
-    _check(_lib.lfem_assemble_adjoint(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref,
+    fn = _lib.lfem_assemble_adjoint if precision == FP64 else _lib.lfem_assemble_adjoint_mixed
+    _check(fn(pat.handle, _ptr(coords), int(coords.shape[1]), rule.ref,
                                       _ptr(_dev_f64(coef, "coef")), _ptr(_dev_f64(gM, "gM")),
                                       _ptr(_dev_f64(gA, "gA")), _ptr(_dev_f64(gMC, "gMC")), _ptr(gx), _ptr(gc),
                                       _stream(stream)))
@@ -438,15 +441,19 @@ def pattern_csr_noalloc(conn: torch.Tensor, n_nodes: int, dim: int, order: int, 
 
 
 class AssembleFn(torch.autograd.Function):
-    """(coords, coef) -> (M, A, MC) CSR values in FP64; backward calls the adjoint kernel."""
+    """(coords, coef) -> (M, A, MC) CSR values; backward calls the adjoint kernel.
+    precision FP64 (default): FP64 values and adjoint; MIXED: float values from the
+    mixed assembly and the mixed adjoint (gradients in double)."""
 
     @staticmethod
-    def forward(ctx, coords, coef, pat: Pattern, rule):
+    def forward(ctx, coords, coef, pat: Pattern, rule, precision: int = FP64):
         rule = as_rule(rule)
         which = MASS | STIFF | (CMASS if coef is not None else 0)
-        out = assemble(pat, coords.detach().contiguous(), rule, None if coef is None else coef.detach().contiguous(),
-                       which=which, precision=FP64)
-        ctx.pat, ctx.rule = pat, rule
+        cf = None if coef is None else coef.detach().contiguous()
+        if cf is not None and precision != FP64:
+            cf = cf.float()
+        out = assemble(pat, coords.detach().contiguous(), rule, cf, which=which, precision=precision)
+        ctx.pat, ctx.rule, ctx.precision = pat, rule, precision
         ctx.save_for_backward(coords, coef if coef is not None else torch.empty(0, device=coords.device))
         ctx.has_coef = coef is not None
         mc = out.get("MC", torch.zeros_like(out["M"]))
@@ -459,5 +466,8 @@ class AssembleFn(torch.autograd.Function):
         c = lambda g: None if g is None else g.contiguous().to(torch.float64)
         gx, gc = assemble_adjoint(ctx.pat, coords.detach().contiguous(), ctx.rule,
                                   None if coef is None else coef.detach().contiguous(), c(gM), c(gA),
-                                  c(gMC) if ctx.has_coef else None, want_coef_grad=ctx.has_coef)
-        return gx, gc, None, None
+                                  c(gMC) if ctx.has_coef else None, want_coef_grad=ctx.has_coef,
+                                  precision=ctx.precision)
+        if gc is not None and coef is not None:
+            gc = gc.to(coef.dtype)
+        return gx, gc, None, None, None

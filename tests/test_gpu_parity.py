@@ -164,6 +164,28 @@ def test_adjoint_matches_oracle(name, lfem):
     assert np.abs(gc.cpu().numpy() - ogc).max() <= 1e-11 * np.abs(ogc).max()
 
 
+@pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p2", "sphere_p1", "space_curve_p2"])
+def test_mixed_adjoint_matches_oracle(name, lfem):
+    """The mixed adjoint (FP32 geometry, double node sums, double recomputation of
+    badly conditioned elements) within 1e-6 of the oracle, relative to max |g|."""
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    orp, oci = oracle.pattern(e, x.shape[0])
+    rng = np.random.default_rng(17)
+    gM, gA, gC = rng.normal(size=(3, oci.size))
+    gx, gc = lfem.assemble_adjoint(pat, to_dev(x), rule, to_dev(coef), to_dev(gM), to_dev(gA), to_dev(gC),
+                                   want_coef_grad=True, precision=lfem.MIXED)
+    ogx, ogc = oracle.adjoint(x, e, d, p, rule.xi, rule.w, coef, (orp, oci), gM, gA, gC)
+    assert np.abs(gx.cpu().numpy() - ogx).max() <= 1e-6 * np.abs(ogx).max()
+    assert np.abs(gc.cpu().numpy() - ogc).max() <= 1e-6 * np.abs(ogc).max()
+    # kappa = 1: every element of dimension >= 2 is recomputed in double
+    pat.set_mixed_kappa(1.0)
+    gx1, _ = lfem.assemble_adjoint(pat, to_dev(x), rule, to_dev(coef), to_dev(gM), to_dev(gA), to_dev(gC),
+                                   precision=lfem.MIXED)
+    if d >= 2:
+        assert pat.fallback_count() == e.shape[0]
+        assert np.abs(gx1.cpu().numpy() - ogx).max() <= 1e-10 * np.abs(ogx).max()
+
+
 def test_autograd_function(lfem):
     """AssembleFn backward against the oracle adjoint of L = u^T M u + v^T A v + w^T MC w."""
     x, e, d, p, rule, coef, pat = prepare("ellipsoid_p2", lfem)
