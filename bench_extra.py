@@ -256,13 +256,17 @@ def run_c5(args):
     rows = torch.repeat_interleave(torch.arange(N, device="cuda"), rp[1:] - rp[:-1])
     xt = xd.clone().requires_grad_(True)
 
-    def fwd_bwd():
+    def fwd_bwd(precision=lfem.FP64):
         xt.grad = None
-        M, A, _ = lfem.AssembleFn.apply(xt, None, pat, rule)
-        L = (M * u[rows] * u[col]).sum() + (A * v[rows] * v[col]).sum()
+        M, A, _ = lfem.AssembleFn.apply(xt, None, pat, rule, precision)
+        L = (M.double() * u[rows] * u[col]).sum() + (A.double() * v[rows] * v[col]).sum()
         L.backward()
         return L
 
+    ms_adj_mixed = timed(lambda: fwd_bwd(lfem.MIXED), 10, 2)
+    fwd_bwd(lfem.MIXED)
+    torch.cuda.synchronize()
+    g_mixed = xt.grad.cpu().numpy().copy()
     ms_adj = timed(fwd_bwd, 10, 2)
     L = fwd_bwd()
     torch.cuda.synchronize()
@@ -273,6 +277,7 @@ def run_c5(args):
                             vn[rr] * vn[cn], None)
     t_orc = time.perf_counter() - t0
     gerr = float(np.abs(xt.grad.cpu().numpy() - ogx).max() / np.abs(ogx).max())
+    gerr_mixed = float(np.abs(g_mixed - ogx).max() / np.abs(ogx).max())
     # the right-hand sides of the flow on the final surface (Sec. 5.1): load
     # vector of the nodal mean curvature field and the non-linear vectors,
     # FP64, against the oracle
@@ -303,6 +308,7 @@ def run_c5(args):
           {"config": {"elements": int(e.shape[0]), "steps": steps, "tau": tau, "precision": "mixed, graph replay"},
            "fp64_assembly_ms": ms64, "adjoint_fwd_bwd_ms": ms_adj, "fp64_fallback_elements_final": fallback,
            "adjoint_vs_oracle_max_rel": gerr, "oracle_adjoint_s": t_orc, "L": float(L),
+           "adjoint_mixed_fwd_bwd_ms": ms_adj_mixed, "adjoint_mixed_vs_oracle_max_rel": gerr_mixed,
            "load_vector_ms": ms_load, "mcf_nonlinear_ms": ms_nl, "mcf_nonlinear_vs_oracle_max_rel": nl_err,
            "dziuk_step_ms": min(t_mcf), "dziuk_step_cg_iterations": cg_it, "dziuk_step_vs_oracle_max_rel": mcf_err})
 

@@ -262,8 +262,9 @@ lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int am
 /* The same adjoint with FP32 geometry and per-point algebra (coordinates split
  * into exact float pairs as in LFEM_MIXED), the element's node gradients summed
  * per node in double, and a double recomputation of every element whose
- * metric fails the conditioning threshold (lfem_set_mixed_kappa) or the
- * finiteness test; the count is reported by lfem_mixed_fallback_count.
+ * metric may have cond(G) > sqrt(kappa_max) (G^{-1} enters the derivative
+ * twice; kappa_max from lfem_set_mixed_kappa) or fails the finiteness test;
+ * the count is reported by lfem_mixed_fallback_count.
  * Arguments and outputs as for lfem_assemble_adjoint (double). */
 lfem_status lfem_assemble_adjoint_mixed(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                                         const double* coef, const double* gM, const double* gA, const double* gMC,

@@ -193,6 +193,8 @@ __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
   constexpr int REF = Ref<D, P>::REF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* gsm = reinterpret_cast<double*>(smem_raw);  // [chunk][REF][NA]
+  __shared__ int s_nredo;
+  __shared__ int s_redo[128];  // mixed: chunk elements to recompute in double (chunk <= 128)
   const int64_t t = a.tile_begin + blockIdx.x;
   const int32_t r0 = a.tile_row0[t], r1 = a.tile_row0[t + 1];
   const int32_t el0 = a.tile_elem_ptr[t];
@@ -204,6 +206,8 @@ __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
   for (int ci = 0; ci < nchunks; ++ci) {
     const int c0 = ci * a.chunk;
     const int cn = max(0, min(a.chunk, nel - c0));
+    if (MIXED && threadIdx.x == 0) s_nredo = 0;
+    if (MIXED) __syncthreads();
     for (int j = threadIdx.x; j < cn; j += blockDim.x) {
       const int64_t e = a.tile_elem[el0 + c0 + j];
       int32_t nodes[REF];
@@ -212,10 +216,11 @@ __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
       const bool owner = nodes[0] >= r0 && nodes[0] < r1;
       double ge[REF][NA];
       bool redo = false;
-      if constexpr (MIXED) adjoint_element<D, NA, P, PosT, float>(a, e, nodes, tbf, owner && a.g_coef != nullptr, ge, redo);
-      if (!MIXED || redo) {
+      if constexpr (MIXED) {
+        adjoint_element<D, NA, P, PosT, float>(a, e, nodes, tbf, owner && a.g_coef != nullptr, ge, redo);
+        if (redo) s_redo[atomicAdd(&s_nredo, 1)] = j;  // recomputed below by whole warps
+      } else {
         adjoint_element<D, NA, P, PosT, double>(a, e, nodes, tb, owner && a.g_coef != nullptr, ge, redo);
-        if (MIXED && owner) atomicAdd(a.fallback, 1ull);
       }
 #pragma unroll
       for (int ai = 0; ai < REF; ++ai)
@@ -223,6 +228,28 @@ __global__ void __launch_bounds__(128) k_adjoint_tiles(const AdjArgs a) {
         for (int i = 0; i < NA; ++i) gsm[((size_t)j * REF + ai) * NA + i] = ge[ai][i];
     }
     __syncthreads();
+    if constexpr (MIXED) {
+      // double recomputation over the compacted list (the FP64 pipe costs the
+      // same for a warp instruction with few active lanes)
+      const int nr = s_nredo;
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        const int j = s_redo[t];
+        const int64_t e = a.tile_elem[el0 + c0 + j];
+        int32_t nodes[REF];
+#pragma unroll
+        for (int b = 0; b < REF; ++b) nodes[b] = __ldg(a.conn + e * REF + b);
+        const bool owner = nodes[0] >= r0 && nodes[0] < r1;
+        double ge[REF][NA];
+        bool unused = false;
+        adjoint_element<D, NA, P, PosT, double>(a, e, nodes, tb, owner && a.g_coef != nullptr, ge, unused);
+        if (owner) atomicAdd(a.fallback, 1ull);
+#pragma unroll
+        for (int ai = 0; ai < REF; ++ai)
+#pragma unroll
+          for (int i = 0; i < NA; ++i) gsm[((size_t)j * REF + ai) * NA + i] = ge[ai][i];
+      }
+      __syncthreads();
+    }
     for (int w = threadIdx.x; w < nrows * NA; w += blockDim.x) {
       const int rl = w / NA, i = w - rl * NA;
       const int32_t r = r0 + rl;

@@ -574,7 +574,14 @@ static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int am
   a.tab = tab;
   a.chunk = 128;
   a.mixed = mixed ? 1 : 0;
-  a.qmin = p->qmin;
+  // G^{-1} enters the adjoint twice (d(s G^{-1})), so its conditioning test
+  // uses sqrt(kappa_max): q >= 4k'/(1+k')^2 with k' = sqrt(k), k from qmin
+  {
+    const double q = p->qmin;
+    const double k = q > 0.0 ? (2.0 - q + 2.0 * std::sqrt(1.0 - q)) / q : 0.0;  // inverse of q = 4k/(1+k)^2
+    const double ka = k > 1.0 ? std::sqrt(k) : 1.0;
+    a.qmin = q > 0.0 ? (float)(4.0 * ka / ((1.0 + ka) * (1.0 + ka))) : 0.0f;
+  }
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
   if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
   if (g_coef && !gMC && p->n_elem > 0) {
