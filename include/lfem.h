@@ -127,6 +127,11 @@ void lfem_pattern_destroy(lfem_pattern_t p);
  *           a matrix not requested may be NULL.
  * Work per CSR slot is summed in a fixed order; the result does not depend on
  * scheduling (bit-identical reruns).  No atomics are used.
+ * Surfaces, curves and bulk triangles of order 1, 2 run on row tiles;
+ * tetrahedra and orders 3, 4 compute every element once into a local-matrix
+ * buffer owned by the pattern ([n_elem][matrices][U], allocated on first use
+ * or when a call needs more; that call allocates device memory, so make it
+ * before any stream capture).
  */
 lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                           const void* coef, int coef_is_fp32, unsigned which, lfem_precision prec, void* M,
