@@ -42,14 +42,18 @@
 #define ORACLE_MUTATION 0 /* >0 only in tests that plant a known mistake */
 #endif
 
-#define MAXREF 15
+#define MAXREF 35
 #define MAXD 3
 
 static int n_ref(int dim, int order) {
   if (order == 1) return dim + 1;
   if (order == 2) return (dim + 1) * (dim + 2) / 2;
-  /* orders 3, 4 on curves and triangles: C(p + d, d) */
-  if ((order == 3 || order == 4) && dim <= 2) return dim == 1 ? order + 1 : (order + 1) * (order + 2) / 2;
+  /* orders 3, 4: C(p + d, d) */
+  if (order == 3 || order == 4) {
+    if (dim == 1) return order + 1;
+    if (dim == 2) return (order + 1) * (order + 2) / 2;
+    return (order + 1) * (order + 2) * (order + 3) / 6;
+  }
   return -1;
 }
 
@@ -63,14 +67,18 @@ static const int (*edge_list(int dim))[2] {
 }
 
 /*
- * Orders p = 3, 4 (curves and triangles): the Lagrange basis of the nodes
+ * Orders p = 3, 4: the Lagrange basis of the nodes
  * lambda = alpha / p, |alpha| = p, written in barycentric coordinates as
  *   phi_alpha = prod_i l_{alpha_i}(lambda_i),  l_k(t) = prod_{j<k} (p t - j) / (j + 1),
  * which is 1 at its own node and 0 at every other (l_k vanishes at t = j/p,
  * j < k).  Node order: corners; then, edge by edge in the P2 edge order
  * (i, j), the p - 1 nodes alpha = (p - k) e_i + k e_j, k = 1..p-1 (from corner
  * i towards j); then the triangle's interior nodes (every alpha_i >= 1) in
- * increasing (alpha_1, alpha_2).
+ * increasing (alpha_1, alpha_2).  Tetrahedra: after the edges, the face
+ * nodes face by face in the order (0,1,2), (0,1,3), (0,2,3), (1,2,3), each
+ * face (i, j, l) with its nodes alpha_i, alpha_j, alpha_l >= 1 in increasing
+ * (alpha_j, alpha_l); then the interior nodes (all four >= 1) in increasing
+ * (alpha_1, alpha_2, alpha_3).
  */
 static int node_multi_indices(int dim, int p, int (*al)[MAXD + 1]) {
   int cnt = 0;
@@ -79,7 +87,7 @@ static int node_multi_indices(int dim, int p, int (*al)[MAXD + 1]) {
     al[cnt++][i] = p;
   }
   const int(*ed)[2] = edge_list(dim);
-  const int ne = dim == 1 ? 1 : 3;
+  const int ne = dim == 1 ? 1 : (dim == 2 ? 3 : 6);
   for (int k = 0; k < ne; ++k)
     for (int t = 1; t < p; ++t) {
       for (int c = 0; c <= dim; ++c) al[cnt][c] = 0;
@@ -95,6 +103,27 @@ static int node_multi_indices(int dim, int p, int (*al)[MAXD + 1]) {
         al[cnt][2] = a2;
         ++cnt;
       }
+  if (dim == 3) {
+    static const int FACES3[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+    for (int f = 0; f < 4; ++f)
+      for (int aj = 1; aj < p; ++aj)
+        for (int al2 = 1; aj + al2 < p; ++al2) {
+          for (int c = 0; c <= dim; ++c) al[cnt][c] = 0;
+          al[cnt][FACES3[f][0]] = p - aj - al2;
+          al[cnt][FACES3[f][1]] = aj;
+          al[cnt][FACES3[f][2]] = al2;
+          ++cnt;
+        }
+    for (int a1 = 1; a1 < p; ++a1)
+      for (int a2 = 1; a1 + a2 < p; ++a2)
+        for (int a3 = 1; a1 + a2 + a3 < p; ++a3) {
+          al[cnt][0] = p - a1 - a2 - a3;
+          al[cnt][1] = a1;
+          al[cnt][2] = a2;
+          al[cnt][3] = a3;
+          ++cnt;
+        }
+  }
   return cnt;
 }
 
@@ -298,7 +327,7 @@ static void element_qp(int dim, int order, int n, const double* X /*[ref][n]*/, 
 
 static int check_combo(int dim, int order, int n) {
   if (dim < 1 || dim > 3 || n < dim || n > 3) return 1;
-  if (order < 1 || order > 4 || (order > 2 && dim > 2)) return 1;
+  if (order < 1 || order > 4) return 1;
   if (dim == 2 && n == 3) return 0;
   if (dim == n) return 0;
   if (dim == 1) return 0;

@@ -77,7 +77,7 @@ def n_ref(dim: int, order: int) -> int:
     """Local nodes per element, C(p+d, d) (Sec. 4, dim(E))."""
     from math import comb
 
-    if order in (1, 2) or (order in (3, 4) and dim <= 2):
+    if order in (1, 2, 3, 4) and dim in (1, 2, 3):
         return comb(order + dim, dim)
     raise ValueError((dim, order))
 

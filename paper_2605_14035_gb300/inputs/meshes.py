@@ -139,21 +139,39 @@ def icosphere(level: int, order: int = 1):
     return renumber_first_touch(v, f)
 
 
+TET_FACES = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+
+
+def _face_alphas(p: int):
+    """Interior multi-indices (a_0, a_1, a_2) >= 1 of a triangle, |a| = p, in
+    increasing (a_1, a_2)."""
+    return [(p - a1 - a2, a1, a2) for a1 in range(1, p) for a2 in range(1, p - a1)]
+
+
 def to_order(v: np.ndarray, f: np.ndarray, order: int, project=None):
-    """Order-p nodes (p = 3, 4) from a P1 curve or triangle mesh (the node
-    generation of the paper's preprocessing, Sec. 4): corners keep their
-    numbers; each edge gets p - 1 nodes at lambda = k/p, numbered along the
-    edge from its lower to its higher vertex number and shared by the elements
-    that meet there; each triangle gets its (p-1)(p-2)/2 interior nodes.  Local
-    order: corners, then per local edge (0,1) [, (1,2), (2,0)] the nodes from the
-    edge's first corner to its second, then the interior nodes in increasing
-    (alpha_1, alpha_2) for barycentric alpha / p.  Positions are the straight
-    ones (sum lambda_i x_i), then `project` if given."""
-    if order not in (3, 4):
+    """Order-p nodes (p = 2, 3, 4) from a P1 curve, triangle or tetrahedron mesh
+    (the node generation of the paper's preprocessing, Sec. 4): corners keep
+    their numbers; each edge gets p - 1 nodes at lambda = k/p, numbered along
+    the edge from its lower to its higher vertex number and shared by the
+    elements that meet there.  Triangles then get their (p-1)(p-2)/2 interior
+    nodes; tetrahedra get per face the (p-1)(p-2)/2 face nodes, shared by the
+    two tets of the face and numbered on the face's vertices sorted by number,
+    then per tet its (p-1)(p-2)(p-3)/6 interior nodes.  Node blocks: vertices,
+    edge nodes (edges in lexicographic (low, high) order), face nodes (faces in
+    lexicographic order of sorted vertex triples), element interior nodes.
+    Local order: corners; per local edge (0,1) [, (1,2), (2,0) [, (0,3), (1,3),
+    (2,3)]] the nodes from the edge's first corner to its second; triangles:
+    interior nodes in increasing (alpha_1, alpha_2); tets: faces (0,1,2),
+    (0,1,3), (0,2,3), (1,2,3), each (i, j, l) with its nodes in increasing
+    (alpha_j, alpha_l), then interior nodes in increasing (alpha_1, alpha_2,
+    alpha_3).  Positions are the straight ones, sum_i lambda_i x_i summed left
+    to right (face nodes over the sorted vertices), then `project` if given."""
+    if order not in (2, 3, 4):
         raise ValueError(order)
     dim = f.shape[1] - 1
-    local_edges = [(0, 1)] if dim == 1 else TRI_EDGES
+    local_edges = [(0, 1)] if dim == 1 else (TRI_EDGES if dim == 2 else TET_EDGES)
     nv = v.shape[0]
+    nE = f.shape[0]
     edges, eid = _edge_ids(f, nv, local_edges)          # edges[k] = (low, high)
     n_e = edges.shape[0]
     cols, pos = [f], [v]
@@ -166,17 +184,58 @@ def to_order(v: np.ndarray, f: np.ndarray, order: int, project=None):
         for k in range(1, order):
             kk = np.where(forward, k, order - k)
             cols.append((nv + eid[:, le] * (order - 1) + (kk - 1))[:, None])
+    base = nv + n_e * (order - 1)
     if dim == 2:
-        alphas = [(order - a1 - a2, a1, a2) for a1 in range(1, order) for a2 in range(1, order - a1)]
-        base = nv + n_e * (order - 1)
+        alphas = _face_alphas(order)
         n_int = len(alphas)
+        ints = []
         for t, al in enumerate(alphas):
             lam = np.array(al, float) / order
-            pos.append(lam[0] * v[f[:, 0]] + lam[1] * v[f[:, 1]] + lam[2] * v[f[:, 2]])
-            cols.append((base + np.arange(f.shape[0]) * n_int + t)[:, None])
-        # interior positions were appended per t; reorder to element-major numbering
-        ints = np.stack(pos[2:], axis=1).reshape(-1, v.shape[1])
-        pos = [pos[0], pos[1], ints]
+            ints.append(lam[0] * v[f[:, 0]] + lam[1] * v[f[:, 1]] + lam[2] * v[f[:, 2]])
+            cols.append((base + np.arange(nE) * n_int + t)[:, None])
+        if n_int:
+            pos.append(np.stack(ints, axis=1).reshape(-1, v.shape[1]))  # element-major numbering
+    if dim == 3:
+        falphas = _face_alphas(order)
+        nfi = len(falphas)
+        n_faces = 0
+        if nfi:
+            tri = np.stack([f[:, list(fc)] for fc in TET_FACES], axis=1)      # [nE][4][3] local vertex order
+            srt = np.sort(tri, axis=2).astype(np.int64)
+            key = (srt[:, :, 0] * nv + srt[:, :, 1]) * nv + srt[:, :, 2]
+            uniq, fid = np.unique(key.ravel(), return_inverse=True)
+            fid = fid.reshape(nE, 4)
+            n_faces = uniq.shape[0]
+            g = np.stack([uniq // (nv * nv), (uniq // nv) % nv, uniq % nv], axis=1)
+            fpos = []
+            for al in falphas:
+                lam = np.array(al, float) / order
+                fpos.append(lam[0] * v[g[:, 0]] + lam[1] * v[g[:, 1]] + lam[2] * v[g[:, 2]])
+            pos.append(np.stack(fpos, axis=1).reshape(-1, v.shape[1]))
+            index = {al: t for t, al in enumerate(falphas)}
+            for lf in range(4):
+                rank = np.argsort(np.argsort(tri[:, lf, :], axis=1, kind="stable"), axis=1)  # rank of each corner
+                for al in falphas:
+                    # the node's weights on the sorted vertices, then its number on the face
+                    t_of = np.empty(nE, np.int64)
+                    for e_al in set(map(tuple, rank)):
+                        sel = np.all(rank == np.array(e_al), axis=1)
+                        srt_al = [0, 0, 0]
+                        for c in range(3):
+                            srt_al[e_al[c]] = al[c]
+                        t_of[sel] = index[tuple(srt_al)]
+                    cols.append((base + fid[:, lf] * nfi + t_of)[:, None])
+        cbase = base + n_faces * nfi
+        calphas = [(order - a1 - a2 - a3, a1, a2, a3) for a1 in range(1, order) for a2 in range(1, order - a1)
+                   for a3 in range(1, order - a1 - a2)]
+        n_ci = len(calphas)
+        cpos = []
+        for t, al in enumerate(calphas):
+            lam = np.array(al, float) / order
+            cpos.append(lam[0] * v[f[:, 0]] + lam[1] * v[f[:, 1]] + lam[2] * v[f[:, 2]] + lam[3] * v[f[:, 3]])
+            cols.append((cbase + np.arange(nE) * n_ci + t)[:, None])
+        if n_ci:
+            pos.append(np.stack(cpos, axis=1).reshape(-1, v.shape[1]))
     x = np.vstack(pos)
     if project is not None:
         x[nv:] = project(x[nv:])

@@ -1,4 +1,4 @@
-"""Orders 3 and 4 (curves and triangles) in the oracle, pinned independently
+"""Orders 3 and 4 (curves, triangles, tetrahedra) in the oracle, pinned independently
 of its product formula: the Lagrange basis obtained by inverting the
 Vandermonde matrix of the nodes (exact rationals), exact reference mass and
 stiffness matrices, the Lagrange property, partition of unity and finite
@@ -15,16 +15,23 @@ from paper_2605_14035_gb300.inputs import quadrature
 sympy = pytest.importorskip("sympy")
 
 
+TET_EDGES = [(0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3)]
+TET_FACES = [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]
+
+
 def node_alphas(dim, p):
     """The documented node order: corners, then edge by edge ((0,1) for curves;
-    (0,1), (1,2), (2,0) for triangles) the nodes (p-k) e_i + k e_j, k = 1..p-1,
-    then interior nodes in increasing (alpha_1, alpha_2)."""
+    (0,1), (1,2), (2,0) for triangles; those and (0,3), (1,3), (2,3) for tets)
+    the nodes (p-k) e_i + k e_j, k = 1..p-1, then for triangles the interior
+    nodes in increasing (alpha_1, alpha_2); for tets the face nodes face by face
+    ((0,1,2), (0,1,3), (0,2,3), (1,2,3); on face (i,j,l) increasing (alpha_j,
+    alpha_l)), then the interior nodes in increasing (alpha_1, alpha_2, alpha_3)."""
     al = []
     for i in range(dim + 1):
         a = [0] * (dim + 1)
         a[i] = p
         al.append(a)
-    edges = [(0, 1)] if dim == 1 else [(0, 1), (1, 2), (2, 0)]
+    edges = [(0, 1)] if dim == 1 else ([(0, 1), (1, 2), (2, 0)] if dim == 2 else TET_EDGES)
     for i, j in edges:
         for k in range(1, p):
             a = [0] * (dim + 1)
@@ -34,6 +41,17 @@ def node_alphas(dim, p):
         for a1 in range(1, p):
             for a2 in range(1, p - a1):
                 al.append([p - a1 - a2, a1, a2])
+    if dim == 3:
+        for i, j, l in TET_FACES:
+            for aj in range(1, p):
+                for al_ in range(1, p - aj):
+                    a = [0] * 4
+                    a[i], a[j], a[l] = p - aj - al_, aj, al_
+                    al.append(a)
+        for a1 in range(1, p):
+            for a2 in range(1, p - a1):
+                for a3 in range(1, p - a1 - a2):
+                    al.append([p - a1 - a2 - a3, a1, a2, a3])
     return al
 
 
@@ -56,28 +74,32 @@ def vandermonde_basis(dim, p):
 
 
 def integrate_ref(expr, xs):
-    """Exact integral over the reference interval / triangle, monomial by monomial:
-    int_0^1 x^a = 1/(a+1); over the triangle x^a y^b -> a! b! / (a+b+2)!."""
+    """Exact integral over the reference interval / triangle / tetrahedron,
+    monomial by monomial: int_0^1 x^a = 1/(a+1); over the triangle x^a y^b ->
+    a! b! / (a+b+2)!; over the tetrahedron x^a y^b z^c -> a! b! c! / (a+b+c+3)!."""
     from math import factorial
 
     total = sympy.Rational(0)
     for mono, coef in sympy.Poly(sympy.expand(expr), *xs).terms():
         if len(xs) == 1:
             total += coef * sympy.Rational(1, mono[0] + 1)
-        else:
+        elif len(xs) == 2:
             a, b = mono
             total += coef * sympy.Rational(factorial(a) * factorial(b), factorial(a + b + 2))
+        else:
+            a, b, c = mono
+            total += coef * sympy.Rational(factorial(a) * factorial(b) * factorial(c), factorial(a + b + c + 3))
     return total
 
 
-@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4)])
+@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4), (3, 3), (3, 4)])
 def test_lagrange_property_and_partition_of_unity(dim, p):
     nodes = np.array([[float(c) for c in n] for n in ref_nodes(dim, p)])
     phi, dphi = oracle.tabulate(dim, p, nodes)
     assert np.abs(phi - np.eye(len(nodes))).max() < 1e-13
     rng = np.random.default_rng(3)
     pts = rng.uniform(0, 1, (20, dim))
-    if dim == 2:
+    if dim >= 2:
         pts = pts[pts.sum(1) < 1]
     phi, dphi = oracle.tabulate(dim, p, pts)
     assert np.abs(phi.sum(1) - 1).max() < 1e-13
@@ -90,17 +112,29 @@ def test_lagrange_property_and_partition_of_unity(dim, p):
         assert np.abs(fd - dphi[:, :, m]).max() < 1e-7
 
 
-@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4)])
+@pytest.mark.parametrize("dim,p", [(1, 3), (1, 4), (2, 3), (2, 4), (3, 3), (3, 4)])
 def test_reference_matrices_against_vandermonde_basis(dim, p):
     """Affine reference element (the identity map): oracle M and A against the
-    exact integrals of the Vandermonde-built basis."""
+    exact integrals of the Vandermonde-built basis (curves, triangles: exact
+    rational integration; tets: the basis evaluated at a degree-9 conical rule,
+    itself checked exact on every monomial up to degree 9, which integrates the
+    degree <= 8 products exactly)."""
     xs, basis = vandermonde_basis(dim, p)
     n = len(basis)
-    Mx = np.array([[float(integrate_ref(basis[a] * basis[b], xs)) for b in range(n)] for a in range(n)])
     grads = [[sympy.diff(f, x) for x in xs] for f in basis]
-    Ax = np.array([[float(integrate_ref(sum(grads[a][k] * grads[b][k] for k in range(dim)), xs)) for b in range(n)]
-                   for a in range(n)])
-    rule = quadrature.gauss_interval(6) if dim == 1 else quadrature.tri_16pt_deg8()
+    if dim <= 2:
+        Mx = np.array([[float(integrate_ref(basis[a] * basis[b], xs)) for b in range(n)] for a in range(n)])
+        Ax = np.array([[float(integrate_ref(sum(grads[a][k] * grads[b][k] for k in range(dim)), xs))
+                        for b in range(n)] for a in range(n)])
+    else:
+        exact = quadrature.collapsed_gauss(3, 5)
+        pts = [exact.xi[:, k] for k in range(3)]
+        ev = lambda f: np.broadcast_to(np.asarray(sympy.lambdify(xs, f, "numpy")(*pts), float), exact.w.shape)
+        B = np.stack([ev(f) for f in basis])                                   # [n][Q]
+        G = np.stack([np.stack([ev(g) for g in gr]) for gr in grads])          # [n][3][Q]
+        Mx = (B * exact.w) @ B.T
+        Ax = np.einsum("akq,bkq,q->ab", G, G, exact.w)
+    rule = {1: quadrature.gauss_interval(6), 2: quadrature.tri_16pt_deg8(), 3: quadrature.collapsed_gauss(3, 5)}[dim]
     x = np.array([[float(c) for c in nd] for nd in ref_nodes(dim, p)])
     conn = np.arange(n, dtype=np.int32)[None, :]
     M, A, _ = oracle.local_matrices(x, conn, dim, p, rule.xi, rule.w)
