@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-elems", type=int, default=0, help="elements in the oracle sample (0 = auto)")
     ap.add_argument("--skip-fp64", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2q16", "p4"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2q16", "p4", "tet34"],
                     help="c2 (default): P2 perturbed sphere; c1 P1 sphere; c3 P2 tets + boundary; "
                          "c4 512-mesh batch; c5 evolving ellipsoid + adjoint")
     ap.add_argument("--batch-meshes", type=int, default=512)

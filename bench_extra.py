@@ -387,5 +387,56 @@ def run_p4(args):
            "fp64": res["fp64"], "mixed": res["mixed"], "lift_order_ms": min(t_lift)})
 
 
+def run_tet34(args):
+    """Orders 3 and 4 on tetrahedra: the P1 Kuhn cube (16^3 cells, 24576 tets)
+    lifted on the GPU (lfem_lift_order), then M + A with the 64-point degree-7
+    conical rule, FP64 and mixed.  Affine elements: sum M = 1 and A 1 = 0 are
+    checked on the results."""
+    import torch
+
+    from paper_2605_14035_gb300 import lfem
+    from paper_2605_14035_gb300.inputs import meshes, quadrature
+
+    x1, e1 = meshes.kuhn_cube_p2(16, order=1)
+    xd1, ed1 = torch.from_numpy(x1).cuda(), torch.from_numpy(e1).cuda()
+    p1 = lfem.Pattern(ed1, x1.shape[0], 3, 1)
+    rule = quadrature.paper_rule(3)
+    flush = torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    timed = _timer(torch, flush)
+    res = {}
+    for order in (3, 4):
+        t_lift = []
+        for _ in range(3):
+            a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            xp, ep = lfem.lift_order(p1, xd1, order)
+            b0.record()
+            torch.cuda.synchronize()
+            t_lift.append(a0.elapsed_time(b0))
+        pat = lfem.Pattern(ep, xp.shape[0], 3, order)
+        rp, ci = pat.csr()
+        rows = torch.repeat_interleave(torch.arange(xp.shape[0], device="cuda"), rp[1:] - rp[:-1])
+        r = {"elements": int(ep.shape[0]), "nodes": int(xp.shape[0]), "nnz_per_matrix": pat.nnz,
+             "lift_order_ms": min(t_lift)}
+        for prec, dt, name in ((lfem.MIXED, torch.float32, "mixed"), (lfem.FP64, torch.float64, "fp64")):
+            out = {k: torch.empty(pat.nnz, dtype=dt, device="cuda") for k in ("M", "A")}
+            ms = timed(lambda: lfem.assemble(pat, xp, rule, which=3, precision=prec, out=out), args.steps,
+                       args.warmup)
+            rowsum = torch.zeros(xp.shape[0], dtype=torch.float64, device="cuda")
+            rowsum.index_add_(0, rows, out["A"].double())
+            r[name] = {"ms_per_step": ms, "value": ep.shape[0] / (ms * 1e-3),
+                       "volume_minus_1": float(out["M"].double().sum()) - 1.0,
+                       "max_abs_A_rowsum": float(rowsum.abs().max())}
+            if name == "mixed":
+                r["fallback_elements_mixed"] = pat.fallback_count()
+            pat.sync_status()
+        res[f"p{order}"] = r
+    _line(args, "tet_p4_kuhn16_M_A_rule64", res["p4"]["mixed"]["value"], "elements/s",
+          res["p4"]["mixed"]["ms_per_step"],
+          {"config": {"cells": "16^3 Kuhn cube", "quadrature": "tet 64-point degree 7", "l2": "flushed between steps"},
+           "p3": res["p3"], "p4": res["p4"]})
+
+
 def run(args):
-    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "c2q16": run_c2q16, "p4": run_p4}[args.workload](args)
+    return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "c2q16": run_c2q16, "p4": run_p4,
+            "tet34": run_tet34}[args.workload](args)

@@ -19,13 +19,18 @@
  *                              Edge-node order: segment (0,1); triangle (0,1),(1,2),(2,0);
  *                              tetrahedron (0,1),(1,2),(2,0),(0,3),(1,3),(2,3).
  *  - Supported (dim, ambient): (1,1) (1,2) (1,3) (2,2) (2,3) (3,3); order 1 or 2
- *    (Table ellFEM_overview); orders 3 and 4 on curves and triangles (dim <= 2),
- *    for lfem_pattern, lfem_assemble and the vector assemblies (not for the
- *    adjoint, the stage entry points, batches or lfem_pattern_csr_noalloc).
+ *    (Table ellFEM_overview); orders 3 and 4 for lfem_pattern and lfem_assemble
+ *    (every (dim, ambient)), and on curves and triangles also for the vector
+ *    assemblies (not for the adjoint, the stage entry points, batches or
+ *    lfem_pattern_csr_noalloc).
  *    Order-p node order (p = 3, 4): corners; then per edge (i, j) in the order
  *    above the p - 1 nodes at barycentric ((p-k) e_i + k e_j) / p, k = 1..p-1;
  *    then the triangle's interior nodes alpha / p (every alpha_i >= 1) in
- *    increasing (alpha_1, alpha_2).  Anything else: LFEM_E_UNSUPPORTED.
+ *    increasing (alpha_1, alpha_2); for tetrahedra instead the face nodes,
+ *    face by face in the order (0,1,2), (0,1,3), (0,2,3), (1,2,3), each face
+ *    (i, j, l) with alpha_i, alpha_j, alpha_l >= 1 by increasing (alpha_j,
+ *    alpha_l), then the interior nodes (all four >= 1) by increasing
+ *    (alpha_1, alpha_2, alpha_3).  Anything else: LFEM_E_UNSUPPORTED.
  *  - Quadrature rules are host arrays on the reference simplex (interval [0,1],
  *    triangle conv{0,e1,e2}, tetrahedron conv{0,e1,e2,e3}); weights sum to its
  *    measure.  n_pts <= LFEM_MAX_QPTS.
@@ -92,8 +97,10 @@ typedef struct {
  * may free it afterwards.  The call synchronises the stream once (to size the
  * column array) and returns LFEM_E_INDEX if any node index is outside
  * [0, n_nodes).
- * Limits: n_elem * ref < 2^31; every CSR row shorter than the tile capacity
- * (default 4096 slots); at most 2048 elements meet at one node; nnz < 2^31.
+ * Limits: n_elem * ref < 2^31 (order-3/4 tets: n_elem < 2^25 and n_elem * ref^2
+ * < 2^31); every CSR row shorter than the tile capacity (default 4096 slots);
+ * at most 2048 elements meet at one node; nnz < 2^31.  Order-3/4 tets (more
+ * than 16 nodes) get no row tiles.
  * Ownership: *out owns all of its device memory until lfem_pattern_destroy.
  */
 lfem_status lfem_pattern(const int32_t* conn, int64_t n_elem, int32_t n_nodes, int dim, int order,
@@ -112,7 +119,8 @@ lfem_status lfem_pattern_copy_csr(lfem_pattern_t p, int64_t* row_ptr, int32_t* c
 lfem_status lfem_pattern_info(lfem_pattern_t p, int64_t* n_tiles, int64_t* recompute_x1000, int32_t* max_row,
                               int32_t* tile_slots);
 
-/* Rebuild the row tiles with a different capacity (slots per tile, 256..16384). */
+/* Rebuild the row tiles with a different capacity (slots per tile, 256..16384).
+ * LFEM_E_UNSUPPORTED for elements of more than 16 nodes (order-3/4 tets). */
 lfem_status lfem_pattern_retile(lfem_pattern_t p, int32_t tile_slots, void* cuda_stream);
 
 void lfem_pattern_destroy(lfem_pattern_t p);
@@ -131,7 +139,10 @@ void lfem_pattern_destroy(lfem_pattern_t p);
  * tetrahedra and orders 3, 4 compute every element once into a local-matrix
  * buffer owned by the pattern ([n_elem][matrices][U], allocated on first use
  * or when a call needs more; that call allocates device memory, so make it
- * before any stream capture).
+ * before any stream capture).  Order-3/4 tets take one warp per element and
+ * tabulate the basis on the device (the buffer also holds those tables and,
+ * for LFEM_MIXED, the list of elements redone in double: an element whose
+ * metric fails the conditioning test at any point is redone whole).
  */
 lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                           const void* coef, int coef_is_fp32, unsigned which, lfem_precision prec, void* M,
@@ -218,7 +229,8 @@ void lfem_batch_destroy(lfem_batch_t b);
  * Load vector of the Poisson problem (Sec. 2): b_j = integral over Gamma_h of
  * f_h phi_j, f_h = sum_i f_i phi_i the interpolant of the nodal values, so
  * b = M f.  f: [n_nodes] doubles; b: [n_nodes] doubles, overwritten.  Every
- * (dim, ambient, order) lfem_assemble supports.
+ * (dim, ambient, order) lfem_assemble supports except order-3/4 tetrahedra
+ * (LFEM_E_UNSUPPORTED).
  */
 lfem_status lfem_assemble_load(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                                const double* f, double* b, void* cuda_stream);
@@ -311,16 +323,20 @@ lfem_status lfem_mixed_fallback_count(lfem_pattern_t p, void* cuda_stream, int64
 const char* lfem_last_error(void);
 const char* lfem_status_string(lfem_status s);
 
-/* Order-p nodes from an order-1 curve or triangle mesh (the node generation of
- * the paper's preprocessing, Sec. 4; orders 2..4).  p1 is the order-1
- * pattern of the mesh; its edges are the upper slots (i < j) of the pattern's
- * rows, numbered in CSR order.  Output numbering: the P1 vertices keep their
- * numbers; then p - 1 nodes per edge, from its lower to its higher vertex
- * number, at the straight positions x_lo (1 - k/p) + x_hi k/p; then each
- * triangle's interior nodes at alpha / p in barycentrics (the order-p node
- * order of the conventions above).  Positions are rounded in a fixed order
- * (products, then sums left to right), so any implementation that evaluates
- * the same expressions that way gets the same bits.
+/* Order-p nodes from an order-1 curve, triangle or tetrahedron mesh (the node
+ * generation of the paper's preprocessing, Sec. 4; orders 2..4).  p1 is the
+ * order-1 pattern of the mesh; its edges are the upper slots (i < j) of the
+ * pattern's rows, numbered in CSR order.  Output numbering: the P1 vertices
+ * keep their numbers; then p - 1 nodes per edge, from its lower to its higher
+ * vertex number, at the straight positions x_lo (1 - k/p) + x_hi k/p; then
+ * each triangle's interior nodes at alpha / p in barycentrics; for
+ * tetrahedra instead the (p-1)(p-2)/2 nodes of every face (faces in
+ * lexicographic order of their sorted vertex triples (g0 < g1 < g2), nodes
+ * sum_k (a_k / p) x_{g_k} by increasing (a_1, a_2), shared by the face's two
+ * tets), then each tet's interior nodes (order 4: one, at the centroid).
+ * Local order: that of the conventions above.  Positions are rounded in a
+ * fixed order (products, then sums left to right), so any implementation
+ * that evaluates the same expressions that way gets the same bits.
  *   coords:      [n_vertices][ambient] device doubles (the P1 nodes).
  *   conn_out:    [n_elem][C(order+dim, dim)] device int32, or NULL.
  *   coords_out:  [n_nodes_out][ambient] device doubles, or NULL.

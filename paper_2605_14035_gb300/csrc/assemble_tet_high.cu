@@ -1,0 +1,361 @@
+// Orders 3 and 4 on tetrahedra (20 and 35 nodes; 210 and 630 upper entries
+// per matrix), element-major like the other tets: local matrices into the
+// buffer [nE][nm][U], then every CSR slot sums its list (k_slot_gather).
+//
+// A local matrix this large does not fit one thread's registers, so one warp
+// takes one element:
+//   * the basis table phi_b, grad^phi_b at the rule's points (Eq. F_map with
+//     the Lagrange basis of the nodes alpha/p) is tabulated once per launch in
+//     FP64 by k_tet_high_table and staged into every CTA's shared memory;
+//   * the geometry is computed by lanes over quadrature points: J = sum_b
+//     (x_b - x_0) grad^phi_b^T, s = |det J|, H = w s G^{-1} = (w / s) adj(G)
+//     with adj(G)_mk = c_m . c_k, c_m the cross product of J's other two
+//     columns (Eq. basic integral formula, Eqs. jacobian_inv);
+//   * the entries are spread over the lanes (u = lane + 32 k) and summed over
+//     the points (Eqs. reference_quadrature_mass, reference_quadrature_stiffness):
+//       M_ab += (w s phi_b) phi_a,  A_ab += grad^phi_a . (H grad^phi_b),
+//       C_ab += (c_q w s phi_b) phi_a,
+//     with the per-point node factors (w s phi_b, H grad^phi_b) computed once
+//     per node into shared memory.
+// LFEM_MIXED: float geometry and sums; an element whose metric fails the
+// conditioning test (or is not finite) anywhere is listed and recomputed in
+// FP64 by a second launch over the list.
+#include "dispatch.cuh"
+
+namespace lfem {
+
+constexpr int kTetHighWarps = 4;
+
+template <int P>
+struct TetHigh {
+  static constexpr int REF = (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int U = REF * (REF + 1) / 2;
+  static constexpr int NU = (U + 31) / 32;  // entries per lane
+};
+
+template <typename R>
+struct alignas(4 * sizeof(R) > 16 ? 16 : 4 * sizeof(R)) V4 {
+  R x, y, z, w;
+};
+
+// Barycentric multi-index of local node a (library node order): corners;
+// edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3), each from its first corner
+// towards its second; faces (0,1,2), (0,1,3), (0,2,3), (1,2,3), each face
+// (i, j, l) by increasing (alpha_j, alpha_l); interior nodes by increasing
+// (alpha_1, alpha_2, alpha_3).
+__device__ void tet_node_alpha(int p, int a, int (&al)[4]) {
+  const int E[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+  const int F[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+  al[0] = al[1] = al[2] = al[3] = 0;
+  if (a < 4) {
+    al[a] = p;
+    return;
+  }
+  int r = a - 4;
+  if (r < 6 * (p - 1)) {
+    const int k = r / (p - 1), t = r % (p - 1) + 1;
+    al[E[k][0]] = p - t;
+    al[E[k][1]] = t;
+    return;
+  }
+  r -= 6 * (p - 1);
+  const int nf = (p - 1) * (p - 2) / 2;
+  if (r < 4 * nf) {
+    const int f = r / nf;
+    int t = r % nf;
+    for (int aj = 1; aj < p; ++aj)
+      for (int al2 = 1; aj + al2 < p; ++al2)
+        if (t-- == 0) {
+          al[F[f][0]] = p - aj - al2;
+          al[F[f][1]] = aj;
+          al[F[f][2]] = al2;
+          return;
+        }
+  }
+  r -= 4 * nf;
+  for (int a1 = 1; a1 < p; ++a1)
+    for (int a2 = 1; a1 + a2 < p; ++a2)
+      for (int a3 = 1; a1 + a2 + a3 < p; ++a3)
+        if (r-- == 0) {
+          al[0] = p - a1 - a2 - a3;
+          al[1] = a1;
+          al[2] = a2;
+          al[3] = a3;
+          return;
+        }
+}
+
+// phi_alpha = prod_i l_{alpha_i}(lambda_i) with l_k(t) = prod_{j<k} (p t - j) / (j + 1):
+// value and derivative of one factor.
+__device__ __forceinline__ void lagrange_1d(int p, int k, double t, double& v, double& dv) {
+  v = 1.0;
+  dv = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double inv = 1.0 / (double)(j + 1);
+    const double f = ((double)p * t - (double)j) * inv;
+    dv = fma(dv, f, v * ((double)p * inv));
+    v *= f;
+  }
+}
+
+// table[q][b] = (phi_b, d phi_b / d xi_1, d xi_2, d xi_3) at point q, in FP64 and float.
+template <int P>
+__global__ void k_tet_high_table(TabRef rule_ref, V4<double>* __restrict__ t64, V4<float>* __restrict__ t32) {
+  constexpr int REF = TetHigh<P>::REF;
+  const int Q = rule_ref.q;
+  const double* rule = bank<double>() + rule_ref.off64;  // w[Q], then xi[Q][3]
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Q * REF; t += gridDim.x * blockDim.x) {
+    const int q = t / REF, b = t - q * REF;
+    int al[4];
+    tet_node_alpha(P, b, al);
+    const double x1 = rule[Q + 3 * q], x2 = rule[Q + 3 * q + 1], x3 = rule[Q + 3 * q + 2];
+    const double lam[4] = {1.0 - (x1 + x2 + x3), x1, x2, x3};
+    double v[4], dv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lagrange_1d(P, al[i], lam[i], v[i], dv[i]);
+    // d phi / d lambda_i, then the chain rule with lambda_0 = 1 - xi_1 - xi_2 - xi_3
+    const double d0 = dv[0] * v[1] * v[2] * v[3], d1 = v[0] * dv[1] * v[2] * v[3];
+    const double d2 = v[0] * v[1] * dv[2] * v[3], d3 = v[0] * v[1] * v[2] * dv[3];
+    const V4<double> r{v[0] * v[1] * v[2] * v[3], d1 - d0, d2 - d0, d3 - d0};
+    t64[t] = r;
+    t32[t] = V4<float>{(float)r.x, (float)r.y, (float)r.z, (float)r.w};
+  }
+}
+
+// One matrix of one element: MODE 0 mass, 1 stiffness, 2 coefficient-weighted mass.
+template <int P, typename R, typename RS, int MODE>
+__device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane,
+                                              const uint32_t (&pk)[TetHigh<P>::NU], RS* dst) {
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU;
+  R acc[NU];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) acc[k] = (R)0;
+  for (int q = 0; q < Q; ++q) {
+    const V4<R> g0 = geo[2 * q], g1 = geo[2 * q + 1];
+    const V4<R>* tq = tab + q * REF;
+    for (int b = lane; b < REF; b += 32) {
+      const V4<R> d = tq[b];
+      V4<R> h;
+      if constexpr (MODE == 1) {
+        h.x = (R)0;
+        h.y = fma(g0.y, d.y, fma(g0.z, d.z, g0.w * d.w));
+        h.z = fma(g0.z, d.y, fma(g1.x, d.z, g1.y * d.w));
+        h.w = fma(g0.w, d.y, fma(g1.y, d.z, g1.z * d.w));
+      } else {
+        h.x = (MODE == 0 ? g0.x : g0.x * g1.w) * d.x;
+        h.y = h.z = h.w = (R)0;
+      }
+      hb[b] = h;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const int ia = (int)(pk[k] & 255u), ib = (int)(pk[k] >> 8);
+      const V4<R> hv = hb[ib];
+      if constexpr (MODE == 1) {
+        const V4<R> da = tq[ia];
+        acc[k] = fma(da.y, hv.y, fma(da.z, hv.z, fma(da.w, hv.w, acc[k])));
+      } else {
+        acc[k] = fma(tq[ia].x, hv.x, acc[k]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    const int u = lane + 32 * k;
+    if (u < U) dst[u] = (RS)acc[k];
+  }
+}
+
+// list == nullptr: every element; else the list[0 .. *list_n) (FP64 recomputation).
+// flags (float pass only): flags[0] counts, flags[1 ..] lists the elements to redo.
+template <int P, typename R, typename RS>
+__global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassArgs a, const V4<R>* __restrict__ gtab,
+                                                                 const uint32_t* __restrict__ list,
+                                                                 const uint32_t* __restrict__ list_n,
+                                                                 uint32_t* __restrict__ flags) {
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU;
+  const int Q = a.tab.q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V4<R>* tab = reinterpret_cast<V4<R>*>(smem_raw);  // [Q][REF]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V4<R>* rel = tab + Q * REF + warp * (2 * REF + 2 * Q);  // [REF] x_b - x_0
+  V4<R>* hb = rel + REF;                                 // [REF] per-point node factors
+  V4<R>* geo = hb + REF;                                 // [Q][2] (w s, H00, H01, H02), (H11, H12, H22, c_q)
+  for (int t = threadIdx.x; t < Q * REF; t += blockDim.x) tab[t] = gtab[t];
+  __syncthreads();
+  const double* w64 = bank<double>() + a.tab.off64;
+  // this lane's upper entries u = lane + 32 k as (a, b), row-major upper layout
+  uint32_t pk[NU];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    const int u = lane + 32 * k;
+    int r = 0, start = 0;
+    if (u < U)
+      while (start + (REF - r) <= u) {
+        start += REF - r;
+        ++r;
+      }
+    pk[k] = u < U ? (uint32_t)r | ((uint32_t)(r + u - start) << 8) : 0u;
+  }
+  const int64_t n_work = list ? (int64_t)*list_n : a.n_elem;
+  for (int64_t i = (int64_t)blockIdx.x * kTetHighWarps + warp; i < n_work;
+       i += (int64_t)gridDim.x * kTetHighWarps) {
+    const int64_t e = list ? (int64_t)list[1 + i] : i;
+    const int32_t* cn = a.conn + e * REF;
+    const int64_t n0 = __ldg(cn);
+    const double x0 = __ldg(a.coords + 3 * n0), y0 = __ldg(a.coords + 3 * n0 + 1), z0 = __ldg(a.coords + 3 * n0 + 2);
+    for (int b = lane; b < REF; b += 32) {
+      const int64_t nb = __ldg(cn + b);
+      rel[b] = V4<R>{(R)(__ldg(a.coords + 3 * nb) - x0), (R)(__ldg(a.coords + 3 * nb + 1) - y0),
+                     (R)(__ldg(a.coords + 3 * nb + 2) - z0), (R)0};
+    }
+    __syncwarp();
+    bool bad = false, redo = false;
+    for (int q = lane; q < Q; q += 32) {
+      const V4<R>* tq = tab + q * REF;
+      R J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int b = 1; b < REF; ++b) {
+        const V4<R> r = rel[b], d = tq[b];
+        J[0][0] = fma(r.x, d.y, J[0][0]);
+        J[0][1] = fma(r.x, d.z, J[0][1]);
+        J[0][2] = fma(r.x, d.w, J[0][2]);
+        J[1][0] = fma(r.y, d.y, J[1][0]);
+        J[1][1] = fma(r.y, d.z, J[1][1]);
+        J[1][2] = fma(r.y, d.w, J[1][2]);
+        J[2][0] = fma(r.z, d.y, J[2][0]);
+        J[2][1] = fma(r.z, d.z, J[2][1]);
+        J[2][2] = fma(r.z, d.w, J[2][2]);
+      }
+      R c[3][3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+        c[m][0] = J[1][m1] * J[2][m2] - J[2][m1] * J[1][m2];
+        c[m][1] = J[2][m1] * J[0][m2] - J[0][m1] * J[2][m2];
+        c[m][2] = J[0][m1] * J[1][m2] - J[1][m1] * J[0][m2];
+      }
+      const R det = J[0][0] * c[0][0] + J[1][0] * c[0][1] + J[2][0] * c[0][2];
+      const R s = fabs(det);
+      const R wq = (R)w64[q];
+      const R f = wq * rcp_(s);
+      R H[6];
+      int h = 0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = m; k < 3; ++k) H[h++] = f * (c[m][0] * c[k][0] + c[m][1] * c[k][1] + c[m][2] * c[k][2]);
+      R tr = 0;
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) tr = fma(J[ii][m], J[ii][m], tr);
+      tr *= (R)(1.0 / 3.0);
+      const R quality = (s * s) * rcp_(tr * tr * tr);
+      bad |= !(s > (R)0) || !isfinite(s) || !(quality > (sizeof(R) == 8 ? (R)1e-28 : (R)1e-12));
+      if constexpr (sizeof(R) == 4) redo |= quality < (R)a.qmin;
+      R cq = (R)0;
+      if (a.which & LFEM_CMASS)
+        cq = a.coef_f32 ? (R)__ldg(static_cast<const float*>(a.coef) + e * Q + q)
+                        : (R)__ldg(static_cast<const double*>(a.coef) + e * Q + q);
+      geo[2 * q] = V4<R>{wq * s, H[0], H[1], H[2]};
+      geo[2 * q + 1] = V4<R>{H[3], H[4], H[5], cq};
+    }
+    if constexpr (sizeof(R) == 4) {
+      if (__any_sync(0xffffffffu, bad || redo)) {
+        if (lane == 0) {
+          flags[1 + atomicAdd(flags, 1u)] = (uint32_t)e;
+          atomicAdd(a.fallback, 1ull);
+        }
+        __syncwarp();
+        continue;
+      }
+    } else {
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_DEGENERATE);
+    }
+    __syncwarp();
+    RS* dst = static_cast<RS*>(a.lbuf) + (size_t)e * a.nm * U;
+    if (a.which & LFEM_MASS) {
+      tet_high_pass<P, R, RS, 0>(tab, hb, geo, Q, lane, pk, dst);
+      dst += U;
+    }
+    if (a.which & LFEM_STIFF) {
+      tet_high_pass<P, R, RS, 1>(tab, hb, geo, Q, lane, pk, dst);
+      dst += U;
+    }
+    if (a.which & LFEM_CMASS) tet_high_pass<P, R, RS, 2>(tab, hb, geo, Q, lane, pk, dst);
+  }
+}
+
+template <int P, typename R>
+static size_t tet_high_smem(int Q) {
+  return sizeof(V4<R>) * ((size_t)Q * TetHigh<P>::REF + (size_t)kTetHighWarps * (2 * TetHigh<P>::REF + 2 * Q));
+}
+
+template <int P, typename R, typename RS>
+static lfem_status launch_tet_high_pass(const TwoPassArgs& a, const V4<R>* gtab, const uint32_t* list,
+                                        uint32_t* flags, int64_t n, int sms, cudaStream_t st) {
+  const size_t smem = tet_high_smem<P, R>(a.tab.q);
+  auto kern = k_tet_high<P, R, RS>;
+  LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  LFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTetHighWarps * 32, smem));
+  if (occ < 1) return fail(LFEM_E_TOO_LARGE, "order-3/4 tet tables exceed shared memory");
+  int64_t g = (n + kTetHighWarps - 1) / kTetHighWarps;
+  if (g > (int64_t)sms * occ) g = (int64_t)sms * occ;
+  if (g < 1) g = 1;
+  kern<<<(unsigned)g, kTetHighWarps * 32, smem, st>>>(a, gtab, list, list, flags);
+  LFEM_CUDA(cudaGetLastError());
+  return LFEM_OK;
+}
+
+template <int P>
+static lfem_status run_tet_high_p(bool mixed, const TwoPassArgs& a, void* scratch, int sms, cudaStream_t st) {
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U;
+  const int Q = a.tab.q;
+  V4<double>* t64 = static_cast<V4<double>*>(scratch);
+  V4<float>* t32 = reinterpret_cast<V4<float>*>(t64 + (size_t)Q * REF);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(t32 + (size_t)Q * REF);
+  if (a.n_elem > 0) {
+    k_tet_high_table<P><<<(Q * REF + 127) / 128, 128, 0, st>>>(a.tab, t64, t32);
+    LFEM_CUDA(cudaGetLastError());
+    lfem_status s;
+    if (mixed) {
+      LFEM_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), st));
+      if ((s = launch_tet_high_pass<P, float, float>(a, t32, nullptr, flags, a.n_elem, sms, st)) != LFEM_OK) return s;
+      // the listed elements again in FP64 (the grid covers whatever the count turns out to be)
+      if ((s = launch_tet_high_pass<P, double, float>(a, t64, flags, nullptr, (int64_t)sms * kTetHighWarps, sms,
+                                                      st)) != LFEM_OK)
+        return s;
+    } else if ((s = launch_tet_high_pass<P, double, double>(a, t64, nullptr, nullptr, a.n_elem, sms, st)) != LFEM_OK) {
+      return s;
+    }
+  }
+  if (a.nnz > 0) {
+    int64_t g = (a.nnz + 255) / 256;
+    if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
+    if (mixed) k_slot_gather<U, float><<<(unsigned)g, 256, 0, st>>>(a);
+    else k_slot_gather<U, double><<<(unsigned)g, 256, 0, st>>>(a);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  return LFEM_OK;
+}
+
+size_t tet_high_scratch_bytes(int P, int Q, int64_t n_elem) {
+  const int REF = P == 3 ? TetHigh<3>::REF : TetHigh<4>::REF;
+  return (size_t)Q * REF * (sizeof(V4<double>) + sizeof(V4<float>)) + sizeof(uint32_t) * ((size_t)n_elem + 1);
+}
+
+lfem_status run_tet_high(int P, bool mixed, const TwoPassArgs& a, void* scratch, int sms, cudaStream_t st) {
+  if (P == 3) return run_tet_high_p<3>(mixed, a, scratch, sms, st);
+  if (P == 4) return run_tet_high_p<4>(mixed, a, scratch, sms, st);
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
+lfem_status bank_upload_tet_high(const void* src, size_t bytes, size_t offset) {
+  LFEM_CUDA(cudaMemcpyToSymbol(c_bank, src, bytes, offset, cudaMemcpyHostToDevice));
+  return LFEM_OK;
+}
+
+}  // namespace lfem

@@ -27,7 +27,7 @@ lfem_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool supported(int dim, int ambient, int order) {
-  if (order < 1 || order > 4 || (order > 2 && dim > 2)) return false;
+  if (order < 1 || order > 4) return false;
   if (dim < 1 || dim > 3 || ambient < dim || ambient > 3) return false;
   if (dim == 2 && ambient == 3) return true;
   if (dim == ambient) return true;
@@ -94,6 +94,15 @@ static void lagrange_factor(int p, int k, double t, double& v, double& dv) {
 
 static void host_tables(int dim, int order, const lfem_quad* quad, std::vector<double>& out) {
   const int Q = quad->n_pts, REF = n_ref(dim, order), NE = n_edges(dim, order);
+  if (dim == 3 && order >= 3) {
+    // order-3/4 tets tabulate their basis on the device: the rule alone, w[Q] then xi[Q][3]
+    out.assign((size_t)Q * 4, 0.0);
+    for (int q = 0; q < Q; ++q) {
+      out[q] = quad->w[q];
+      for (int m = 0; m < 3; ++m) out[Q + q * 3 + m] = quad->xi[q * 3 + m];
+    }
+    return;
+  }
   out.assign((size_t)Q * (1 + REF + REF * dim + NE * dim), 0.0);
   double* w = out.data();
   double* phi = w + Q;
@@ -237,7 +246,7 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
   memcpy(blob.data(), t64.data(), b64);
   memcpy(blob.data() + b64, t32.data(), t32.size() * sizeof(float));
   for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch, bank_upload_vec,
-                  bank_upload_high}) {
+                  bank_upload_high, bank_upload_tet_high}) {
     lfem_status us = up(blob.data(), blob.size(), used);
     if (us != LFEM_OK) return us;
   }
@@ -309,16 +318,17 @@ lfem_status lfem_pattern(const int32_t* conn, int64_t n_elem, int32_t n_nodes, i
   *out = nullptr;
   if (n_elem < 0 || n_nodes < 0) return fail(LFEM_E_ARG, "negative size");
   if (n_elem > 0 && !conn) return fail(LFEM_E_ARG, "conn is NULL");
-  if (dim < 1 || dim > 3 || order < 1 || order > 4 || (order > 2 && dim > 2))
-    return fail(LFEM_E_UNSUPPORTED, "dim/order");
+  if (dim < 1 || dim > 3 || order < 1 || order > 4) return fail(LFEM_E_UNSUPPORTED, "dim/order");
   const int ref = n_ref(dim, order);
-  if (n_elem >= (1ll << 27) || n_elem * ref >= (1ll << 31)) return fail(LFEM_E_TOO_LARGE, "too many elements");
+  const int ksh = ref > 16 ? 6 : 4;
+  if (n_elem >= (1ll << (31 - ksh)) || n_elem * ref >= (1ll << 31)) return fail(LFEM_E_TOO_LARGE, "too many elements");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   lfem_pattern_s* p = new lfem_pattern_s();
   cudaGetDevice(&p->device);
   p->dim = dim;
   p->order = order;
   p->ref = ref;
+  p->key_shift = ksh;
   p->n_elem = n_elem;
   p->n_nodes = n_nodes;
   // default tile capacity: all of a tile's local matrices stay in shared memory
@@ -438,8 +448,11 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   a.status = p->d.status;
   a.fallback = reinterpret_cast<unsigned long long*>(p->d.status + 2);
   if (p->dim == 3 || p->order >= 3) {
-    // bulk tets and orders 3, 4: element-major two passes (local-matrix buffer owned by the pattern)
-    const size_t need = (size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8);
+    // bulk tets and orders 3, 4: element-major two passes (local-matrix buffer owned by the pattern;
+    // order-3/4 tets keep their basis tables and recomputation list behind the local matrices)
+    const bool tet_high = p->dim == 3 && p->order >= 3;
+    const size_t lbytes = ((size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8) + 255) / 256 * 256;
+    const size_t need = lbytes + (tet_high ? tet_high_scratch_bytes(p->order, tab.q, p->n_elem) : 0);
     if (need > p->d.elem_buf_bytes) {
       if (p->d.elem_buf) cudaFree(p->d.elem_buf);
       p->d.elem_buf = nullptr;
@@ -471,6 +484,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
     LFEM_CUDA(cudaDeviceGetAttribute(&sms3, cudaDevAttrMultiProcessorCount, p->device));
     if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
     if (p->dim != 3) return run_twopass_high(p->dim, ambient, p->order, mixed, ta, sms3, st);
+    if (tet_high) return run_tet_high(p->order, mixed, ta, static_cast<char*>(p->d.elem_buf) + lbytes, sms3, st);
     FastBankTet fbt;
     const bool fast3 = mixed && fast_tables_host(3, p->order, quad, fbt.v + (p->order == 1 ? FastBankTet::OFF31
                                                                                           : FastBankTet::OFF32));
@@ -547,6 +561,7 @@ static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int am
                                   double* g_coords, double* g_coef, bool mixed, void* cuda_stream) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
+  if (p->order > 2) return fail(LFEM_E_UNSUPPORTED, "the adjoint covers orders 1 and 2");
   if (!g_coords && p->n_nodes > 0) return fail(LFEM_E_ARG, "g_coords is NULL");
   if (p->n_elem > 0 && !coords) return fail(LFEM_E_ARG, "coords is NULL");
   if (gMC && !coef) return fail(LFEM_E_ARG, "gMC given without coef");
@@ -651,6 +666,7 @@ static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int am
                                   const double* u, double* out, int kind, cudaStream_t st) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
+  if (p->dim == 3 && p->order >= 3) return fail(LFEM_E_UNSUPPORTED, "vectors of order-3/4 tetrahedra");
   if (kind == 1 && !(p->dim == 2 && ambient == 3))
     return fail(LFEM_E_UNSUPPORTED, "the non-linear vectors need a surface (dim 2 in R^3)");
   if (p->n_elem > 0 && (!coords || !u)) return fail(LFEM_E_ARG, "coords or nodal values are NULL");

@@ -38,7 +38,9 @@ constexpr int kMaxTileEntries = 16384;    // incidences x ref per tile (node-lis
 // ----------------------------------------------------------------------------
 // C(p + d, d) local nodes: P1, P2 on every simplex; orders 3 and 4 on curves and triangles.
 __host__ __device__ constexpr int n_ref(int d, int p) {
-  return p == 1 ? d + 1 : (p == 2 ? (d + 1) * (d + 2) / 2 : (d == 1 ? p + 1 : (p + 1) * (p + 2) / 2));
+  return p == 1 ? d + 1
+                : (p == 2 ? (d + 1) * (d + 2) / 2
+                          : (d == 1 ? p + 1 : (d == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6)));
 }
 __host__ __device__ constexpr int n_upper(int ref) { return ref * (ref + 1) / 2; }
 __host__ __device__ constexpr int n_edges(int d, int p) { return p == 2 ? n_ref(d, 2) - (d + 1) : 0; }
@@ -92,7 +94,9 @@ __host__ __device__ constexpr int edge_j(int k) {
 
 // Column positions of one incidence are stored padded to a power of two so a
 // single vector load fetches them (ref 2 -> 2, 3/4 -> 4, 6 -> 8, 10 -> 16).
-__host__ __device__ constexpr int pos_stride(int ref) { return ref <= 2 ? 2 : (ref <= 4 ? 4 : (ref <= 8 ? 8 : 16)); }
+__host__ __device__ constexpr int pos_stride(int ref) {
+  return ref <= 2 ? 2 : (ref <= 4 ? 4 : (ref <= 8 ? 8 : (ref + 15) / 16 * 16));
+}
 
 template <typename PosT, int REF>
 __device__ __forceinline__ void load_pos(const uint8_t* __restrict__ base, int64_t k, int (&pos)[REF]) {
@@ -480,7 +484,7 @@ struct PatternDev {
   int64_t* row_ptr = nullptr;    // [N+1]
   int32_t* col_idx = nullptr;    // [nnz]
   int32_t* inc_ptr = nullptr;    // [N+1] node-incidence offsets
-  int32_t* inc_key = nullptr;    // [nInc] e * 16 + a, ascending per node
+  int32_t* inc_key = nullptr;    // [nInc] (e << key_shift) | a, ascending per node
   uint8_t* inc_pos = nullptr;    // [nInc][ref] column position of conn[e][b] in row conn[e][a] (u8 or u16)
   int32_t* elem_inc = nullptr;   // [nE][ref] incidence index of (e, a)
   int32_t* tile_row0 = nullptr;  // [T+1]
@@ -511,6 +515,7 @@ struct lfem_pattern_s {
   int64_t n_inc = 0;
   int32_t max_row = 0, max_deg = 0;
   int pos_bytes = 1;
+  int key_shift = 4;     // incidence key (e << key_shift) | a: 4 bits of local index up to 16 nodes, else 6
   int32_t tile_slots = 3072;
   int64_t n_tiles = 0;
   int64_t tile_elems_total = 0;

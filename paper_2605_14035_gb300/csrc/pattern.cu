@@ -227,7 +227,7 @@ __global__ void k_max_i32(const int32_t* __restrict__ a, int64_t n, int32_t* __r
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-__global__ void k_fill_incidence(const int32_t* __restrict__ conn, int64_t n_elem, int ref,
+__global__ void k_fill_incidence(const int32_t* __restrict__ conn, int64_t n_elem, int ref, int ksh,
                                  const int32_t* __restrict__ inc_ptr, int32_t* __restrict__ cursor,
                                  int32_t* __restrict__ inc_key) {
   const int64_t total = n_elem * ref;
@@ -236,16 +236,17 @@ __global__ void k_fill_incidence(const int32_t* __restrict__ conn, int64_t n_ele
     int64_t e = k / ref;
     int a = (int)(k - e * ref);
     int32_t slot = inc_ptr[v] + atomicAdd(&cursor[v], 1);
-    inc_key[slot] = (int32_t)(e * 16 + a);
+    inc_key[slot] = (int32_t)((e << ksh) | a);
   }
 }
 
-__global__ void k_elem_inc_and_raw(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ inc_key,
-                                   int64_t n_inc, int32_t* __restrict__ elem_inc, int32_t* __restrict__ raw) {
+__global__ void k_elem_inc_and_raw(const int32_t* __restrict__ conn, int ref, int ksh,
+                                   const int32_t* __restrict__ inc_key, int64_t n_inc, int32_t* __restrict__ elem_inc,
+                                   int32_t* __restrict__ raw) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_inc; k += (int64_t)gridDim.x * blockDim.x) {
     int32_t key = inc_key[k];
-    int64_t e = key >> 4;
-    int a = key & 15;
+    int64_t e = key >> ksh;
+    int a = key & ((1 << ksh) - 1);
     elem_inc[e * ref + a] = (int32_t)k;
     for (int b = 0; b < ref; ++b) raw[k * ref + b] = conn[e * ref + b];
   }
@@ -281,14 +282,14 @@ __global__ void k_row_compact(const int32_t* __restrict__ raw, const int32_t* __
 }
 
 template <typename PosT>
-__global__ void k_positions(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ inc_key,
+__global__ void k_positions(const int32_t* __restrict__ conn, int ref, int ksh, const int32_t* __restrict__ inc_key,
                             const int32_t* __restrict__ inc_ptr, int32_t n_nodes, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col_idx, PosT* __restrict__ pos) {
   // one thread per node; each incidence of the node gets the positions of its element's nodes in the row
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
     for (int32_t k = inc_ptr[i]; k < inc_ptr[i + 1]; ++k) {
-      int64_t e = inc_key[k] >> 4;
+      int64_t e = inc_key[k] >> ksh;
       for (int b = 0; b < ref; ++b) {
         int32_t c = conn[e * ref + b];
         int64_t lo = rb, hi = re;
@@ -309,7 +310,7 @@ __global__ void k_positions(const int32_t* __restrict__ conn, int ref, const int
 template <typename PosT>
 __global__ void k_slot_lists(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_key,
                              const PosT* __restrict__ inc_pos, const int64_t* __restrict__ row_ptr, int32_t n_nodes,
-                             int ref, int32_t* __restrict__ slot_off, int32_t* __restrict__ slot_ent) {
+                             int ref, int ksh, int32_t* __restrict__ slot_off, int32_t* __restrict__ slot_ent) {
   const int U = ref * (ref + 1) / 2;
   const int ps = pos_stride(ref);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_nodes; r += (int64_t)gridDim.x * blockDim.x) {
@@ -321,8 +322,8 @@ __global__ void k_slot_lists(const int32_t* __restrict__ inc_ptr, const int32_t*
       slot_off[s0 + j] = run;
       for (int32_t k = kb; k < ke; ++k) {
         const int32_t key = inc_key[k];
-        const int32_t e = key >> 4;
-        const int a = key & 15;
+        const int32_t e = key >> ksh;
+        const int a = key & ((1 << ksh) - 1);
         for (int b = 0; b < ref; ++b) {
           if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
           const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
@@ -733,6 +734,7 @@ lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st) 
   PatternDev& d = p->d;
   const int32_t N = p->n_nodes;
   if (tile_slots < 256 || tile_slots > 16384) return fail(LFEM_E_ARG, "tile_slots outside [256, 16384]");
+  if (p->ref > 16) return fail(LFEM_E_UNSUPPORTED, "row tiles hold elements of at most 16 nodes");
   if (p->max_row > tile_slots) return fail(LFEM_E_TOO_LARGE, "a CSR row is longer than the tile capacity");
   // greedy contiguous packing of rows under the slot and incidence budgets
   std::vector<int64_t> rp(N + 1);
@@ -830,7 +832,8 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   scan_exclusive<int32_t, int32_t>(deg, d.inc_ptr, N, scr, st);
   TRY(dalloc(&d.inc_key, n_inc));
   LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((int64_t)N + 1), st));
-  if (n_inc > 0) k_fill_incidence<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, nE, ref, d.inc_ptr, deg, d.inc_key);
+  if (n_inc > 0) k_fill_incidence<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, nE, ref, p->key_shift, d.inc_ptr, deg,
+                                                                       d.inc_key);
   LFEM_CUDA(cudaGetLastError());
   int32_t* sort_scr = nullptr;
   TRY(dalloc(&sort_scr, (int64_t)N + 2));
@@ -839,7 +842,8 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   int32_t* raw = nullptr;
   TRY(dalloc(&raw, n_inc * ref));
   TRY(dalloc(&d.elem_inc, n_inc));
-  if (n_inc > 0) k_elem_inc_and_raw<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, ref, d.inc_key, n_inc, d.elem_inc, raw);
+  if (n_inc > 0) k_elem_inc_and_raw<<<grid_for(n_inc, 256), 256, 0, st>>>(d.conn, ref, p->key_shift, d.inc_key, n_inc,
+                                                                         d.elem_inc, raw);
   LFEM_CUDA(cudaGetLastError());
   TRY(segsort(raw, d.inc_ptr, N, ref, p->max_deg * ref, sort_scr, st));
   int32_t* rowlen = deg;  // reuse
@@ -866,11 +870,11 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   LFEM_CUDA(cudaMemsetAsync(d.inc_pos, 0, (size_t)n_inc * pos_stride(ref) * p->pos_bytes, st));
   if (N > 0) {
     if (p->pos_bytes == 1)
-      k_positions<uint8_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, d.inc_key, d.inc_ptr, N, d.row_ptr,
-                                                               d.col_idx, d.inc_pos);
+      k_positions<uint8_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, p->key_shift, d.inc_key, d.inc_ptr, N,
+                                                               d.row_ptr, d.col_idx, d.inc_pos);
     else
-      k_positions<uint16_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, d.inc_key, d.inc_ptr, N, d.row_ptr,
-                                                                d.col_idx, (uint16_t*)d.inc_pos);
+      k_positions<uint16_t><<<grid_for(N, 128), 128, 0, st>>>(d.conn, ref, p->key_shift, d.inc_key, d.inc_ptr, N,
+                                                                d.row_ptr, d.col_idx, (uint16_t*)d.inc_pos);
   }
   LFEM_CUDA(cudaGetLastError());
   TRY(dalloc(&d.inc_local, n_inc));
@@ -884,10 +888,11 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
     if (N > 0) {
       if (p->pos_bytes == 1)
         k_slot_lists<uint8_t><<<grid_for(N, 128), 128, 0, st>>>(d.inc_ptr, d.inc_key, d.inc_pos, d.row_ptr, N, ref,
-                                                                 d.slot_off, d.slot_ent);
+                                                                 p->key_shift, d.slot_off, d.slot_ent);
       else
         k_slot_lists<uint16_t><<<grid_for(N, 128), 128, 0, st>>>(d.inc_ptr, d.inc_key, (const uint16_t*)d.inc_pos,
-                                                                  d.row_ptr, N, ref, d.slot_off, d.slot_ent);
+                                                                  d.row_ptr, N, ref, p->key_shift, d.slot_off,
+                                                                  d.slot_ent);
       LFEM_CUDA(cudaGetLastError());
     }
     const int32_t tot = (int32_t)(n_inc * ref);
@@ -900,6 +905,8 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   cudaFree(scr64);
   cudaFree(maxv);
   cudaFree(sort_scr);
+  // elements of more than 16 nodes (order-3/4 tets) use the element-major path only
+  if (ref > 16) return LFEM_OK;
   return build_tiles(p, p->tile_slots, st);
 }
 
@@ -977,10 +984,10 @@ lfem_status pattern_csr_noalloc(const int32_t* conn, int64_t nE, int32_t N, int 
     return fail(LFEM_E_TOO_LARGE, "too many elements meet at one node");
   scan_exclusive<int32_t, int32_t>(deg, inc_ptr, N, s32, st);
   LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((size_t)N + 1), st));
-  if (I > 0) k_fill_incidence<<<grid_for(I, 256), 256, 0, st>>>(conn, nE, ref, inc_ptr, deg, key);
+  if (I > 0) k_fill_incidence<<<grid_for(I, 256), 256, 0, st>>>(conn, nE, ref, 4, inc_ptr, deg, key);
   LFEM_CUDA(cudaGetLastError());
   TRY(segsort(key, inc_ptr, N, 1, h[1], sort_scr, st));
-  if (I > 0) k_elem_inc_and_raw<<<grid_for(I, 256), 256, 0, st>>>(conn, ref, key, I, einc, raw);
+  if (I > 0) k_elem_inc_and_raw<<<grid_for(I, 256), 256, 0, st>>>(conn, ref, 4, key, I, einc, raw);
   LFEM_CUDA(cudaGetLastError());
   TRY(segsort(raw, inc_ptr, N, ref, h[1] * ref, sort_scr, st));
   if (N > 0) k_row_unique_count<<<grid_for(N, 128), 128, 0, st>>>(raw, inc_ptr, ref, N, deg);
@@ -1002,10 +1009,16 @@ lfem_status pattern_csr_noalloc(const int32_t* conn, int64_t nE, int32_t N, int 
 // preprocessing, Sec. 4).  Edges are the upper slots (i < j) of the P1
 // pattern's rows, numbered in CSR order (row i ascending, then column j), so
 // edge (i, j)'s number is up_start[i] + (position of j in row i) - (entries of
-// row i with column <= i).  Node numbers: vertices, then p - 1 nodes per edge
-// from its lower to its higher vertex, then each triangle's interior nodes.
-// Positions are the straight ones, rounded in a fixed order (products, then
-// sums left to right; no multiply-add contraction).
+// row i with column <= i).  Tetrahedron faces are numbered in lexicographic
+// order of their sorted vertex triples (g0 < g1 < g2): every face is keyed
+// under g0 by the positions of g1 and g2 in row g0, the keys of each vertex
+// are sorted and made unique, and a face's number is the count of distinct
+// faces before it.  Node numbers: vertices, then p - 1 nodes per edge from its
+// lower to its higher vertex, then the face nodes (tets; face by face, on the
+// sorted vertices by increasing (alpha_1, alpha_2)) or the triangle interior
+// nodes, then the tet interior nodes.  Positions are the straight ones,
+// rounded in a fixed order (products, then sums left to right, face nodes
+// over the sorted vertices; no multiply-add contraction).
 // ---------------------------------------------------------------------------
 __global__ void k_lift_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n,
                              int32_t* __restrict__ up_cnt, int32_t* __restrict__ c_le) {
@@ -1027,35 +1040,130 @@ __global__ void k_lift_corners(const double* __restrict__ x, int64_t n_values, d
     out[i] = x[i];
 }
 
+// Local edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3); local faces (0,1,2),
+// (0,1,3), (0,2,3), (1,2,3) -- face f leaves out corner 3 - f.
+__device__ __forceinline__ int lift_edge_first(int k) { return k < 3 ? k : k - 3; }
+__device__ __forceinline__ int lift_edge_second(int k) { return k < 3 ? (k + 1) % 3 : 3; }
+__device__ __forceinline__ int lift_face_corner(int f, int k) { return k + (k >= 3 - f ? 1 : 0); }
+
+// Position of column c in row r (offset from the row start), or -1.
+__device__ __forceinline__ int64_t row_position(const int64_t* __restrict__ row_ptr,
+                                                const int32_t* __restrict__ col_idx, int32_t r, int32_t c) {
+  int64_t lo = row_ptr[r], hi = row_ptr[r + 1];
+  const int64_t rb = lo, re = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (col_idx[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < re && col_idx[lo] == c) ? lo - rb : -1;
+}
+
+// Local face f of a tet: its corners' global numbers sorted (g[0] < g[1] < g[2])
+// and rank[k] = place of the face's k-th local corner among them.
+__device__ __forceinline__ void tet_face_sorted(const int32_t (&v)[4], int f, int32_t (&g)[3], int (&rank)[3]) {
+  const int32_t a = v[lift_face_corner(f, 0)], b = v[lift_face_corner(f, 1)], c = v[lift_face_corner(f, 2)];
+  rank[0] = (a > b) + (a > c);
+  rank[1] = (b > a) + (b > c);
+  rank[2] = (c > a) + (c > b);
+  g[rank[0]] = a;
+  g[rank[1]] = b;
+  g[rank[2]] = c;
+}
+
+__device__ __forceinline__ int32_t face_key(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                            const int32_t (&g)[3]) {
+  const int64_t p1 = row_position(row_ptr, col_idx, g[0], g[1]), p2 = row_position(row_ptr, col_idx, g[0], g[2]);
+  if (p1 < 0 || p2 < 0 || p2 > 32767) return -1;
+  return (int32_t)((p1 << 16) | p2);
+}
+
+__global__ void k_face_count(const int32_t* __restrict__ conn, int64_t n_elem, int32_t* __restrict__ cnt) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+    for (int a = 0; a < 4; ++a) v[a] = conn[e * 4 + a];
+    for (int f = 0; f < 4; ++f) {
+      int32_t g[3];
+      int rank[3];
+      tet_face_sorted(v, f, g, rank);
+      atomicAdd(&cnt[g[0]], 1);
+    }
+  }
+}
+
+__global__ void k_face_fill(const int32_t* __restrict__ conn, int64_t n_elem, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col_idx, const int32_t* __restrict__ off,
+                            int32_t* __restrict__ cursor, int32_t* __restrict__ keys, int32_t* status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+    for (int a = 0; a < 4; ++a) v[a] = conn[e * 4 + a];
+    for (int f = 0; f < 4; ++f) {
+      int32_t g[3];
+      int rank[3];
+      tet_face_sorted(v, f, g, rank);
+      int32_t key = face_key(row_ptr, col_idx, g);
+      if (key < 0) {
+        atomicOr(status, ST_INDEX);  // the pattern does not hold this face's edges
+        key = INT_MAX;
+      }
+      keys[off[g[0]] + atomicAdd(&cursor[g[0]], 1)] = key;
+    }
+  }
+}
+
+// Per vertex: distinct-key number of every (sorted) key, and the distinct count.
+__global__ void k_face_unique(const int32_t* __restrict__ keys, const int32_t* __restrict__ off, int32_t n,
+                              int32_t* __restrict__ uid, int32_t* __restrict__ fcnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t d = -1, prev = -1;
+    for (int32_t k = off[i]; k < off[i + 1]; ++k) {
+      d += keys[k] != prev;
+      prev = keys[k];
+      uid[k] = d;
+    }
+    fcnt[i] = d + 1;
+  }
+}
+
+struct LiftFaces {
+  const int32_t* off = nullptr;    // [N + 1] per-vertex key ranges
+  const int32_t* keys = nullptr;   // sorted face keys
+  const int32_t* uid = nullptr;    // distinct number of each key within its vertex
+  const int64_t* fbase = nullptr;  // [N + 1] first face number of each vertex
+  int64_t n_faces = 0;
+};
+
+// Index of (p - a1 - a2, a1, a2) in the list of a triangle's interior
+// multi-indices by increasing (a1, a2).
+__device__ __forceinline__ int face_alpha_index(int p, int a1, int a2) {
+  int t = 0;
+  for (int b1 = 1; b1 < a1; ++b1) t += p - 1 - b1;
+  return t + a2 - 1;
+}
+
 __global__ void k_lift_elements(const int32_t* __restrict__ conn, int64_t n_elem, int dim, int na, int order,
                                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                                 const int64_t* __restrict__ up_start, const int32_t* __restrict__ c_le,
-                                int32_t n_vert, int64_t n_edges, const double* __restrict__ x, int32_t* conn_out,
-                                double* coords_out, int32_t* status) {
+                                int32_t n_vert, int64_t n_edges, const LiftFaces fc, const double* __restrict__ x,
+                                int32_t* conn_out, double* coords_out, int32_t* status) {
   const int ref1 = dim + 1;
-  const int n_le = dim == 1 ? 1 : 3;
-  const int n_int = dim == 2 ? (order - 1) * (order - 2) / 2 : 0;
-  const int refp = ref1 + n_le * (order - 1) + n_int;
+  const int n_le = dim == 1 ? 1 : (dim == 2 ? 3 : 6);
+  const int nfi = (order - 1) * (order - 2) / 2;  // interior nodes of one triangle
+  const int nci = dim == 3 ? (order - 1) * (order - 2) * (order - 3) / 6 : 0;
+  const int refp = ref1 + n_le * (order - 1) + (dim == 2 ? nfi : (dim == 3 ? 4 * nfi + nci : 0));
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v[3];
+    int32_t v[4];
     for (int a = 0; a < ref1; ++a) v[a] = conn[e * ref1 + a];
     int32_t* row = conn_out ? conn_out + e * refp : nullptr;
     if (row)
       for (int a = 0; a < ref1; ++a) row[a] = v[a];
     int slot = ref1;
     for (int le = 0; le < n_le; ++le) {
-      const int ia = le, ib = (le + 1) % (dim + 1);  // (0,1) | (0,1),(1,2),(2,0)
-      const int32_t i = v[ia], j = v[ib];
+      const int32_t i = v[lift_edge_first(le)], j = v[lift_edge_second(le)];
       const int32_t lo_v = i < j ? i : j, hi_v = i < j ? j : i;
-      int64_t lo = row_ptr[lo_v], hi = row_ptr[lo_v + 1];
-      const int64_t rb = lo;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (col_idx[mid] < hi_v) lo = mid + 1;
-        else hi = mid;
-      }
-      const int64_t eid = up_start[lo_v] + (lo - rb) - c_le[lo_v];
-      if (lo >= row_ptr[lo_v + 1] || col_idx[lo] != hi_v || eid < 0 || eid >= n_edges) {
+      const int64_t pos = row_position(row_ptr, col_idx, lo_v, hi_v);
+      const int64_t eid = up_start[lo_v] + pos - c_le[lo_v];
+      if (pos < 0 || eid < 0 || eid >= n_edges) {
         atomicOr(status, ST_INDEX);  // the pattern does not hold this edge: skip its nodes
         slot += order - 1;
         continue;
@@ -1072,20 +1180,76 @@ __global__ void k_lift_elements(const int32_t* __restrict__ conn, int64_t n_elem
       }
       slot += order - 1;
     }
+    const int64_t base = (int64_t)n_vert + n_edges * (order - 1);
     if (dim == 2) {
-      const int64_t base = (int64_t)n_vert + n_edges * (order - 1) + e * n_int;
+      const int64_t first = base + e * nfi;
       int t = 0;
       for (int a1 = 1; a1 < order; ++a1)
         for (int a2 = 1; a1 + a2 < order; ++a2, ++t) {
-          if (row) row[slot + t] = (int32_t)(base + t);
+          if (row) row[slot + t] = (int32_t)(first + t);
           if (coords_out) {
             const double l0 = (double)(order - a1 - a2) / order, l1 = (double)a1 / order, l2 = (double)a2 / order;
             for (int c = 0; c < na; ++c) {
               const double s01 = __dadd_rn(__dmul_rn(l0, x[(int64_t)v[0] * na + c]), __dmul_rn(l1, x[(int64_t)v[1] * na + c]));
-              coords_out[(base + t) * na + c] = __dadd_rn(s01, __dmul_rn(l2, x[(int64_t)v[2] * na + c]));
+              coords_out[(first + t) * na + c] = __dadd_rn(s01, __dmul_rn(l2, x[(int64_t)v[2] * na + c]));
             }
           }
         }
+    }
+    if (dim == 3 && nfi > 0) {
+      for (int f = 0; f < 4; ++f, slot += nfi) {
+        int32_t g[3];
+        int rank[3];
+        tet_face_sorted(v, f, g, rank);
+        const int32_t key = face_key(row_ptr, col_idx, g);
+        int32_t lo = fc.off[g[0]], hi = fc.off[g[0] + 1];
+        const int32_t end = hi;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi) >> 1;
+          if (fc.keys[mid] < key) lo = mid + 1;
+          else hi = mid;
+        }
+        const int64_t fid = key < 0 || lo >= end || fc.keys[lo] != key ? -1 : fc.fbase[g[0]] + fc.uid[lo];
+        if (fid < 0 || fid >= fc.n_faces) {
+          atomicOr(status, ST_INDEX);
+          continue;
+        }
+        const int64_t first = base + fid * nfi;
+        int t = 0;
+        for (int aj = 1; aj < order; ++aj)
+          for (int al = 1; aj + al < order; ++al, ++t) {
+            // weights of the local corners (i, j, l), moved onto the sorted corners
+            int w[3];
+            w[rank[0]] = order - aj - al;
+            w[rank[1]] = aj;
+            w[rank[2]] = al;
+            const int64_t node = first + face_alpha_index(order, w[1], w[2]);
+            if (row) row[slot + t] = (int32_t)node;
+            if (coords_out) {
+              const double l0 = (double)w[0] / order, l1 = (double)w[1] / order, l2 = (double)w[2] / order;
+              for (int c = 0; c < na; ++c) {
+                const double s01 = __dadd_rn(__dmul_rn(l0, x[(int64_t)g[0] * na + c]), __dmul_rn(l1, x[(int64_t)g[1] * na + c]));
+                coords_out[node * na + c] = __dadd_rn(s01, __dmul_rn(l2, x[(int64_t)g[2] * na + c]));
+              }
+            }
+          }
+      }
+      const int64_t first = base + fc.n_faces * nfi + e * nci;
+      int t = 0;
+      for (int a1 = 1; a1 < order; ++a1)
+        for (int a2 = 1; a1 + a2 < order; ++a2)
+          for (int a3 = 1; a1 + a2 + a3 < order; ++a3, ++t) {
+            if (row) row[slot + t] = (int32_t)(first + t);
+            if (coords_out) {
+              const double l[4] = {(double)(order - a1 - a2 - a3) / order, (double)a1 / order, (double)a2 / order,
+                                   (double)a3 / order};
+              for (int c = 0; c < na; ++c) {
+                double acc = __dmul_rn(l[0], x[(int64_t)v[0] * na + c]);
+                for (int k = 1; k < 4; ++k) acc = __dadd_rn(acc, __dmul_rn(l[k], x[(int64_t)v[k] * na + c]));
+                coords_out[(first + t) * na + c] = acc;
+              }
+            }
+          }
     }
   }
 }
@@ -1094,21 +1258,38 @@ lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int orde
                        double* coords_out, int64_t* n_nodes_out, cudaStream_t st) {
   PatternDev& d = p->d;
   const int32_t N = p->n_nodes;
+  const int64_t nE = p->n_elem;
+  const int nfi = (order - 1) * (order - 2) / 2;
+  const int nci = p->dim == 3 ? (order - 1) * (order - 2) * (order - 3) / 6 : 0;
+  std::vector<void*> owned;
+  auto cleanup = [&]() {
+    for (void* q : owned) cudaFree(q);
+    owned.clear();
+  };
+  auto alloc32 = [&](int32_t** q, int64_t n) {
+    lfem_status r = dalloc(q, n);
+    if (r == LFEM_OK) owned.push_back(*q);
+    return r;
+  };
+  auto alloc64 = [&](int64_t** q, int64_t n) {
+    lfem_status r = dalloc(q, n);
+    if (r == LFEM_OK) owned.push_back(*q);
+    return r;
+  };
+#define LIFT_TRY(x)           \
+  do {                        \
+    lfem_status r_ = (x);     \
+    if (r_ != LFEM_OK) {      \
+      cleanup();              \
+      return r_;              \
+    }                         \
+  } while (0)
   int32_t *cnt = nullptr, *cle = nullptr;
   int64_t *up = nullptr, *scr = nullptr;
-  auto cleanup = [&]() {
-    if (cnt) cudaFree(cnt);
-    if (cle) cudaFree(cle);
-    if (up) cudaFree(up);
-    if (scr) cudaFree(scr);
-  };
-  lfem_status s = LFEM_OK;
-  if ((s = dalloc(&cnt, (int64_t)N + 1)) != LFEM_OK || (s = dalloc(&cle, (int64_t)N + 1)) != LFEM_OK ||
-      (s = dalloc(&up, (int64_t)N + 1)) != LFEM_OK ||
-      (s = dalloc(&scr, scan_scratch_bytes((int64_t)N + 1, 8) / 8)) != LFEM_OK) {
-    cleanup();
-    return s;
-  }
+  LIFT_TRY(alloc32(&cnt, (int64_t)N + 1));
+  LIFT_TRY(alloc32(&cle, (int64_t)N + 1));
+  LIFT_TRY(alloc64(&up, (int64_t)N + 1));
+  LIFT_TRY(alloc64(&scr, scan_scratch_bytes((int64_t)N + 1, 8) / 8));
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)N + 1), st);
   if (N > 0) k_lift_count<<<grid_for(N, 256), 256, 0, st>>>(d.row_ptr, d.col_idx, N, cnt, cle);
   // up[0..N]: exclusive scan of the N row counts, up[N] = number of edges
@@ -1120,8 +1301,57 @@ lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int orde
     cleanup();
     return cuda_fail(ce, "order lifting");
   }
-  const int n_int = p->dim == 2 ? (order - 1) * (order - 2) / 2 : 0;
-  const int64_t n_out = (int64_t)N + n_edges * (order - 1) + p->n_elem * n_int;
+  LiftFaces fc;
+  if (p->dim == 3 && nfi > 0 && nE > 0) {
+    // faces: per lowest vertex, sorted unique keys (positions of the other two in its row)
+    if (p->max_row > 32767) {
+      cleanup();
+      return fail(LFEM_E_TOO_LARGE, "a CSR row is too long for the face keys");
+    }
+    int32_t *fcnt = nullptr, *foff = nullptr, *fcur = nullptr, *fkeys = nullptr, *fuid = nullptr, *fscr = nullptr,
+            *sort_scr = nullptr, *mx = nullptr;
+    int64_t *fbase = nullptr, *fscr64 = nullptr;
+    LIFT_TRY(alloc32(&fcnt, (int64_t)N + 1));
+    LIFT_TRY(alloc32(&foff, (int64_t)N + 1));
+    LIFT_TRY(alloc32(&fcur, (int64_t)N + 1));
+    LIFT_TRY(alloc32(&fkeys, 4 * nE));
+    LIFT_TRY(alloc32(&fuid, 4 * nE));
+    LIFT_TRY(alloc32(&fscr, scan_scratch_bytes((int64_t)N + 1, 4) / 4));
+    LIFT_TRY(alloc32(&sort_scr, (int64_t)N + 2));
+    LIFT_TRY(alloc32(&mx, 2));
+    LIFT_TRY(alloc64(&fbase, (int64_t)N + 1));
+    LIFT_TRY(alloc64(&fscr64, scan_scratch_bytes((int64_t)N + 1, 8) / 8));
+    cudaMemsetAsync(fcnt, 0, sizeof(int32_t) * ((size_t)N + 1), st);
+    cudaMemsetAsync(fcur, 0, sizeof(int32_t) * ((size_t)N + 1), st);
+    cudaMemsetAsync(mx, 0, 2 * sizeof(int32_t), st);
+    k_face_count<<<grid_for(nE, 128), 128, 0, st>>>(d.conn, nE, fcnt);
+    scan_exclusive<int32_t, int32_t>(fcnt, foff, (int64_t)N, fscr, st);
+    k_face_fill<<<grid_for(nE, 128), 128, 0, st>>>(d.conn, nE, d.row_ptr, d.col_idx, foff, fcur, fkeys, d.status);
+    if (N > 0) k_max_i32<<<grid_for(N, 256), 256, 0, st>>>(fcnt, N, mx);
+    int32_t max_len = 0;
+    cudaMemcpyAsync(&max_len, mx, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      cleanup();
+      return cuda_fail(ce, "order lifting");
+    }
+    LIFT_TRY(segsort(fkeys, foff, N, 1, max_len, sort_scr, st));
+    if (N > 0) k_face_unique<<<grid_for(N, 128), 128, 0, st>>>(fkeys, foff, N, fuid, fcnt);
+    scan_exclusive<int32_t, int64_t>(fcnt, fbase, (int64_t)N, fscr64, st);
+    cudaMemcpyAsync(&fc.n_faces, fbase + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      cleanup();
+      return cuda_fail(ce, "order lifting");
+    }
+    fc.off = foff;
+    fc.keys = fkeys;
+    fc.uid = fuid;
+    fc.fbase = fbase;
+  }
+  const int64_t n_out = (int64_t)N + n_edges * (order - 1) + (p->dim == 2 ? nE * nfi : 0) +
+                        (p->dim == 3 ? fc.n_faces * nfi + nE * nci : 0);
   *n_nodes_out = n_out;
   if (n_out >= INT32_MAX) {
     cleanup();
@@ -1130,10 +1360,9 @@ lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int orde
   if (conn_out || coords_out) {
     if (coords_out && N > 0)
       k_lift_corners<<<grid_for((int64_t)N * na, 256), 256, 0, st>>>(coords, (int64_t)N * na, coords_out);
-    if (p->n_elem > 0)
-      k_lift_elements<<<grid_for(p->n_elem, 128), 128, 0, st>>>(d.conn, p->n_elem, p->dim, na, order, d.row_ptr,
-                                                                d.col_idx, up, cle, N, n_edges, coords, conn_out,
-                                                                coords_out, d.status);
+    if (nE > 0)
+      k_lift_elements<<<grid_for(nE, 128), 128, 0, st>>>(d.conn, nE, p->dim, na, order, d.row_ptr, d.col_idx, up, cle,
+                                                         N, n_edges, fc, coords, conn_out, coords_out, d.status);
     ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // scratch is freed below
     if (ce != cudaSuccess) {
@@ -1141,6 +1370,7 @@ lfem_status lift_order(lfem_pattern_s* p, const double* coords, int na, int orde
       return cuda_fail(ce, "order lifting");
     }
   }
+#undef LIFT_TRY
   cleanup();
   return LFEM_OK;
 }
@@ -1151,8 +1381,8 @@ extern "C" lfem_status lfem_lift_order(lfem_pattern_t p, const double* coords, i
                                        int32_t* conn_out, double* coords_out, int64_t* n_nodes_out,
                                        void* cuda_stream) {
   if (!p || !n_nodes_out) return lfem::fail(LFEM_E_ARG, "NULL argument");
-  if (p->order != 1 || p->dim > 2 || order < 2 || order > 4)
-    return lfem::fail(LFEM_E_UNSUPPORTED, "lifting needs an order-1 curve or triangle pattern and order 2..4");
+  if (p->order != 1 || order < 2 || order > 4)
+    return lfem::fail(LFEM_E_UNSUPPORTED, "lifting needs an order-1 pattern and order 2..4");
   if (ambient < p->dim || ambient > 3) return lfem::fail(LFEM_E_ARG, "ambient");
   if (coords_out && p->n_nodes > 0 && !coords) return lfem::fail(LFEM_E_ARG, "coords is NULL");
   return lfem::lift_order(p, coords, ambient, order, conn_out, coords_out, n_nodes_out, (cudaStream_t)cuda_stream);

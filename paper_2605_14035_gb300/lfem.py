@@ -7,6 +7,7 @@ there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from dataclasses import dataclass
 from typing import Optional
@@ -377,7 +378,7 @@ def lift_order(pat1: Pattern, coords: torch.Tensor, order: int, stream=None):
     n = ctypes.c_int64()
     _check(_lib.lfem_lift_order(pat1.handle, _ptr(coords), int(coords.shape[1]), int(order), None, None,
                                 ctypes.byref(n), _stream(stream)))
-    ref = (order + 1) if pat1.dim == 1 else (order + 1) * (order + 2) // 2
+    ref = math.comb(order + pat1.dim, pat1.dim)
     conn = torch.empty(pat1.n_elem, ref, dtype=torch.int32, device=coords.device)
     out = torch.empty(n.value, coords.shape[1], dtype=torch.float64, device=coords.device)
     _check(_lib.lfem_lift_order(pat1.handle, _ptr(coords), int(coords.shape[1]), int(order), _ptr(conn), _ptr(out),

@@ -83,7 +83,22 @@ def build_cases():
     ec = np.stack([np.arange(40), (np.arange(40) + 1) % 40], axis=1).astype(np.int32)
     unit = lambda y: y / np.linalg.norm(y, axis=1, keepdims=True)  # noqa: E731
     c["circle_p4"] = (*meshes.to_order(xc, ec, 4, project=unit), 1, 4, quadrature.gauss_interval(6))
+    # orders 3 and 4 on tetrahedra (warp-per-element path): curved elements
+    c["cube_p3"] = (*curved_cube(3, 3), 3, 3, quadrature.paper_rule(3))
+    c["cube_p4"] = (*curved_cube(2, 4), 3, 4, quadrature.paper_rule(3))
+    c["cube_p3_gauss27"] = (*curved_cube(2, 3, seed=13), 3, 3, quadrature.collapsed_gauss(3, 3))
     return c
+
+
+def curved_cube(n, order, amp=0.004, seed=12):
+    """Order-p Kuhn cube (n^3 cells) whose generated interior nodes are moved by
+    U(-amp, amp) per component: curved edges, faces and cells, flat boundary."""
+    x1, t1 = meshes.kuhn_cube_p2(n, order=1)
+    x, e = meshes.to_order(x1, t1, order)
+    on_bnd = np.any((x < 1e-12) | (x > 1 - 1e-12), axis=1)
+    move = ~on_bnd & (np.arange(x.shape[0]) >= x1.shape[0])
+    rng = np.random.default_rng(meshes.BASE_SEED + seed)
+    return x + np.where(move[:, None], rng.uniform(-amp, amp, x.shape), 0.0), e
 
 
 def diag_scaled_error(v, ref, rp, ci):

@@ -36,7 +36,7 @@ def prepare(name, lfem, tile_slots=256):
     pts = oracle.eval_points(x, e, d, p, rule.xi)
     coef = coef_field(pts)
     pat = lfem.Pattern(to_dev(e), x.shape[0], d, p)
-    if tile_slots:
+    if tile_slots and not (d == 3 and p >= 3):  # order-3/4 tets have no row tiles
         pat.retile(tile_slots)
     return x, e, d, p, rule, coef, pat
 
@@ -53,7 +53,7 @@ def test_pattern_bit_exact(name, lfem):
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_values(name, lfem):
     x, e, d, p, rule, coef, pat = prepare(name, lfem)
-    assert pat.info()["tiles"] > 2 or x.shape[0] < 50
+    assert pat.info()["tiles"] > 2 or x.shape[0] < 50 or (d == 3 and p >= 3)
     orp, oci, M, A, C = oracle.assemble(x, e, d, p, rule.xi, rule.w, coef)
     out = lfem.assemble(pat, to_dev(x), rule, to_dev(coef), which=7, precision=lfem.FP64)
     torch.cuda.synchronize()
@@ -77,7 +77,7 @@ def test_mixed_values(name, lfem):
     assert abs(out["M"].double().sum().item() - M.sum()) <= MIXED_TOL * abs(M.sum())
 
 
-@pytest.mark.parametrize("name", ["perturbed_sphere_p2", "cube_p2", "cube_p1"])
+@pytest.mark.parametrize("name", ["perturbed_sphere_p2", "cube_p2", "cube_p1", "cube_p3"])
 def test_mixed_conditioning_threshold(name, lfem):
     """kappa_max = 1 sends every element (metric quality < 1) to the double
     recomputation, INFINITY sends none (no degenerate element here); both
@@ -117,6 +117,24 @@ def test_deterministic_and_tile_independent(name, prec, lfem):
                 assert torch.equal(ref[k], other[k]), (k, slots, chunk)
     for k in ref:
         assert torch.equal(ref[k], again[k])
+
+
+@pytest.mark.parametrize("name", ["cube_p3", "cube_p4"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tet_high_deterministic_and_subsets(name, prec, lfem):
+    """Order-3/4 tets: bit-identical reruns, and each matrix alone equals the
+    same matrix assembled with the others."""
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    xd, cd = to_dev(x), to_dev(coef)
+    if prec == 1:
+        cd = cd.float()
+    ref = lfem.assemble(pat, xd, rule, cd, which=7, precision=prec)
+    again = lfem.assemble(pat, xd, rule, cd, which=7, precision=prec)
+    for k in ref:
+        assert torch.equal(ref[k], again[k])
+    for which, k in ((1, "M"), (2, "A"), (4, "MC")):
+        part = lfem.assemble(pat, xd, rule, cd, which=which, precision=prec)
+        assert list(part) == [k] and torch.equal(part[k], ref[k])
 
 
 @pytest.mark.parametrize("which", [1, 2, 4, 3, 5, 6])

@@ -88,7 +88,8 @@ def test_mcf_step(name, lfem):
     assert torch.equal(xin, x1)
 
 
-@pytest.mark.parametrize("kind,order", [("sphere", 3), ("sphere", 4), ("disk", 3), ("disk", 4), ("circle", 4)])
+@pytest.mark.parametrize("kind,order", [("sphere", 3), ("sphere", 4), ("disk", 3), ("disk", 4), ("circle", 4),
+                                        ("sphere", 2), ("cube", 2), ("cube", 3), ("cube", 4), ("cube_jit", 4)])
 def test_lift_order_matches_the_cpu_generator(kind, order, lfem):
     """GPU node generation (P1 -> order p) against the seeded CPU generator:
     identical connectivity and identical coordinate bits."""
@@ -98,6 +99,10 @@ def test_lift_order_matches_the_cpu_generator(kind, order, lfem):
         x, e = meshes.icosphere(2, 1)
     elif kind == "disk":
         x, e = meshes.hex_disk(5, 1)
+    elif kind == "cube":
+        x, e = meshes.kuhn_cube_p2(3, order=1)
+    elif kind == "cube_jit":
+        x, e = meshes.kuhn_cube_p2(4, jitter=0.2, seed=meshes.BASE_SEED + 21, order=1)
     else:
         t = 2 * np.pi * np.arange(30) / 30
         x = np.stack([np.cos(t), np.sin(t)], axis=1)
