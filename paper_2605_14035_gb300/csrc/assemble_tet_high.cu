@@ -342,6 +342,94 @@ static lfem_status run_tet_high_p(bool mixed, const TwoPassArgs& a, void* scratc
   return LFEM_OK;
 }
 
+// Load vector of order-3/4 tets, one warp per element (FP64): lanes over the
+// points compute w_q s_q f_h(x_q), f_h = sum_b f_b phi_b; lanes over the nodes
+// then sum loc_a = sum_q (w s f_h)_q phi_a(q) (Sec. 2, b = M f).
+template <int P>
+__global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_load(const VecArgs a, const V4<double>* __restrict__ gtab) {
+  constexpr int REF = TetHigh<P>::REF;
+  const int Q = a.tab.q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V4<double>* tab = reinterpret_cast<V4<double>*>(smem_raw);  // [Q][REF]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V4<double>* rel = tab + Q * REF + warp * (REF + (REF + Q + 3) / 4);
+  double* fv = reinterpret_cast<double*>(rel + REF);  // [REF] nodal values, then [Q] point factors
+  double* fq = fv + REF;
+  for (int t = threadIdx.x; t < Q * REF; t += blockDim.x) tab[t] = gtab[t];
+  __syncthreads();
+  const double* w64 = bank<double>() + a.tab.off64;
+  for (int64_t e = (int64_t)blockIdx.x * kTetHighWarps + warp; e < a.n_elem; e += (int64_t)gridDim.x * kTetHighWarps) {
+    const int32_t* cn = a.conn + e * REF;
+    const int64_t n0 = __ldg(cn);
+    const double x0 = __ldg(a.coords + 3 * n0), y0 = __ldg(a.coords + 3 * n0 + 1), z0 = __ldg(a.coords + 3 * n0 + 2);
+    for (int b = lane; b < REF; b += 32) {
+      const int64_t nb = __ldg(cn + b);
+      rel[b] = V4<double>{__ldg(a.coords + 3 * nb) - x0, __ldg(a.coords + 3 * nb + 1) - y0,
+                          __ldg(a.coords + 3 * nb + 2) - z0, 0.0};
+      fv[b] = __ldg(a.u + nb);
+    }
+    __syncwarp();
+    for (int q = lane; q < Q; q += 32) {
+      const V4<double>* tq = tab + q * REF;
+      double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      double fh = 0.0;
+      for (int b = 0; b < REF; ++b) {
+        const V4<double> r = rel[b], d = tq[b];
+        fh = fma(fv[b], d.x, fh);
+        J[0][0] = fma(r.x, d.y, J[0][0]);
+        J[0][1] = fma(r.x, d.z, J[0][1]);
+        J[0][2] = fma(r.x, d.w, J[0][2]);
+        J[1][0] = fma(r.y, d.y, J[1][0]);
+        J[1][1] = fma(r.y, d.z, J[1][1]);
+        J[1][2] = fma(r.y, d.w, J[1][2]);
+        J[2][0] = fma(r.z, d.y, J[2][0]);
+        J[2][1] = fma(r.z, d.z, J[2][1]);
+        J[2][2] = fma(r.z, d.w, J[2][2]);
+      }
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[2][1] * J[1][2]) -
+                         J[1][0] * (J[0][1] * J[2][2] - J[2][1] * J[0][2]) +
+                         J[2][0] * (J[0][1] * J[1][2] - J[1][1] * J[0][2]);
+      fq[q] = w64[q] * fabs(det) * fh;
+    }
+    __syncwarp();
+    for (int b = lane; b < REF; b += 32) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc = fma(fq[q], tab[q * REF + b].x, acc);
+      a.loc[e * REF + b] = acc;
+    }
+    __syncwarp();
+  }
+}
+
+template <int P>
+static lfem_status run_tet_high_load_p(const VecArgs& a, void* scratch, int sms, cudaStream_t st) {
+  constexpr int REF = TetHigh<P>::REF;
+  const int Q = a.tab.q;
+  V4<double>* t64 = static_cast<V4<double>*>(scratch);
+  V4<float>* t32 = reinterpret_cast<V4<float>*>(t64 + (size_t)Q * REF);
+  if (a.n_elem > 0) {
+    k_tet_high_table<P><<<(Q * REF + 127) / 128, 128, 0, st>>>(a.tab, t64, t32);
+    LFEM_CUDA(cudaGetLastError());
+    const size_t smem = sizeof(V4<double>) * ((size_t)Q * REF + (size_t)kTetHighWarps * (REF + (REF + Q + 3) / 4));
+    auto kern = k_tet_high_load<P>;
+    LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    LFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTetHighWarps * 32, smem));
+    if (occ < 1) return fail(LFEM_E_TOO_LARGE, "order-3/4 tet tables exceed shared memory");
+    int64_t g = (a.n_elem + kTetHighWarps - 1) / kTetHighWarps;
+    if (g > (int64_t)sms * occ) g = (int64_t)sms * occ;
+    kern<<<(unsigned)g, kTetHighWarps * 32, smem, st>>>(a, t64);
+    LFEM_CUDA(cudaGetLastError());
+  }
+  return run_vec_gather(a, REF, 1, st);
+}
+
+lfem_status run_tet_high_load(int P, const VecArgs& a, void* scratch, int sms, cudaStream_t st) {
+  if (P == 3) return run_tet_high_load_p<3>(a, scratch, sms, st);
+  if (P == 4) return run_tet_high_load_p<4>(a, scratch, sms, st);
+  return fail(LFEM_E_UNSUPPORTED, "element type");
+}
+
 size_t tet_high_scratch_bytes(int P, int Q, int64_t n_elem) {
   const int REF = P == 3 ? TetHigh<3>::REF : TetHigh<4>::REF;
   return (size_t)Q * REF * (sizeof(V4<double>) + sizeof(V4<float>)) + sizeof(uint32_t) * ((size_t)n_elem + 1);

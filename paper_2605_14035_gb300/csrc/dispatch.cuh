@@ -27,6 +27,8 @@ lfem_status run_twopass_high(int D, int NA, int P, bool mixed, const TwoPassArgs
 lfem_status bank_upload_tet_high(const void* src, size_t bytes, size_t offset);
 lfem_status run_tet_high(int P, bool mixed, const TwoPassArgs& a, void* scratch, int sms, cudaStream_t st);
 size_t tet_high_scratch_bytes(int P, int Q, int64_t n_elem);
+lfem_status run_tet_high_load(int P, const VecArgs& a, void* scratch, int sms, cudaStream_t st);
+lfem_status run_vec_gather(const VecArgs& a, int ref, int nc, cudaStream_t st);
 lfem_status run_vectors(int D, int NA, int P, int kind, const VecArgs& a, cudaStream_t st);
 lfem_status run_mcf_solve(int nc, const McfSolveArgs& s, cudaStream_t st, int* iterations);
 

@@ -666,7 +666,6 @@ static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int am
                                   const double* u, double* out, int kind, cudaStream_t st) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
-  if (p->dim == 3 && p->order >= 3) return fail(LFEM_E_UNSUPPORTED, "vectors of order-3/4 tetrahedra");
   if (kind == 1 && !(p->dim == 2 && ambient == 3))
     return fail(LFEM_E_UNSUPPORTED, "the non-linear vectors need a surface (dim 2 in R^3)");
   if (p->n_elem > 0 && (!coords || !u)) return fail(LFEM_E_ARG, "coords or nodal values are NULL");
@@ -675,7 +674,10 @@ static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int am
   lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
   if (s != LFEM_OK) return s;
   const int nc = kind == 0 ? 1 : 4;
-  const size_t need = (size_t)p->n_elem * p->ref * nc * sizeof(double);
+  // order-3/4 tets keep their device basis tables behind the local vectors
+  const bool tet_high = p->dim == 3 && p->order >= 3;
+  const size_t lbytes = ((size_t)p->n_elem * p->ref * nc * sizeof(double) + 255) / 256 * 256;
+  const size_t need = lbytes + (tet_high ? tet_high_scratch_bytes(p->order, tab.q, 0) : 0);
   if (need > p->d.vec_buf_bytes) {
     if (p->d.vec_buf) cudaFree(p->d.vec_buf);
     p->d.vec_buf = nullptr;
@@ -696,7 +698,13 @@ static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int am
   a.out = out;
   a.n_elem = p->n_elem;
   a.n_nodes = p->n_nodes;
+  a.key_shift = p->key_shift;
   a.tab = tab;
+  if (tet_high) {
+    int sms = 0;
+    LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    return run_tet_high_load(p->order, a, reinterpret_cast<char*>(p->d.vec_buf) + lbytes, sms, st);
+  }
   return run_vectors(p->dim, ambient, p->order, kind, a, st);
 }
 

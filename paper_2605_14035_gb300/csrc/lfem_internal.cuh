@@ -446,6 +446,7 @@ struct VecArgs {
   double* out;      // [nc][N]
   int64_t n_elem;
   int32_t n_nodes;
+  int key_shift;    // incidence key (e << key_shift) | a
   TabRef tab;
 };
 

@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(256) k_vec_gather(const VecArgs a, int ref) {
     const int32_t k0 = __ldg(a.inc_ptr + i), k1 = __ldg(a.inc_ptr + i + 1);
     for (int32_t k = k0; k < k1; ++k) {
       const int32_t key = __ldg(a.inc_key + k);
-      const int64_t e = key >> 4;
-      const int lidx = key & 15;
+      const int64_t e = key >> a.key_shift;
+      const int lidx = key & ((1 << a.key_shift) - 1);
       const double* l = a.loc + (e * ref + lidx) * NC;
 #pragma unroll
       for (int c = 0; c < NC; ++c) s[c] += l[c];
@@ -114,6 +114,16 @@ static unsigned vec_grid(int64_t n, int threads) {
   return (unsigned)(g < 152 * 32 ? (g > 0 ? g : 1) : 152 * 32);
 }
 
+lfem_status run_vec_gather(const VecArgs& a, int ref, int nc, cudaStream_t st) {
+  if (a.n_nodes > 0) {
+    if (nc == 1) k_vec_gather<1><<<vec_grid(a.n_nodes, 256), 256, 0, st>>>(a, ref);
+    else if (nc == 4) k_vec_gather<4><<<vec_grid(a.n_nodes, 256), 256, 0, st>>>(a, ref);
+    else return fail(LFEM_E_ARG, "vector components");
+    LFEM_CUDA(cudaGetLastError());
+  }
+  return LFEM_OK;
+}
+
 template <int D, int NA, int P, int KIND>
 static lfem_status launch_vec(const VecArgs& a, cudaStream_t st) {
   constexpr int NC = KIND == 0 ? 1 : 4;
@@ -121,11 +131,7 @@ static lfem_status launch_vec(const VecArgs& a, cudaStream_t st) {
     k_vec_local<D, NA, P, KIND><<<vec_grid(a.n_elem, 128), 128, 0, st>>>(a);
     LFEM_CUDA(cudaGetLastError());
   }
-  if (a.n_nodes > 0) {
-    k_vec_gather<NC><<<vec_grid(a.n_nodes, 256), 256, 0, st>>>(a, Ref<D, P>::REF);
-    LFEM_CUDA(cudaGetLastError());
-  }
-  return LFEM_OK;
+  return run_vec_gather(a, Ref<D, P>::REF, NC, st);
 }
 
 template <int D, int NA, int P>
@@ -150,8 +156,12 @@ lfem_status run_vectors(int D, int NA, int P, int kind, const VecArgs& a, cudaSt
   LFEM_VEC_CASE(2, 3, 2)
   LFEM_VEC_CASE(3, 3, 1)
   LFEM_VEC_CASE(3, 3, 2)
+  LFEM_VEC_CASE(1, 1, 3)
+  LFEM_VEC_CASE(1, 1, 4)
   LFEM_VEC_CASE(1, 2, 3)
   LFEM_VEC_CASE(1, 2, 4)
+  LFEM_VEC_CASE(1, 3, 3)
+  LFEM_VEC_CASE(1, 3, 4)
   LFEM_VEC_CASE(2, 2, 3)
   LFEM_VEC_CASE(2, 2, 4)
   LFEM_VEC_CASE(2, 3, 3)
