@@ -33,7 +33,15 @@
  *    (alpha_1, alpha_2, alpha_3).  Anything else: LFEM_E_UNSUPPORTED.
  *  - Quadrature rules are host arrays on the reference simplex (interval [0,1],
  *    triangle conv{0,e1,e2}, tetrahedron conv{0,e1,e2,e3}); weights sum to its
- *    measure.  n_pts <= LFEM_MAX_QPTS.
+ *    measure.  n_pts <= LFEM_MAX_QPTS.  For order-1 elements quad may be NULL
+ *    in lfem_assemble, lfem_autotune, the adjoints, the vector assemblies,
+ *    lfem_mcf_step and batch items: M and A are then the exact ones of the
+ *    paper's P1 precomputation (exact reference mass matrix and stiffness
+ *    building blocks, Sec. 4.2), computed with the element's degree-2 rule
+ *    (3-point Gauss on [0,1]; the interior 3-point triangle rule; the 4-point
+ *    tet rule), which integrates every order-1 mass and stiffness integrand
+ *    exactly on affine elements.  LFEM_CMASS and coefficient gradients need
+ *    an explicit rule (LFEM_E_ARG).
  *  - Device pointers are caller-owned unless stated.  Outputs are overwritten,
  *    never accumulated into.
  *  - All work is enqueued on the given CUDA stream (NULL = legacy default

@@ -17,4 +17,5 @@ from .oracle import (  # noqa: F401
     load,
     kll,
     mcf_step,
+    p1_exact,
 )

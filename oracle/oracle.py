@@ -112,6 +112,48 @@ def pattern(conn, n_nodes):
     return row_ptr, cols
 
 
+def p1_exact(coords, conn, dim):
+    """Order-1 M and A from the exact reference matrices, the paper's P1
+    precomputation (Sec. 4.2): the element map is affine, so with s_E =
+    sqrt(det G_E), G_E = J_E^T J_E, J_E = [x_1 - x_0, ..., x_d - x_0],
+      M_E = s_E M_ref,            M_ref(a, b) = int_ref lambda_a lambda_b
+                                              = (1 + delta_ab) / (d! (d+1) (d+2)),
+      A_E = s_E sum_mn (G_E^-1)_mn A_ref_mn,  A_ref_mn(a, b) = |ref| d_m lambda_a d_n lambda_b,
+    with |ref| = 1 / d! and d_m lambda_0 = -1, d_m lambda_k = delta_mk.  Then
+    summed into the pattern's slots (Eqs. M matrix, A matrix).  numpy, no
+    quadrature.  Returns (row_ptr, col_idx, M, A)."""
+    from math import factorial
+
+    x = np.asarray(coords, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+    e = np.asarray(conn, dtype=np.int64)
+    assert e.shape[1] == dim + 1
+    N = x.shape[0]
+    X = x[e]                                         # [nE][d+1][n]
+    T = X[:, 1:, :] - X[:, :1, :]                    # rows t_m = x_m - x_0 (columns of J)
+    G = np.einsum("emi,eki->emk", T, T)
+    s = np.sqrt(np.linalg.det(G))
+    Gi = np.linalg.inv(G)
+    m_ref = (1.0 + np.eye(dim + 1)) / (factorial(dim) * (dim + 1) * (dim + 2))
+    dl = np.vstack([-np.ones(dim), np.eye(dim)])     # [d+1][d], d_m lambda_a
+    a_ref = np.einsum("am,bn->mnab", dl, dl) / factorial(dim)
+    Ml = s[:, None, None] * m_ref[None]
+    Al = s[:, None, None] * np.einsum("emn,mnab->eab", Gi, a_ref)
+    rp, ci = pattern(conn, N)
+    rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(rp))
+    keys = rows * N + ci
+    ref = dim + 1
+    I = np.repeat(e, ref, axis=1).ravel()
+    J = np.tile(e, (1, ref)).ravel()
+    slot = np.searchsorted(keys, I * N + J)
+    M = np.zeros(keys.size)
+    A = np.zeros(keys.size)
+    np.add.at(M, slot, Ml.ravel())
+    np.add.at(A, slot, Al.ravel())
+    return rp, ci, M, A
+
+
 def eval_points(coords, conn, dim, order, xi, mutation=0):
     """Physical points F_E(xi_q) for every element (Eq. F_map): [nE][Q][n]."""
     coords = _f64(coords)

@@ -52,10 +52,18 @@ static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
 
 extern "C" {
 
-lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigned which, int coef_is_fp32,
+lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsigned which, int coef_is_fp32,
                               void* cuda_stream, lfem_batch_t* out) {
-  if (!out || !items || n_items <= 0) return fail(LFEM_E_ARG, "batch arguments");
+  if (!out || !items_in || n_items <= 0) return fail(LFEM_E_ARG, "batch arguments");
   *out = nullptr;
+  // items without a rule: order 1 takes the exact rule, anything else is an error
+  std::vector<lfem_batch_item> items_v(items_in, items_in + n_items);
+  for (auto& it : items_v) {
+    if (it.quad || !it.pattern) continue;
+    if (it.pattern->order != 1 || (which & LFEM_CMASS)) return fail(LFEM_E_ARG, "batch item without a quadrature rule");
+    it.quad = exact_p1_rule(it.pattern->dim);
+  }
+  const lfem_batch_item* items = items_v.data();
   if (which == 0 || (which & ~7u)) return fail(LFEM_E_ARG, "which");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::vector<MeshRec> recs(n_items);

@@ -211,6 +211,40 @@ static std::mutex g_tab_mu;
 static std::map<TabKey, TabRef> g_tabs;
 static std::map<int, size_t> g_bank_used;  // bytes per device
 
+// Order 1 without a rule: the paper's P1 precomputation (Sec. 4.2) uses the exact
+// reference mass matrix and stiffness building blocks.  On affine order-1
+// elements the mass integrand is a polynomial of degree 2 and the stiffness
+// integrand a constant, so any rule exact to degree 2 returns exactly those
+// matrices; these are the degree-2 rules of each element (3-point Gauss on the
+// interval, the interior 3-point triangle rule, the 4-point tet rule with
+// a = (5 - sqrt 5) / 20), which the compile-time kernels also take.
+const lfem_quad* exact_p1_rule(int dim) {
+  static double xi1[3], w1[3], xi2[6], w2[3], xi3[12], w3[4];
+  static lfem_quad q1{3, xi1, w1}, q2{3, xi2, w2}, q3{4, xi3, w3};
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const double h = std::sqrt(15.0) / 10.0;
+    xi1[0] = 0.5 - h;
+    xi1[1] = 0.5;
+    xi1[2] = 0.5 + h;
+    w1[0] = w1[2] = 5.0 / 18.0;
+    w1[1] = 8.0 / 18.0;
+    const double t[6] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+    for (int k = 0; k < 6; ++k) xi2[k] = t[k];
+    w2[0] = w2[1] = w2[2] = 1.0 / 6.0;
+    const double a = (5.0 - std::sqrt(5.0)) / 20.0, b = 1.0 - 3.0 * a;
+    for (int q = 0; q < 4; ++q)
+      for (int m = 0; m < 3; ++m) xi3[q * 3 + m] = (q == m + 1) ? b : a;
+    for (int q = 0; q < 4; ++q) w3[q] = 1.0 / 24.0;
+  });
+  return dim == 1 ? &q1 : (dim == 2 ? &q2 : (dim == 3 ? &q3 : nullptr));
+}
+
+// The rule an entry point uses: the caller's, or for order 1 without one the exact rule.
+static const lfem_quad* resolve_rule(const lfem_quad* quad, int dim, int order) {
+  return quad ? quad : (order == 1 ? exact_p1_rule(dim) : nullptr);
+}
+
 lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t st, TabRef* out) {
   if (!quad || quad->n_pts <= 0 || !quad->xi || !quad->w) return fail(LFEM_E_ARG, "quadrature rule missing");
   if (quad->n_pts > LFEM_MAX_QPTS) return fail(LFEM_E_UNSUPPORTED, "more than LFEM_MAX_QPTS quadrature points");
@@ -418,7 +452,9 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   if ((which & LFEM_MASS) && !M) return fail(LFEM_E_ARG, "M is NULL");
   if ((which & LFEM_STIFF) && !A) return fail(LFEM_E_ARG, "A is NULL");
   if ((which & LFEM_CMASS) && (!MC || !coef)) return fail(LFEM_E_ARG, "MC or coef is NULL");
+  if ((which & LFEM_CMASS) && !quad) return fail(LFEM_E_ARG, "LFEM_CMASS needs a quadrature rule");
   if (p->n_elem > 0 && !coords) return fail(LFEM_E_ARG, "coords is NULL");
+  quad = resolve_rule(quad, p->dim, p->order);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   TabRef tab;
   lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
@@ -565,6 +601,8 @@ static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int am
   if (!g_coords && p->n_nodes > 0) return fail(LFEM_E_ARG, "g_coords is NULL");
   if (p->n_elem > 0 && !coords) return fail(LFEM_E_ARG, "coords is NULL");
   if (gMC && !coef) return fail(LFEM_E_ARG, "gMC given without coef");
+  if (!quad && (gMC || g_coef)) return fail(LFEM_E_ARG, "coefficient gradients need a quadrature rule");
+  quad = resolve_rule(quad, p->dim, p->order);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   TabRef tab;
   lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
@@ -670,6 +708,7 @@ static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int am
     return fail(LFEM_E_UNSUPPORTED, "the non-linear vectors need a surface (dim 2 in R^3)");
   if (p->n_elem > 0 && (!coords || !u)) return fail(LFEM_E_ARG, "coords or nodal values are NULL");
   if (p->n_nodes > 0 && !out) return fail(LFEM_E_ARG, "output is NULL");
+  quad = resolve_rule(quad, p->dim, p->order);
   TabRef tab;
   lfem_status s = get_tables(p->dim, p->order, quad, st, &tab);
   if (s != LFEM_OK) return s;
@@ -722,6 +761,7 @@ lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, c
     return fail(LFEM_E_UNSUPPORTED, "mean curvature flow needs a curve in R^2 or a surface in R^3");
   if (!(tau >= 0.0) || !(rtol > 0.0) || max_iter <= 0) return fail(LFEM_E_ARG, "tau, rtol or max_iter");
   if (!iterations || (p->n_nodes > 0 && (!coords || !coords_out))) return fail(LFEM_E_ARG, "NULL argument");
+  quad = resolve_rule(quad, p->dim, p->order);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nc = ambient;
   const size_t nnz = (size_t)p->nnz, n = (size_t)p->n_nodes;
@@ -806,7 +846,10 @@ static std::string tune_key(lfem_pattern_t p, int ambient, const lfem_quad* quad
 lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad, const void* coef,
                           int coef_is_fp32, unsigned which, lfem_precision prec, void* M, void* A, void* MC,
                           const char* cache_path, void* cuda_stream, int32_t* best_slots) {
-  if (!p || !quad) return fail(LFEM_E_ARG, "NULL argument");
+  if (!p) return fail(LFEM_E_ARG, "NULL argument");
+  if (!quad && (which & LFEM_CMASS)) return fail(LFEM_E_ARG, "LFEM_CMASS needs a quadrature rule");
+  quad = resolve_rule(quad, p->dim, p->order);
+  if (!quad) return fail(LFEM_E_ARG, "quadrature rule missing");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const std::string key = tune_key(p, ambient, quad, prec, which);
   int best = 0;

@@ -46,6 +46,8 @@ __host__ __device__ constexpr int n_upper(int ref) { return ref * (ref + 1) / 2;
 __host__ __device__ constexpr int n_edges(int d, int p) { return p == 2 ? n_ref(d, 2) - (d + 1) : 0; }
 
 bool supported(int dim, int ambient, int order);
+// The degree-2 rule that makes order-1 M and A exact (used when no rule is given).
+const lfem_quad* exact_p1_rule(int dim);
 
 // Reference tables (Lagrange basis, Sec. 3.1; quadrature rule, Sec. 3.2.2) in
 // constant memory.  One 64 KB bank per device, append-only registry keyed by

@@ -142,7 +142,20 @@ class QuadRule:
         return ctypes.byref(self._c)
 
 
+class _ExactP1:
+    """No rule: order-1 elements get their exact reference matrices (NULL rule in the C ABI)."""
+
+    ref = None
+    n_pts = 0
+    _c = None
+
+
+EXACT_P1 = _ExactP1()
+
+
 def as_rule(rule) -> QuadRule:
+    if rule is None or isinstance(rule, _ExactP1):
+        return EXACT_P1
     if isinstance(rule, QuadRule):
         return rule
     return QuadRule(np.asarray(rule.xi), np.asarray(rule.w))
@@ -286,7 +299,7 @@ class Batch:
             it.pattern = pat.handle.value
             it.coords = coords.data_ptr()
             it.ambient = int(coords.shape[1])
-            it.quad = ctypes.addressof(rule._c)
+            it.quad = None if rule._c is None else ctypes.addressof(rule._c)
             it.coef = None if coef is None else coef.data_ptr()
             it.M = None if outs["M"] is None else outs["M"].data_ptr()
             it.A = None if outs["A"] is None else outs["A"].data_ptr()

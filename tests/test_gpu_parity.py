@@ -137,6 +137,28 @@ def test_tet_high_deterministic_and_subsets(name, prec, lfem):
         assert list(part) == [k] and torch.equal(part[k], ref[k])
 
 
+@pytest.mark.parametrize("name", ["sphere_p1", "disk_p1", "cube_p1", "curve_p1"])
+def test_p1_exact_reference_matrices(name, lfem):
+    """No rule for order 1: the exact reference matrices (Sec. 4.2), against the
+    closed-form oracle; LFEM_CMASS still needs a rule."""
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    orp, oci, M, A = oracle.p1_exact(x, e, d)
+    xd = to_dev(x)
+    for prec, tol in ((lfem.FP64, FP64_TOL), (lfem.MIXED, MIXED_TOL)):
+        out = lfem.assemble(pat, xd, None, which=3, precision=prec)
+        for k, ref in (("M", M), ("A", A)):
+            err = diag_scaled_error(out[k].double().cpu().numpy(), ref, orp, oci)
+            assert err <= tol, (prec, k, err)
+    pat.sync_status()
+    with pytest.raises(lfem.LfemError):
+        lfem.assemble(pat, xd, None, to_dev(coef), which=4)
+    f = np.random.default_rng(3).standard_normal(x.shape[0])
+    b = lfem.assemble_load(pat, xd, None, to_dev(f)).cpu().numpy()
+    Md = np.zeros((x.shape[0], x.shape[0]))
+    Md[np.repeat(np.arange(x.shape[0]), np.diff(orp)), oci] = M
+    assert np.abs(b - Md @ f).max() <= 1e-12 * np.abs(Md @ f).max()
+
+
 @pytest.mark.parametrize("which", [1, 2, 4, 3, 5, 6])
 def test_subsets_of_matrices(which, lfem):
     x, e, d, p, rule, coef, pat = prepare("ellipsoid_p2", lfem)
