@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--batch-meshes", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--batch-slots", default="2048,3072", help="tile capacities the batch workload tries")
+    ap.add_argument("--tile-slots", type=int, default=0, help="fixed tile capacity (implies no autotuning)")
+    ap.add_argument("--batch-slots", default="2048,2560,3072", help="tile capacities the batch workload tries")
     return ap.parse_args()
 
 
@@ -261,7 +262,9 @@ def main():
     del pts
     nnz = pat.nnz
     tuned = None
-    if not args.no_autotune:
+    if args.tile_slots:
+        pat.retile(args.tile_slots)
+    elif not args.no_autotune:
         tuned = lfem.autotune(pat, xd, rule, coef32, which=7, precision=lfem.MIXED)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()

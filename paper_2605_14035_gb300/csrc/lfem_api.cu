@@ -861,7 +861,9 @@ lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, c
       if (k == key) best = v;
   }
   if (!best) {
-    const int cand[] = {512, 1024, 1536, 2048, 3072, 4096, 6144, 8192};
+    // finer steps around the capacities where a tile's elements still fit one
+    // phase-1 round of the mixed kernel and two CTAs share an SM
+    const int cand[] = {512, 1024, 1536, 2048, 2304, 2560, 2688, 2816, 3072, 4096, 6144, 8192};
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     LFEM_CUDA(cudaEventCreate(&e0));
