@@ -31,6 +31,9 @@ struct TetHigh {
   static constexpr int REF = (P + 1) * (P + 2) * (P + 3) / 6;
   static constexpr int U = REF * (REF + 1) / 2;
   static constexpr int NU = (U + 31) / 32;  // entries per lane
+  // table row stride in 16-byte units, odd: lanes reading rows of different
+  // points (the geometry phase) then fall on distinct banks
+  static constexpr int ROW = REF | 1;
 };
 
 template <typename R>
@@ -98,7 +101,8 @@ __device__ __forceinline__ void lagrange_1d(int p, int k, double t, double& v, d
   }
 }
 
-// table[q][b] = (phi_b, d phi_b / d xi_1, d xi_2, d xi_3) at point q, in FP64 and float.
+// table[q][b] = (phi_b, d phi_b / d xi_1, d xi_2, d xi_3) at point q, in FP64 and
+// float; rows ROW apart (the padding entries are never read).
 template <int P>
 __global__ void k_tet_high_table(TabRef rule_ref, V4<double>* __restrict__ t64, V4<float>* __restrict__ t32) {
   constexpr int REF = TetHigh<P>::REF;
@@ -117,8 +121,8 @@ __global__ void k_tet_high_table(TabRef rule_ref, V4<double>* __restrict__ t64, 
     const double d0 = dv[0] * v[1] * v[2] * v[3], d1 = v[0] * dv[1] * v[2] * v[3];
     const double d2 = v[0] * v[1] * dv[2] * v[3], d3 = v[0] * v[1] * v[2] * dv[3];
     const V4<double> r{v[0] * v[1] * v[2] * v[3], d1 - d0, d2 - d0, d3 - d0};
-    t64[t] = r;
-    t32[t] = V4<float>{(float)r.x, (float)r.y, (float)r.z, (float)r.w};
+    t64[q * TetHigh<P>::ROW + b] = r;
+    t32[q * TetHigh<P>::ROW + b] = V4<float>{(float)r.x, (float)r.y, (float)r.z, (float)r.w};
   }
 }
 
@@ -126,13 +130,13 @@ __global__ void k_tet_high_table(TabRef rule_ref, V4<double>* __restrict__ t64, 
 template <int P, typename R, typename RS, int MODE>
 __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane,
                                               const uint32_t (&pk)[TetHigh<P>::NU], RS* dst) {
-  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU;
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU, ROW = TetHigh<P>::ROW;
   R acc[NU];
 #pragma unroll
   for (int k = 0; k < NU; ++k) acc[k] = (R)0;
   for (int q = 0; q < Q; ++q) {
     const V4<R> g0 = geo[2 * q], g1 = geo[2 * q + 1];
-    const V4<R>* tq = tab + q * REF;
+    const V4<R>* tq = tab + q * ROW;
     for (int b = lane; b < REF; b += 32) {
       const V4<R> d = tq[b];
       V4<R> h;
@@ -175,15 +179,15 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
                                                                  const uint32_t* __restrict__ list,
                                                                  const uint32_t* __restrict__ list_n,
                                                                  uint32_t* __restrict__ flags) {
-  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU;
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU, ROW = TetHigh<P>::ROW;
   const int Q = a.tab.q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V4<R>* tab = reinterpret_cast<V4<R>*>(smem_raw);  // [Q][REF]
+  V4<R>* tab = reinterpret_cast<V4<R>*>(smem_raw);  // [Q][ROW]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  V4<R>* rel = tab + Q * REF + warp * (2 * REF + 2 * Q);  // [REF] x_b - x_0
+  V4<R>* rel = tab + Q * ROW + warp * (2 * REF + 2 * Q);  // [REF] x_b - x_0
   V4<R>* hb = rel + REF;                                 // [REF] per-point node factors
   V4<R>* geo = hb + REF;                                 // [Q][2] (w s, H00, H01, H02), (H11, H12, H22, c_q)
-  for (int t = threadIdx.x; t < Q * REF; t += blockDim.x) tab[t] = gtab[t];
+  for (int t = threadIdx.x; t < Q * ROW; t += blockDim.x) tab[t] = gtab[t];
   __syncthreads();
   const double* w64 = bank<double>() + a.tab.off64;
   // this lane's upper entries u = lane + 32 k as (a, b), row-major upper layout
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
     __syncwarp();
     bool bad = false, redo = false;
     for (int q = lane; q < Q; q += 32) {
-      const V4<R>* tq = tab + q * REF;
+      const V4<R>* tq = tab + q * ROW;
       R J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       for (int b = 1; b < REF; ++b) {
         const V4<R> r = rel[b], d = tq[b];
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
 
 template <int P, typename R>
 static size_t tet_high_smem(int Q) {
-  return sizeof(V4<R>) * ((size_t)Q * TetHigh<P>::REF + (size_t)kTetHighWarps * (2 * TetHigh<P>::REF + 2 * Q));
+  return sizeof(V4<R>) * ((size_t)Q * TetHigh<P>::ROW + (size_t)kTetHighWarps * (2 * TetHigh<P>::REF + 2 * Q));
 }
 
 template <int P, typename R, typename RS>
@@ -312,11 +316,11 @@ static lfem_status launch_tet_high_pass(const TwoPassArgs& a, const V4<R>* gtab,
 
 template <int P>
 static lfem_status run_tet_high_p(bool mixed, const TwoPassArgs& a, void* scratch, int sms, cudaStream_t st) {
-  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U;
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, ROW = TetHigh<P>::ROW;
   const int Q = a.tab.q;
   V4<double>* t64 = static_cast<V4<double>*>(scratch);
-  V4<float>* t32 = reinterpret_cast<V4<float>*>(t64 + (size_t)Q * REF);
-  uint32_t* flags = reinterpret_cast<uint32_t*>(t32 + (size_t)Q * REF);
+  V4<float>* t32 = reinterpret_cast<V4<float>*>(t64 + (size_t)Q * ROW);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(t32 + (size_t)Q * ROW);
   if (a.n_elem > 0) {
     k_tet_high_table<P><<<(Q * REF + 127) / 128, 128, 0, st>>>(a.tab, t64, t32);
     LFEM_CUDA(cudaGetLastError());
@@ -347,15 +351,15 @@ static lfem_status run_tet_high_p(bool mixed, const TwoPassArgs& a, void* scratc
 // then sum loc_a = sum_q (w s f_h)_q phi_a(q) (Sec. 2, b = M f).
 template <int P>
 __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_load(const VecArgs a, const V4<double>* __restrict__ gtab) {
-  constexpr int REF = TetHigh<P>::REF;
+  constexpr int REF = TetHigh<P>::REF, ROW = TetHigh<P>::ROW;
   const int Q = a.tab.q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V4<double>* tab = reinterpret_cast<V4<double>*>(smem_raw);  // [Q][REF]
+  V4<double>* tab = reinterpret_cast<V4<double>*>(smem_raw);  // [Q][ROW]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  V4<double>* rel = tab + Q * REF + warp * (REF + (REF + Q + 3) / 4);
+  V4<double>* rel = tab + Q * ROW + warp * (REF + (REF + Q + 3) / 4);
   double* fv = reinterpret_cast<double*>(rel + REF);  // [REF] nodal values, then [Q] point factors
   double* fq = fv + REF;
-  for (int t = threadIdx.x; t < Q * REF; t += blockDim.x) tab[t] = gtab[t];
+  for (int t = threadIdx.x; t < Q * ROW; t += blockDim.x) tab[t] = gtab[t];
   __syncthreads();
   const double* w64 = bank<double>() + a.tab.off64;
   for (int64_t e = (int64_t)blockIdx.x * kTetHighWarps + warp; e < a.n_elem; e += (int64_t)gridDim.x * kTetHighWarps) {
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_load(const VecA
     }
     __syncwarp();
     for (int q = lane; q < Q; q += 32) {
-      const V4<double>* tq = tab + q * REF;
+      const V4<double>* tq = tab + q * ROW;
       double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       double fh = 0.0;
       for (int b = 0; b < REF; ++b) {
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_load(const VecA
     __syncwarp();
     for (int b = lane; b < REF; b += 32) {
       double acc = 0.0;
-      for (int q = 0; q < Q; ++q) acc = fma(fq[q], tab[q * REF + b].x, acc);
+      for (int q = 0; q < Q; ++q) acc = fma(fq[q], tab[q * ROW + b].x, acc);
       a.loc[e * REF + b] = acc;
     }
     __syncwarp();
@@ -403,14 +407,14 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_load(const VecA
 
 template <int P>
 static lfem_status run_tet_high_load_p(const VecArgs& a, void* scratch, int sms, cudaStream_t st) {
-  constexpr int REF = TetHigh<P>::REF;
+  constexpr int REF = TetHigh<P>::REF, ROW = TetHigh<P>::ROW;
   const int Q = a.tab.q;
   V4<double>* t64 = static_cast<V4<double>*>(scratch);
-  V4<float>* t32 = reinterpret_cast<V4<float>*>(t64 + (size_t)Q * REF);
+  V4<float>* t32 = reinterpret_cast<V4<float>*>(t64 + (size_t)Q * ROW);
   if (a.n_elem > 0) {
     k_tet_high_table<P><<<(Q * REF + 127) / 128, 128, 0, st>>>(a.tab, t64, t32);
     LFEM_CUDA(cudaGetLastError());
-    const size_t smem = sizeof(V4<double>) * ((size_t)Q * REF + (size_t)kTetHighWarps * (REF + (REF + Q + 3) / 4));
+    const size_t smem = sizeof(V4<double>) * ((size_t)Q * ROW + (size_t)kTetHighWarps * (REF + (REF + Q + 3) / 4));
     auto kern = k_tet_high_load<P>;
     LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -431,8 +435,8 @@ lfem_status run_tet_high_load(int P, const VecArgs& a, void* scratch, int sms, c
 }
 
 size_t tet_high_scratch_bytes(int P, int Q, int64_t n_elem) {
-  const int REF = P == 3 ? TetHigh<3>::REF : TetHigh<4>::REF;
-  return (size_t)Q * REF * (sizeof(V4<double>) + sizeof(V4<float>)) + sizeof(uint32_t) * ((size_t)n_elem + 1);
+  const int ROW = P == 3 ? TetHigh<3>::ROW : TetHigh<4>::ROW;
+  return (size_t)Q * ROW * (sizeof(V4<double>) + sizeof(V4<float>)) + sizeof(uint32_t) * ((size_t)n_elem + 1);
 }
 
 lfem_status run_tet_high(int P, bool mixed, const TwoPassArgs& a, void* scratch, int sms, cudaStream_t st) {
