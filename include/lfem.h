@@ -1,8 +1,8 @@
 /*
  * lfem.h -- C ABI of the GB300 (sm_103a) isoparametric finite-element assembly library.
  *
- * The library assembles, for P1/P2 Lagrange elements on curves and surfaces
- * (d = 1, 2 in R^{d+1}) and in bulk domains (d = n = 2, 3):
+ * The library assembles, for Lagrange elements of order 1 to 4 on curves and
+ * surfaces (d = 1, 2 in R^{d+1}) and in bulk domains (d = n = 2, 3):
  *   mass                    M_ij  = int phi_i phi_j                  (Sec. 2.2; Eq. M matrix)
  *   stiffness               A_ij  = int grad_G phi_i . grad_G phi_j   (Sec. 2.2; Eq. A matrix)
  *   coefficient-weighted    MC_ij = int c phi_i phi_j, c given at quadrature points
