@@ -71,17 +71,66 @@ def coef_from_points(pts):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clock, power and clock-event reasons of one GPU, read through NVML
+    (read-only queries) every millisecond while running, so that even a
+    millisecond-long timed region gets samples; `mark(t0, t1)` restricts the
+    summary to the samples taken between two host times.  Falls back to
+    nvidia-smi at 200 ms when NVML cannot be loaded."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
+        self.rows = []
+        self.window = None
+        self.nvml = None
+
+    def _nvml_open(self):
+        import ctypes
+
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h)) != 0:
+            return None
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        mx = ctypes.c_uint()
+        lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx))
+        return lib, h, reasons, mx.value
+
+    def _loop(self):
+        import ctypes
+
+        lib, h, reasons, mx = self.nvml
+        clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop:
+            ok = lib.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(clk)) == 0
+            lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw))
+            reasons(h, ctypes.byref(rs))
+            if ok:
+                act = [n for n, b in self.BITS.items() if rs.value & b]
+                self.rows.append((time.perf_counter(), float(clk.value), float(mx), pw.value / 1000.0, act))
+            time.sleep(0.001)
 
     def __enter__(self):
+        import threading
+
+        try:
+            self.nvml = self._nvml_open()
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.stop = False
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -90,33 +139,44 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
     def __exit__(self, *exc):
-        self.out = ""
+        if self.nvml is not None:
+            self.stop = True
+            self.thread.join(timeout=5)
+            return
+        out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                out, _ = self.proc.communicate(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out, _ = self.proc.communicate()
-
-    def summary(self):
-        rows = []
-        for line in (self.out or "").strip().splitlines():
+                out, _ = self.proc.communicate()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (out or "").strip().splitlines():
             f = [t.strip() for t in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+                act = [names[i] for i, v in enumerate(f[5:9]) if v.lower() == "active"]
+                self.rows.append((None, float(f[1]), float(f[2]), float(f[3]), act))
             except ValueError:
                 continue
+
+    def summary(self):
+        rows = self.rows
+        if self.window is not None and rows and rows[0][0] is not None:
+            inside = [r for r in rows if self.window[0] <= r[0] <= self.window[1]]
+            rows = inside or rows
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
-        loaded = [r for r in rows if r[2] > 0] or rows
-        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+        reasons = sorted({a for r in rows for a in r[4]})
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[3] for r in rows),
+                "source": "nvml 1 ms" if self.nvml is not None else "nvidia-smi 200 ms"}
 
 
 def dist_init(backend):
@@ -272,12 +332,13 @@ def main():
     def barrier():
         rank_barrier(dist)
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, clk=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
+        t_host0 = time.perf_counter()
         evs = []
         for _ in range(steps):
             flush.fill_(1.0)  # untimed: evict L2 between steps
@@ -287,6 +348,8 @@ def main():
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize()
+        if clk is not None:
+            clk.mark(t_host0, time.perf_counter())
         barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
         return max_over_ranks(sum(ms), dist, dev), ms
@@ -308,7 +371,7 @@ def main():
         except ValueError:
             pass
     with ClockSampler(sm_index) as clk:
-        tot_ms, per = timed(step_mixed, args.steps, args.warmup)
+        tot_ms, per = timed(step_mixed, args.steps, args.warmup, clk)
     clocks = clk.summary()
     fallback = pat.fallback_count()
     pat.sync_status()

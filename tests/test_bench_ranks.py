@@ -70,3 +70,20 @@ bench.run_reference(args)
     p = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """Samples outside the marked host-time window are dropped; reasons are the
+    union over the window; the median SM clock is over the window."""
+    import bench
+
+    c = bench.ClockSampler(0)
+    c.nvml = object()  # summary label only
+    c.rows = [(0.0, 1000.0, 2070.0, 100.0, ["sw_power_cap"]),
+              (1.0, 2070.0, 2070.0, 900.0, []),
+              (1.5, 2060.0, 2070.0, 950.0, ["hw_slowdown"]),
+              (3.0, 500.0, 2070.0, 50.0, [])]
+    c.mark(0.9, 2.0)
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 2065.0 and s["reasons"] == ["hw_slowdown"]
+    assert s["sm_max_mhz"] == 2070.0 and s["power_w_max"] == 950.0
