@@ -146,6 +146,7 @@ class ClockSampler:
         if self.nvml is not None:
             self.stop = True
             self.thread.join(timeout=5)
+            self.nvml[0].nvmlShutdown()
             return
         out = ""
         if self.proc is not None:
