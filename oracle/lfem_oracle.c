@@ -104,7 +104,11 @@ static int node_multi_indices(int dim, int p, int (*al)[MAXD + 1]) {
         ++cnt;
       }
   if (dim == 3) {
+#if ORACLE_MUTATION == 9
+    static const int FACES3[4][3] = {{0, 1, 2}, {0, 2, 3}, {0, 1, 3}, {1, 2, 3}}; /* planted: face order */
+#else
     static const int FACES3[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+#endif
     for (int f = 0; f < 4; ++f)
       for (int aj = 1; aj < p; ++aj)
         for (int al2 = 1; aj + al2 < p; ++al2) {
@@ -132,7 +136,11 @@ static void lag_factor(int p, int k, double t, double* v, double* dv) {
   double val = 1.0, der = 0.0;
   for (int j = 0; j < k; ++j) {
     const double f = (p * t - j) / (j + 1), df = (double)p / (j + 1);
+#if ORACLE_MUTATION == 10
+    der = der * f + val * df * 0.5; /* planted: half of the product rule's new term */
+#else
     der = der * f + val * df;
+#endif
     val *= f;
   }
   *v = val;

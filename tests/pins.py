@@ -27,6 +27,39 @@ REF_NODES = {
          [0, 0, 0.5], [0.5, 0, 0.5], [0, 0.5, 0.5]], float),
 }
 
+
+
+def _high_order_nodes(d, p):
+    """Reference coordinates of the order-p nodes (p = 3, 4) in the documented
+    order: corners; per edge ((0,1); (0,1),(1,2),(2,0); those and (0,3),(1,3),
+    (2,3)) the nodes ((p-k) e_i + k e_j)/p; triangles: interior by increasing
+    (a1, a2); tets: faces (0,1,2),(0,1,3),(0,2,3),(1,2,3), each (i,j,l) by
+    increasing (a_j, a_l), then the interior by increasing (a1, a2, a3)."""
+    al = [[p if c == i else 0 for c in range(d + 1)] for i in range(d + 1)]
+    edges = {1: [(0, 1)], 2: [(0, 1), (1, 2), (2, 0)], 3: [(0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3)]}[d]
+    for i, j in edges:
+        for k in range(1, p):
+            a = [0] * (d + 1)
+            a[i], a[j] = p - k, k
+            al.append(a)
+    if d == 2:
+        al += [[p - a1 - a2, a1, a2] for a1 in range(1, p) for a2 in range(1, p - a1)]
+    if d == 3:
+        for i, j, l in [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]:
+            for aj in range(1, p):
+                for a_l in range(1, p - aj):
+                    a = [0] * 4
+                    a[i], a[j], a[l] = p - aj - a_l, aj, a_l
+                    al.append(a)
+        al += [[p - a1 - a2 - a3, a1, a2, a3] for a1 in range(1, p) for a2 in range(1, p - a1)
+               for a3 in range(1, p - a1 - a2)]
+    return np.array(al, float)[:, 1:] / p
+
+
+for _d in (1, 2, 3):
+    for _p in (3, 4):
+        REF_NODES[(_d, _p)] = _high_order_nodes(_d, _p)
+
 COMBOS = [(1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]  # (d, n)
 
 

@@ -27,12 +27,13 @@ def test_pin(name):
     assert fn() < tol
 
 
-@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_planted_mistake_is_caught(mutation):
     """Each planted mistake (wrong bubble scale, swapped edge nodes, wrong surface
     element, J^-1 for J^-T, dropped weight, dropped factor in the adjoint, load
     vector without the surface element, reference instead of tangential
-    gradient of the normal field) fails a pin."""
+    gradient of the normal field, tet face nodes out of order, half of the
+    product rule in the order-p basis gradients) fails a pin."""
     assert pins.failing_checks(mutation), f"mutation {mutation} passed every pin"
 
 
