@@ -146,7 +146,10 @@ class ClockSampler:
         if self.nvml is not None:
             self.stop = True
             self.thread.join(timeout=5)
-            self.nvml[0].nvmlShutdown()
+            try:
+                self.nvml[0].nvmlShutdown()
+            except (AttributeError, OSError):
+                pass
             return
         out = ""
         if self.proc is not None:
