@@ -55,3 +55,29 @@ def test_host_side_errors_without_gpu(libpath):
     assert lib.lfem_assemble(None, None, 3, None, None, 0, 1, 0, None, None, None, None) == 1
     lib.lfem_set_mixed_kappa.argtypes = [ctypes.c_void_p, ctypes.c_double]
     assert lib.lfem_set_mixed_kappa(None, 2.0) == 1
+
+
+def declared_arities():
+    """Number of parameters of every entry point the header declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(lfem_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_arities_match_header():
+    """Every argtypes list in the Python binding has the header's parameter count."""
+    from paper_2605_14035_gb300 import lfem
+
+    ar = declared_arities()
+    assert len(ar) >= 15
+    lib = lfem.lib()
+    bad = {}
+    for n in lfem.EXPORTS:
+        t = getattr(lib, n).argtypes
+        if t is not None and n in ar and len(t) != ar[n]:
+            bad[n] = (len(t), ar[n])
+    assert not bad, bad
