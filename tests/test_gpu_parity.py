@@ -311,3 +311,51 @@ def test_edge_cases(lfem):
     with pytest.raises(lfem.LfemError) as ei:
         lfem.Pattern(to_dev(conn), 7, 4, 1)
     assert ei.value.code == 3
+
+
+def test_tet_high_edge_cases(lfem):
+    """Order-3/4 tets: an empty mesh, a single reference element (against the
+    oracle, both precisions), a flattened element (status LFEM_E_DEGENERATE in
+    both precisions), node generation on one tet, and an empty order-1 mesh
+    without a rule."""
+    from paper_2605_14035_gb300.inputs import meshes
+
+    rule = CASES["cube_p3"][4]
+    for p in (3, 4):
+        ref = (p + 1) * (p + 2) * (p + 3) // 6
+        pat = lfem.Pattern(torch.empty(0, ref, dtype=torch.int32, device="cuda"), 5, 3, p)
+        assert pat.nnz == 0
+        xd = torch.zeros(5, 3, dtype=torch.float64, device="cuda")
+        for prec in (lfem.FP64, lfem.MIXED):
+            out = lfem.assemble(pat, xd, rule, which=3, precision=prec)
+            assert out["M"].numel() == 0 and out["A"].numel() == 0
+        assert torch.equal(lfem.assemble_load(pat, xd, rule, torch.ones(5, dtype=torch.float64, device="cuda")),
+                           torch.zeros(5, dtype=torch.float64, device="cuda"))
+        pat.sync_status()
+        # one tet with its generated nodes, plus an unused node
+        x1 = np.vstack([np.zeros(3), np.eye(3)]) * np.array([1.0, 0.8, 1.3]) + 0.1
+        x, e = meshes.to_order(x1, np.array([[0, 1, 2, 3]], dtype=np.int32), p)
+        x = np.vstack([x, [[5.0, 5.0, 5.0]]])
+        pat = lfem.Pattern(to_dev(e), x.shape[0], 3, p)
+        orp, oci, M, A, _ = oracle.assemble(x, e, 3, p, rule.xi, rule.w)
+        assert np.array_equal(pat.csr()[1].cpu().numpy(), oci)
+        for prec, tol in ((lfem.FP64, FP64_TOL), (lfem.MIXED, MIXED_TOL)):
+            out = lfem.assemble(pat, to_dev(x), rule, which=3, precision=prec)
+            for k, r in (("M", M), ("A", A)):
+                assert diag_scaled_error(out[k].double().cpu().numpy(), r, orp, oci) <= tol, (p, prec, k)
+        pat.sync_status()
+        # every node on one plane: zero volume
+        xf = x.copy()
+        xf[:, 2] = 0.0
+        for prec in (lfem.FP64, lfem.MIXED):
+            lfem.assemble(pat, to_dev(xf), rule, which=1, precision=prec)
+            with pytest.raises(lfem.LfemError) as ei:
+                pat.sync_status()
+            assert ei.value.code == 7
+        # node generation on a single tet
+        p1 = lfem.Pattern(to_dev(np.array([[0, 1, 2, 3]], dtype=np.int32)), 4, 3, 1)
+        xg, eg = lfem.lift_order(p1, to_dev(x1), p)
+        assert np.array_equal(eg.cpu().numpy(), e) and np.array_equal(xg.cpu().numpy(), x[:-1])
+    pat = lfem.Pattern(torch.empty(0, 3, dtype=torch.int32, device="cuda"), 4, 2, 1)
+    out = lfem.assemble(pat, torch.zeros(4, 3, dtype=torch.float64, device="cuda"), None, which=3)
+    assert out["M"].numel() == 0
