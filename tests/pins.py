@@ -15,7 +15,7 @@ from paper_2605_14035_gb300.inputs import meshes, quadrature
 
 RNG = np.random.default_rng(12345)
 
-# Reference nodes of the P1/P2 simplices in the documented local order.
+# Reference nodes of the simplices in the documented local order (orders 3, 4 added below).
 REF_NODES = {
     (1, 1): np.array([[0.0], [1.0]]),
     (1, 2): np.array([[0.0], [1.0], [0.5]]),
@@ -26,7 +26,6 @@ REF_NODES = {
         [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0.5, 0, 0], [0.5, 0.5, 0], [0, 0.5, 0],
          [0, 0, 0.5], [0.5, 0, 0.5], [0, 0.5, 0.5]], float),
 }
-
 
 
 def _high_order_nodes(d, p):
@@ -244,12 +243,17 @@ def check_fd(mutation=0, n_coords=12, seed=7):
 
 def check_load_is_mass_times_f(mutation=0):
     """The load vector of the interpolant f_h = sum f_i phi_i is b = M f (Sec. 2),
-    on curved P2 surfaces, a P1 sphere, a P2 curve and P2 tets; relative to max |b|."""
+    on curved P2 surfaces, a P1 sphere, a P2 curve, P2 tets, and orders 3, 4 on
+    the sphere and the cube; relative to max |b|."""
     worst = 0.0
     rng = np.random.default_rng(21)
-    for (x, e), d, p in ((meshes.icosphere(2, 2), 2, 2), (meshes.icosphere(2, 1), 2, 1),
-                         (meshes.closed_curve_p2(60, seed=4), 1, 2), (meshes.kuhn_cube_p2(2), 3, 2)):
-        r = quadrature.default_rule(d, p)
+    x1, t1 = meshes.kuhn_cube_p2(1, order=1)
+    cases = [(meshes.icosphere(2, 2), 2, 2, None), (meshes.icosphere(2, 1), 2, 1, None),
+             (meshes.closed_curve_p2(60, seed=4), 1, 2, None), (meshes.kuhn_cube_p2(2), 3, 2, None),
+             (meshes.icosphere_high(1, 3), 2, 3, quadrature.tri_16pt_deg8()),
+             (meshes.to_order(x1, t1, 4), 3, 4, quadrature.collapsed_gauss(3, 4))]
+    for (x, e), d, p, r in cases:
+        r = r or quadrature.default_rule(d, p)
         f = rng.standard_normal(x.shape[0])
         rp, ci, M, _, _ = oracle.assemble(x, e, d, p, r.xi, r.w, mutation=mutation)
         b = oracle.load(x, e, d, p, r.xi, r.w, f, mutation=mutation)
