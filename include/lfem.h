@@ -193,6 +193,11 @@ lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, c
  * values of that CTA's tiles are left unwritten.  The CUDA context stays usable. */
 lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve);
 
+/* Test knob: the number of device allocations (cudaMalloc) the library has
+ * made successfully in this process, across all devices and threads.  Used to
+ * check that an entry point allocates nothing; it never resets. */
+long long lfem_debug_alloc_count(void);
+
 /* ---------------------------------------------------------------------------
  * Batches: many meshes of uneven sizes and different element types assembled
  * by one persistent launch over all their row tiles (mixed precision only;
@@ -371,6 +376,9 @@ lfem_status lfem_lift_order(lfem_pattern_t p1, const double* coords, int ambient
  * nothing is written.  If nnz > col_capacity the call writes row_ptr, sets *nnz
  * and returns LFEM_E_TOO_LARGE.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset (or
+ * anything else that destroys the device's primary context) it is stale and
+ * the entry point must not be called again on that device.
  * The call synchronises the stream.  All calls share the one array: calls that
  * overlap on the GPU race, so issue them one at a time.
  */

@@ -78,7 +78,7 @@ struct PipeArgs {
   int cap_nodes;   // most nodes in a tile
   int cap_nel;     // most elements in a tile
   int max_u;       // largest local upper triangle among the meshes
-  int64_t cap_lsm; // largest nel * nm * U over the meshes (local-matrix words)
+  int64_t cap_lsm; // largest nel * nm * lsm_stride(U) over the meshes (local-matrix words)
   int max_q;       // most quadrature points among the meshes
   int coef_bytes;  // 4 or 8 if the weighted mass is requested, else 0
   float qmin;
@@ -376,15 +376,16 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
                                              Prefetch&& prefetch) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
+  constexpr int UP = lsm_stride(U);
   constexpr int ENTB = (int)sizeof(EntT);
   using Acc = typename AccOf<R>::T;
   const int nm = a.nm, Q = mr.tab.q;
   const int coef_bytes = a.coef_bytes;
   const TabView<R> tb = tab_view<D, P, R>(mr.tab);
   const TileHdr h = *reinterpret_cast<const TileHdr*>(mb);
-  // local matrices matrix-major: lsm[m * nel * U + e * U + u]; a contribution
-  // entry is the word offset e * U + u
-  const int mstride = h.nel * U;
+  // local matrices matrix-major: lsm[m * nel * UP + e * UP + u] (row stride U
+  // rounded up to even); a contribution entry is the word offset e * UP + u
+  const int mstride = h.nel * UP;
   const TileLayout TL = tile_layout(h.nel, h.ns, h.nl, h.nle, h.nnodes, REF, ENTB);
   const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
   const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
@@ -419,8 +420,8 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
         const float* cs = coef_bytes == 4 ? static_cast<const float*>(mr.coef) + cg : nullptr;
         const double* cd = coef_bytes == 8 ? static_cast<const double*>(mr.coef) + cg : nullptr;
         Checks ck;
-        element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * U,
-                                     mstride, ck);
+        element_fast_store2<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * UP,
+                                      mstride, ck);
         const uint32_t fl = !ck.good ? 2u : (ck.cond ? 0u : 1u);
         if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
       }
@@ -441,7 +442,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     if (coef_bytes) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
     R qual = (R)1;
     bool bad = false;
-    R* dst = lsm + (size_t)jt * U;
+    R* dst = lsm + (size_t)jt * UP;
     if constexpr (sizeof(R) == 4) {
       ElemData<D, NA, P, float> ed;
       element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
@@ -492,7 +493,7 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
 #pragma unroll
       for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
       bool bad = false;
-      R* d = lsm + (size_t)j * U + (fl == 2 ? 0 : ia * mstride);
+      R* d = lsm + (size_t)j * UP + (fl == 2 ? 0 : ia * mstride);
       element_fp64_lean<D, NA, P, float>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw, d,
                                          mstride, bad);
       if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
@@ -631,12 +632,19 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
     tma_load_block(meta_of(buf), r.meta + r.meta_off[tile], bytes, &mbar[buf]);
   };
   // prologue: item i into buffer 0
-  if (threadIdx.x == 0 && !(a.starve && blockIdx.x == 0)) load_block(i, 0);
+  const bool issued0 = !(a.starve && blockIdx.x == 0);
+  if (threadIdx.x == 0 && issued0) load_block(i, 0);
   {
     const bool ok = mbar_wait_bounded(&mbar[0], 0, a.wait_ns);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
-      return;  // nothing was issued for this barrier, or it never completed within the bound
+      // the copy (if one was issued) did not land within the bound: report, and
+      // give it one more bounded wait so that it does not write into the shared
+      // memory of a CTA that starts here after this one returns
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        if (issued0) mbar_wait_bounded(&mbar[0], 0, a.wait_ns);
+      }
+      return;
     }
   }
   issue_gathers(s_rec[0], want_coef, meta_of(0), node_of(0), coef_of(0));

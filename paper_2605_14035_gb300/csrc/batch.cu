@@ -119,7 +119,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     cap_nodes = std::max(cap_nodes, p->max_tile_nodes);
     cap_nel = std::max(cap_nel, p->max_tile_nel);
     max_u = std::max(max_u, n_upper(p->ref));
-    cap_lsm = std::max(cap_lsm, (int64_t)p->max_tile_nel * nm * n_upper(p->ref));
+    cap_lsm = std::max(cap_lsm, (int64_t)p->max_tile_nel * nm * lsm_stride(n_upper(p->ref)));
     max_q = std::max(max_q, tab.q);
     n_el += p->tile_elems_total;
     for (int64_t t = 0; t < p->n_tiles; ++t) work.push_back(make_int2(i, (int)t));
@@ -136,8 +136,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
       const lfem_pattern_s* p = items[i].pattern;
       const int d = p->dim, o = p->order;
       const int off = d == 1 ? (o == 1 ? FastBank::OFF11 : FastBank::OFF12) : (o == 1 ? FastBank::OFF21 : FastBank::OFF22);
-      const int size = d == 1 ? (o == 1 ? FastLayout<1, 1>::SIZE : FastLayout<1, 2>::SIZE)
-                              : (o == 1 ? FastLayout<2, 1>::SIZE : FastLayout<2, 2>::SIZE);
+      const int size = fast_table_size(d, o);
       tab.assign(size, 0.f);
       bool fast = fast_tables_host(d, o, items[i].quad, tab.data());
       if (fast && seen[d - 1][o - 1]) {
@@ -157,9 +156,9 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     if (b->d_status) cudaFree(b->d_status);
     delete b;
   };
-  if (cudaMalloc(&b->d_meshes, sizeof(MeshRec) * n_items) != cudaSuccess ||
-      cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, work.size())) != cudaSuccess ||
-      cudaMalloc(&b->d_status, 4 * sizeof(int32_t)) != cudaSuccess) {
+  if (dev_malloc((void**)&b->d_meshes, sizeof(MeshRec) * n_items) != cudaSuccess ||
+      dev_malloc((void**)&b->d_items, sizeof(int2) * std::max<size_t>(1, work.size())) != cudaSuccess ||
+      dev_malloc((void**)&b->d_status, 4 * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return fail(LFEM_E_NOMEM, "batch allocation failed");

@@ -1,4 +1,5 @@
 // C ABI of the library: argument checks, reference tables, dispatch.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +18,13 @@ namespace lfem {
 static thread_local std::string g_err;
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+static std::atomic<long long> g_alloc_count{0};
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_alloc_count.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
 lfem_status fail(lfem_status s, const std::string& msg) {
   g_err = msg;
   return s;
@@ -156,13 +164,19 @@ static void host_tables(int dim, int order, const lfem_quad* quad, std::vector<d
   }
 }
 
-// Compile-time-quadrature tables (layout of FastLayout<dim, order>): edge
-// bubble gradients, weighted basis products and weighted symmetric gradient
-// products per quadrature point.
+// Compile-time-quadrature tables: packed pairs (FastLayout2) for curves and
+// triangles, the per-point layout (FastLayout) for tetrahedra.  Edge bubble
+// gradients, reference gradients, weights and weighted basis products.
+int fast_table_size(int dim, int order) {
+  if (dim == 1) return order == 1 ? FastLayout2<1, 1>::SIZE : FastLayout2<1, 2>::SIZE;
+  if (dim == 2) return order == 1 ? FastLayout2<2, 1>::SIZE : FastLayout2<2, 2>::SIZE;
+  return order == 1 ? FastLayout<3, 1>::SIZE : FastLayout<3, 2>::SIZE;
+}
+
 bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
   const int REF = n_ref(dim, order), NE = n_edges(dim, order), U = n_upper(REF), NK = dim * (dim + 1) / 2;
   const int QF = dim == 1 ? 3 : (dim == 2 ? (order == 1 ? 3 : 7) : (order == 1 ? 4 : 14));
-  if (!quad || quad->n_pts != QF) return false;
+  if (!quad || quad->n_pts != QF || (order != 1 && order != 2)) return false;
   std::vector<double> t;
   host_tables(dim, order, quad, t);
   const int Q = QF;
@@ -170,32 +184,58 @@ bool fast_tables_host(int dim, int order, const lfem_quad* quad, float* dst) {
   const double* phi = w + Q;
   const double* dphi = phi + Q * REF;
   const double* dpsi = dphi + Q * REF * dim;
-  const int per_q = NE * dim + U + (dim >= 2 ? REF * dim + 1 : NK * U);
+  auto tm = [&](int q, int u) -> double {  // w_q phi_a phi_b of upper entry u (0 past the end)
+    for (int a = 0; a < REF; ++a)
+      for (int b = a; b < REF; ++b)
+        if (upper_index(REF, a, b) == u) return w[q] * phi[q * REF + a] * phi[q * REF + b];
+    return 0.0;
+  };
+  if (dim <= 2) {
+    // packed layout (FastLayout2): point pairs (2k, 2k+1); with Q odd the last
+    // pair is point Q-1 twice with half its weight in each half
+    const int QP = (Q + 1) / 2, UH = (U + 1) / 2;
+    const int per_pair = 2 * NE * dim + (dim == 2 ? 2 * REF * dim + 2 : 2 * U);
+    for (int k = 0; k < QP; ++k) {
+      float* d = dst + (size_t)k * per_pair;
+      for (int h = 0; h < 2; ++h) {
+        const int q = std::min(2 * k + h, Q - 1);
+        const double wq = (2 * k + 1 >= Q) ? 0.5 * w[q] : w[q];
+        for (int e = 0; e < NE; ++e)
+          for (int m = 0; m < dim; ++m) d[2 * (e * dim + m) + h] = (float)dpsi[(q * NE + e) * dim + m];
+        float* r = d + 2 * NE * dim;
+        if (dim == 2) {
+          for (int b = 0; b < REF; ++b)
+            for (int m = 0; m < dim; ++m) r[2 * (b * dim + m) + h] = (float)dphi[(q * REF + b) * dim + m];
+          r[2 * REF * dim + h] = (float)wq;
+        } else {
+          for (int a = 0; a < REF; ++a)
+            for (int b = a; b < REF; ++b)
+              r[2 * upper_index(REF, a, b) + h] = (float)(wq * dphi[q * REF + a] * dphi[q * REF + b]);
+        }
+      }
+    }
+    float* mass = dst + (size_t)QP * per_pair;
+    for (int q = 0; q < Q; ++q)
+      for (int j = 0; j < UH; ++j) {
+        mass[2 * (q * UH + j)] = (float)tm(q, 2 * j);
+        mass[2 * (q * UH + j) + 1] = (float)tm(q, 2 * j + 1);
+      }
+    return true;
+  }
+  const int per_q = NE * dim + U + REF * dim + 1;
   for (int q = 0; q < Q; ++q) {
     float* d = dst + (size_t)q * per_q;
     for (int k = 0; k < NE; ++k)
       for (int m = 0; m < dim; ++m) d[k * dim + m] = (float)dpsi[(q * NE + k) * dim + m];
-    float* tm = d + NE * dim;
-    float* ta = tm + U;
-    for (int a = 0; a < REF; ++a)
-      for (int b = a; b < REF; ++b) {
-        const int u = upper_index(REF, a, b);
-        tm[u] = (float)(w[q] * phi[q * REF + a] * phi[q * REF + b]);
-        if (dim >= 2) continue;
-        const double* ga = dphi + (q * REF + a) * dim;
-        const double* gb = dphi + (q * REF + b) * dim;
-        int kk = 0;
-        for (int m = 0; m < dim; ++m)
-          for (int n = m; n < dim; ++n, ++kk)
-            ta[kk * U + u] = (float)(m == n ? w[q] * ga[m] * gb[m] : w[q] * (ga[m] * gb[n] + ga[n] * gb[m]));
-      }
-    if (dim >= 2) {
-      // triangles, tetrahedra: reference gradients and the weight (stiffness point by point)
-      for (int b = 0; b < REF; ++b)
-        for (int m = 0; m < dim; ++m) ta[b * dim + m] = (float)dphi[(q * REF + b) * dim + m];
-      ta[REF * dim] = (float)w[q];
-    }
+    float* tmq = d + NE * dim;
+    for (int u = 0; u < U; ++u) tmq[u] = (float)tm(q, u);
+    // tetrahedra: reference gradients and the weight (stiffness point by point)
+    float* ta = tmq + U;
+    for (int b = 0; b < REF; ++b)
+      for (int m = 0; m < dim; ++m) ta[b * dim + m] = (float)dphi[(q * REF + b) * dim + m];
+    ta[REF * dim] = (float)w[q];
   }
+  (void)NK;
   return true;
 }
 
@@ -436,6 +476,8 @@ lfem_status lfem_set_mixed_kappa(lfem_pattern_t p, double kappa_max) {
   return LFEM_OK;
 }
 
+long long lfem_debug_alloc_count(void) { return lfem::g_alloc_count.load(std::memory_order_relaxed); }
+
 lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   p->debug_starve = starve ? 1 : 0;
@@ -493,7 +535,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
       if (p->d.elem_buf) cudaFree(p->d.elem_buf);
       p->d.elem_buf = nullptr;
       p->d.elem_buf_bytes = 0;
-      if (cudaMalloc(&p->d.elem_buf, need ? need : 16) != cudaSuccess) {
+      if (dev_malloc(&p->d.elem_buf, need ? need : 16) != cudaSuccess) {
         cudaGetLastError();
         return fail(LFEM_E_NOMEM, "element buffer allocation failed");
       }
@@ -552,7 +594,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   pa.cap_nodes = p->max_tile_nodes;
   pa.cap_nel = p->max_tile_nel;
   pa.max_u = n_upper(p->ref);
-  pa.cap_lsm = (int64_t)p->max_tile_nel * nm * n_upper(p->ref);
+  pa.cap_lsm = (int64_t)p->max_tile_nel * nm * lsm_stride(n_upper(p->ref));
   pa.max_q = tab.q;
   pa.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
   pa.qmin = a.qmin;
@@ -721,7 +763,7 @@ static lfem_status vectors_common(lfem_pattern_t p, const double* coords, int am
     if (p->d.vec_buf) cudaFree(p->d.vec_buf);
     p->d.vec_buf = nullptr;
     p->d.vec_buf_bytes = 0;
-    if (cudaMalloc(&p->d.vec_buf, need ? need : 16) != cudaSuccess) {
+    if (dev_malloc((void**)&p->d.vec_buf, need ? need : 16) != cudaSuccess) {
       cudaGetLastError();
       return fail(LFEM_E_NOMEM, "local-vector buffer allocation failed");
     }
@@ -773,7 +815,7 @@ lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, c
     if (p->d.mcf_buf) cudaFree(p->d.mcf_buf);
     p->d.mcf_buf = nullptr;
     p->d.mcf_buf_bytes = 0;
-    if (cudaMalloc(&p->d.mcf_buf, need) != cudaSuccess) {
+    if (dev_malloc(&p->d.mcf_buf, need) != cudaSuccess) {
       cudaGetLastError();
       return fail(LFEM_E_NOMEM, "flow-step scratch allocation failed");
     }

@@ -17,6 +17,10 @@ void set_error(const std::string& msg);
 lfem_status fail(lfem_status s, const std::string& msg);
 lfem_status cuda_fail(cudaError_t e, const char* what);
 
+// Every device allocation of the library goes through dev_malloc, which counts
+// the successful ones (lfem_debug_alloc_count).
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 #define LFEM_CUDA(call)                                   \
   do {                                                    \
     cudaError_t _e = (call);                              \

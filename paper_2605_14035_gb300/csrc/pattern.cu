@@ -421,7 +421,7 @@ template <typename T>
 static lfem_status dalloc(T** p, int64_t n) {
   *p = nullptr;
   if (n <= 0) n = 1;
-  cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
+  cudaError_t e = dev_malloc((void**)p, (size_t)n * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -554,7 +554,9 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
   const int nn = n_nodes[t];
   const int64_t s0 = row_ptr[r0];
   const int ns = (int)(row_ptr[r1] - s0);
+  // entries address local matrices of row stride lsm_stride(U) (U rounded up to even)
   const int U = ref * (ref + 1) / 2;
+  const int UP = U + (U & 1);
   const int ps = pos_stride(ref);
   uint8_t* blk = meta + off[t];
   const int nl_t = nl_in[t], nle_t = nle_in[t];
@@ -626,7 +628,7 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
         for (int b = 0; b < ref; ++b) {
           if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
           const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
-          const uint32_t ent = (uint32_t)loc * (uint32_t)U + (uint32_t)u;
+          const uint32_t ent = (uint32_t)loc * (uint32_t)UP + (uint32_t)u;
           if (c > 2) {
             if (lbeg + w < nle_t) put(lent, lbeg + w, ent);
           } else {
@@ -664,7 +666,8 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   for (int64_t t = 0; t < T; ++t) mnel = std::max(mnel, hep[t + 1] - hep[t]);
   // entries are local-matrix word offsets e * U + u
   // (all ones marks an absent entry, so two-byte entries stay below 0xFFFF)
-  const int entb = std::max((int64_t)mnel * (ref * (ref + 1) / 2) < 65535 ? 2 : 4, p->min_ent_bytes);
+  const int ulsm = ref * (ref + 1) / 2 + ((ref * (ref + 1) / 2) & 1);  // local-matrix row stride (even)
+  const int entb = std::max((int64_t)mnel * ulsm < 65535 ? 2 : 4, p->min_ent_bytes);
   int32_t *tmp_nodes = nullptr, *nn = nullptr, *nl = nullptr, *nle = nullptr;
   int64_t *bytes = nullptr, *scr = nullptr, *mx = nullptr;
   TRY(dalloc(&tmp_nodes, p->tile_elems_total * ref));
@@ -984,10 +987,12 @@ lfem_status pattern_csr_noalloc(const int32_t* conn, int64_t nE, int32_t N, int 
     return fail(LFEM_E_TOO_LARGE, "too many elements meet at one node");
   scan_exclusive<int32_t, int32_t>(deg, inc_ptr, N, s32, st);
   LFEM_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * ((size_t)N + 1), st));
-  if (I > 0) k_fill_incidence<<<grid_for(I, 256), 256, 0, st>>>(conn, nE, ref, 4, inc_ptr, deg, key);
+  // incidence key (e << ksh) | a, as in lfem_pattern: 4 bits of local index up to 16 nodes, else 6
+  const int ksh = ref > 16 ? 6 : 4;
+  if (I > 0) k_fill_incidence<<<grid_for(I, 256), 256, 0, st>>>(conn, nE, ref, ksh, inc_ptr, deg, key);
   LFEM_CUDA(cudaGetLastError());
   TRY(segsort(key, inc_ptr, N, 1, h[1], sort_scr, st));
-  if (I > 0) k_elem_inc_and_raw<<<grid_for(I, 256), 256, 0, st>>>(conn, ref, 4, key, I, einc, raw);
+  if (I > 0) k_elem_inc_and_raw<<<grid_for(I, 256), 256, 0, st>>>(conn, ref, ksh, key, I, einc, raw);
   LFEM_CUDA(cudaGetLastError());
   TRY(segsort(raw, inc_ptr, N, ref, h[1] * ref, sort_scr, st));
   if (N > 0) k_row_unique_count<<<grid_for(N, 128), 128, 0, st>>>(raw, inc_ptr, ref, N, deg);
@@ -1395,7 +1400,9 @@ extern "C" lfem_status lfem_pattern_csr_noalloc(const int32_t* conn, int64_t n_e
   if ((n_elem > 0 && !conn) || !row_ptr || (col_capacity > 0 && !col_idx))
     return lfem::fail(LFEM_E_ARG, "NULL argument");
   if (dim < 1 || dim > 3 || (order != 1 && order != 2)) return lfem::fail(LFEM_E_UNSUPPORTED, "dim/order");
-  if (n_elem >= (1ll << 27)) return lfem::fail(LFEM_E_TOO_LARGE, "too many elements");
+  // the incidence key (e << ksh) | a must fit 31 bits (ksh = 4 up to 16 local nodes, else 6)
+  const int ksh = lfem::n_ref(dim, order) > 16 ? 6 : 4;
+  if (n_elem >= (1ll << (31 - ksh))) return lfem::fail(LFEM_E_TOO_LARGE, "too many elements");
   return lfem::pattern_csr_noalloc(conn, n_elem, n_nodes, dim, order, row_ptr, col_idx, col_capacity, nnz,
                                    (cudaStream_t)cuda_stream);
 }

@@ -30,7 +30,7 @@ EXPORTS = (
     "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_lift_order", "lfem_assemble_adjoint", "lfem_assemble_adjoint_mixed",
     "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
-    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_autotune",
+    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_debug_alloc_count", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
     "lfem_batch_info", "lfem_batch_destroy",
 )
@@ -97,6 +97,8 @@ def _load():
     lib.lfem_last_error.restype = ctypes.c_char_p
     lib.lfem_status_string.restype = ctypes.c_char_p
     lib.lfem_status_string.argtypes = [I]
+    lib.lfem_debug_alloc_count.argtypes = []
+    lib.lfem_debug_alloc_count.restype = ctypes.c_longlong
     return lib
 
 

@@ -82,8 +82,11 @@ def test_noalloc_limits(lfem):
 
 
 def test_noalloc_takes_no_device_memory(lfem):
-    """After the first call (which looks the array up), further calls leave the
-    device's free memory unchanged although they need megabytes of scratch."""
+    """After the first call (which looks the array up), further calls make no
+    device allocation (the library's own allocation counter does not move) and
+    leave the device's free memory unchanged although they need megabytes of
+    scratch.  The counter is the primary check: free memory is device-wide and
+    only a secondary one."""
     from paper_2605_14035_gb300.inputs import meshes
 
     x, e = meshes.icosphere(5, 2)  # about 4.6 MB of scratch
@@ -92,9 +95,15 @@ def test_noalloc_takes_no_device_memory(lfem):
     ci = torch.zeros(40 * e.shape[0], dtype=torch.int32, device="cuda")
     lfem.pattern_csr_noalloc(ed, x.shape[0], 2, 2, rp, ci)
     torch.cuda.synchronize()
+    lib = lfem.lib()
+    n0 = lib.lfem_debug_alloc_count()
     free0, _ = torch.cuda.mem_get_info()
     for _ in range(3):
         lfem.pattern_csr_noalloc(ed, x.shape[0], 2, 2, rp, ci)
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
+    assert lib.lfem_debug_alloc_count() == n0
+    # the counter itself works: building a pattern allocates
+    lfem.Pattern(ed, x.shape[0], 2, 2)
+    assert lib.lfem_debug_alloc_count() > n0
     assert free1 == free0
