@@ -95,10 +95,6 @@ struct alignas(16) FastBank {
 };
 static_assert(FastBank::OFF12 % 2 == 0 && FastBank::OFF21 % 2 == 0 && FastBank::OFF22 % 2 == 0, "even offsets");
 
-// Local-matrix row stride of an element in shared memory: U rounded up to
-// even, so that entry pairs are 8-byte aligned (64-bit stores).
-__host__ __device__ constexpr int lsm_stride(int u) { return u + (u & 1); }
-
 // Tetrahedra (P1, P2).
 struct FastBankTet {
   static constexpr int OFF31 = 0;
@@ -276,29 +272,30 @@ __device__ __forceinline__ void tri_fast2(const ElemData<2, NA, P, float>& ed, c
 
 // Mass-type matrix of a curve or triangle from per-point factors f_q (s_q, or
 // s_q c_q), two entries per instruction: V_u = sum_q f_q TM[q][u], written as
-// float pairs to dst[0 .. lsm_stride(U)) (8-byte aligned; the pad entry is 0).
+// float pairs (entries 2j, 2j + 1) to dst[6 j] (the tile's interleaved
+// local-matrix layout, dst already offset to the matrix slot; the pad entry
+// of an odd U is 0).
 template <int D, int P, typename Bank>
 __device__ __forceinline__ void contract_mass2(const Bank& bank, const float (&f)[FastLayout2<D, P>::Q], float* dst) {
   using L = FastLayout2<D, P>;
   constexpr int OFF = Bank::template off<D, P>();
   const float* tv = bank.v;
-  float2* d2 = reinterpret_cast<float2*>(dst);
 #pragma unroll
   for (int j = 0; j < L::UH; ++j) {
     float2 acc = mul2(f2(f[0]), tab2<OFF>(tv, L::tmu(0, j)));
 #pragma unroll
     for (int q = 1; q < L::Q; ++q) acc = fma2(f2(f[q]), tab2<OFF>(tv, L::tmu(q, j)), acc);
-    d2[j] = acc;
+    *reinterpret_cast<float2*>(dst + 6 * j) = acc;
   }
 }
 
 // Local matrices of one curve or triangle with the compile-time rule, stored
-// as float pairs (row stride lsm_stride(U), matrices in the order M, A, MC,
-// mstride floats apart; mstride and dst 8-byte aligned).
+// into the element's block of the interleaved layout (dst = element base,
+// 8-byte aligned; matrix slots in the order M, A, MC of the requested ones).
 template <int D, int NA, int P, typename Bank>
 __device__ __forceinline__ void element_fast_store2(const ElemData<D, NA, P, float>& ed, const Bank& bank,
                                                     const float* cs, const double* cd, float qthr, unsigned which,
-                                                    float* dst, int mstride, Checks& ck) {
+                                                    float* dst, Checks& ck) {
   using L = FastLayout2<D, P>;
   constexpr int Q = L::Q, UP = lsm_stride(L::U);
   float cq[Q];
@@ -312,22 +309,22 @@ __device__ __forceinline__ void element_fast_store2(const ElemData<D, NA, P, flo
   if constexpr (D == 2) tri_fast2<NA, P>(ed, bank, qthr, do_a, sq, Ao, ck);
   else curve_fast2<NA, P>(ed, bank, do_a, sq, Ao, ck);
   int slot = 0;
-  if (which & LFEM_MASS) contract_mass2<D, P>(bank, sq, dst + mstride * slot++);
+  if (which & LFEM_MASS) contract_mass2<D, P>(bank, sq, dst + 2 * slot++);
   if (do_a) {
-    float2* d2 = reinterpret_cast<float2*>(dst + mstride * slot++);
+    float* d = dst + 2 * slot++;
 #pragma unroll
-    for (int j = 0; j < UP / 2; ++j) d2[j] = make_float2(Ao[2 * j], Ao[2 * j + 1]);
+    for (int j = 0; j < UP / 2; ++j) *reinterpret_cast<float2*>(d + 6 * j) = make_float2(Ao[2 * j], Ao[2 * j + 1]);
   }
   if (which & LFEM_CMASS) {
     float sc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) sc[q] = sq[q] * cq[q];
-    contract_mass2<D, P>(bank, sc, dst + mstride * slot);
+    contract_mass2<D, P>(bank, sc, dst + 2 * slot);
   }
 }
 
-// Mass-type matrix from per-point factors f_q (s_q, or s_q c_q):
-// V_u = sum_q f_q TM[q][u], written to dst[u].
+// Mass-type matrix of a tetrahedron from per-point factors f_q (s_q, or
+// s_q c_q): V_u = sum_q f_q TM[q][u], written to dst[u].
 template <int D, int P, typename Bank>
 __device__ __forceinline__ void contract_mass(const Bank& bank, const float (&f)[FastLayout<D, P>::Q], float* dst) {
   using L = FastLayout<D, P>;

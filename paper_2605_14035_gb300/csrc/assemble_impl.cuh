@@ -230,11 +230,13 @@ __device__ __noinline__ void element_fp64(const double* __restrict__ coords, con
 
 // Double recomputation of one element, one matrix per pass so the registers
 // needed stay below those of the float hot path (upper layout, stored as RS).
-template <int D, int NA, int P, typename RS>
+// IL = false: matrix k at dst[k stride_m + u]; IL = true: the interleaved
+// tile layout, matrix slot slot0 + k at dst[lsm_word(u, slot0 + k)].
+template <int D, int NA, int P, typename RS, bool IL = false>
 __device__ __forceinline__ void element_fp64_lean(const double* __restrict__ coords,
                                                   const int32_t (&nd)[Ref<D, P>::REF], TabRef tab, const void* coef,
                                                   int coef_f32, int64_t e, unsigned which, RS* dst, int stride_m,
-                                                  bool& bad) {
+                                                  bool& bad, int slot0 = 0) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   double X[REF][NA];
@@ -244,23 +246,27 @@ __device__ __forceinline__ void element_fp64_lean(const double* __restrict__ coo
   const TabView<double> tb = tab_view<D, P, double>(tab);
   double qual = 1.0;
   double V[U], dummy1[U], dummy2[U];
-  int slot = 0;
+  int slot = slot0;
+  auto put = [&](int u, double v) {
+    if constexpr (IL) dst[lsm_word(u, slot)] = (RS)v;
+    else dst[slot * stride_m + u] = (RS)v;
+  };
   if (which & LFEM_MASS) {
     element_pass<D, NA, P, double, true, false, false>(ed, tb, coef, coef_f32, e, V, dummy1, dummy2, qual, bad);
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[slot * stride_m + u] = (RS)V[u];
+    for (int u = 0; u < U; ++u) put(u, V[u]);
     ++slot;
   }
   if (which & LFEM_STIFF) {
     element_pass<D, NA, P, double, false, true, false>(ed, tb, coef, coef_f32, e, dummy1, V, dummy2, qual, bad);
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[slot * stride_m + u] = (RS)V[u];
+    for (int u = 0; u < U; ++u) put(u, V[u]);
     ++slot;
   }
   if (which & LFEM_CMASS) {
     element_pass<D, NA, P, double, false, false, true>(ed, tb, coef, coef_f32, e, dummy1, dummy2, V, qual, bad);
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[slot * stride_m + u] = (RS)V[u];
+    for (int u = 0; u < U; ++u) put(u, V[u]);
   }
 }
 

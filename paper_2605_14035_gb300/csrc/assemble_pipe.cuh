@@ -1,29 +1,36 @@
 // Persistent, pipelined assembly kernel.
 //
-// Each CTA walks the row tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// For every tile it needs one contiguous metadata block (see TileHdr: element
-// ids, row/incidence offsets, column positions, the tile's node list and the
-// local node indices of its elements), the coordinates of the tile's nodes and
-// the coefficients of its elements.  While tile t is computed, the next tile's
-// block is copied by the tensor memory accelerator (one cp.async.bulk with an
-// mbarrier) into the other buffer, and as soon as it lands the next tile's
-// node coordinates and coefficients are gathered with cp.async into that
-// buffer as well: the global-memory latency of tile t+grid hides behind the
-// arithmetic of tile t.
+// Each CTA walks the work items k = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (a work item is one row tile of one mesh).  A tile's metadata block has two
+// parts (see TileHdr): the front part (element ids, node list, local node
+// indices) is needed from the start of the tile, the back part (the slots'
+// contribution entries) only by phase 2.  The pipeline, per CTA:
+//   front part of item k+2   TMA bulk copy issued at the start of item k
+//                            (three front buffers)
+//   node coordinates (and general-rule coefficients) of item k+1
+//                            cp.async gathers issued at the start of item k,
+//                            as soon as item k+1's front part is there
+//                            (two node buffers)
+//   back part of item k+1    TMA bulk copy issued when item k's phase 2 is
+//                            done (one back buffer)
+// so the global-memory latency of every copy hides behind a whole item of
+// arithmetic.  Only the issuing thread touches the work-item records (a ring
+// of four in shared memory, each fetched by cp.async three items ahead).
 //
 // Per tile (Sec. 3.2 / 3.3 of the paper; Eqs. reference_quadrature_mass,
 // reference_quadrature_stiffness, M matrix, A matrix):
 //   split    node coordinates -> float pairs (mixed) once per node
-//   phase 1  two threads per element (quadrature points split between them):
-//            geometry and local upper-triangle matrices of every element of
-//            the tile -> shared memory
-//   phase 2  one writer per CSR slot: slots with one or two contributions
-//            take a thread each (plain sum, coalesced stores); longer lists
-//            are summed in ascending element order with a compensated pair --
-//            fixed order, no atomics
+//   phase 1  geometry and local upper-triangle matrices of every element of
+//            the tile -> shared memory (interleaved layout: one address per
+//            entry serves M, A and MC)
+//   phase 2  slots with more than two contributions are summed first, in
+//            ascending element order with a compensated pair, into shared
+//            memory; then every slot is the sum of its two entries (the second
+//            may be the zero word), four consecutive slots per thread with
+//            16-byte stores -- one writer per slot, fixed order, no atomics
 //
-// Every mbarrier wait is bounded by the global timer; on timeout the CTA
-// records ST_TIMEOUT in the status word, waits (bounded) for its own copy and
+// Every wait is bounded by the global timer; on timeout the CTA records
+// ST_TIMEOUT in the status word, waits (bounded) for the copies it issued and
 // returns, leaving the context usable.
 #pragma once
 
@@ -32,9 +39,9 @@
 
 namespace lfem {
 
-constexpr int kPipeTPE = 2;  // threads per element in phase 1
+constexpr int kPipeTPE = 2;  // threads per element in phase 1 (general rules)
 
-// Launch shape: the float kernel fits 170 registers, so 192 threads and two
+// Launch shape: the float kernel fits 160 registers, so 192 threads and two
 // CTAs per SM; the double kernel needs more registers: 256 threads, one CTA.
 template <typename R>
 struct PipeOcc;
@@ -49,63 +56,76 @@ struct PipeOcc<double> {
   static constexpr int MIN_BLOCKS = 1;
 };
 
-// One mesh of a launch: its inputs, outputs, tables and tile blocks.
+// One mesh of a launch: its inputs, outputs and tables.
 struct MeshRec {
   const double* coords;
   const void* coef;
-  const uint8_t* meta;
-  const int64_t* meta_off;
   void* out[3];
   TabRef tab;
   int type;  // element type id (elem_type_id)
-  int na, ref, entb, coef_f32, pad;
+  int na, ref, entb, coef_f32;
+  int c16;  // coords is 16-byte aligned: node runs arrive by bulk copies
 };
 
 __host__ __device__ constexpr int elem_type_id(int d, int na, int p) { return d * 100 + na * 10 + p; }
 constexpr int kFastTypeOffset = 1000;
 
-// Arguments of a persistent launch over work items (mesh, tile).  With one
-// mesh and no item list, item i is tile i of mesh 0.
+// Arguments of a persistent launch over work items.  Item k is items[k]: the
+// block of one tile and the index of its mesh (meshes[mesh], or one).
 struct PipeArgs {
   MeshRec one;              // the mesh when meshes is NULL
   const MeshRec* meshes;    // device table of a batch, or NULL
-  const int2* items;  // (mesh, tile), or NULL
+  const ItemRef* items;     // [n_items]
   int64_t n_items;
   int nm;
   unsigned which;
   int chunk;       // elements per phase-1 round (threads / kPipeTPE)
-  int cap_bytes;   // largest metadata block
+  int cap_front;   // largest front part
+  int cap_back;    // largest back part
   int cap_nodes;   // most nodes in a tile
   int cap_nel;     // most elements in a tile
   int max_u;       // largest local upper triangle among the meshes
-  int64_t cap_lsm; // largest nel * nm * lsm_stride(U) over the meshes (local-matrix words)
+  int64_t cap_lsm; // local-matrix words: 3 nel UP + 6 (nl + 1), largest over the tiles
   int max_q;       // most quadrature points among the meshes
   int coef_bytes;  // 4 or 8 if the weighted mass is requested, else 0
+  int coef_smem;   // bytes per coefficient staged in shared memory: coef_bytes if a
+                   // general-rule tile may need them, else 0 (compile-time-rule
+                   // tiles read theirs from global memory)
+  int vec_out;     // every output array is 16-byte aligned: phase 2 may store 16 bytes at once
   float qmin;
   int32_t* status;
   unsigned long long* fallback;
-  int starve;         // test knob: CTA 0 skips its first metadata copy
-  long long wait_ns;  // bound of every mbarrier wait
+  int starve;         // test knob: CTA 0 skips its first front copy
+  long long wait_ns;  // bound of every wait
 };
 
+// Local-matrix words of a tile with nel elements of upper size u and nl long slots.
+__host__ __device__ constexpr int64_t lsm_words(int64_t nel, int u, int64_t nl) {
+  return (int64_t)kLsmSlots * nel * lsm_stride(u) + 6 * (nl + 1);
+}
+
 struct PipeSmem {
-  size_t mbar, rec, meta0, meta1, node0, node1, coef0, coef1, lsm, flag, total;
+  size_t mbar, refs, rec, front, back, node0, node1, coef0, coef1, lsm, flag, total;
+  size_t front_stride;
 };
 
 template <typename R>
-__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, int cap_bytes, int cap_nodes,
-                                                     int cap_nel, int q, int coef_bytes) {
+__host__ __device__ inline PipeSmem pipe_smem_layout(int na, int64_t cap_lsm, int cap_front, int cap_back,
+                                                     int cap_nodes, int cap_nel, int q, int coef_bytes) {
   auto al = [](size_t b) { return (b + 127) / 128 * 128; };
   PipeSmem L;
   size_t o = 0;
-  L.mbar = o;
+  L.mbar = o;  // 6 mbarriers (3 front buffers, the back buffer, 2 node buffers), then flags
   o += 128;
-  L.rec = o;  // the MeshRec of the current and of the next item
-  o += al(2 * sizeof(MeshRec));
-  L.meta0 = o;
-  o += al(cap_bytes);
-  L.meta1 = o;
-  o += al(cap_bytes);
+  L.refs = o;  // ring of 4 work-item records
+  o += al(4 * sizeof(ItemRef));
+  L.rec = o;  // the MeshRec of each front buffer's item
+  o += al(3 * sizeof(MeshRec));
+  L.front = o;
+  L.front_stride = al(cap_front);
+  o += 3 * L.front_stride;
+  L.back = o;
+  o += al(cap_back);
   L.node0 = o;
   o += al((size_t)cap_nodes * na * 8);
   L.node1 = o;
@@ -171,72 +191,45 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-template <typename PosT, int REF>
-__device__ __forceinline__ void load_pos_smem(const uint8_t* base, int k, int (&pos)[REF]) {
-  constexpr int BYTES = pos_stride(REF) * (int)sizeof(PosT);
-  const uint8_t* p = base + (size_t)k * BYTES;
-  uint32_t w[BYTES >= 4 ? BYTES / 4 : 1];
-  if constexpr (BYTES == 2) {
-    w[0] = *reinterpret_cast<const unsigned short*>(p);
-  } else if constexpr (BYTES == 4) {
-    w[0] = *reinterpret_cast<const unsigned int*>(p);
-  } else if constexpr (BYTES == 8) {
-    const uint2 v = *reinterpret_cast<const uint2*>(p);
-    w[0] = v.x;
-    w[1] = v.y;
-  } else {
-#pragma unroll
-    for (int h = 0; h < BYTES / 16; ++h) {
-      const uint4 v = reinterpret_cast<const uint4*>(p)[h];
-      w[4 * h + 0] = v.x;
-      w[4 * h + 1] = v.y;
-      w[4 * h + 2] = v.z;
-      w[4 * h + 3] = v.w;
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < REF; ++b) {
-    if constexpr (sizeof(PosT) == 1) pos[b] = (w[b >> 2] >> (8 * (b & 3))) & 0xFF;
-    else pos[b] = (w[b >> 1] >> (16 * (b & 1))) & 0xFFFF;
-  }
-}
 
 // Store to global memory by an explicitly global address (a generic store
 // could alias shared memory and would pin later shared loads behind it).
 __device__ __forceinline__ void st_global(float* p, float v) { __stcg(p, v); }
 __device__ __forceinline__ void st_global(double* p, double v) { __stcg(p, v); }
+// Four consecutive values at a 16-byte aligned address.
+__device__ __forceinline__ void st_global4(float* p, const float (&v)[4]) {
+  __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void st_global4(double* p, const double (&v)[4]) {
+  __stcg(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+  __stcg(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
+}
 
-// Issue the gathers of a tile's node coordinates and element coefficients.
-__device__ __forceinline__ void issue_gathers(const MeshRec& mr, bool want_coef, const uint8_t* meta,
-                                              double* nodes_dst, void* coef_dst) {
-  const TileHdr h = *reinterpret_cast<const TileHdr*>(meta);
-  const TileLayout L = tile_layout(h.nel, h.ns, h.nl, h.nle, h.nnodes, mr.ref, mr.entb);
-  const int32_t* nd = reinterpret_cast<const int32_t*>(meta + L.nodes);
-  const int na = mr.na;
-  // a thread per node (no division by the runtime sizes)
-  for (int v = threadIdx.x; v < h.nnodes; v += blockDim.x) {
-    const double* src = mr.coords + (int64_t)nd[v] * na;
-    for (int c = 0; c < na; ++c) cp_async8(nodes_dst + v * na + c, src + c);
-  }
-  // compile-time-rule tiles read their coefficients straight from global memory
-  if (want_coef && mr.type < kFastTypeOffset) {
-    const int q = mr.tab.q;
-    const int32_t* el = reinterpret_cast<const int32_t*>(meta + L.elem);
-    for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
-      const int64_t g0 = (int64_t)el[j] * q;
-      if (mr.coef_f32) {
-        for (int qq = 0; qq < q; ++qq)
-          cp_async4(static_cast<float*>(coef_dst) + j * q + qq, static_cast<const float*>(mr.coef) + g0 + qq);
-      } else {
-        for (int qq = 0; qq < q; ++qq)
-          cp_async8(static_cast<double*>(coef_dst) + j * q + qq, static_cast<const double*>(mr.coef) + g0 + qq);
-      }
+// General-rule tiles: cp.async gathers of the tile's element coefficients
+// from its front part (compile-time-rule tiles read theirs from global memory
+// in phase 1).
+__device__ __forceinline__ void issue_coef_gathers(const MeshRec& mr, bool want_coef, const uint8_t* front,
+                                                   void* coef_dst) {
+  if (!want_coef || mr.type >= kFastTypeOffset) return;
+  const TileHdr h = *reinterpret_cast<const TileHdr*>(front);
+  const TileLayout L = tile_layout(h, mr.ref, mr.entb);
+  const int q = mr.tab.q;
+  const int32_t* el = reinterpret_cast<const int32_t*>(front + L.elem);
+  for (int j = threadIdx.x; j < h.nel; j += blockDim.x) {
+    const int64_t g0 = (int64_t)el[j] * q;
+    if (mr.coef_f32) {
+      for (int qq = 0; qq < q; ++qq)
+        cp_async4(static_cast<float*>(coef_dst) + j * q + qq, static_cast<const float*>(mr.coef) + g0 + qq);
+    } else {
+      for (int qq = 0; qq < q; ++qq)
+        cp_async8(static_cast<double*>(coef_dst) + j * q + qq, static_cast<const double*>(mr.coef) + g0 + qq);
     }
   }
-  cp_async_commit();
 }
 
 // Element data from split node coordinates held in shared memory (hi, lo pairs).
@@ -304,8 +297,9 @@ __device__ __forceinline__ R pair_sum(R v) {
   return v + __shfl_xor_sync(0xffffffffu, v, 1);
 }
 
-// Local matrices of one element by a lane pair; the even lane stores the
-// first half of the entries, the odd lane the second half.
+// Local matrices of one element by a lane pair, stored into the element's
+// block of the interleaved tile layout (dst = element base; matrix slots im,
+// ia, ic); stride_m is unused by this layout.
 template <int D, int NA, int P, typename R, bool DM, bool DA, bool DC>
 __device__ __forceinline__ void element_pair(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb, const void* coef,
                                              int coef_f32, int sub, bool store, R* dst, int stride_m, int im,
@@ -326,13 +320,13 @@ __device__ __forceinline__ void element_pair(const ElemData<D, NA, P, R>& ed, co
   if (store && lane_m) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (DM) dst[im * stride_m + u] = Mo[u];
-      if (DC) dst[ic * stride_m + u] = Co[u];
+      if (DM) dst[lsm_word(u, im)] = Mo[u];
+      if (DC) dst[lsm_word(u, ic)] = Co[u];
     }
   }
   if (store && lane_a) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[ia * stride_m + u] = Ao[u];
+    for (int u = 0; u < U; ++u) dst[lsm_word(u, ia)] = Ao[u];
   }
 }
 
@@ -366,35 +360,76 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   }
 }
 
-// Everything done for one tile whose block, node coordinates and coefficients
-// are in shared memory: split, phase 1 (+ the double fallback), the prefetch
-// hook of the next item after the first phase-1 round, phase 2.
-template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename Prefetch>
-__device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* mb, double* xd,
-                                             const void* coef_s, R* lsm, uint32_t* flist, int* nflag,
-                                             const FastBank& fb,
-                                             Prefetch&& prefetch) {
+// Node coordinates of a tile into its node buffer, issued by one warp: with a
+// 16-byte aligned coordinate array every run is one TMA bulk copy (lane r
+// issues run r; lane 0 first posts the total byte count on the mbarrier) and
+// the extras are cp.async gathers; otherwise every position is gathered by
+// cp.async and the mbarrier phase completes by a plain arrival (those copies
+// are then waited for with cp.async.wait_group before the next barrier).
+__device__ __forceinline__ void issue_node_copies(const MeshRec& mr, const uint8_t* front, double* dst, uint64_t* mb,
+                                                  int lane) {
+  const TileHdr h = *reinterpret_cast<const TileHdr*>(front);
+  const TileLayout L = tile_layout(h, mr.ref, mr.entb);
+  const int na = mr.na;
+  if (mr.c16) {
+    const int4* runs = reinterpret_cast<const int4*>(front + L.runs);
+    const int2* extras = reinterpret_cast<const int2*>(front + L.extras);
+    uint32_t bytes = 0;
+    for (int r = lane; r < h.nruns; r += 32) bytes += (uint32_t)runs[r].y * (uint32_t)na * 8u;
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb)), "r"(bytes)
+                   : "memory");
+    __syncwarp();
+    for (int r = lane; r < h.nruns; r += 32) {
+      const int4 q = runs[r];
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(dst + (size_t)q.z * na)),
+          "l"(mr.coords + (int64_t)q.x * na), "r"((uint32_t)q.y * (uint32_t)na * 8u), "r"(smem_addr(mb))
+          : "memory");
+    }
+    for (int x = lane; x < h.nextra; x += 32) {
+      const int2 e = extras[x];
+      for (int c = 0; c < na; ++c) cp_async8(dst + (size_t)e.y * na + c, mr.coords + (int64_t)e.x * na + c);
+    }
+  } else {
+    const int32_t* nd = reinterpret_cast<const int32_t*>(front + L.nodes);
+    for (int v = lane; v < h.nnodes; v += 32)
+      for (int c = 0; c < na; ++c) cp_async8(dst + (size_t)v * na + c, mr.coords + (int64_t)nd[v] * na + c);
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mb)) : "memory");
+  }
+}
+
+// Everything done for one tile whose front part, node coordinates and
+// coefficients are in shared memory: split, phase 1 (+ the double fallback),
+// then -- once wait_back() says the back part has landed -- phase 2.  Returns
+// false if that wait ran out (nothing is written then).
+template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename IssueNext, typename WaitBack>
+__device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* front,
+                                             const uint8_t* back, double* xd, const void* coef_s, R* lsm,
+                                             uint32_t* flist, int* nflag, const FastBank& fb, IssueNext&& issue_next,
+                                             WaitBack&& wait_back) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   constexpr int UP = lsm_stride(U);
+  constexpr int EW = kLsmSlots * UP;  // words of one element's local matrices
   constexpr int ENTB = (int)sizeof(EntT);
   using Acc = typename AccOf<R>::T;
   const int nm = a.nm, Q = mr.tab.q;
   const int coef_bytes = a.coef_bytes;
   const TabView<R> tb = tab_view<D, P, R>(mr.tab);
-  const TileHdr h = *reinterpret_cast<const TileHdr*>(mb);
-  // local matrices matrix-major: lsm[m * nel * UP + e * UP + u] (row stride U
-  // rounded up to even); a contribution entry is the word offset e * UP + u
-  const int mstride = h.nel * UP;
-  const TileLayout TL = tile_layout(h.nel, h.ns, h.nl, h.nle, h.nnodes, REF, ENTB);
-  const int32_t* t_elem = reinterpret_cast<const int32_t*>(mb + TL.elem);
-  const int32_t* t_nodes = reinterpret_cast<const int32_t*>(mb + TL.nodes);
-  const uint16_t* t_en = reinterpret_cast<const uint16_t*>(mb + TL.enodes);
-  const EntT* t_pair = reinterpret_cast<const EntT*>(mb + TL.pair);
-  const int4* t_lrec = reinterpret_cast<const int4*>(mb + TL.lrec);
-  const EntT* t_lent = reinterpret_cast<const EntT*>(mb + TL.lent);
+  const TileHdr h = *reinterpret_cast<const TileHdr*>(front);
+  const TileLayout TL = tile_layout(h, REF, ENTB);
+  const int32_t* t_elem = reinterpret_cast<const int32_t*>(front + TL.elem);
+  const int32_t* t_nodes = reinterpret_cast<const int32_t*>(front + TL.nodes);
+  const uint16_t* t_en = reinterpret_cast<const uint16_t*>(front + TL.enodes);
+  const EntT* t_pair = reinterpret_cast<const EntT*>(back + TL.pair);
+  const int4* t_lrec = reinterpret_cast<const int4*>(back + TL.lrec);
+  const EntT* t_lent = reinterpret_cast<const EntT*>(back + TL.lent);
 
-  if (threadIdx.x == 0) *nflag = 0;  // visible after the next barrier (split, or the one after phase 1)
+  // (*nflag is 0 on entry)
   // node coordinates -> (hi, lo) float pairs in place (mixed)
   if constexpr (sizeof(R) == 4) {
     for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
@@ -406,71 +441,62 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
     }
     __syncthreads();
   }
+  // the copies of the next items, issued while phase 1 runs
+  issue_next();
 
-  bool prefetched = false;
   if constexpr (FAST && sizeof(R) == 4) {
     // ---- phase 1, compile-time rule: one thread per element, every element of the tile
-    for (int c0 = 0; c0 < h.nel; c0 += (int)blockDim.x) {
-      const int jt = c0 + (int)threadIdx.x;
-      if (jt < h.nel) {
-        ElemData<D, NA, P, float> ed;
-        element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), t_en + (size_t)jt * REF, ed);
-        // coefficients of the element from global memory (loaded first, used last)
-        const int64_t cg = (int64_t)t_elem[jt] * Q;
-        const float* cs = coef_bytes == 4 ? static_cast<const float*>(mr.coef) + cg : nullptr;
-        const double* cd = coef_bytes == 8 ? static_cast<const double*>(mr.coef) + cg : nullptr;
-        Checks ck;
-        element_fast_store2<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * UP,
-                                      mstride, ck);
-        const uint32_t fl = !ck.good ? 2u : (ck.cond ? 0u : 1u);
-        if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
-      }
-      if (!prefetched) {
-        prefetch();
-        prefetched = true;
-      }
-    }
-  } else
-  // ---- phase 1: a lane pair per element, every element of the tile
-  for (int c0 = 0; c0 < h.nel; c0 += a.chunk) {
-    const int cn = min(a.chunk, h.nel - c0);
-    const int jj = threadIdx.x / kPipeTPE, sub = threadIdx.x % kPipeTPE;
-    const bool active = jj < cn;
-    const int jt = c0 + (active ? jj : 0);
-    const uint16_t* en = t_en + (size_t)jt * REF;
-    const void* cf = coef_s;
-    if (coef_bytes) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
-    R qual = (R)1;
-    bool bad = false;
-    R* dst = lsm + (size_t)jt * UP;
-    if constexpr (sizeof(R) == 4) {
+    for (int jt = threadIdx.x; jt < h.nel; jt += blockDim.x) {
       ElemData<D, NA, P, float> ed;
-      element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
-      element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, mstride, a.which, qual, bad);
-    } else {
-      double X[REF][NA];
-#pragma unroll
-      for (int bb = 0; bb < REF; ++bb)
-#pragma unroll
-        for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
-      ElemData<D, NA, P, double> ed;
-      load_element_data<D, NA, P, double>(X, ed);
-      element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, mstride, a.which, qual, bad);
+      element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), t_en + (size_t)jt * REF, ed);
+      // coefficients of the element from global memory (loaded first, used last)
+      const int64_t cg = (int64_t)t_elem[jt] * Q;
+      const float* cs = coef_bytes == 4 ? static_cast<const float*>(mr.coef) + cg : nullptr;
+      const double* cd = coef_bytes == 8 ? static_cast<const double*>(mr.coef) + cg : nullptr;
+      Checks ck;
+      element_fast_store2<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, reinterpret_cast<float*>(lsm) + (size_t)jt * EW,
+                                    ck);
+      const uint32_t fl = !ck.good ? 2u : (ck.cond ? 0u : 1u);
+      if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
     }
-    const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
-    const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
-    if (active && sub == 0) {
+  } else {
+    // ---- phase 1: a lane pair per element, every element of the tile
+    for (int c0 = 0; c0 < h.nel; c0 += a.chunk) {
+      const int cn = min(a.chunk, h.nel - c0);
+      const int jj = threadIdx.x / kPipeTPE, sub = threadIdx.x % kPipeTPE;
+      const bool active = jj < cn;
+      const int jt = c0 + (active ? jj : 0);
+      const uint16_t* en = t_en + (size_t)jt * REF;
+      const void* cf = coef_s;
+      if (coef_bytes) cf = static_cast<const uint8_t*>(cf) + (size_t)jt * Q * coef_bytes;
+      R qual = (R)1;
+      bool bad = false;
+      R* dst = lsm + (size_t)jt * EW;
       if constexpr (sizeof(R) == 4) {
-        const uint32_t fl = bad2 ? 2u : ((D > 1 && q2 < (R)a.qmin) ? 1u : 0u);
-        if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
+        ElemData<D, NA, P, float> ed;
+        element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
+        element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, 0, a.which, qual, bad);
       } else {
-        const int32_t n0 = t_nodes[en[0]];
-        if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
+        double X[REF][NA];
+#pragma unroll
+        for (int bb = 0; bb < REF; ++bb)
+#pragma unroll
+          for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
+        ElemData<D, NA, P, double> ed;
+        load_element_data<D, NA, P, double>(X, ed);
+        element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, 0, a.which, qual, bad);
       }
-    }
-    if (!prefetched) {
-      prefetch();
-      prefetched = true;
+      const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
+      const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
+      if (active && sub == 0) {
+        if constexpr (sizeof(R) == 4) {
+          const uint32_t fl = bad2 ? 2u : ((D > 1 && q2 < (R)a.qmin) ? 1u : 0u);
+          if (fl) flist[atomicAdd(nflag, 1)] = (uint32_t)jt | (fl << 30);
+        } else {
+          const int32_t n0 = t_nodes[en[0]];
+          if (bad2 && n0 >= h.r0 && n0 < h.r0 + h.nrows) atomicOr(a.status, ST_DEGENERATE);
+        }
+      }
     }
   }
   if constexpr (sizeof(R) == 4) {
@@ -493,63 +519,94 @@ __device__ __forceinline__ void process_tile(const PipeArgs& a, const MeshRec& m
 #pragma unroll
       for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
       bool bad = false;
-      R* d = lsm + (size_t)j * UP + (fl == 2 ? 0 : ia * mstride);
-      element_fp64_lean<D, NA, P, float>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw, d,
-                                         mstride, bad);
+      R* d = lsm + (size_t)j * EW;
+      element_fp64_lean<D, NA, P, float, true>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw, d,
+                                               0, bad, fl == 2 ? 0 : ia);
       if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
         atomicAdd(a.fallback, 1ull);
         if (bad) atomicOr(a.status, ST_DEGENERATE);
       }
     }
   }
-  if (!prefetched) prefetch();
+  // the back part (slot entries) must have landed; this also orders phase 1's
+  // shared-memory writes before phase 2's reads
+  if (!wait_back()) return false;
+
+  // ---- phase 2a: slots with more than two contributions (vertex diagonals),
+  // summed in ascending (element, a, b) order with a compensated pair into the
+  // long-result words; the six zero words after them
+  const int LB = kLsmSlots * h.nel * UP;
+  if (threadIdx.x < 6) lsm[LB + 6 * h.nl + threadIdx.x] = (R)0;
+  if (threadIdx.x == 0) *nflag = 0;  // every thread has read it (fallback loop); the next tile's after a barrier
+  for (int j = threadIdx.x; j < h.nl; j += blockDim.x) {
+    const int4 r = t_lrec[j];
+    uint32_t ent = t_lent[r.y];
+    Acc c0, c1, c2;
+    acc_init(c0, lsm[ent]);
+    if (nm > 1) acc_init(c1, lsm[ent + 2]);
+    if (nm > 2) acc_init(c2, lsm[ent + 4]);
+    for (int k = r.y + 1; k < r.z; ++k) {
+      ent = t_lent[k];
+      acc_add(c0, lsm[ent]);
+      if (nm > 1) acc_add(c1, lsm[ent + 2]);
+      if (nm > 2) acc_add(c2, lsm[ent + 4]);
+    }
+    R* lr = lsm + LB + 6 * r.w;
+    lr[0] = (R)acc_final(c0);
+    if (nm > 1) lr[2] = (R)acc_final(c1);
+    if (nm > 2) lr[4] = (R)acc_final(c2);
+  }
   __syncthreads();
 
-  // ---- phase 2: one writer per CSR slot, each slot's contributions summed
-  // in ascending (element, a, b) order -- fixed order, no atomics.  Slots with
-  // one or two contributions (nearly all of them on surfaces) take a thread
-  // each, consecutive slots on consecutive threads (coalesced stores, no
-  // loop); the few longer lists (the diagonal of a node of high valence) are
-  // summed with a compensated pair from the long list.
+  // ---- phase 2b: every slot = its first entry + its second entry (the zero
+  // word for a single contribution or a long result), four consecutive slots
+  // per thread, one writer per slot -- fixed order, no atomics
   {
-    constexpr EntT NONE = (EntT)~(EntT)0;
-    R* o0 = reinterpret_cast<R*>(mr.out[0]) + h.s0;
-    R* o1 = nm > 1 ? reinterpret_cast<R*>(mr.out[1]) + h.s0 : o0;
-    R* o2 = nm > 2 ? reinterpret_cast<R*>(mr.out[2]) + h.s0 : o0;
-    const R* l1 = lsm + mstride;
-    const R* l2 = lsm + 2 * mstride;
-#pragma unroll 2
-    for (int s = threadIdx.x; s < h.ns; s += blockDim.x) {
-      const EntT x = t_pair[2 * s], y = t_pair[2 * s + 1];
-      if (x == NONE) continue;
-      R v0 = lsm[x], v1 = nm > 1 ? l1[x] : (R)0, v2 = nm > 2 ? l2[x] : (R)0;
-      if (y != NONE) {
-        v0 += lsm[y];
-        if (nm > 1) v1 += l1[y];
-        if (nm > 2) v2 += l2[y];
+    R* o[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) o[m] = reinterpret_cast<R*>(mr.out[m < nm ? m : 0]);
+    const int64_t gs0 = h.s0 - h.apad;  // global slot of padded slot 0 (a multiple of 4)
+    const int ng = TL.npad >> 2;
+    const int lo = h.apad, hi = h.apad + h.ns;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      uint32_t x[4], y[4];
+      if constexpr (ENTB == 2) {
+        const uint4 w = reinterpret_cast<const uint4*>(t_pair)[g];
+        x[0] = w.x & 0xFFFFu, y[0] = w.x >> 16;
+        x[1] = w.y & 0xFFFFu, y[1] = w.y >> 16;
+        x[2] = w.z & 0xFFFFu, y[2] = w.z >> 16;
+        x[3] = w.w & 0xFFFFu, y[3] = w.w >> 16;
+      } else {
+        const uint4 w0 = reinterpret_cast<const uint4*>(t_pair)[2 * g];
+        const uint4 w1 = reinterpret_cast<const uint4*>(t_pair)[2 * g + 1];
+        x[0] = w0.x, y[0] = w0.y, x[1] = w0.z, y[1] = w0.w;
+        x[2] = w1.x, y[2] = w1.y, x[3] = w1.z, y[3] = w1.w;
       }
-      st_global(o0 + s, v0);
-      if (nm > 1) st_global(o1 + s, v1);
-      if (nm > 2) st_global(o2 + s, v2);
-    }
-    for (int j = threadIdx.x; j < h.nl; j += blockDim.x) {
-      const int4 r = t_lrec[j];
-      uint32_t ent = t_lent[r.y];
-      Acc c0, c1, c2;
-      acc_init(c0, lsm[ent]);
-      if (nm > 1) acc_init(c1, l1[ent]);
-      if (nm > 2) acc_init(c2, l2[ent]);
-      for (int k = r.y + 1; k < r.z; ++k) {
-        ent = t_lent[k];
-        acc_add(c0, lsm[ent]);
-        if (nm > 1) acc_add(c1, l1[ent]);
-        if (nm > 2) acc_add(c2, l2[ent]);
+      R v[3][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[0][i] = lsm[x[i]] + lsm[y[i]];
+        if (nm > 1) v[1][i] = lsm[x[i] + 2] + lsm[y[i] + 2];
+        if (nm > 2) v[2][i] = lsm[x[i] + 4] + lsm[y[i] + 4];
       }
-      st_global(o0 + r.x, (R)acc_final(c0));
-      if (nm > 1) st_global(o1 + r.x, (R)acc_final(c1));
-      if (nm > 2) st_global(o2 + r.x, (R)acc_final(c2));
+      const int p0 = 4 * g;
+      const int64_t gs = gs0 + p0;
+      if (a.vec_out && p0 >= lo && p0 + 4 <= hi) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+          if (m < nm) st_global4(o[m] + gs, v[m]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (p0 + i >= lo && p0 + i < hi) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+              if (m < nm) st_global(o[m] + gs + i, v[m][i]);
+          }
+      }
     }
   }
+  return true;
 }
 
 // Element type of a launch; the compile-time-rule variant has its own id, so a
@@ -561,20 +618,23 @@ struct EType {
   static constexpr int id = elem_type_id(D_, NA_, P_) + (FAST_ ? kFastTypeOffset : 0);
 };
 
-template <typename R, typename EntT, typename T0, typename... Ts, typename Prefetch>
-__device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* mb,
-                                              double* xd, const void* coef_s, R* lsm, uint32_t* flist, int* nflag,
-                                              const FastBank& fb, Prefetch&& prefetch) {
+template <typename R, typename EntT, typename T0, typename... Ts, typename IssueNext, typename WaitBack>
+__device__ __forceinline__ bool dispatch_tile(int type, const PipeArgs& a, const MeshRec& mr, const uint8_t* front,
+                                              const uint8_t* back, double* xd, const void* coef_s, R* lsm,
+                                              uint32_t* flist, int* nflag, const FastBank& fb, IssueNext&& issue_next,
+                                              WaitBack&& wait_back) {
   if (type == T0::id) {
-    process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, mb, xd, coef_s, lsm, flist, nflag, fb, prefetch);
+    return process_tile<T0::D, T0::NA, T0::P, T0::FAST, R, EntT>(a, mr, front, back, xd, coef_s, lsm, flist, nflag,
+                                                                 fb, issue_next, wait_back);
   } else {
     if constexpr (sizeof...(Ts) > 0) {
-      dispatch_tile<R, EntT, Ts...>(type, a, mr, mb, xd, coef_s, lsm, flist, nflag, fb, prefetch);
+      return dispatch_tile<R, EntT, Ts...>(type, a, mr, front, back, xd, coef_s, lsm, flist, nflag, fb, issue_next,
+                                           wait_back);
     } else {
       // no variant for this tile's type: report it, keep the pipeline's steps
       if (threadIdx.x == 0) atomicOr(a.status, ST_TYPE);
-      prefetch();
-      __syncthreads();
+      issue_next();
+      return wait_back();
     }
   }
 }
@@ -582,106 +642,153 @@ __device__ __forceinline__ void dispatch_tile(int type, const PipeArgs& a, const
 // Persistent launch over work items; Types lists the element types the launch
 // may meet (one for a single mesh, several for a batch).
 template <typename R, typename EntT, typename... Types>
-__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k_assemble_pipe(const PipeArgs a, const __grid_constant__ FastBank fb) {
+__global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
+    k_assemble_pipe(const PipeArgs a, const __grid_constant__ FastBank fb) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const bool want_coef = a.coef_bytes != 0;
-  const PipeSmem L =
-      pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes);
+  const PipeSmem L = pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q,
+                                         a.coef_smem);
+  // mbarriers: [0..2] front buffers, [3] the back buffer, [4], [5] node buffers
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
-  int* s_flag = reinterpret_cast<int*>(smem_raw + L.mbar + 64);
+  int* s_nflag = reinterpret_cast<int*>(smem_raw + L.mbar + 68);
+  ItemRef* s_ref = reinterpret_cast<ItemRef*>(smem_raw + L.refs);
+  MeshRec* s_rec = reinterpret_cast<MeshRec*>(smem_raw + L.rec);
   // buffers as shared-memory base + offset (no pointer arrays: a pointer
   // loaded back from local memory would turn every access generic)
-  MeshRec* s_rec = reinterpret_cast<MeshRec*>(smem_raw + L.rec);
-  auto meta_of = [&](int buf) { return smem_raw + (buf ? L.meta1 : L.meta0); };
-  auto node_of = [&](int buf) { return reinterpret_cast<double*>(smem_raw + (buf ? L.node1 : L.node0)); };
-  auto coef_of = [&](int buf) { return static_cast<void*>(smem_raw + (buf ? L.coef1 : L.coef0)); };
+  auto front_of = [&](int f) { return smem_raw + L.front + (size_t)f * L.front_stride; };
+  uint8_t* s_back = smem_raw + L.back;
+  auto node_of = [&](int b) { return reinterpret_cast<double*>(smem_raw + (b ? L.node1 : L.node0)); };
+  auto coef_of = [&](int b) { return static_cast<void*>(smem_raw + (b ? L.coef1 : L.coef0)); };
   R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
   uint32_t* flist = reinterpret_cast<uint32_t*>(smem_raw + L.flag);
-  int* s_nflag = reinterpret_cast<int*>(smem_raw + L.mbar + 68);
 
-  int64_t i = blockIdx.x;
-  if (i >= a.n_items) return;
-  if (threadIdx.x == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    fence_mbar_init();
-    *s_flag = 0;
-  }
-  __syncthreads();
+  const int64_t G = gridDim.x;
+  const int64_t i0 = blockIdx.x;
+  if (i0 >= a.n_items) return;
+  auto exists = [&](int64_t k) { return i0 + k * G < a.n_items; };
+  // the copies are issued by the last warp (it has the fewest phase-1
+  // elements), the whole-block ones by its last thread, the producer
+  const bool pwarp = threadIdx.x >= blockDim.x - 32;
+  const bool producer = threadIdx.x == blockDim.x - 1;
+  const int lane = threadIdx.x & 31;
+  // copies in flight per mbarrier (bit b; the producer's record) and the
+  // parity of each mbarrier's next phase (the same in every thread); each
+  // mbarrier has at most one phase in flight
+  uint32_t pend = 0, par = 0;
 
-  auto item = [&](int64_t k, int& mesh, int64_t& tile) {
-    if (a.items) {
-      const int2 v = a.items[k];
-      mesh = v.x;
-      tile = v.y;
-    } else {
-      mesh = 0;
-      tile = k;
-    }
+  // producer: mesh record of item k and the TMA copy of its front part into front buffer k % 3
+  auto load_front = [&](int64_t k) {
+    const int f = (int)(k % 3);
+    const ItemRef& r = s_ref[k & 3];
+    s_rec[f] = a.meshes ? a.meshes[r.mesh] : a.one;
+    tma_load_block(front_of(f), r.front, (uint32_t)r.front_bytes, &mbar[f]);
+    pend |= 1u << f;
   };
-  // thread 0: item k's MeshRec into s_rec[buf] (read by all after the next
-  // barrier) and one bulk copy of its metadata block
-  auto load_block = [&](int64_t k, int buf) {
-    int mesh;
-    int64_t tile;
-    item(k, mesh, tile);
-    MeshRec& r = s_rec[buf];
-    if (a.meshes) r = a.meshes[mesh];
-    else r = a.one;
-    const uint32_t bytes = (uint32_t)(r.meta_off[tile + 1] - r.meta_off[tile]);
-    tma_load_block(meta_of(buf), r.meta + r.meta_off[tile], bytes, &mbar[buf]);
+  // producer: TMA copy of item k's back part into the back buffer
+  auto load_back = [&](int64_t k) {
+    const ItemRef& r = s_ref[k & 3];
+    tma_load_block(s_back, r.front + r.front_bytes, (uint32_t)r.back_bytes, &mbar[3]);
+    pend |= 1u << 3;
   };
-  // prologue: item i into buffer 0
-  const bool issued0 = !(a.starve && blockIdx.x == 0);
-  if (threadIdx.x == 0 && issued0) load_block(i, 0);
-  {
-    const bool ok = mbar_wait_bounded(&mbar[0], 0, a.wait_ns);
-    if (__syncthreads_or(!ok)) {
-      // the copy (if one was issued) did not land within the bound: report, and
-      // give it one more bounded wait so that it does not write into the shared
-      // memory of a CTA that starts here after this one returns
-      if (threadIdx.x == 0) {
-        atomicOr(a.status, ST_TIMEOUT);
-        if (issued0) mbar_wait_bounded(&mbar[0], 0, a.wait_ns);
-      }
-      return;
-    }
-  }
-  issue_gathers(s_rec[0], want_coef, meta_of(0), node_of(0), coef_of(0));
-
-  for (int it = 0; i < a.n_items; i += gridDim.x, ++it) {
-    const int b = it & 1, nb = b ^ 1;
-    const int64_t in = i + gridDim.x;
-    // next item's metadata block: one bulk copy into the other buffer
-    if (in < a.n_items && threadIdx.x == 0) {
-      fence_proxy_async();
-      load_block(in, nb);
+  // last warp: node coordinates of the item whose front part is in buffer f, into node buffer b
+  auto load_nodes = [&](int f, int b) {
+    fence_proxy_async();
+    issue_node_copies(s_rec[f], front_of(f), node_of(b), &mbar[4 + b], lane);
+    pend |= 1u << (4 + b);
+  };
+  // one thread's bounded wait for the next phase of mbarrier b (each thread
+  // waits for itself; the outcome is agreed on at the next barrier)
+  auto wait_one = [&](int b) -> bool { return mbar_wait_bounded(&mbar[b], (par >> b) & 1u, a.wait_ns); };
+  auto passed = [&](int b) {
+    par ^= 1u << b;
+    pend &= ~(1u << b);
+  };
+  // a wait ran out: report it, give every copy still in flight one more
+  // bounded wait (so that none lands in the shared memory of a later CTA), stop
+  auto bail = [&]() {
+    if (producer) {
+      atomicOr(a.status, ST_TIMEOUT);
+      for (int b = 0; b < 6; ++b)
+        if (pend & (1u << b)) mbar_wait_bounded(&mbar[b], (par >> b) & 1u, a.wait_ns);
     }
     cp_async_wait_all();
-    __syncthreads();
+  };
 
-    auto prefetch_next = [&]() {
-      // all threads: wait for the next block (bounded), then gather its nodes and coefficients
-      if (in < a.n_items) {
-        const bool ok = mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
-        if (__syncthreads_or(!ok)) {
-          if (threadIdx.x == 0) *s_flag = 1;
-        } else {
-          issue_gathers(s_rec[nb], want_coef, meta_of(nb), node_of(nb), coef_of(nb));
-        }
-      }
-    };
-    const MeshRec& mr = s_rec[b];
-    dispatch_tile<R, EntT, Types...>(mr.type, a, mr, meta_of(b), node_of(b), coef_of(b), lsm, flist, s_nflag, fb,
-                                     prefetch_next);
-    if (*s_flag) {
-      // the next block never arrived: report, wait (bounded) for the copy, stop
-      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
-      if (in < a.n_items) mbar_wait_bounded(&mbar[nb], (uint32_t)(((it + 1) >> 1) & 1), a.wait_ns);
-      cp_async_wait_all();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 6; ++b) mbar_init(&mbar[b], 1);
+    fence_mbar_init();
+    *s_nflag = 0;
+  }
+  // records of items 0, 1, 2
+  if (threadIdx.x < 3 && exists(threadIdx.x)) s_ref[threadIdx.x] = a.items[i0 + (int64_t)threadIdx.x * G];
+  __syncthreads();
+  if (producer) {
+    if (!(a.starve && blockIdx.x == 0)) load_front(0);
+    if (exists(1)) load_front(1);
+  }
+  {
+    const bool ok = wait_one(0);
+    if (__syncthreads_or(!ok)) {
+      bail();
       return;
     }
-    __syncthreads();
+    passed(0);
+  }
+  // item 0's node coordinates and coefficients
+  if (pwarp) load_nodes(0, 0);
+  issue_coef_gathers(s_rec[0], want_coef, front_of(0), coef_of(0));
+  cp_async_commit();
+
+  for (int64_t k = 0; exists(k); ++k) {
+    const int f = (int)(k % 3), nb = (int)(k & 1);
+    const bool has1 = exists(k + 1);
+    const int f1 = (int)((k + 1) % 3);
+    // item k's node coordinates and coefficients and item k+2's record have
+    // landed, item k+1's front part is here, item k-1 has left every buffer
+    // (one barrier)
+    cp_async_wait_all();
+    {
+      bool ok = wait_one(4 + nb);
+      if (has1) ok = ok && wait_one(f1);
+      if (__syncthreads_or(!ok)) {
+        bail();
+        return;
+      }
+      passed(4 + nb);
+      if (has1) passed(f1);
+    }
+    // the copies for items k+1 .. k+3 (called by every thread once item k's
+    // split is done, so that their issue overlaps phase 1)
+    auto issue_next = [&]() {
+      if (producer) {
+        fence_proxy_async();
+        load_back(k);
+        if (exists(k + 2)) load_front(k + 2);
+        if (exists(k + 3)) {
+          const ItemRef* src = a.items + (i0 + (k + 3) * G);
+          ItemRef* dst = s_ref + ((k + 3) & 3);
+          cp_async16(dst, src);
+          cp_async16(reinterpret_cast<uint8_t*>(dst) + 16, reinterpret_cast<const uint8_t*>(src) + 16);
+        }
+      }
+      if (has1) {
+        if (pwarp) load_nodes(f1, nb ^ 1);
+        issue_coef_gathers(s_rec[f1], want_coef, front_of(f1), coef_of(nb ^ 1));
+      }
+      cp_async_commit();
+    };
+    auto wait_back = [&]() -> bool {
+      const bool ok = wait_one(3);
+      if (__syncthreads_or(!ok)) return false;
+      passed(3);
+      return true;
+    };
+    const MeshRec& mr = s_rec[f];
+    if (!dispatch_tile<R, EntT, Types...>(mr.type, a, mr, front_of(f), s_back, node_of(nb), coef_of(nb), lsm, flist,
+                                          s_nflag, fb, issue_next, wait_back)) {
+      bail();
+      return;
+    }
   }
   cp_async_wait_all();
 }
@@ -689,8 +796,9 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS) k
 template <typename R, typename EntT, typename... Types>
 lfem_status launch_pipe_types(const PipeArgs& a, const FastBank& fb, int sm_count, cudaStream_t st) {
   if (a.n_items == 0) return LFEM_OK;
-  const size_t smem =
-      pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
+  const size_t smem = pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q,
+                                          a.coef_smem)
+                          .total;
   if (smem > 227 * 1024) return fail(LFEM_E_TOO_LARGE, "pipelined tile needs more than 227 KB of shared memory");
   auto kern = k_assemble_pipe<R, EntT, Types...>;
   LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -704,7 +812,6 @@ lfem_status launch_pipe_types(const PipeArgs& a, const FastBank& fb, int sm_coun
   return LFEM_OK;
 }
 
-// Single mesh of type (D, NA, P).
 // Single mesh of type (D, NA, P); fast: the rule is the compile-time one (float only).
 template <int D, int NA, int P, typename R>
 lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, bool fast, const FastBank& fb, int sm_count,
@@ -715,6 +822,7 @@ lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, bool fast, const FastB
     if (fast) {
       PipeArgs af = a;
       af.one.type = TF::id;  // the tile dispatch matches the variant's id
+      af.coef_smem = 0;      // coefficients are read from global memory
       return ent_bytes == 2 ? launch_pipe_types<R, uint16_t, TF>(af, fb, sm_count, st)
                             : launch_pipe_types<R, uint32_t, TF>(af, fb, sm_count, st);
     }
@@ -725,7 +833,8 @@ lfem_status launch_pipe(const PipeArgs& a, int ent_bytes, bool fast, const FastB
 
 template <typename R>
 size_t pipe_smem_bytes(const PipeArgs& a) {
-  return pipe_smem_layout<R>(3, a.cap_lsm, a.cap_bytes, a.cap_nodes, a.cap_nel, a.max_q, a.coef_bytes).total;
+  return pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q, a.coef_smem)
+      .total;
 }
 
 }  // namespace lfem

@@ -18,6 +18,11 @@ static lfem_status launch_batch(const PipeArgs& a, const FastBank& fb, int sms, 
                                                                                                        st);
 }
 
+__global__ void k_set_item_mesh(ItemRef* refs, int64_t n, int mesh) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) refs[t].mesh = mesh;
+}
+
 static bool batch_type_ok(int d, int na) { return (d == 1 && na == 2) || (d == 2 && (na == 2 || na == 3)); }
 
 lfem_status bank_upload_batch(const void* src, size_t bytes, size_t offset) {
@@ -33,7 +38,7 @@ struct lfem_batch_s {
   int device = 0;
   PipeArgs args{};
   MeshRec* d_meshes = nullptr;
-  int2* d_items = nullptr;
+  ItemRef* d_items = nullptr;
   int32_t* d_status = nullptr;  // [0] status bits, [2..3] fallback count
   int ent_bytes = 2;
   int64_t n_elements = 0;
@@ -67,10 +72,11 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
   if (which == 0 || (which & ~7u)) return fail(LFEM_E_ARG, "which");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::vector<MeshRec> recs(n_items);
-  std::vector<int2> work;
-  int cap_bytes = 0, cap_nodes = 0, cap_nel = 0, max_u = 0, max_q = 0, ent_bytes = 2;
+  std::vector<int64_t> item_off(n_items + 1, 0);  // first work item of each mesh
+  int cap_front = 0, cap_back = 0, cap_nodes = 0, cap_nel = 0, max_u = 0, max_q = 0, ent_bytes = 2;
   int64_t cap_lsm = 0;
   int64_t n_el = 0;
+  int vec_out = 1;
   int nm = 0;
   for (unsigned bit = 1; bit <= 4; bit <<= 1) nm += (which & bit) ? 1 : 0;
   for (int i = 0; i < n_items; ++i) {
@@ -103,26 +109,28 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     MeshRec& r = recs[i];
     r.coords = it.coords;
     r.coef = it.coef;
-    r.meta = p->d.tile_meta;
-    r.meta_off = p->d.tile_meta_off;
     int m = 0;
     if (which & LFEM_MASS) r.out[m++] = it.M;
     if (which & LFEM_STIFF) r.out[m++] = it.A;
     if (which & LFEM_CMASS) r.out[m++] = it.MC;
+    for (int k = 0; k < m; ++k)
+      if (reinterpret_cast<uintptr_t>(r.out[k]) % 16) vec_out = 0;
     r.tab = tab;
     r.type = elem_type_id(p->dim, it.ambient, p->order);
     r.na = it.ambient;
     r.ref = p->ref;
     r.entb = p->ent_bytes;
     r.coef_f32 = coef_is_fp32 ? 1 : 0;
-    cap_bytes = std::max(cap_bytes, p->max_tile_bytes);
+    r.c16 = reinterpret_cast<uintptr_t>(it.coords) % 16 == 0 ? 1 : 0;
+    cap_front = std::max(cap_front, p->max_tile_front);
+    cap_back = std::max(cap_back, p->max_tile_back);
     cap_nodes = std::max(cap_nodes, p->max_tile_nodes);
     cap_nel = std::max(cap_nel, p->max_tile_nel);
     max_u = std::max(max_u, n_upper(p->ref));
-    cap_lsm = std::max(cap_lsm, (int64_t)p->max_tile_nel * nm * lsm_stride(n_upper(p->ref)));
+    cap_lsm = std::max(cap_lsm, lsm_words(p->max_tile_nel, n_upper(p->ref), p->max_tile_nl));
     max_q = std::max(max_q, tab.q);
     n_el += p->tile_elems_total;
-    for (int64_t t = 0; t < p->n_tiles; ++t) work.push_back(make_int2(i, (int)t));
+    item_off[i + 1] = item_off[i] + p->n_tiles;
   }
   lfem_batch_s* b = new lfem_batch_s();
   cudaGetDevice(&b->device);
@@ -157,14 +165,21 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     delete b;
   };
   if (dev_malloc((void**)&b->d_meshes, sizeof(MeshRec) * n_items) != cudaSuccess ||
-      dev_malloc((void**)&b->d_items, sizeof(int2) * std::max<size_t>(1, work.size())) != cudaSuccess ||
+      dev_malloc((void**)&b->d_items, sizeof(ItemRef) * std::max<int64_t>(1, item_off[n_items])) != cudaSuccess ||
       dev_malloc((void**)&b->d_status, 4 * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return fail(LFEM_E_NOMEM, "batch allocation failed");
   }
   cudaMemcpyAsync(b->d_meshes, recs.data(), sizeof(MeshRec) * n_items, cudaMemcpyHostToDevice, st);
-  if (!work.empty()) cudaMemcpyAsync(b->d_items, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st);
+  // work items: every mesh's tile records, mesh by mesh, tagged with the mesh index
+  for (int i = 0; i < n_items; ++i) {
+    const int64_t n = item_off[i + 1] - item_off[i];
+    if (n == 0) continue;
+    cudaMemcpyAsync(b->d_items + item_off[i], items[i].pattern->d.tile_refs, sizeof(ItemRef) * n,
+                    cudaMemcpyDeviceToDevice, st);
+    k_set_item_mesh<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b->d_items + item_off[i], n, i);
+  }
   cudaMemsetAsync(b->d_status, 0, 4 * sizeof(int32_t), st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -174,17 +189,22 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
   PipeArgs& a = b->args;
   a.meshes = b->d_meshes;
   a.items = b->d_items;
-  a.n_items = (int64_t)work.size();
+  a.n_items = item_off[n_items];
   a.nm = nm;
   a.which = which;
   a.chunk = PipeOcc<float>::THREADS / kPipeTPE;
-  a.cap_bytes = cap_bytes;
+  a.cap_front = cap_front;
+  a.cap_back = cap_back;
   a.cap_nodes = cap_nodes;
   a.cap_nel = cap_nel;
   a.max_u = max_u;
   a.cap_lsm = cap_lsm;
+  a.vec_out = vec_out;
   a.max_q = max_q;
   a.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
+  a.coef_smem = 0;  // staged only for general-rule items
+  for (int i = 0; i < n_items; ++i)
+    if (recs[i].type < kFastTypeOffset) a.coef_smem = a.coef_bytes;
   a.qmin = 0.0f;
   for (int i = 0; i < n_items; ++i) a.qmin = std::max(a.qmin, items[i].pattern->qmin);
   a.status = b->d_status;

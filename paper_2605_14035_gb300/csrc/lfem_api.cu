@@ -355,7 +355,7 @@ static lfem_status run_pipe(int dim, int NA, int P, bool mixed, const PipeArgs& 
 
 static void destroy_dev(PatternDev& d) {
   void* ptrs[] = {d.conn,      d.row_ptr,       d.col_idx,   d.inc_ptr,   d.inc_key, d.inc_pos,    d.elem_inc,
-                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off,
+                  d.tile_row0, d.tile_elem_ptr, d.tile_elem, d.inc_local, d.status,  d.tile_meta, d.tile_meta_off, d.tile_refs,
                   d.slot_off,  d.slot_ent,      d.elem_buf,  d.vec_buf,   d.mcf_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -575,8 +575,6 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   MeshRec& mr = pa.one;
   mr.coords = coords;
   mr.coef = coef;
-  mr.meta = p->d.tile_meta;
-  mr.meta_off = p->d.tile_meta_off;
   for (int m = 0; m < 3; ++m) mr.out[m] = a.out[m];
   mr.tab = tab;
   mr.type = elem_type_id(p->dim, ambient, p->order);
@@ -584,19 +582,25 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   mr.ref = p->ref;
   mr.entb = p->ent_bytes;
   mr.coef_f32 = a.coef_f32;
+  mr.c16 = reinterpret_cast<uintptr_t>(coords) % 16 == 0 ? 1 : 0;
   pa.meshes = nullptr;
-  pa.items = nullptr;
+  pa.items = p->d.tile_refs;
   pa.n_items = p->n_tiles;
   pa.nm = nm;
   pa.which = which;
   pa.chunk = (mixed ? PipeOcc<float>::THREADS : PipeOcc<double>::THREADS) / kPipeTPE;
-  pa.cap_bytes = p->max_tile_bytes;
+  pa.cap_front = p->max_tile_front;
+  pa.cap_back = p->max_tile_back;
   pa.cap_nodes = p->max_tile_nodes;
   pa.cap_nel = p->max_tile_nel;
   pa.max_u = n_upper(p->ref);
-  pa.cap_lsm = (int64_t)p->max_tile_nel * nm * lsm_stride(n_upper(p->ref));
+  pa.cap_lsm = lsm_words(p->max_tile_nel, n_upper(p->ref), p->max_tile_nl);
+  pa.vec_out = 1;
+  for (int m = 0; m < nm; ++m)
+    if (reinterpret_cast<uintptr_t>(a.out[m]) % 16) pa.vec_out = 0;
   pa.max_q = tab.q;
   pa.coef_bytes = (which & LFEM_CMASS) ? (coef_is_fp32 ? 4 : 8) : 0;
+  pa.coef_smem = pa.coef_bytes;
   pa.qmin = a.qmin;
   pa.status = p->d.status;
   pa.fallback = a.fallback;
@@ -905,7 +909,7 @@ lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, c
   if (!best) {
     // finer steps around the capacities where a tile's elements still fit one
     // phase-1 round of the mixed kernel and two CTAs share an SM
-    const int cand[] = {512, 1024, 1536, 2048, 2304, 2560, 2688, 2816, 3072, 4096, 6144, 8192};
+    const int cand[] = {512, 1024, 1536, 2048, 2304, 2560, 2816, 3072, 3328, 3584, 4096, 6144, 8192};
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     LFEM_CUDA(cudaEventCreate(&e0));

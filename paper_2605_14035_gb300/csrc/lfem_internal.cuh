@@ -384,42 +384,65 @@ __device__ __forceinline__ void gather_coords(const double* __restrict__ coords,
 }
 
 // ----------------------------------------------------------------------------
-// Per-tile metadata block (built once per topology, staged by one TMA bulk copy):
-//   header   TileHdr (32 B)
-//   elem     int32  [nel]          element ids, ascending
-//   nodes    int32  [nnodes]       distinct nodes of the tile's elements, ascending
-//   enodes   uint16 [nel][ref]     local node index of each element node
-//   soff     uint16 [ns + 1]       start of each slot's contribution list in sent
-//   sent     EntT   [nent]         contributions, (local element << UB) | upper index,
-//                                  per slot in ascending (element, a, b) order
-// every section starts on a 16-byte boundary; the block size is a multiple of 16.
-// A row's contributions are contiguous: ref per incidence of the row.
+// Per-tile metadata block (built once per topology).  Two contiguous parts,
+// each staged by one TMA bulk copy:
+//   front (needed from the start of a tile: triple-buffered)
+//     header   TileHdr (48 B)
+//     elem     int32  [nel]          element ids, ascending
+//     nodes    int32  [nnodes]       global node id of every position of the tile's
+//                                    node buffer (runs, then extras)
+//     enodes   uint16 [nel][ref]     node-buffer position of each element node
+//     runs     int4   [nruns]        {first node, count, position, 0}: the node buffer
+//                                    is these runs of consecutive node ids (first node,
+//                                    count and position even, so that each run is one
+//                                    16-byte aligned bulk copy of the coordinates), the
+//                                    tile's nodes plus gaps of at most kRunGap nodes
+//     extras   int2   [nextra]       {node, position}: nodes copied one by one (the
+//                                    mesh's last node when an even run would pass it)
+//   back (needed by phase 2 only: single-buffered)
+//     pair     EntT   [npad][2]      the two contribution entries of every slot, in
+//                                    padded slot order p = slot + apad (apad = s0 mod 4,
+//                                    so that slot groups of four are 16-byte aligned in
+//                                    the output); npad = apad + ns rounded up to 4
+//     lrec     int4   [nl]           slots with more than two contributions:
+//                                    {slot, first, end, long index}
+//     lent     EntT   [nle]          their entries, each run in ascending (e, a, b)
+// every section starts on a 16-byte boundary; each part's size is a multiple of 16.
+//
+// Entries address the tile's local matrices in shared memory, laid out with
+// the three matrix slots of an entry pair side by side:
+//   word(e, u, m) = 6 (e UP/2 + u/2) + 2 m + (u mod 2)      (UP = U rounded up to even)
+// so one address serves M, A and MC (offsets 0, 2, 4 words).  After the nel
+// elements (3 nel UP words) come the long-list results, 6 words per long slot
+// (word LB + 6 li + 2 m, LB = 3 nel UP), then six zero words: ZERO = LB + 6 nl.
+// A slot with one contribution has ZERO as its second entry; a long slot has
+// its result as the first and ZERO as the second.
 // ----------------------------------------------------------------------------
 struct TileHdr {
   int64_t s0;
-  int32_t r0, nrows, ns, nent, nel, nnodes;
+  int32_t r0, nrows, ns, nruns, nel, nnodes;  // nnodes: positions of the node buffer
   int32_t nl, nle;  // slots with more than two contributions, and their entries
-  int32_t pad[2];
+  int32_t apad;     // s0 mod 4: padded slot p = slot + apad
+  int32_t nextra;
 };
 static_assert(sizeof(TileHdr) == 48, "tile header");
+constexpr int kRunGap = 2;  // node-id gaps up to this length are copied inside a run
 
 __host__ __device__ constexpr int al16(int64_t b) { return (int)((b + 15) / 16 * 16); }
 
-// Tile block after the header:
-//   elem[nel] (int32)   global element ids
-//   nodes[nnodes]       global node ids (sorted)
-//   enodes[nel][ref]    (u16) tile-local node index of each element node
-//   pair[ns][2]         (EntT) slots with one or two contributions: their
-//                       entries (the second all ones for one); all ones in
-//                       both for a slot on the long list
-//   lrec[nl]            (int4) long slots: {slot, first, end, 0} into lent
-//   lent[nle]           (EntT) entries of the long slots, each slot's run in
-//                       ascending (element, a, b) order
-// An entry is the word offset e_local * U + u of a local upper-triangle entry.
+// Local-matrix row stride of an element: U rounded up to even, so that entry
+// pairs are 8-byte aligned (64-bit stores).
+__host__ __device__ constexpr int lsm_stride(int u) { return u + (u & 1); }
+constexpr int kLsmSlots = 3;  // matrix slots per local entry in shared memory
+__host__ __device__ constexpr int lsm_word(int u, int m) { return 6 * (u >> 1) + 2 * m + (u & 1); }
+
 struct TileLayout {
-  int elem, nodes, enodes, pair, lrec, lent, total;
+  int elem, nodes, enodes, runs, extras, front;  // front part: offsets from its start; front = its size
+  int pair, lrec, lent, back;                    // back part: offsets from its start; back = its size
+  int npad;
 };
-__host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nl, int nle, int nnodes, int ref, int entb) {
+__host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nl, int nle, int nnodes, int ref, int entb,
+                                                  int apad, int nruns, int nextra) {
   TileLayout L;
   int o = (int)sizeof(TileHdr);
   L.elem = o;
@@ -428,15 +451,35 @@ __host__ __device__ inline TileLayout tile_layout(int nel, int ns, int nl, int n
   o += al16(4ll * nnodes);
   L.enodes = o;
   o += al16(2ll * ref * nel);
+  L.runs = o;
+  o += 16 * nruns;
+  L.extras = o;
+  o += al16(8ll * nextra);
+  L.front = o;
+  L.npad = (apad + ns + 3) / 4 * 4;
+  if (L.npad < 4) L.npad = 4;
+  o = 0;
   L.pair = o;
-  o += al16(2ll * entb * ns);
+  o += al16(2ll * entb * L.npad);
   L.lrec = o;
-  o += al16(16ll * nl);
+  o += 16 * nl;
   L.lent = o;
   o += al16((int64_t)entb * nle);
-  L.total = o;
+  L.back = o;
   return L;
 }
+__host__ __device__ inline TileLayout tile_layout(const TileHdr& h, int ref, int entb) {
+  return tile_layout(h.nel, h.ns, h.nl, h.nle, h.nnodes, ref, entb, h.apad, h.nruns, h.nextra);
+}
+
+// One work item of a persistent launch: the tile block of a mesh.
+struct ItemRef {
+  const uint8_t* front;  // device address of the block (front part, then back part)
+  int32_t front_bytes, back_bytes;
+  int32_t mesh, tile;
+  int32_t pad[2];
+};
+static_assert(sizeof(ItemRef) == 32, "item record");
 
 // ----------------------------------------------------------------------------
 // Pattern handle
@@ -509,6 +552,7 @@ struct PatternDev {
   size_t mcf_buf_bytes = 0;
   uint8_t* tile_meta = nullptr;  // per-tile metadata blocks (see TileHdr)
   int64_t* tile_meta_off = nullptr;  // [T+1] byte offsets, multiples of 16
+  ItemRef* tile_refs = nullptr;  // [T] block address and part sizes per tile
 };
 
 }  // namespace lfem
@@ -526,7 +570,7 @@ struct lfem_pattern_s {
   int32_t tile_slots = 3072;
   int64_t n_tiles = 0;
   int64_t tile_elems_total = 0;
-  int32_t max_tile_nel = 0, max_tile_nodes = 0, max_tile_bytes = 0;
+  int32_t max_tile_nel = 0, max_tile_nodes = 0, max_tile_front = 0, max_tile_back = 0, max_tile_nl = 0;
   int ent_bytes = 2;     // 2 or 4: contribution entry width in the tile blocks
   int min_ent_bytes = 2; // batches may ask for the wider entries
   int debug_starve = 0;  // test knob: the first CTA skips its first metadata copy (bounded wait runs out)

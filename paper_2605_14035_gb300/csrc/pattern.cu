@@ -436,13 +436,10 @@ static lfem_status dalloc(T** p, int64_t n) {
     if (_s != LFEM_OK) return _s;       \
   } while (0)
 
-// Distinct nodes of each tile's elements (sorted), and the tile's block size.
-__global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ tile_row0,
-                             const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ inc_ptr,
-                             const int32_t* __restrict__ tile_elem_ptr, const int32_t* __restrict__ tile_elem,
-                             int entb, const int32_t* __restrict__ nl_in, const int32_t* __restrict__ nle_in,
-                             int32_t* __restrict__ tmp_nodes, int32_t* __restrict__ n_nodes_out,
-                             int64_t* __restrict__ bytes_out) {
+// Distinct nodes of each tile's elements (sorted).
+__global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const int32_t* __restrict__ tile_elem_ptr,
+                             const int32_t* __restrict__ tile_elem, int32_t* __restrict__ tmp_nodes,
+                             int32_t* __restrict__ n_nodes_out) {
   extern __shared__ int32_t sn[];
   __shared__ int32_t wsum[32];
   const int t = blockIdx.x;
@@ -481,12 +478,68 @@ __global__ void k_tile_nodes(const int32_t* __restrict__ conn, int ref, const in
   int32_t* out = tmp_nodes + (int64_t)e0 * ref;
   for (int i = beg; i < end; ++i)
     if (i == 0 || sn[i] != sn[i - 1]) out[excl++] = sn[i];
-  if (threadIdx.x == 0) {
-    const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
-    const int ns = (int)(row_ptr[r1] - row_ptr[r0]);
-    n_nodes_out[t] = total;
-    bytes_out[t] = tile_layout(nel, ns, nl_in[t], nle_in[t], total, ref, entb).total;
+  if (threadIdx.x == 0) n_nodes_out[t] = total;
+}
+
+// Node buffer of each tile (one thread per tile, a serial pass over its sorted
+// node list): runs of consecutive node ids, with gaps of up to kRunGap nodes
+// copied along, each run widened to even first node and even count (a 16-byte
+// aligned bulk copy of 2- or 3-component double coordinates); a run that
+// would end past the mesh's last node N-1 stops one short and N-1 becomes an
+// extra, copied on its own.  Per distinct node its buffer position; per tile
+// the counts and the block's part sizes.
+__global__ void k_tile_runs(const int32_t* __restrict__ tmp_nodes, const int32_t* __restrict__ n_nodes,
+                            const int32_t* __restrict__ tile_elem_ptr, int ref, int32_t N,
+                            const int32_t* __restrict__ tile_row0, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ nl_in, const int32_t* __restrict__ nle_in, int entb, int64_t T,
+                            int4* __restrict__ runs_tmp, int2* __restrict__ extras_tmp, int32_t* __restrict__ pos_tmp,
+                            int32_t* __restrict__ nruns_out, int32_t* __restrict__ nextra_out,
+                            int32_t* __restrict__ nbuf_out, int64_t* __restrict__ bytes_out,
+                            int32_t* __restrict__ front_out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const int64_t base = (int64_t)tile_elem_ptr[t] * ref;
+  const int32_t* tn = tmp_nodes + base;
+  int32_t* pos = pos_tmp + base;
+  int4* runs = runs_tmp + base;
+  int2* extras = extras_tmp + base;
+  const int nn = n_nodes[t];
+  int nr = 0, nx = 0, P = 0;
+  int x_node = -1, x_idx = -1;  // at most one extra: node N - 1
+  int i = 0;
+  while (i < nn) {
+    const int a = tn[i] & ~1;
+    int end = tn[i] + 1, j = i + 1;
+    while (j < nn && tn[j] - end <= kRunGap) end = tn[j++] + 1;
+    int b = (end + 1) & ~1;
+    if (b > N) b -= 2;  // end == N, N odd: N - 1 is left out of the run
+    if (b > a) {
+      runs[nr++] = make_int4(a, b - a, P, 0);
+      for (int k = i; k < j; ++k)
+        if (tn[k] < b) pos[k] = P + (tn[k] - a);
+      P += b - a;
+    }
+    for (int k = i; k < j; ++k)
+      if (tn[k] >= b) {
+        x_node = tn[k];
+        x_idx = k;
+      }
+    i = j;
   }
+  if (x_idx >= 0) {
+    extras[nx++] = make_int2(x_node, P);
+    pos[x_idx] = P;
+  }
+  const int nbuf = P + nx;
+  nruns_out[t] = nr;
+  nextra_out[t] = nx;
+  nbuf_out[t] = nbuf;
+  const int32_t nel = tile_elem_ptr[t + 1] - tile_elem_ptr[t];
+  const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
+  const int ns = (int)(row_ptr[r1] - row_ptr[r0]);
+  const TileLayout L = tile_layout(nel, ns, nl_in[t], nle_in[t], nbuf, ref, entb, (int)(row_ptr[r0] & 3), nr, nx);
+  bytes_out[t] = L.front + L.back;
+  front_out[t] = L.front;
 }
 
 // Contributions of slot j of a row: local pairs (incidence k, node b) of the
@@ -542,27 +595,40 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
                             const int32_t* __restrict__ tile_elem_ptr, const int32_t* __restrict__ tile_elem,
                             const int32_t* __restrict__ tmp_nodes, const int32_t* __restrict__ n_nodes,
                             const int32_t* __restrict__ nl_in, const int32_t* __restrict__ nle_in,
-                            const int64_t* __restrict__ off, int entb, uint8_t* __restrict__ meta) {
+                            const int64_t* __restrict__ off, int entb, uint8_t* __restrict__ meta,
+                            const int4* __restrict__ runs_tmp, const int2* __restrict__ extras_tmp,
+                            const int32_t* __restrict__ pos_tmp, const int32_t* __restrict__ nruns_in,
+                            const int32_t* __restrict__ nextra_in, const int32_t* __restrict__ nbuf_in) {
   __shared__ int s_nl, s_nle;
   const int t = blockIdx.x;
   const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
   const int32_t i0 = inc_ptr[r0];
   const int nrows = r1 - r0;
-  const int nent = (inc_ptr[r1] - i0) * ref;
   const int32_t e0 = tile_elem_ptr[t];
   const int nel = tile_elem_ptr[t + 1] - e0;
-  const int nn = n_nodes[t];
+  const int nn = n_nodes[t];                                // distinct nodes
+  const int nbuf = nbuf_in[t], nr = nruns_in[t], nx = nextra_in[t];  // node-buffer positions, runs, extras
   const int64_t s0 = row_ptr[r0];
   const int ns = (int)(row_ptr[r1] - s0);
-  // entries address local matrices of row stride lsm_stride(U) (U rounded up to even)
+  // entries address the interleaved local-matrix layout (see TileHdr):
+  // word(e, u) = 6 (e UP/2 + u/2) + (u mod 2); long results from LB; zeros at ZERO
   const int U = ref * (ref + 1) / 2;
-  const int UP = U + (U & 1);
+  const int UP = lsm_stride(U);
   const int ps = pos_stride(ref);
   uint8_t* blk = meta + off[t];
   const int nl_t = nl_in[t], nle_t = nle_in[t];
-  const TileLayout L = tile_layout(nel, ns, nl_t, nle_t, nn, ref, entb);
-  for (int i = threadIdx.x; i < L.total / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(blk)[i] = 0u;
+  const int apad = (int)(s0 & 3);
+  const TileLayout L = tile_layout(nel, ns, nl_t, nle_t, nbuf, ref, entb, apad, nr, nx);
+  const uint32_t LB = (uint32_t)(kLsmSlots * nel * UP), ZERO = LB + 6u * (uint32_t)nl_t;
+  auto word = [&](int loc, int u) -> uint32_t { return 6u * (uint32_t)(loc * (UP / 2) + (u >> 1)) + (uint32_t)(u & 1); };
+  for (int i = threadIdx.x; i < (L.front + L.back) / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(blk)[i] = 0u;
   if (threadIdx.x == 0) s_nl = s_nle = 0;
+  __syncthreads();
+  uint8_t* bk = blk + L.front;
+  for (int i = threadIdx.x; i < 2 * L.npad; i += blockDim.x) {
+    if (entb == 2) reinterpret_cast<uint16_t*>(bk + L.pair)[i] = (uint16_t)ZERO;
+    else reinterpret_cast<uint32_t*>(bk + L.pair)[i] = ZERO;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     TileHdr h;
@@ -570,23 +636,38 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
     h.r0 = r0;
     h.nrows = nrows;
     h.ns = ns;
-    h.nent = nent;
+    h.nruns = nr;
     h.nel = nel;
-    h.nnodes = nn;
+    h.nnodes = nbuf;
     h.nl = nl_t;
     h.nle = nle_t;
-    h.pad[0] = h.pad[1] = 0;
+    h.apad = apad;
+    h.nextra = nx;
     *reinterpret_cast<TileHdr*>(blk) = h;
   }
   int32_t* el = reinterpret_cast<int32_t*>(blk + L.elem);
   int32_t* nd = reinterpret_cast<int32_t*>(blk + L.nodes);
   uint16_t* en = reinterpret_cast<uint16_t*>(blk + L.enodes);
-  uint8_t* pr = blk + L.pair;
-  int4* lrec = reinterpret_cast<int4*>(blk + L.lrec);
-  uint8_t* lent = blk + L.lent;
+  uint8_t* pr = bk + L.pair;
+  int4* lrec = reinterpret_cast<int4*>(bk + L.lrec);
+  uint8_t* lent = bk + L.lent;
   for (int i = threadIdx.x; i < nel; i += blockDim.x) el[i] = tile_elem[e0 + i];
   const int32_t* tn = tmp_nodes + (int64_t)e0 * ref;
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) nd[i] = tn[i];
+  const int32_t* tpos = pos_tmp + (int64_t)e0 * ref;
+  const int4* truns = runs_tmp + (int64_t)e0 * ref;
+  const int2* textra = extras_tmp + (int64_t)e0 * ref;
+  int4* runs = reinterpret_cast<int4*>(blk + L.runs);
+  int2* extras = reinterpret_cast<int2*>(blk + L.extras);
+  // global node id of every buffer position, the runs and the extras
+  for (int r = 0; r < nr; ++r) {
+    const int4 q = truns[r];
+    for (int j = threadIdx.x; j < q.y; j += blockDim.x) nd[q.z + j] = q.x + j;
+  }
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) runs[r] = truns[r];
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    extras[x] = textra[x];
+    nd[textra[x].y] = textra[x].x;
+  }
   for (int i = threadIdx.x; i < nel * ref; i += blockDim.x) {
     const int32_t v = conn[(int64_t)tile_elem[e0 + i / ref] * ref + (i % ref)];
     int lo = 0, hi = nn;
@@ -595,9 +676,8 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
       if (tn[mid] < v) lo = mid + 1;
       else hi = mid;
     }
-    en[i] = (uint16_t)lo;
+    en[i] = (uint16_t)tpos[lo];
   }
-  const uint32_t NONE = entb == 2 ? 0xFFFFu : 0xFFFFFFFFu;
   auto put = [&](uint8_t* base, int64_t i, uint32_t v) {
     if (entb == 2) reinterpret_cast<uint16_t*>(base)[i] = (uint16_t)v;
     else reinterpret_cast<uint32_t*>(base)[i] = v;
@@ -612,15 +692,15 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
     for (int j = 0; j < len; ++j) {
       const int c = slot_count(inc_pos, ps, ref, kb, ke, j);
       const int slot = slot0 + j;
+      const int pp = slot + apad;  // padded slot
       int w = 0, lbeg = 0;
       if (c > 2) {
         const int li = atomicAdd(&s_nl, 1);
         lbeg = atomicAdd(&s_nle, c);
-        if (li < nl_t && lbeg + c <= nle_t) lrec[li] = make_int4(slot, lbeg, lbeg + c, 0);
-        put(pr, 2ll * slot, NONE);
-        put(pr, 2ll * slot + 1, NONE);
-      } else {
-        put(pr, 2ll * slot + 1, NONE);
+        if (li < nl_t && lbeg + c <= nle_t) {
+          lrec[li] = make_int4(slot, lbeg, lbeg + c, li);
+          put(pr, 2ll * pp, LB + 6u * (uint32_t)li);  // the long result; second entry stays ZERO
+        }
       }
       for (int k = kb; k < ke; ++k) {
         const int lk = inc_local[k];
@@ -628,11 +708,11 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
         for (int b = 0; b < ref; ++b) {
           if ((int)inc_pos[(int64_t)k * ps + b] != j) continue;
           const int u = a <= b ? a * ref - a * (a - 1) / 2 + (b - a) : b * ref - b * (b - 1) / 2 + (a - b);
-          const uint32_t ent = (uint32_t)loc * (uint32_t)UP + (uint32_t)u;
+          const uint32_t ent = word(loc, u);
           if (c > 2) {
             if (lbeg + w < nle_t) put(lent, lbeg + w, ent);
           } else {
-            put(pr, 2ll * slot + w, ent);
+            put(pr, 2ll * pp + w, ent);
           }
           ++w;
         }
@@ -649,6 +729,21 @@ __global__ void k_max_i64(const int64_t* __restrict__ a, int64_t n, int64_t* __r
   if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)out, (unsigned long long)m);
 }
 
+// Work-item records of a pattern's tiles: block address and part sizes.
+__global__ void k_tile_refs(uint8_t* meta, const int64_t* __restrict__ off, const int64_t* __restrict__ bytes,
+                            const int32_t* __restrict__ front, int64_t T, ItemRef* __restrict__ refs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  ItemRef r;
+  r.front = meta + off[t];
+  r.front_bytes = front[t];
+  r.back_bytes = (int32_t)(bytes[t] - front[t]);
+  r.mesh = 0;
+  r.tile = (int32_t)t;
+  r.pad[0] = r.pad[1] = 0;
+  refs[t] = r;
+}
+
 // Build the per-tile metadata blocks from the tile lists.
 static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   PatternDev& d = p->d;
@@ -656,29 +751,36 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
   const int ref = p->ref;
   if (d.tile_meta) cudaFree(d.tile_meta);
   if (d.tile_meta_off) cudaFree(d.tile_meta_off);
+  if (d.tile_refs) cudaFree(d.tile_refs);
   d.tile_meta = nullptr;
   d.tile_meta_off = nullptr;
-  // largest element count per tile decides the contribution entry width
+  d.tile_refs = nullptr;
   std::vector<int32_t> hep(T + 1);
   LFEM_CUDA(cudaMemcpyAsync(hep.data(), d.tile_elem_ptr, sizeof(int32_t) * (T + 1), cudaMemcpyDeviceToHost, st));
   LFEM_CUDA(cudaStreamSynchronize(st));
   int32_t mnel = 0;
   for (int64_t t = 0; t < T; ++t) mnel = std::max(mnel, hep[t + 1] - hep[t]);
-  // entries are local-matrix word offsets e * U + u
-  // (all ones marks an absent entry, so two-byte entries stay below 0xFFFF)
-  const int ulsm = ref * (ref + 1) / 2 + ((ref * (ref + 1) / 2) & 1);  // local-matrix row stride (even)
-  const int entb = std::max((int64_t)mnel * ulsm < 65535 ? 2 : 4, p->min_ent_bytes);
-  int32_t *tmp_nodes = nullptr, *nn = nullptr, *nl = nullptr, *nle = nullptr;
-  int64_t *bytes = nullptr, *scr = nullptr, *mx = nullptr;
+  int32_t *tmp_nodes = nullptr, *nn = nullptr, *nl = nullptr, *nle = nullptr, *front = nullptr;
+  int32_t *pos_tmp = nullptr, *nruns = nullptr, *nextra = nullptr, *nbuf = nullptr;
+  int4* runs_tmp = nullptr;
+  int2* extras_tmp = nullptr;
+  int64_t *bytes = nullptr, *scr = nullptr;
   TRY(dalloc(&tmp_nodes, p->tile_elems_total * ref));
+  TRY(dalloc(&pos_tmp, p->tile_elems_total * ref));
+  TRY(dalloc(&runs_tmp, p->tile_elems_total * ref));
+  TRY(dalloc(&extras_tmp, p->tile_elems_total * ref));
+  TRY(dalloc(&nruns, T + 1));
+  TRY(dalloc(&nextra, T + 1));
+  TRY(dalloc(&nbuf, T + 1));
   TRY(dalloc(&nn, T + 1));
   TRY(dalloc(&nl, T + 1));
   TRY(dalloc(&nle, T + 1));
+  TRY(dalloc(&front, T + 1));
   TRY(dalloc(&bytes, T + 1));
-  TRY(dalloc(&mx, 4));
   TRY(dalloc(&scr, scan_scratch_bytes(T, 8) / 8));
   TRY(dalloc(&d.tile_meta_off, T + 1));
-  LFEM_CUDA(cudaMemsetAsync(mx, 0, 4 * sizeof(int64_t), st));
+  TRY(dalloc(&d.tile_refs, T));
+  std::vector<int32_t> hnl(T);
   if (T > 0) {
     if (p->pos_bytes == 1)
       k_tile_long<uint8_t><<<(unsigned)T, 128, 0, st>>>(ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.inc_pos, nl, nle);
@@ -686,49 +788,78 @@ static lfem_status build_tile_blocks(lfem_pattern_s* p, cudaStream_t st) {
       k_tile_long<uint16_t><<<(unsigned)T, 128, 0, st>>>(ref, d.tile_row0, d.row_ptr, d.inc_ptr,
                                                           (const uint16_t*)d.inc_pos, nl, nle);
     LFEM_CUDA(cudaGetLastError());
+    LFEM_CUDA(cudaMemcpyAsync(hnl.data(), nl, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, st));
+    LFEM_CUDA(cudaStreamSynchronize(st));
+  }
+  int32_t mnl = 0;
+  for (int64_t t = 0; t < T; ++t) mnl = std::max(mnl, hnl[t]);
+  // entries are words of the interleaved local-matrix layout; the largest is
+  // the last zero word, 3 nel UP + 6 nl + 5
+  const int64_t max_word = (int64_t)kLsmSlots * mnel * lsm_stride(n_upper(ref)) + 6ll * mnl + 5;
+  const int entb = std::max(max_word <= 65535 ? 2 : 4, p->min_ent_bytes);
+  if (T > 0) {
     const size_t smem = sizeof(int32_t) * kMaxTileEntries;
     LFEM_CUDA(cudaFuncSetAttribute(k_tile_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tile_nodes<<<(unsigned)T, 512, smem, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.tile_elem_ptr,
-                                                 d.tile_elem, entb, nl, nle, tmp_nodes, nn, bytes);
+    k_tile_nodes<<<(unsigned)T, 512, smem, st>>>(d.conn, ref, d.tile_elem_ptr, d.tile_elem, tmp_nodes, nn);
+    LFEM_CUDA(cudaGetLastError());
+    k_tile_runs<<<grid_for(T, 128), 128, 0, st>>>(tmp_nodes, nn, d.tile_elem_ptr, ref, p->n_nodes, d.tile_row0,
+                                                  d.row_ptr, nl, nle, entb, T, runs_tmp, extras_tmp, pos_tmp, nruns,
+                                                  nextra, nbuf, bytes, front);
     LFEM_CUDA(cudaGetLastError());
   }
   scan_exclusive<int64_t, int64_t>(bytes, d.tile_meta_off, T, scr, st);
-  if (T > 0) {
-    k_max_i64<<<grid_for(T, 256), 256, 0, st>>>(bytes, T, mx);
-    LFEM_CUDA(cudaGetLastError());
-  }
-  int64_t total = 0, hmax[1] = {0};
+  int64_t total = 0;
+  std::vector<int64_t> hbytes(T);
+  std::vector<int32_t> hfront(T), hnn(T);
   LFEM_CUDA(cudaMemcpyAsync(&total, d.tile_meta_off + T, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  LFEM_CUDA(cudaMemcpyAsync(hmax, mx, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  if (T > 0) {
+    LFEM_CUDA(cudaMemcpyAsync(hbytes.data(), bytes, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, st));
+    LFEM_CUDA(cudaMemcpyAsync(hfront.data(), front, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, st));
+    LFEM_CUDA(cudaMemcpyAsync(hnn.data(), nbuf, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, st));
+  }
   LFEM_CUDA(cudaStreamSynchronize(st));
   TRY(dalloc(&d.tile_meta, total));
   if (T > 0) {
     if (p->pos_bytes == 1)
       k_tile_fill<uint8_t><<<(unsigned)T, 128, 0, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr, d.inc_local,
                                                          d.inc_pos, d.tile_elem_ptr, d.tile_elem, tmp_nodes, nn,
-                                                         nl, nle, d.tile_meta_off, entb, d.tile_meta);
+                                                         nl, nle, d.tile_meta_off, entb, d.tile_meta, runs_tmp,
+                                                         extras_tmp, pos_tmp, nruns, nextra, nbuf);
     else
       k_tile_fill<uint16_t><<<(unsigned)T, 128, 0, st>>>(d.conn, ref, d.tile_row0, d.row_ptr, d.inc_ptr,
                                                           d.inc_local, (const uint16_t*)d.inc_pos, d.tile_elem_ptr,
                                                           d.tile_elem, tmp_nodes, nn, nl, nle, d.tile_meta_off, entb,
-                                                          d.tile_meta);
+                                                          d.tile_meta, runs_tmp, extras_tmp, pos_tmp, nruns, nextra,
+                                                          nbuf);
+    LFEM_CUDA(cudaGetLastError());
+    k_tile_refs<<<grid_for(T, 256), 256, 0, st>>>(d.tile_meta, d.tile_meta_off, bytes, front, T, d.tile_refs);
     LFEM_CUDA(cudaGetLastError());
   }
-  std::vector<int32_t> hnn(T);
-  LFEM_CUDA(cudaMemcpyAsync(hnn.data(), nn, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, st));
-  LFEM_CUDA(cudaStreamSynchronize(st));
-  int32_t mnn = 0;
-  for (int64_t t = 0; t < T; ++t) mnn = std::max(mnn, hnn[t]);
+  int32_t mnn = 0, mfront = 0, mback = 0;
+  for (int64_t t = 0; t < T; ++t) {
+    mnn = std::max(mnn, hnn[t]);
+    mfront = std::max(mfront, hfront[t]);
+    mback = std::max(mback, (int32_t)(hbytes[t] - hfront[t]));
+  }
   p->max_tile_nel = mnel;
   p->max_tile_nodes = mnn;
-  p->max_tile_bytes = (int32_t)hmax[0];
+  p->max_tile_front = mfront;
+  p->max_tile_back = mback;
+  p->max_tile_nl = mnl;
   p->ent_bytes = entb;
+  LFEM_CUDA(cudaStreamSynchronize(st));
   cudaFree(tmp_nodes);
+  cudaFree(pos_tmp);
+  cudaFree(runs_tmp);
+  cudaFree(extras_tmp);
+  cudaFree(nruns);
+  cudaFree(nextra);
+  cudaFree(nbuf);
   cudaFree(nn);
   cudaFree(nl);
   cudaFree(nle);
+  cudaFree(front);
   cudaFree(bytes);
-  cudaFree(mx);
   cudaFree(scr);
   return LFEM_OK;
 }

@@ -77,6 +77,32 @@ def test_mixed_values(name, lfem):
     assert abs(out["M"].double().sum().item() - M.sum()) <= MIXED_TOL * abs(M.sum())
 
 
+@pytest.mark.parametrize("name", ["perturbed_sphere_p2", "disk_p1", "curve_p2"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_unaligned_buffers(name, prec, lfem):
+    """Coordinates 8 bytes and outputs one value off a 16-byte boundary: node
+    coordinates then arrive by per-node gathers instead of bulk copies and
+    phase 2 stores value by value; the result is the aligned one, bit for bit,
+    and within the tolerance of the oracle."""
+    x, e, d, p, rule, coef, pat = prepare(name, lfem)
+    orp, oci, M, A, C = oracle.assemble(x, e, d, p, rule.xi, rule.w, coef)
+    dt = torch.float64 if prec == 0 else torch.float32
+    cd = to_dev(coef).to(dt)
+    ref = lfem.assemble(pat, to_dev(x), rule, cd, which=7, precision=prec)
+    flat = torch.zeros(x.size + 1, dtype=torch.float64, device="cuda")
+    xu = flat[1:].view(x.shape)
+    xu.copy_(to_dev(x))
+    assert xu.data_ptr() % 16 == 8
+    outs = {k: torch.full((pat.nnz + 1,), -1.0, dtype=dt, device="cuda")[1:] for k in ("M", "A", "MC")}
+    got = lfem.assemble(pat, xu, rule, cd, which=7, precision=prec, out=outs)
+    torch.cuda.synchronize()
+    tol = FP64_TOL if prec == 0 else MIXED_TOL
+    for k, r in (("M", M), ("A", A), ("MC", C)):
+        assert torch.equal(got[k], ref[k]), k
+        assert diag_scaled_error(got[k].double().cpu().numpy(), r, orp, oci) <= tol, k
+    pat.sync_status()
+
+
 @pytest.mark.parametrize("name", ["perturbed_sphere_p2", "cube_p2", "cube_p1", "cube_p3"])
 def test_mixed_conditioning_threshold(name, lfem):
     """kappa_max = 1 sends every element (metric quality < 1) to the double
