@@ -19,7 +19,8 @@
 //
 // Per tile (Sec. 3.2 / 3.3 of the paper; Eqs. reference_quadrature_mass,
 // reference_quadrature_stiffness, M matrix, A matrix):
-//   split    node coordinates -> float pairs (mixed) once per node
+//   split    node coordinates -> float pairs (mixed) once per node, done for
+//            item k+1 at the end of item k (no barrier of its own)
 //   phase 1  geometry and local upper-triangle matrices of every element of
 //            the tile -> shared memory (interleaved layout: one address per
 //            entry serves M, A and MC)
@@ -95,11 +96,14 @@ struct PipeArgs {
   float qmin;
   int32_t* status;
   unsigned long long* fallback;
+  unsigned int* next_item;  // tile tickets (0 at launch): items past the first gridDim.x
+                                  // go to whichever CTA asks first
   int starve;         // test knob: CTA 0 skips its first front copy
   long long wait_ns;  // bound of every wait
 };
 
-// Local-matrix words of a tile with nel elements of upper size u and nl long slots.
+// Local-matrix words of a tile with nel elements of upper size u and nl long
+// slots: the elements, six result words per long slot, six zero words.
 __host__ __device__ constexpr int64_t lsm_words(int64_t nel, int u, int64_t nl) {
   return (int64_t)kLsmSlots * nel * lsm_stride(u) + 6 * (nl + 1);
 }
@@ -360,12 +364,13 @@ __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R
   }
 }
 
-// Node coordinates of a tile into its node buffer, issued by one warp: with a
-// 16-byte aligned coordinate array every run is one TMA bulk copy (lane r
-// issues run r; lane 0 first posts the total byte count on the mbarrier) and
-// the extras are cp.async gathers; otherwise every position is gathered by
-// cp.async and the mbarrier phase completes by a plain arrival (those copies
-// are then waited for with cp.async.wait_group before the next barrier).
+// Node coordinates of a tile into its node buffer, by one warp.  With a
+// 16-byte aligned coordinate array lane 0 first posts the byte count of the
+// runs on the mbarrier, then every run is one TMA bulk copy (lane r issues
+// run r) and the extras are loaded and stored by the lanes; otherwise the
+// lanes load and store every position.  Lane 0 arrives on the mbarrier once
+// the lanes' own stores are done, so the phase completes when both the bulk
+// copies and the stores are in place.
 __device__ __forceinline__ void issue_node_copies(const MeshRec& mr, const uint8_t* front, double* dst, uint64_t* mb,
                                                   int lane) {
   const TileHdr h = *reinterpret_cast<const TileHdr*>(front);
@@ -378,7 +383,7 @@ __device__ __forceinline__ void issue_node_copies(const MeshRec& mr, const uint8
     for (int r = lane; r < h.nruns; r += 32) bytes += (uint32_t)runs[r].y * (uint32_t)na * 8u;
     for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
     if (lane == 0)
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb)), "r"(bytes)
+      asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb)), "r"(bytes)
                    : "memory");
     __syncwarp();
     for (int r = lane; r < h.nruns; r += 32) {
@@ -391,21 +396,38 @@ __device__ __forceinline__ void issue_node_copies(const MeshRec& mr, const uint8
     }
     for (int x = lane; x < h.nextra; x += 32) {
       const int2 e = extras[x];
-      for (int c = 0; c < na; ++c) cp_async8(dst + (size_t)e.y * na + c, mr.coords + (int64_t)e.x * na + c);
+      for (int c = 0; c < na; ++c) dst[(size_t)e.y * na + c] = __ldg(mr.coords + (int64_t)e.x * na + c);
     }
   } else {
     const int32_t* nd = reinterpret_cast<const int32_t*>(front + L.nodes);
     for (int v = lane; v < h.nnodes; v += 32)
-      for (int c = 0; c < na; ++c) cp_async8(dst + (size_t)v * na + c, mr.coords + (int64_t)nd[v] * na + c);
-    __syncwarp();
-    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mb)) : "memory");
+      for (int c = 0; c < na; ++c) dst[(size_t)v * na + c] = __ldg(mr.coords + (int64_t)nd[v] * na + c);
+  }
+  __threadfence_block();
+  __syncwarp();
+  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mb)) : "memory");
+}
+
+// Node coordinates of a tile -> (hi, lo) float pairs in place (float kernels;
+// nothing for the double kernels), by every thread.
+template <typename R>
+__device__ __forceinline__ void split_nodes(double* xd, int nvals) {
+  if constexpr (sizeof(R) == 4) {
+    for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+      float hi, lo;
+      bool ok = true;
+      split_f64(xd[i], hi, lo, ok);
+      if (!ok) hi = __int_as_float(0x7fc00000);  // out of float range: NaN forces the double path
+      reinterpret_cast<float2*>(xd)[i] = make_float2(hi, lo);
+    }
   }
 }
 
-// Everything done for one tile whose front part, node coordinates and
-// coefficients are in shared memory: split, phase 1 (+ the double fallback),
-// then -- once wait_back() says the back part has landed -- phase 2.  Returns
-// false if that wait ran out (nothing is written then).
+// Everything done for one tile whose front part, (split) node coordinates and
+// coefficients are in shared memory: the next items' copies (issue_next),
+// phase 1, then -- once wait_back() says the back part has landed -- the
+// double fallback (if any element was flagged) and phase 2.  Returns false if
+// that wait ran out (nothing is written then).
 template <int D, int NA, int P, bool FAST, typename R, typename EntT, typename IssueNext, typename WaitBack>
 __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& mr, const uint8_t* front,
                                              const uint8_t* back, double* xd, const void* coef_s, R* lsm,
@@ -429,18 +451,10 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
   const int4* t_lrec = reinterpret_cast<const int4*>(back + TL.lrec);
   const EntT* t_lent = reinterpret_cast<const EntT*>(back + TL.lent);
 
-  // (*nflag is 0 on entry)
-  // node coordinates -> (hi, lo) float pairs in place (mixed)
-  if constexpr (sizeof(R) == 4) {
-    for (int i = threadIdx.x; i < h.nnodes * NA; i += blockDim.x) {
-      float hi, lo;
-      bool ok = true;
-      split_f64(xd[i], hi, lo, ok);
-      if (!ok) hi = __int_as_float(0x7fc00000);  // out of float range: NaN forces the double path
-      reinterpret_cast<float2*>(xd)[i] = make_float2(hi, lo);
-    }
-    __syncthreads();
-  }
+  // (the node coordinates in xd are already split for the float kernels;
+  // *nflag is 0 on entry)
+  const int LB = kLsmSlots * h.nel * UP;  // long-slot results after the elements, then six zero words
+  if (threadIdx.x < 6) lsm[LB + 6 * h.nl + threadIdx.x] = (R)0;
   // the copies of the next items, issued while phase 1 runs
   issue_next();
 
@@ -499,57 +513,74 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
       }
     }
   }
+  // the back part (slot entries) must have landed; the barrier also
+  // publishes phase 1's local matrices and the flag count
+  if (!wait_back()) return false;
   if constexpr (sizeof(R) == 4) {
-    __syncthreads();
-    // rare path: double recomputation of flagged elements from global
-    // coordinates -- every requested matrix for an element that failed the
-    // finiteness test (2), the stiffness alone for one that failed only the
-    // conditioning test (1): mass-type matrices need s, not G^{-1}
-    // (a compacted list, so that whole warps work on it: the FP64 pipe costs
-    // the same for a warp instruction with few active lanes)
-    const int ia = (a.which & LFEM_MASS) ? 1 : 0;
-    const int nf = *nflag;
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-      const uint32_t v = flist[i];
-      const int j = (int)(v & 0x3FFFFFFFu), fl = (int)(v >> 30);
-      const unsigned fw = fl == 2 ? a.which : (a.which & LFEM_STIFF);
-      if (!fw) continue;
-      const uint16_t* en = t_en + (size_t)j * REF;
-      int32_t nd[REF];
+    const int nf = *nflag;  // the same in every thread after the barrier
+    if (nf > 0) {
+      // rare path: double recomputation of flagged elements from global
+      // coordinates -- every requested matrix for an element that failed the
+      // finiteness test (2), the stiffness alone for one that failed only the
+      // conditioning test (1): mass-type matrices need s, not G^{-1}
+      // (a compacted list, so that whole warps work on it: the FP64 pipe costs
+      // the same for a warp instruction with few active lanes)
+      const int ia = (a.which & LFEM_MASS) ? 1 : 0;
+      for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const uint32_t v = flist[i];
+        const int j = (int)(v & 0x3FFFFFFFu), fl = (int)(v >> 30);
+        const unsigned fw = fl == 2 ? a.which : (a.which & LFEM_STIFF);
+        if (!fw) continue;
+        const uint16_t* en = t_en + (size_t)j * REF;
+        int32_t nd[REF];
 #pragma unroll
-      for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
-      bool bad = false;
-      R* d = lsm + (size_t)j * EW;
-      element_fp64_lean<D, NA, P, float, true>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw, d,
-                                               0, bad, fl == 2 ? 0 : ia);
-      if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
-        atomicAdd(a.fallback, 1ull);
-        if (bad) atomicOr(a.status, ST_DEGENERATE);
+        for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
+        bool bad = false;
+        R* d = lsm + (size_t)j * EW;
+        element_fp64_lean<D, NA, P, float, true>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw,
+                                                 d, 0, bad, fl == 2 ? 0 : ia);
+        if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
+          atomicAdd(a.fallback, 1ull);
+          if (bad) atomicOr(a.status, ST_DEGENERATE);
+        }
       }
+      __syncthreads();
+      if (threadIdx.x == 0) *nflag = 0;  // every thread has read it; the next tile's phase 1 follows a barrier
     }
   }
-  // the back part (slot entries) must have landed; this also orders phase 1's
-  // shared-memory writes before phase 2's reads
-  if (!wait_back()) return false;
 
   // ---- phase 2a: slots with more than two contributions (vertex diagonals),
-  // summed in ascending (element, a, b) order with a compensated pair into the
-  // long-result words; the six zero words after them
-  const int LB = kLsmSlots * h.nel * UP;
-  if (threadIdx.x < 6) lsm[LB + 6 * h.nl + threadIdx.x] = (R)0;
-  if (threadIdx.x == 0) *nflag = 0;  // every thread has read it (fallback loop); the next tile's after a barrier
+  // one thread each, summed in ascending (element, a, b) order with a
+  // compensated pair into the long-result words; entries and values are
+  // loaded four at a time so that only the additions form a chain
   for (int j = threadIdx.x; j < h.nl; j += blockDim.x) {
     const int4 r = t_lrec[j];
-    uint32_t ent = t_lent[r.y];
     Acc c0, c1, c2;
-    acc_init(c0, lsm[ent]);
-    if (nm > 1) acc_init(c1, lsm[ent + 2]);
-    if (nm > 2) acc_init(c2, lsm[ent + 4]);
-    for (int k = r.y + 1; k < r.z; ++k) {
-      ent = t_lent[k];
-      acc_add(c0, lsm[ent]);
-      if (nm > 1) acc_add(c1, lsm[ent + 2]);
-      if (nm > 2) acc_add(c2, lsm[ent + 4]);
+    bool first = true;
+    for (int k0 = r.y; k0 < r.z; k0 += 4) {
+      uint32_t ent[4];
+      R v0[4], v1[4], v2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ent[i] = k0 + i < r.z ? (uint32_t)t_lent[k0 + i] : 0u;
+        v0[i] = lsm[ent[i]];
+        v1[i] = nm > 1 ? lsm[ent[i] + 2] : (R)0;
+        v2[i] = nm > 2 ? lsm[ent[i] + 4] : (R)0;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (k0 + i >= r.z) break;
+        if (first) {
+          acc_init(c0, v0[i]);
+          acc_init(c1, v1[i]);
+          acc_init(c2, v2[i]);
+          first = false;
+        } else {
+          acc_add(c0, v0[i]);
+          acc_add(c1, v1[i]);
+          acc_add(c2, v2[i]);
+        }
+      }
     }
     R* lr = lsm + LB + 6 * r.w;
     lr[0] = (R)acc_final(c0);
@@ -665,7 +696,11 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
   const int64_t G = gridDim.x;
   const int64_t i0 = blockIdx.x;
   if (i0 >= a.n_items) return;
-  auto exists = [&](int64_t k) { return i0 + k * G < a.n_items; };
+  // item index of the CTA's k-th work item in s_item[k & 3] (-1: none): the
+  // first is blockIdx.x, every later one a ticket drawn three items ahead
+  // (items past the first gridDim.x go to whichever CTA asks first)
+  int* s_item = reinterpret_cast<int*>(smem_raw + L.mbar + 80);
+  auto item_of = [&](int64_t k) -> int { return s_item[k & 3]; };
   // the copies are issued by the last warp (it has the fewest phase-1
   // elements), the whole-block ones by its last thread, the producer
   const bool pwarp = threadIdx.x >= blockDim.x - 32;
@@ -676,10 +711,42 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
   // mbarrier has at most one phase in flight
   uint32_t pend = 0, par = 0;
 
+  // producer: a ticket for the CTA's item k into s_item[k & 3] and its record
+  // into s_ref[k & 3] (cp.async, landed by the next cp.async wait); the ticket
+  // was drawn at the previous call, so the atomic's latency is not waited for
+  unsigned int tk = 0;
+  auto draw = [&](int64_t k) {
+    const int64_t idx = G + (int64_t)tk;
+    tk = atomicAdd(a.next_item, 1u);
+    const int it = idx < a.n_items ? (int)idx : -1;
+    s_item[k & 3] = it;
+    if (it >= 0) {
+      const ItemRef* src = a.items + it;
+      ItemRef* dst = s_ref + (k & 3);
+      cp_async16(dst, src);
+      cp_async16(reinterpret_cast<uint8_t*>(dst) + 16, reinterpret_cast<const uint8_t*>(src) + 16);
+    }
+  };
+  // a record is used only if its copies fit the buffers and meet the bulk
+  // copies' 16-byte rules; otherwise the producer flags it (s_bad, ST_ITEM),
+  // issues nothing, and the CTA stops at its next barrier
+  int* s_bad = reinterpret_cast<int*>(smem_raw + L.mbar + 72);
+  auto rec_ok = [&](const ItemRef& r) {
+    const bool ok = r.front != nullptr && ((reinterpret_cast<uintptr_t>(r.front) & 15) == 0) &&
+                    r.front_bytes >= (int)sizeof(TileHdr) && r.front_bytes <= a.cap_front &&
+                    (r.front_bytes & 15) == 0 && r.back_bytes >= 16 && r.back_bytes <= a.cap_back &&
+                    (r.back_bytes & 15) == 0 && (!a.meshes || r.mesh >= 0);
+    if (!ok) {
+      *s_bad = 1;
+      atomicOr(a.status, ST_ITEM);
+    }
+    return ok;
+  };
   // producer: mesh record of item k and the TMA copy of its front part into front buffer k % 3
   auto load_front = [&](int64_t k) {
     const int f = (int)(k % 3);
     const ItemRef& r = s_ref[k & 3];
+    if (!rec_ok(r)) return;
     s_rec[f] = a.meshes ? a.meshes[r.mesh] : a.one;
     tma_load_block(front_of(f), r.front, (uint32_t)r.front_bytes, &mbar[f]);
     pend |= 1u << f;
@@ -687,6 +754,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
   // producer: TMA copy of item k's back part into the back buffer
   auto load_back = [&](int64_t k) {
     const ItemRef& r = s_ref[k & 3];
+    if (!rec_ok(r)) return;
     tma_load_block(s_back, r.front + r.front_bytes, (uint32_t)r.back_bytes, &mbar[3]);
     pend |= 1u << 3;
   };
@@ -703,6 +771,13 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
     par ^= 1u << b;
     pend &= ~(1u << b);
   };
+  // item k+1's node coordinates: wait for them, split them (every thread)
+  auto nodes_ready = [&](int f, int b) -> bool {
+    if (!wait_one(4 + b)) return false;
+    const TileHdr h = *reinterpret_cast<const TileHdr*>(front_of(f));
+    split_nodes<R>(node_of(b), h.nnodes * s_rec[f].na);
+    return true;
+  };
   // a wait ran out: report it, give every copy still in flight one more
   // bounded wait (so that none lands in the shared memory of a later CTA), stop
   auto bail = [&]() {
@@ -718,16 +793,26 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
     for (int b = 0; b < 6; ++b) mbar_init(&mbar[b], 1);
     fence_mbar_init();
     *s_nflag = 0;
+    *s_bad = 0;
+    s_item[0] = (int)i0;
+    const ItemRef* src = a.items + i0;
+    cp_async16(s_ref, src);
+    cp_async16(reinterpret_cast<uint8_t*>(s_ref) + 16, reinterpret_cast<const uint8_t*>(src) + 16);
   }
-  // records of items 0, 1, 2
-  if (threadIdx.x < 3 && exists(threadIdx.x)) s_ref[threadIdx.x] = a.items[i0 + (int64_t)threadIdx.x * G];
+  if (producer) {
+    tk = atomicAdd(a.next_item, 1u);
+    draw(1);
+    draw(2);
+  }
+  cp_async_commit();  // (wait_group waits for committed groups only)
+  cp_async_wait_all();
   __syncthreads();
   if (producer) {
     if (!(a.starve && blockIdx.x == 0)) load_front(0);
-    if (exists(1)) load_front(1);
+    if (item_of(1) >= 0) load_front(1);
   }
   {
-    const bool ok = wait_one(0);
+    const bool ok = (*s_bad == 0) && wait_one(0);
     if (__syncthreads_or(!ok)) {
       bail();
       return;
@@ -738,18 +823,19 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
   if (pwarp) load_nodes(0, 0);
   issue_coef_gathers(s_rec[0], want_coef, front_of(0), coef_of(0));
   cp_async_commit();
+  bool carry = nodes_ready(0, 0);
 
-  for (int64_t k = 0; exists(k); ++k) {
+  for (int64_t k = 0; item_of(k) >= 0; ++k) {
     const int f = (int)(k % 3), nb = (int)(k & 1);
-    const bool has1 = exists(k + 1);
+    const bool has1 = item_of(k + 1) >= 0;
     const int f1 = (int)((k + 1) % 3);
-    // item k's node coordinates and coefficients and item k+2's record have
-    // landed, item k+1's front part is here, item k-1 has left every buffer
-    // (one barrier)
+    // item k's node coordinates (split), coefficients and item k+3's record
+    // have landed, item k+1's front part is here, item k-1 has left every
+    // buffer (one barrier)
     cp_async_wait_all();
     {
-      bool ok = wait_one(4 + nb);
-      if (has1) ok = ok && wait_one(f1);
+      bool ok = carry && *s_bad == 0;
+      if (has1 && ok) ok = wait_one(f1);
       if (__syncthreads_or(!ok)) {
         bail();
         return;
@@ -757,18 +843,17 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
       passed(4 + nb);
       if (has1) passed(f1);
     }
-    // the copies for items k+1 .. k+3 (called by every thread once item k's
-    // split is done, so that their issue overlaps phase 1)
+    // the copies for items k+1 .. k+3 (called by every thread at the start of
+    // item k's phase 1, so that their issue overlaps it)
     auto issue_next = [&]() {
       if (producer) {
         fence_proxy_async();
         load_back(k);
-        if (exists(k + 2)) load_front(k + 2);
-        if (exists(k + 3)) {
-          const ItemRef* src = a.items + (i0 + (k + 3) * G);
-          ItemRef* dst = s_ref + ((k + 3) & 3);
-          cp_async16(dst, src);
-          cp_async16(reinterpret_cast<uint8_t*>(dst) + 16, reinterpret_cast<const uint8_t*>(src) + 16);
+        if (item_of(k + 2) >= 0) {
+          load_front(k + 2);
+          draw(k + 3);
+        } else {
+          s_item[(k + 3) & 3] = -1;
         }
       }
       if (has1) {
@@ -778,7 +863,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
       cp_async_commit();
     };
     auto wait_back = [&]() -> bool {
-      const bool ok = wait_one(3);
+      const bool ok = *s_bad == 0 && wait_one(3);
       if (__syncthreads_or(!ok)) return false;
       passed(3);
       return true;
@@ -789,6 +874,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
       bail();
       return;
     }
+    carry = has1 ? nodes_ready(f1, nb ^ 1) : true;
   }
   cp_async_wait_all();
 }
@@ -796,6 +882,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
 template <typename R, typename EntT, typename... Types>
 lfem_status launch_pipe_types(const PipeArgs& a, const FastBank& fb, int sm_count, cudaStream_t st) {
   if (a.n_items == 0) return LFEM_OK;
+  if (a.n_items >= 0x7FFFFFFF) return fail(LFEM_E_TOO_LARGE, "more than 2^31 - 1 tiles in one launch");
   const size_t smem = pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q,
                                           a.coef_smem)
                           .total;

@@ -39,7 +39,7 @@ struct lfem_batch_s {
   PipeArgs args{};
   MeshRec* d_meshes = nullptr;
   ItemRef* d_items = nullptr;
-  int32_t* d_status = nullptr;  // [0] status bits, [2..3] fallback count
+  int32_t* d_status = nullptr;  // [0] status bits, [2..3] fallback count, [4..5] tile tickets
   int ent_bytes = 2;
   int64_t n_elements = 0;
   FastBank fb{};  // compile-time-rule tables, one per (dim, order)
@@ -51,6 +51,7 @@ static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
   int sms = 0;
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   LFEM_CUDA(cudaMemsetAsync(b->d_status + 2, 0, sizeof(unsigned long long), st));
+  LFEM_CUDA(cudaMemsetAsync(b->d_status + 4, 0, sizeof(unsigned long long), st));  // tile tickets
   return b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, b->fb, sms, st)
                            : launch_batch<uint32_t>(b->args, b->fb, sms, st);
 }
@@ -166,7 +167,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
   };
   if (dev_malloc((void**)&b->d_meshes, sizeof(MeshRec) * n_items) != cudaSuccess ||
       dev_malloc((void**)&b->d_items, sizeof(ItemRef) * std::max<int64_t>(1, item_off[n_items])) != cudaSuccess ||
-      dev_malloc((void**)&b->d_status, 4 * sizeof(int32_t)) != cudaSuccess) {
+      dev_malloc((void**)&b->d_status, 6 * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return fail(LFEM_E_NOMEM, "batch allocation failed");
@@ -180,7 +181,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
                     cudaMemcpyDeviceToDevice, st);
     k_set_item_mesh<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b->d_items + item_off[i], n, i);
   }
-  cudaMemsetAsync(b->d_status, 0, 4 * sizeof(int32_t), st);
+  cudaMemsetAsync(b->d_status, 0, 6 * sizeof(int32_t), st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cleanup();
@@ -209,6 +210,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
   for (int i = 0; i < n_items; ++i) a.qmin = std::max(a.qmin, items[i].pattern->qmin);
   a.status = b->d_status;
   a.fallback = reinterpret_cast<unsigned long long*>(b->d_status + 2);
+  a.next_item = reinterpret_cast<unsigned int*>(b->d_status + 4);
   a.starve = 0;
   a.wait_ns = 2000000000ll;
   const size_t smem = pipe_smem_bytes<float>(a);
@@ -258,6 +260,7 @@ lfem_status lfem_batch_sync_status(lfem_batch_t b, void* cuda_stream) {
   LFEM_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int32_t), st));
   LFEM_CUDA(cudaStreamSynchronize(st));
   if (h & ST_TIMEOUT) return fail(LFEM_E_TIMEOUT, "a bounded device wait ran out");
+  if (h & ST_ITEM) return fail(LFEM_E_CUDA, "a work-item record failed its size or alignment check");
   if (h & ST_TYPE) return fail(LFEM_E_UNSUPPORTED, "a tile met a kernel without its element type");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
   return LFEM_OK;

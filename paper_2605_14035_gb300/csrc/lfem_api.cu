@@ -603,12 +603,14 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   pa.coef_smem = pa.coef_bytes;
   pa.qmin = a.qmin;
   pa.status = p->d.status;
+  pa.next_item = reinterpret_cast<unsigned int*>(p->d.status + 4);
   pa.fallback = a.fallback;
   pa.starve = p->debug_starve;
   pa.wait_ns = 2000000000ll;  // 2 s bound on every mbarrier wait
   int sms = 0;
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
+  LFEM_CUDA(cudaMemsetAsync(p->d.status + 4, 0, sizeof(unsigned long long), st));  // tile tickets
   // the usual rules run with compile-time quadrature (tables as kernel parameters)
   FastBank fb;
   bool fast = false;
@@ -738,6 +740,7 @@ lfem_status lfem_sync_status(lfem_pattern_t p, void* cuda_stream) {
   LFEM_CUDA(cudaMemsetAsync(p->d.status, 0, sizeof(int32_t), st));
   LFEM_CUDA(cudaStreamSynchronize(st));
   if (h & ST_TIMEOUT) return fail(LFEM_E_TIMEOUT, "a bounded device wait ran out");
+  if (h & ST_ITEM) return fail(LFEM_E_CUDA, "a work-item record failed its size or alignment check");
   if (h & ST_INDEX) return fail(LFEM_E_INDEX, "node index out of range");
   if (h & ST_TYPE) return fail(LFEM_E_UNSUPPORTED, "a tile met a kernel without its element type");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");

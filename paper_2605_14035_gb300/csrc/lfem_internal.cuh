@@ -28,7 +28,7 @@ cudaError_t dev_malloc(void** p, size_t bytes);
   } while (0)
 
 // Device status bits (pattern status word).
-enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2, ST_TIMEOUT = 4, ST_TYPE = 8 };
+enum : int32_t { ST_DEGENERATE = 1, ST_INDEX = 2, ST_TIMEOUT = 4, ST_TYPE = 8, ST_ITEM = 16 };
 
 // Tile limits.
 constexpr int kMaxTileIncidences = 4096;  // incidences (e, a) per tile; local index fits 12 bits
@@ -405,7 +405,7 @@ __device__ __forceinline__ void gather_coords(const double* __restrict__ coords,
 //                                    so that slot groups of four are 16-byte aligned in
 //                                    the output); npad = apad + ns rounded up to 4
 //     lrec     int4   [nl]           slots with more than two contributions:
-//                                    {slot, first, end, long index}
+//                                    {slot, first, end, long index li}
 //     lent     EntT   [nle]          their entries, each run in ascending (e, a, b)
 // every section starts on a 16-byte boundary; each part's size is a multiple of 16.
 //
@@ -424,8 +424,9 @@ struct TileHdr {
   int32_t nl, nle;  // slots with more than two contributions, and their entries
   int32_t apad;     // s0 mod 4: padded slot p = slot + apad
   int32_t nextra;
+  int32_t pad[4];
 };
-static_assert(sizeof(TileHdr) == 48, "tile header");
+static_assert(sizeof(TileHdr) == 64, "tile header");
 constexpr int kRunGap = 2;  // node-id gaps up to this length are copied inside a run
 
 __host__ __device__ constexpr int al16(int64_t b) { return (int)((b + 15) / 16 * 16); }

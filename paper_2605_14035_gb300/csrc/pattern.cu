@@ -611,7 +611,8 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
   const int64_t s0 = row_ptr[r0];
   const int ns = (int)(row_ptr[r1] - s0);
   // entries address the interleaved local-matrix layout (see TileHdr):
-  // word(e, u) = 6 (e UP/2 + u/2) + (u mod 2); long results from LB; zeros at ZERO
+  // word(e, u) = 6 (e UP/2 + u/2) + (u mod 2); a long slot's first entry is
+  // its result word LB + 6 li; zeros at ZERO
   const int U = ref * (ref + 1) / 2;
   const int UP = lsm_stride(U);
   const int ps = pos_stride(ref);
@@ -643,6 +644,7 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
     h.nle = nle_t;
     h.apad = apad;
     h.nextra = nx;
+    h.pad[0] = h.pad[1] = h.pad[2] = h.pad[3] = 0;
     *reinterpret_cast<TileHdr*>(blk) = h;
   }
   int32_t* el = reinterpret_cast<int32_t*>(blk + L.elem);
@@ -699,7 +701,7 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
         lbeg = atomicAdd(&s_nle, c);
         if (li < nl_t && lbeg + c <= nle_t) {
           lrec[li] = make_int4(slot, lbeg, lbeg + c, li);
-          put(pr, 2ll * pp, LB + 6u * (uint32_t)li);  // the long result; second entry stays ZERO
+          put(pr, 2ll * pp, LB + 6u * (uint32_t)li);  // second entry stays ZERO
         }
       }
       for (int k = kb; k < ke; ++k) {
@@ -931,8 +933,8 @@ lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_
   const int32_t N = p->n_nodes;
   const int64_t n_inc = nE * ref;
   p->n_inc = n_inc;
-  TRY(dalloc(&d.status, 4));
-  LFEM_CUDA(cudaMemsetAsync(d.status, 0, 4 * sizeof(int32_t), st));
+  TRY(dalloc(&d.status, 6));  // status bits, pad, fallback count (int64), tile ticket counter (int64)
+  LFEM_CUDA(cudaMemsetAsync(d.status, 0, 6 * sizeof(int32_t), st));
   TRY(dalloc(&d.conn, n_inc));
   if (n_inc > 0)
     LFEM_CUDA(cudaMemcpyAsync(d.conn, conn_in, sizeof(int32_t) * n_inc, cudaMemcpyDeviceToDevice, st));
