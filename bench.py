@@ -33,6 +33,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 256 << 20
+# FP64 path: algorithmic flops per P2 surface element with the 7-point rule
+# (M + A + MC; counted per quadrature point: Jacobian 36, metric 18, normal
+# and its norm 16, w s G^-1 and metric quality 12, mass-type products 96,
+# stiffness gradients 48 and products 84 -> 310; x 7 points, + 33 for the
+# corner edge vectors and edge-node deviations of the element)
+FP64_FLOPS_PER_ELEMENT = 7 * 310 + 33
+FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of one GB300
 WORKLOAD = "p2_perturbed_sphere_r8_M_A_MC"
 KERNEL = "k_assemble_pipe<float,u16,EType<2,3,2,fast>>"
 
@@ -54,7 +61,7 @@ def parse():
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-slots", type=int, default=0, help="fixed tile capacity (implies no autotuning)")
-    ap.add_argument("--batch-slots", default="2048,2560,3072", help="tile capacities the batch workload tries")
+    ap.add_argument("--no-batch", action="store_true", help="leave the 512-mesh batch out of the default line")
     return ap.parse_args()
 
 
@@ -261,8 +268,12 @@ def measured_traffic(kernel, workload):
     return None
 
 
-def oracle_sample(x, e, rule, n_elem):
-    """Time the oracle on the first n_elem elements (pattern of that sub-mesh built beforehand)."""
+def oracle_sample(x, e, rule, n_elem, threads=1, keep=False):
+    """Time the oracle on the first n_elem elements (pattern of that sub-mesh
+    built beforehand): the single-thread assembly (threads = 1) or the
+    all-core one (threads = 0: every thread OpenMP offers; bit-identical
+    results).  Returns the seconds, and with keep the oracle's
+    (row_ptr, col_idx, M, A, MC)."""
     import oracle
 
     sub = np.ascontiguousarray(e[:n_elem])
@@ -270,21 +281,73 @@ def oracle_sample(x, e, rule, n_elem):
     coef = coef_from_points(pts)
     pat = oracle.pattern(sub, x.shape[0])
     t0 = time.perf_counter()
-    oracle.assemble(x, sub, 2, 2, rule.xi, rule.w, coef, pat=pat)
+    if threads == 1:
+        res = oracle.assemble(x, sub, 2, 2, rule.xi, rule.w, coef, pat=pat)
+    else:
+        res = oracle.assemble_threads(x, sub, 2, 2, rule.xi, rule.w, coef, pat=pat, threads=threads)
     dt = time.perf_counter() - t0
-    return dt
+    return (dt, res) if keep else dt
+
+
+def host_description():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def diag_scaled(v, ref, rows, cols, n):
+    """max |v - ref| / sqrt(|ref_ii ref_jj|) over all entries (the tolerance metric)."""
+    d = np.zeros(n)
+    isd = rows == cols
+    d[rows[isd]] = np.abs(ref[isd])
+    den = np.sqrt(d[rows] * d[cols])
+    return float((np.abs(v - ref) / den).max())
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle as it stands, on bounded samples of the workload."""
+    """Reference arm: the FP64 CPU oracle as it stands, run on every host core
+    (its all-core assembly, bit-identical to the single-thread one), one
+    assembly of the whole workload mesh per step (pattern and coefficients
+    prepared once, outside the timed steps)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
+
     x, e, rule = make_inputs(args.level)
-    n = args.cpu_sample_elems or 200000
+    n = min(args.cpu_sample_elems or e.shape[0], e.shape[0])
+    sub = np.ascontiguousarray(e[:n])
+    coef = coef_from_points(oracle.eval_points(x, sub, 2, 2, rule.xi))
+    pat = oracle.pattern(sub, x.shape[0])
+    threads = oracle.max_threads()
+
+    def step():
+        oracle.assemble_threads(x, sub, 2, 2, rule.xi, rule.w, coef, pat=pat)
+
     for _ in range(args.warmup):
-        oracle_sample(x, e, rule, min(n, 2000))
-    times = [oracle_sample(x, e, rule, n) for _ in range(args.steps)]
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = n * args.steps / tot
     line = {
@@ -292,8 +355,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": int(e.shape[0]), "sample_elements_per_step": n},
-        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n} elements of the workload per step, M+A+MC, FP64, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{'all' if n == e.shape[0] else f'first {n}'} elements of the workload per step, "
+                                   f"M+A+MC, FP64, {threads} threads", "host": host_description()},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -319,17 +383,25 @@ def main():
     nE, N = e.shape[0], x.shape[0]
     xd = torch.from_numpy(x).to(dev)
     ed = torch.from_numpy(e).to(dev)
+    # the pattern (CSR, incidence maps and row tiles) is built once per topology: timed on its own
+    torch.cuda.synchronize()
+    t_pat = time.perf_counter()
     pat = lfem.Pattern(ed, N, 2, 2)
+    torch.cuda.synchronize()
+    pattern_ms = 1e3 * (time.perf_counter() - t_pat)
     pts = lfem.eval_points(ed, 2, 2, xd, rule)
     coef64 = coef_from_points(pts).contiguous()
     coef32 = coef64.float()
     del pts
     nnz = pat.nnz
     tuned = None
+    t_tune = time.perf_counter()
     if args.tile_slots:
         pat.retile(args.tile_slots)
     elif not args.no_autotune:
         tuned = lfem.autotune(pat, xd, rule, coef32, which=7, precision=lfem.MIXED)
+    torch.cuda.synchronize()
+    tune_ms = 1e3 * (time.perf_counter() - t_tune)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -385,8 +457,13 @@ def main():
     if not args.skip_fp64:
         tot64, per64 = timed(step_fp64, max(3, args.steps // 4), max(1, args.warmup // 2))
         k64 = max(3, args.steps // 4)
-        res["fp64"] = {"value": world * nE * k64 / (tot64 * 1e-3), "unit": "elements/s",
-                       "ms_per_step": tot64 / k64}
+        ms64 = tot64 / k64
+        gflops = FP64_FLOPS_PER_ELEMENT * nE / (ms64 * 1e-3) / 1e9
+        res["fp64"] = {"value": world * nE * k64 / (tot64 * 1e-3), "unit": "elements/s", "ms_per_step": ms64,
+                       "roofline": {"bound": "fp64 alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS,
+                                    "unit": "GFLOP/s", "frac": gflops / FP64_PEAK_GFLOPS,
+                                    "flops_per_element": FP64_FLOPS_PER_ELEMENT,
+                                    "peak_kind": "nominal GB300 FP64 (no measured FP64 peak)"}}
         # accuracy of the mixed path against the FP64 path on every entry (diagonal-scaled)
         rp, ci = pat.csr()
         rows = torch.repeat_interleave(torch.arange(N, device=dev), rp[1:] - rp[:-1])
@@ -476,11 +553,58 @@ def main():
     traffic = measured_traffic(KERNEL, f"{WORKLOAD}_tile{info['tile_slots']}")
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
         n_s = args.cpu_sample_elems or nE
-        dt = oracle_sample(x, e, rule, n_s)
-        cpu = {"value": n_s / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {n_s} elements of the workload, M+A+MC, FP64, single thread, {dt:.1f} s"}
+        # the oracle's values for the parity keys (all cores, bit-identical to one thread)
+        _, ores = oracle_sample(x, e, rule, n_s, threads=0, keep=True)
+        dt_one = oracle_sample(x, e, rule, min(n_s, 400000), threads=1)
+        n_one = min(n_s, 400000)
+        # the all-core timing in a process of its own (no torch runtime beside it): the reference arm
+        cpu = None
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "3",
+                                "--warmup", "1", "--level", str(args.level)] +
+                               (["--cpu-sample-elems", str(n_s)] if args.cpu_sample_elems else []),
+                               capture_output=True, text=True, timeout=600,
+                               env={k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE")})
+            ref_line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+            cpu = dict(ref_line["cpu_baseline"])
+            cpu["sample"] += f"; {ref_line['ms_per_step']:.0f} ms per assembly, after one warm-up, in a separate process"
+        except (subprocess.SubprocessError, OSError, ValueError, IndexError, KeyError) as ex:
+            cpu = {"value": None, "unit": "elements/s", "kind": "oracle", "error": str(ex)[:200]}
+        cpu["single_thread"] = {"value": n_one / dt_one, "unit": "elements/s", "cores": 1,
+                                "sample": f"first {n_one} elements, {dt_one:.2f} s, in the benchmark process"}
+        if n_s == nE:
+            # the benchmarked configuration against the oracle, entry by entry
+            orp, oci, oM, oA, oC = ores
+            rp, ci = pat.csr()
+            rp_h, ci_h = rp.cpu().numpy(), ci.cpu().numpy()
+            pattern_equal = bool(np.array_equal(rp_h, orp) and np.array_equal(ci_h, oci))
+            rows = np.repeat(np.arange(N), np.diff(orp))
+            cols = oci.astype(np.int64)
+            parity = {"pattern_equal": pattern_equal, "tolerance": {"fp64": 1e-12, "mixed": 1e-6},
+                      "metric": "max |v - v*| / sqrt(|v*_ii v*_jj|) over every entry, v* = FP64 oracle"}
+            if pattern_equal:
+                parity["mixed_vs_oracle"] = {k: diag_scaled(out_mixed[k].double().cpu().numpy(), r, rows, cols, N)
+                                             for k, r in (("M", oM), ("A", oA), ("MC", oC))}
+                if not args.skip_fp64:
+                    parity["fp64_vs_oracle"] = {k: diag_scaled(out_fp64[k].cpu().numpy(), r, rows, cols, N)
+                                                for k, r in (("M", oM), ("A", oA), ("MC", oC))}
+                parity["ok"] = all(v <= 1e-6 for v in parity["mixed_vs_oracle"].values()) and all(
+                    v <= 1e-12 for v in parity.get("fp64_vs_oracle", {}).values())
+            del rows, cols, ores
+
+    # the 512-mesh batch (mixed, M + A, tile capacities tuned by the library)
+    batch = None
+    if not args.no_batch:
+        import bench_extra
+
+        del out_fp64, out_mixed, outd, xin, cin, flush
+        torch.cuda.empty_cache()
+        batch = bench_extra.measure_batch(args)
 
     line = {
         "metric": "elements/s", "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
@@ -502,6 +626,10 @@ def main():
                 "serial": {"value": world * nE * k_e2e / (tot_e2e * 1e-3), "ms_per_step": tot_e2e / k_e2e}},
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "pattern_build_ms": pattern_ms,
+        "tile_tuning_ms": tune_ms,
+        "parity": parity,
+        "batch": batch,
         **res,
     }
     if rank == 0:

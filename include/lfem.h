@@ -232,6 +232,24 @@ lfem_status lfem_batch_sync_status(lfem_batch_t b, void* cuda_stream);
 lfem_status lfem_batch_info(lfem_batch_t b, int64_t* n_work_items, int64_t* n_elements, int32_t* cap_elements);
 void lfem_batch_destroy(lfem_batch_t b);
 
+/* Tile capacity of a batch's meshes, per element family (dim, order): the
+ * batch (the same items, which and coef_is_fp32 as lfem_batch_create) is
+ * launched with each candidate capacity of the P2 triangle meshes, then of the
+ * P1 triangles, the P2 curves and the P1 curves (each family's patterns
+ * retiled together, the others held), and every pattern is left at its
+ * family's fastest (the paper's batchwise processing, Remark "Batch
+ * computations", Sec. 3.3; tuned here by measurement).  best_slots (host
+ * int32[4], may be NULL): capacities of P1 curves, P2 curves, P1 triangles,
+ * P2 triangles (0 for a family the batch does not hold).  If cache_path is not NULL, the
+ * result is read from / appended to that text file, keyed by which, the
+ * (dim, ambient, order) counts, the element-count bucket and the GPU name.
+ * Create the batch after this call (a batch keeps the tile blocks it was
+ * created with); the outputs of the items are overwritten.  Synchronises the
+ * stream.  Errors: as lfem_batch_create; LFEM_E_TOO_LARGE if no candidate
+ * fits. */
+lfem_status lfem_batch_autotune(const lfem_batch_item* items, int n_items, unsigned which, int coef_is_fp32,
+                                const char* cache_path, void* cuda_stream, int32_t* best_slots);
+
 /* ---------------------------------------------------------------------------
  * Vector assembly on the pattern's node incidences, FP64, deterministic (each
  * element's local vector once, then every node sums its incidences in

@@ -13,6 +13,8 @@ from .oracle import (  # noqa: F401
     geometry,
     local_matrices,
     assemble,
+    assemble_threads,
+    max_threads,
     adjoint,
     load,
     kll,

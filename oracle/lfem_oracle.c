@@ -34,6 +34,7 @@
  *     metric G = J^T J, see oracle_adjoint.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -715,3 +716,97 @@ int oracle_kll(const double* coords, const int32_t* conn, int64_t nE, int64_t n_
 }
 
 int oracle_mutation_id(void) { return ORACLE_MUTATION; }
+
+/*
+ * The same global assembly on every host core (the timed CPU baseline), with
+ * the result bit-identical to oracle_assemble: elements are taken in chunks;
+ * the chunk's local matrices are computed element-parallel into a buffer,
+ * then each thread adds them row by row -- for a row i, its incident
+ * elements of the chunk in increasing e, for each the local rows a with
+ * conn[e][a] = i in increasing a, each local column b in increasing b -- so
+ * that every slot receives its contributions in the single-thread order
+ * (e, a, b), with the same Neumaier sums.  nthreads <= 0: all threads OpenMP
+ * offers.  Returns the codes of oracle_assemble, or 3 if out of memory.
+ */
+int oracle_assemble_threads(const double* coords, int n, const int32_t* conn, int64_t nE, int64_t n_nodes, int dim,
+                            int order, int nq, const double* xi, const double* w, const double* coef,
+                            const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, double* M, double* A,
+                            double* MC, int nthreads) {
+  int ref = n_ref(dim, order);
+  if (check_combo(dim, order, n)) return 1;
+  const int64_t chunk = 65536;
+  const int64_t rr = (int64_t)ref * ref;
+  double* acc = (double*)calloc((size_t)nnz * 6, sizeof(double));
+  double* loc = (double*)malloc(sizeof(double) * (size_t)(chunk < nE ? chunk : (nE > 0 ? nE : 1)) * rr * 3);
+  int64_t* inc_ptr = (int64_t*)calloc((size_t)n_nodes + 1, sizeof(int64_t));
+  int64_t* inc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nE * ref > 0 ? nE * ref : 1));
+  int64_t* fill = (int64_t*)calloc((size_t)n_nodes + 1, sizeof(int64_t));
+  int rc = 0;
+  if (!acc || !loc || !inc_ptr || !inc || !fill) rc = 3;
+  /* node -> incidences (e * ref + a), ascending in e then a: a counting sort */
+  if (!rc) {
+    for (int64_t k = 0; k < nE * ref; ++k) {
+      if (conn[k] < 0 || conn[k] >= n_nodes) {
+        rc = 2;
+        break;
+      }
+      ++inc_ptr[conn[k] + 1];
+    }
+  }
+  if (!rc) {
+    for (int64_t i = 0; i < n_nodes; ++i) inc_ptr[i + 1] += inc_ptr[i];
+    for (int64_t k = 0; k < nE * ref; ++k) inc[inc_ptr[conn[k]] + fill[conn[k]]++] = k;
+  }
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  /* per row, the next incidence not yet added */
+  for (int64_t i = 0; i < n_nodes && !rc; ++i) fill[i] = inc_ptr[i];
+  for (int64_t c0 = 0; c0 < nE && !rc; c0 += chunk) {
+    const int64_t c1 = c0 + chunk < nE ? c0 + chunk : nE;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = c0; e < c1; ++e) {
+      double X[MAXREF * MAXD];
+      double* Ml = loc + (e - c0) * rr * 3;
+      gather(coords, n, conn, ref, e, X);
+      local_matrices(dim, order, n, X, nq, xi, w, coef ? coef + e * nq : NULL, Ml, Ml + rr, Ml + 2 * rr);
+    }
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(| : bad)
+    for (int64_t i = 0; i < n_nodes; ++i) {
+      int64_t k = fill[i];
+      for (; k < inc_ptr[i + 1] && inc[k] / ref < c1; ++k) {
+        const int64_t e = inc[k] / ref;
+        const int a = (int)(inc[k] % ref);
+        const double* Ml = loc + (e - c0) * rr * 3;
+        for (int b = 0; b < ref; ++b) {
+          int64_t s = find_slot(row_ptr, col_idx, i, conn[e * ref + b]);
+          if (s < 0) {
+            bad = 1;
+            continue;
+          }
+          neumaier_add(&acc[6 * s + 0], &acc[6 * s + 1], Ml[a * ref + b]);
+          neumaier_add(&acc[6 * s + 2], &acc[6 * s + 3], Ml[rr + a * ref + b]);
+          neumaier_add(&acc[6 * s + 4], &acc[6 * s + 5], Ml[2 * rr + a * ref + b]);
+        }
+      }
+      fill[i] = k;
+    }
+    if (bad) rc = 2;
+  }
+  if (!rc) {
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < nnz; ++s) {
+      if (M) M[s] = acc[6 * s + 0] + acc[6 * s + 1];
+      if (A) A[s] = acc[6 * s + 2] + acc[6 * s + 3];
+      if (MC) MC[s] = acc[6 * s + 4] + acc[6 * s + 5];
+    }
+  }
+  free(acc);
+  free(loc);
+  free(inc_ptr);
+  free(inc);
+  free(fill);
+  return rc;
+}
+
+/* Threads the all-core assembly uses by default. */
+int oracle_max_threads(void) { return omp_get_max_threads(); }

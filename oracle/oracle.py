@@ -31,8 +31,8 @@ def build(mutation: int = 0, force: bool = False) -> str:
     path = _lib_path(mutation)
     if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
         tmp = f"{path}.{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", f"-DORACLE_MUTATION={mutation}",
-               _SRC, "-o", tmp, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-fopenmp",
+               f"-DORACLE_MUTATION={mutation}", _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, path)
     return path
@@ -51,11 +51,13 @@ def _lib(mutation: int = 0):
         lib.oracle_geometry.argtypes = [P, I, P, L, I, I, I, P, P, P, P]
         lib.oracle_local.argtypes = [P, I, P, L, I, I, I, P, P, P, P, P, P]
         lib.oracle_assemble.argtypes = [P, I, P, L, I, I, I, P, P, P, P, P, L, P, P, P]
+        lib.oracle_assemble_threads.argtypes = [P, I, P, L, L, I, I, I, P, P, P, P, P, L, P, P, P, I]
         lib.oracle_adjoint.argtypes = [P, I, P, L, L, I, I, I, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_load.argtypes = [P, I, P, L, L, I, I, I, P, P, P, P]
         lib.oracle_kll.argtypes = [P, P, L, L, I, I, P, P, P, P]
         for f in ("oracle_tabulate", "oracle_eval_points", "oracle_geometry", "oracle_local",
-                  "oracle_assemble", "oracle_adjoint", "oracle_load", "oracle_kll", "oracle_mutation_id"):
+                  "oracle_assemble", "oracle_assemble_threads", "oracle_max_threads", "oracle_adjoint", "oracle_load",
+                  "oracle_kll", "oracle_mutation_id"):
             getattr(lib, f).restype = ctypes.c_int
         _libs[mutation] = lib
         return lib
@@ -228,6 +230,39 @@ def assemble(coords, conn, dim, order, xi, w, coef=None, pat=None, mutation=0):
     if rc:
         raise ValueError(f"oracle_assemble failed ({rc})")
     return row_ptr, col_idx, M, A, C
+
+
+def assemble_threads(coords, conn, dim, order, xi, w, coef=None, pat=None, n_nodes=None, threads=0):
+    """The same global assembly on every host core (or `threads`): bit-identical
+    to assemble() -- each slot's contributions are added in the same order with
+    the same compensated sums.  Returns (row_ptr, col_idx, M, A, MC)."""
+    coords = _f64(coords)
+    conn = _i32(conn)
+    xi = _f64(xi).reshape(-1, dim)
+    w = _f64(w)
+    coef = _f64(coef)
+    n = coords.shape[1]
+    nn = coords.shape[0] if n_nodes is None else n_nodes
+    if pat is None:
+        pat = pattern(conn, nn)
+    row_ptr, col_idx = pat
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = _i32(col_idx)
+    nnz = col_idx.shape[0]
+    M = np.zeros(nnz)
+    A = np.zeros(nnz)
+    C = np.zeros(nnz)
+    rc = _lib().oracle_assemble_threads(_p(coords), n, _p(conn), conn.shape[0], nn, dim, order, xi.shape[0], _p(xi),
+                                        _p(w), _p(coef), _p(row_ptr), _p(col_idx), nnz, _p(M), _p(A), _p(C),
+                                        int(threads))
+    if rc:
+        raise ValueError(f"oracle_assemble_threads failed ({rc})")
+    return row_ptr, col_idx, M, A, C
+
+
+def max_threads():
+    """Threads the all-core oracle uses by default."""
+    return int(_lib().oracle_max_threads())
 
 
 def load(coords, conn, dim, order, xi, w, f, mutation=0):

@@ -103,9 +103,13 @@ struct PipeArgs {
 };
 
 // Local-matrix words of a tile with nel elements of upper size u and nl long
-// slots: the elements, six result words per long slot, six zero words.
-__host__ __device__ constexpr int64_t lsm_words(int64_t nel, int u, int64_t nl) {
-  return (int64_t)kLsmSlots * nel * lsm_stride(u) + 6 * (nl + 1);
+// slots, ns matrix slots per entry pair: the elements, 2 ns result words per
+// long slot, 2 ns zero words.  The float kernels keep all three slots (the
+// tile blocks' words address that layout directly); the double kernels keep
+// the requested matrices only (ns = nm) and map each word W of the
+// three-slot layout to 2 ns (W / 6) + W mod 6.
+__host__ __device__ constexpr int64_t lsm_words(int64_t nel, int u, int64_t nl, int ns = kLsmSlots) {
+  return (int64_t)ns * nel * lsm_stride(u) + 2ll * ns * (nl + 1);
 }
 
 struct PipeSmem {
@@ -303,7 +307,8 @@ __device__ __forceinline__ R pair_sum(R v) {
 
 // Local matrices of one element by a lane pair, stored into the element's
 // block of the interleaved tile layout (dst = element base; matrix slots im,
-// ia, ic); stride_m is unused by this layout.
+// ia, ic); stride_m is the number of matrix slots per entry pair (entry u of
+// slot m at word 2 stride_m (u / 2) + 2 m + u mod 2).
 template <int D, int NA, int P, typename R, bool DM, bool DA, bool DC>
 __device__ __forceinline__ void element_pair(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb, const void* coef,
                                              int coef_f32, int sub, bool store, R* dst, int stride_m, int im,
@@ -324,13 +329,13 @@ __device__ __forceinline__ void element_pair(const ElemData<D, NA, P, R>& ed, co
   if (store && lane_m) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (DM) dst[lsm_word(u, im)] = Mo[u];
-      if (DC) dst[lsm_word(u, ic)] = Co[u];
+      if (DM) dst[2 * stride_m * (u >> 1) + 2 * im + (u & 1)] = Mo[u];
+      if (DC) dst[2 * stride_m * (u >> 1) + 2 * ic + (u & 1)] = Co[u];
     }
   }
   if (store && lane_a) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[lsm_word(u, ia)] = Ao[u];
+    for (int u = 0; u < U; ++u) dst[2 * stride_m * (u >> 1) + 2 * ia + (u & 1)] = Ao[u];
   }
 }
 
@@ -436,7 +441,14 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   constexpr int UP = lsm_stride(U);
-  constexpr int EW = kLsmSlots * UP;  // words of one element's local matrices
+  // matrix slots per entry pair: three (float), the requested ones (double)
+  constexpr bool COMPACT = sizeof(R) == 8;
+  const int NS = COMPACT ? a.nm : kLsmSlots;
+  const int EW = NS * UP;  // words of one element's local matrices
+  auto wconv = [&](uint32_t w) -> uint32_t {
+    if constexpr (COMPACT) return 2u * (uint32_t)NS * (w / 6u) + w % 6u;
+    else return w;
+  };
   constexpr int ENTB = (int)sizeof(EntT);
   using Acc = typename AccOf<R>::T;
   const int nm = a.nm, Q = mr.tab.q;
@@ -453,8 +465,8 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
 
   // (the node coordinates in xd are already split for the float kernels;
   // *nflag is 0 on entry)
-  const int LB = kLsmSlots * h.nel * UP;  // long-slot results after the elements, then six zero words
-  if (threadIdx.x < 6) lsm[LB + 6 * h.nl + threadIdx.x] = (R)0;
+  const int LB = NS * h.nel * UP;  // long-slot results after the elements, then 2 NS zero words
+  if (threadIdx.x < 2 * NS) lsm[LB + 2 * NS * h.nl + threadIdx.x] = (R)0;
   // the copies of the next items, issued while phase 1 runs
   issue_next();
 
@@ -489,7 +501,7 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
       if constexpr (sizeof(R) == 4) {
         ElemData<D, NA, P, float> ed;
         element_data_from_pairs<D, NA, P>(reinterpret_cast<const float2*>(xd), en, ed);
-        element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, 0, a.which, qual, bad);
+        element_pair_dispatch<D, NA, P, float>(ed, tb, cf, mr.coef_f32, sub, active, dst, NS, a.which, qual, bad);
       } else {
         double X[REF][NA];
 #pragma unroll
@@ -498,7 +510,7 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
           for (int i = 0; i < NA; ++i) X[bb][i] = xd[en[bb] * NA + i];
         ElemData<D, NA, P, double> ed;
         load_element_data<D, NA, P, double>(X, ed);
-        element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, 0, a.which, qual, bad);
+        element_pair_dispatch<D, NA, P, double>(ed, tb, cf, mr.coef_f32, sub, active, dst, NS, a.which, qual, bad);
       }
       const R q2 = fmin(qual, __shfl_xor_sync(0xffffffffu, qual, 1));
       const bool bad2 = bad || __shfl_xor_sync(0xffffffffu, (int)bad, 1);
@@ -562,7 +574,7 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
       R v0[4], v1[4], v2[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        ent[i] = k0 + i < r.z ? (uint32_t)t_lent[k0 + i] : 0u;
+        ent[i] = k0 + i < r.z ? wconv(t_lent[k0 + i]) : 0u;
         v0[i] = lsm[ent[i]];
         v1[i] = nm > 1 ? lsm[ent[i] + 2] : (R)0;
         v2[i] = nm > 2 ? lsm[ent[i] + 4] : (R)0;
@@ -582,7 +594,7 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
         }
       }
     }
-    R* lr = lsm + LB + 6 * r.w;
+    R* lr = lsm + LB + 2 * NS * r.w;
     lr[0] = (R)acc_final(c0);
     if (nm > 1) lr[2] = (R)acc_final(c1);
     if (nm > 2) lr[4] = (R)acc_final(c2);
@@ -616,6 +628,8 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
       R v[3][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
+        x[i] = wconv(x[i]);
+        y[i] = wconv(y[i]);
         v[0][i] = lsm[x[i]] + lsm[y[i]];
         if (nm > 1) v[1][i] = lsm[x[i] + 2] + lsm[y[i] + 2];
         if (nm > 2) v[2][i] = lsm[x[i] + 4] + lsm[y[i] + 4];
@@ -742,12 +756,21 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
     }
     return ok;
   };
-  // producer: mesh record of item k and the TMA copy of its front part into front buffer k % 3
+  // producer: mesh record of item k (a batch's by cp.async: read from the next
+  // item on, after a cp.async wait) and the TMA copy of its front part into
+  // front buffer k % 3
   auto load_front = [&](int64_t k) {
     const int f = (int)(k % 3);
     const ItemRef& r = s_ref[k & 3];
     if (!rec_ok(r)) return;
-    s_rec[f] = a.meshes ? a.meshes[r.mesh] : a.one;
+    if (a.meshes) {
+      static_assert(sizeof(MeshRec) % 16 == 0, "mesh records are copied in 16-byte pieces");
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(a.meshes + r.mesh);
+      uint8_t* dst = reinterpret_cast<uint8_t*>(s_rec + f);
+      for (int o = 0; o < (int)sizeof(MeshRec); o += 16) cp_async16(dst + o, src + o);
+    } else {
+      s_rec[f] = a.one;
+    }
     tma_load_block(front_of(f), r.front, (uint32_t)r.front_bytes, &mbar[f]);
     pend |= 1u << f;
   };
@@ -811,6 +834,8 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
     if (!(a.starve && blockIdx.x == 0)) load_front(0);
     if (item_of(1) >= 0) load_front(1);
   }
+  cp_async_commit();  // (the mesh records of a batch)
+  cp_async_wait_all();
   {
     const bool ok = (*s_bad == 0) && wait_one(0);
     if (__syncthreads_or(!ok)) {
@@ -886,7 +911,17 @@ lfem_status launch_pipe_types(const PipeArgs& a, const FastBank& fb, int sm_coun
   const size_t smem = pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q,
                                           a.coef_smem)
                           .total;
-  if (smem > 227 * 1024) return fail(LFEM_E_TOO_LARGE, "pipelined tile needs more than 227 KB of shared memory");
+  if (smem > 227 * 1024) {
+    const PipeSmem L = pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q,
+                                           a.coef_smem);
+    return fail(LFEM_E_TOO_LARGE,
+                "pipelined tile needs " + std::to_string(smem / 1024) + " KB of shared memory (more than 227 KB): " +
+                    "local matrices " + std::to_string((L.flag - L.lsm) / 1024) + " KB for " +
+                    std::to_string(a.cap_nel) + " elements, node buffers " +
+                    std::to_string((L.coef0 - L.node0) / 1024) + " KB for " + std::to_string(a.cap_nodes) +
+                    " nodes, front parts " + std::to_string((L.back - L.front) / 1024) + " KB, back part " +
+                    std::to_string((L.node0 - L.back) / 1024) + " KB; use a smaller tile capacity");
+  }
   auto kern = k_assemble_pipe<R, EntT, Types...>;
   LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

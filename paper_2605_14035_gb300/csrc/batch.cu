@@ -4,11 +4,20 @@
 // and replayed.
 #include <algorithm>
 #include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "dispatch.cuh"
 
 namespace lfem {
+
+#define TRY_STATUS(x)                   \
+  do {                                  \
+    lfem_status _s = (x);               \
+    if (_s != LFEM_OK) return _s;       \
+  } while (0)
 
 template <typename EntT>
 static lfem_status launch_batch(const PipeArgs& a, const FastBank& fb, int sms, cudaStream_t st) {
@@ -282,6 +291,122 @@ void lfem_batch_destroy(lfem_batch_t b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_status) cudaFree(b->d_status);
   delete b;
+}
+
+lfem_status lfem_batch_autotune(const lfem_batch_item* items, int n_items, unsigned which, int coef_is_fp32,
+                                const char* cache_path, void* cuda_stream, int32_t* best_slots) {
+  if (!items || n_items <= 0) return fail(LFEM_E_ARG, "batch arguments");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the distinct patterns of each element family: (dim, order) = curves P1,
+  // curves P2, triangles P1, triangles P2 (a P1 triangle tile holds about six
+  // times the elements of a P2 one of the same capacity)
+  std::vector<lfem_pattern_s*> fam[4];
+  int64_t n_el = 0;
+  int counts[3][4][3] = {};  // (dim, ambient, order) histogram for the cache key
+  for (int i = 0; i < n_items; ++i) {
+    lfem_pattern_s* p = items[i].pattern;
+    if (!p) return fail(LFEM_E_ARG, "batch item without pattern");
+    if (!batch_type_ok(p->dim, items[i].ambient) || p->order > 2)
+      return fail(LFEM_E_UNSUPPORTED, "element type not supported in batches");
+    auto& v = fam[2 * (p->dim - 1) + (p->order - 1)];
+    if (std::find(v.begin(), v.end(), p) == v.end()) v.push_back(p);
+    n_el += p->n_elem;
+    ++counts[p->dim][items[i].ambient][p->order];
+  }
+  std::string name = "gpu";
+  {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (auto& c : name)
+      if (c == ' ') c = '_';
+  }
+  int bucket = 0;
+  for (int64_t n = n_el; n > 1; n >>= 1) ++bucket;
+  std::ostringstream k;
+  k << "batch_w" << which << "_f" << coef_is_fp32;
+  for (int d = 1; d <= 2; ++d)
+    for (int a = 2; a <= 3; ++a)
+      for (int o = 1; o <= 2; ++o)
+        if (counts[d][a][o]) k << "_d" << d << "n" << a << "p" << o << "x" << counts[d][a][o];
+  k << "_e2^" << bucket << "_" << name;
+  const std::string key = k.str();
+  int best[4] = {0, 0, 0, 0};
+  bool cached = false;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string kk;
+    int v[4];
+    while (in >> kk >> v[0] >> v[1] >> v[2] >> v[3])
+      if (kk == key) {
+        for (int f = 0; f < 4; ++f) best[f] = v[f];
+        cached = true;
+      }
+  }
+  auto retile = [&](int f, int slots) -> lfem_status {
+    for (lfem_pattern_s* p : fam[f])
+      if (p->tile_slots != slots) {
+        lfem_status s = build_tiles(p, std::max(slots, (int)p->max_row), st);
+        if (s != LFEM_OK) return s;
+      }
+    return LFEM_OK;
+  };
+  if (!cached) {
+    // one family at a time (P2 triangles first: they carry most of the work),
+    // the others held at their current (or already tuned) capacities; a
+    // candidate whose launch does not fit is skipped
+    const int cand[] = {1024, 1536, 2048, 2304, 2560, 3072};
+    cudaEvent_t e0, e1;
+    LFEM_CUDA(cudaEventCreate(&e0));
+    LFEM_CUDA(cudaEventCreate(&e1));
+    for (int f : {3, 2, 1, 0}) {
+      if (fam[f].empty()) continue;
+      float best_ms = 1e30f;
+      for (int c : cand) {
+        if (retile(f, c) != LFEM_OK) continue;
+        lfem_batch_t b = nullptr;
+        if (lfem_batch_create(items, n_items, which, coef_is_fp32, cuda_stream, &b) != LFEM_OK) continue;
+        lfem_status s = lfem_batch_assemble(b, cuda_stream);  // warm-up
+        if (s == LFEM_OK) s = lfem_batch_sync_status(b, cuda_stream);
+        if (s != LFEM_OK) {
+          lfem_batch_destroy(b);
+          continue;
+        }
+        const int reps = 3;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == LFEM_OK; ++r) s = lfem_batch_assemble(b, cuda_stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (s == LFEM_OK) s = lfem_batch_sync_status(b, cuda_stream);
+        lfem_batch_destroy(b);
+        if (s == LFEM_OK && ms < best_ms) {
+          best_ms = ms;
+          best[f] = c;
+        }
+      }
+      if (!best[f]) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(LFEM_E_TOO_LARGE, "no tile capacity fits this batch");
+      }
+      TRY_STATUS(retile(f, best[f]));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cache_path) {
+      std::ofstream out(cache_path, std::ios::app);
+      out << key << " " << best[0] << " " << best[1] << " " << best[2] << " " << best[3] << "\n";
+    }
+  } else {
+    for (int f = 0; f < 4; ++f)
+      if (!fam[f].empty() && best[f]) TRY_STATUS(retile(f, best[f]));
+  }
+  LFEM_CUDA(cudaStreamSynchronize(st));
+  if (best_slots)
+    for (int f = 0; f < 4; ++f) best_slots[f] = best[f];
+  return LFEM_OK;
 }
 
 }  // extern "C"

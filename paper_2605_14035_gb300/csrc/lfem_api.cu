@@ -594,7 +594,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
   pa.cap_nodes = p->max_tile_nodes;
   pa.cap_nel = p->max_tile_nel;
   pa.max_u = n_upper(p->ref);
-  pa.cap_lsm = lsm_words(p->max_tile_nel, n_upper(p->ref), p->max_tile_nl);
+  pa.cap_lsm = lsm_words(p->max_tile_nel, n_upper(p->ref), p->max_tile_nl, mixed ? kLsmSlots : nm);
   pa.vec_out = 1;
   for (int m = 0; m < nm; ++m)
     if (reinterpret_cast<uintptr_t>(a.out[m]) % 16) pa.vec_out = 0;

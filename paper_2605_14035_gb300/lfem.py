@@ -32,7 +32,7 @@ EXPORTS = (
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
     "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_debug_alloc_count", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
-    "lfem_batch_info", "lfem_batch_destroy",
+    "lfem_batch_info", "lfem_batch_destroy", "lfem_batch_autotune",
 )
 
 
@@ -85,6 +85,7 @@ def _load():
         "lfem_batch_graph_launch": [P, P],
         "lfem_batch_sync_status": [P, P],
         "lfem_batch_info": [P, P, P, P],
+        "lfem_batch_autotune": [P, I, U, I, ctypes.c_char_p, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -276,6 +277,43 @@ def autotune(pat: Pattern, coords: torch.Tensor, rule, coef=None, which: int = M
     return int(best.value)
 
 
+def _batch_items(meshes, which):
+    """lfem_batch_item records of the meshes, with their float outputs."""
+    items = (_BatchItem * len(meshes))()
+    kept = []
+    coef_f32 = 1
+    for i, m in enumerate(meshes):
+        pat, coords, rule = m["pattern"], _dev_f64(m["coords"], "coords"), as_rule(m["rule"])
+        coef = m.get("coef")
+        if coef is not None:
+            coef_f32 = int(coef.dtype == torch.float32)
+        outs = {k: (torch.empty(max(pat.nnz, 1), dtype=torch.float32, device=coords.device) if which & bit
+                    else None) for k, bit in (("M", MASS), ("A", STIFF), ("MC", CMASS))}
+        kept.append({"pattern": pat, "coords": coords, "rule": rule, "coef": coef, "out": outs})
+        it = items[i]
+        it.pattern = pat.handle.value
+        it.coords = coords.data_ptr()
+        it.ambient = int(coords.shape[1])
+        it.quad = None if rule._c is None else ctypes.addressof(rule._c)
+        it.coef = None if coef is None else coef.data_ptr()
+        it.M = None if outs["M"] is None else outs["M"].data_ptr()
+        it.A = None if outs["A"] is None else outs["A"].data_ptr()
+        it.MC = None if outs["MC"] is None else outs["MC"].data_ptr()
+    return items, kept, coef_f32
+
+
+def batch_autotune(meshes, which: int = MASS | STIFF, cache_path: Optional[str] = None, stream=None):
+    """lfem_batch_autotune: retile the meshes' patterns to the fastest tile
+    capacity per element family; returns the capacities of
+    (P1 curves, P2 curves, P1 triangles, P2 triangles), 0 for absent ones."""
+    items, kept, coef_f32 = _batch_items(meshes, int(which))
+    best = (ctypes.c_int32 * 4)()
+    _check(_lib.lfem_batch_autotune(items, len(meshes), int(which), coef_f32,
+                                    None if cache_path is None else cache_path.encode(), _stream(stream), best))
+    del kept
+    return tuple(int(v) for v in best)
+
+
 class Batch:
     """Many meshes assembled by one persistent launch (lfem_batch_*), mixed precision.
 
@@ -286,26 +324,7 @@ class Batch:
 
     def __init__(self, meshes, which: int = MASS | STIFF, stream=None):
         self.which = int(which)
-        self.meshes = []
-        items = (_BatchItem * len(meshes))()
-        coef_f32 = 1
-        for i, m in enumerate(meshes):
-            pat, coords, rule = m["pattern"], _dev_f64(m["coords"], "coords"), as_rule(m["rule"])
-            coef = m.get("coef")
-            if coef is not None:
-                coef_f32 = int(coef.dtype == torch.float32)
-            outs = {k: (torch.empty(max(pat.nnz, 1), dtype=torch.float32, device=coords.device) if which & bit
-                        else None) for k, bit in (("M", MASS), ("A", STIFF), ("MC", CMASS))}
-            self.meshes.append({"pattern": pat, "coords": coords, "rule": rule, "coef": coef, "out": outs})
-            it = items[i]
-            it.pattern = pat.handle.value
-            it.coords = coords.data_ptr()
-            it.ambient = int(coords.shape[1])
-            it.quad = None if rule._c is None else ctypes.addressof(rule._c)
-            it.coef = None if coef is None else coef.data_ptr()
-            it.M = None if outs["M"] is None else outs["M"].data_ptr()
-            it.A = None if outs["A"] is None else outs["A"].data_ptr()
-            it.MC = None if outs["MC"] is None else outs["MC"].data_ptr()
+        items, self.meshes, coef_f32 = _batch_items(meshes, self.which)
         self._items = items
         h = ctypes.c_void_p()
         _check(_lib.lfem_batch_create(items, len(meshes), self.which, coef_f32, _stream(stream), ctypes.byref(h)))

@@ -79,3 +79,31 @@ def test_batch_rejects_tets(lfem):
     with pytest.raises(lfem.LfemError) as ei:
         lfem.Batch([{"pattern": pat, "coords": torch.from_numpy(x).cuda(), "rule": rule}], which=1)
     assert ei.value.code == 3
+
+
+def test_batch_autotune_per_family_and_cache(lfem, tmp_path):
+    """lfem_batch_autotune picks a capacity per element family (dim, order) from
+    its candidates, leaves every pattern at it, writes the cache and reads it
+    back; the batch made afterwards still matches single-mesh assembly bit for
+    bit."""
+    _, meshes, meta = make_batch(lfem, which=3)
+    spec = [{k: m[k] for k in ("pattern", "coords", "rule")} for m in meshes]
+    cache = str(tmp_path / "batch_tune.txt")
+    best = lfem.batch_autotune(spec, which=3, cache_path=cache)
+    cand = {1024, 1536, 2048, 2304, 2560, 3072}
+    assert all(v in cand for v in best)  # every family is present in this batch
+    for name, (x, e, d, p, rule, coef) in zip(NAMES, meta):
+        want = best[2 * (d - 1) + (p - 1)]
+        info = meshes[NAMES.index(name)]["pattern"].info()
+        assert info["tile_slots"] == max(want, info["max_row"]), name
+    text = open(cache).read().split()
+    assert text[1:] == [str(v) for v in best] and text[0].startswith("batch_w3")
+    # a second call reads the cache: the same answer
+    assert lfem.batch_autotune(spec, which=3, cache_path=cache) == best
+    batch = lfem.Batch(spec, which=3)
+    batch.assemble()
+    batch.sync_status()
+    for i, m in enumerate(meshes):
+        single = lfem.assemble(m["pattern"], m["coords"], m["rule"], which=3, precision=lfem.MIXED)
+        for k in ("M", "A"):
+            assert torch.equal(batch.outputs(i)[k], single[k]), (NAMES[i], k)
