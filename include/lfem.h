@@ -193,6 +193,12 @@ lfem_status lfem_autotune(lfem_pattern_t p, const double* coords, int ambient, c
  * values of that CTA's tiles are left unwritten.  The CUDA context stays usable. */
 lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve);
 
+/* Test knob: with wide != 0 the pattern's tile blocks store their slot
+ * entries in 32 bits even when 16 would do (batches widen them that way when
+ * a mesh needs it); the tiles are rebuilt on the stream.  Results do not
+ * depend on the width. */
+lfem_status lfem_debug_wide_entries(lfem_pattern_t p, int wide, void* cuda_stream);
+
 /* Test knob: the number of device allocations (cudaMalloc) the library has
  * made successfully in this process, across all devices and threads.  Used to
  * check that an entry point allocates nothing; it never resets. */

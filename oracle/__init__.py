@@ -21,3 +21,4 @@ from .oracle import (  # noqa: F401
     mcf_step,
     p1_exact,
 )
+from .lift import lift_order  # noqa: F401

@@ -273,6 +273,126 @@ __device__ __forceinline__ void element_data_from_pairs(const float2* __restrict
   }
 }
 
+// The same element data in double from the split pairs: each difference of
+// hi parts and of lo parts is exact in double, so e and dl are the exact
+// differences of the double coordinates up to one final rounding.
+template <int D, int NA, int P>
+__device__ __forceinline__ void element_data64_from_pairs(const float2* __restrict__ xs,
+                                                          const uint16_t* __restrict__ en,
+                                                          ElemData<D, NA, P, double>& ed) {
+  constexpr int REF = Ref<D, P>::REF;
+  double xh[REF][NA], xl[REF][NA];
+#pragma unroll
+  for (int b = 0; b < REF; ++b) {
+    const int v = en[b];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float2 t = xs[v * NA + i];
+      xh[b][i] = (double)t.x;
+      xl[b][i] = (double)t.y;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m)
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ed.e[m][i] = (xh[m + 1][i] - xh[0][i]) + (xl[m + 1][i] - xl[0][i]);
+#pragma unroll
+  for (int k = 0; k < Ref<D, P>::NE; ++k) {
+    const int I = edge_i<D>(k), J = edge_j<D>(k), Ed = D + 1 + k;
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+      ed.dl[k][i] = ((xh[Ed][i] - xh[I][i]) + (xl[Ed][i] - xl[I][i])) -
+                    0.5 * ((xh[J][i] - xh[I][i]) + (xl[J][i] - xl[I][i]));
+  }
+}
+
+// A triangle that failed the conditioning test, again: per quadrature point
+// the geometry in double -- J from the exact differences of the split
+// coordinates and the rule's double tables, s = |det DF|, and the R^{-T}
+// factors c1, c2, c3 (as in tri_fast2) -- rounded to float, then the float
+// contraction, one point at a time (few registers: this rare path shares the
+// kernel with the hot one).  Every factor is then accurate to float rounding,
+// so the error no longer grows with the conditioning (the float |det DF| of
+// nearly parallel edge vectors loses about log2 cond(J) bits).  Every
+// requested matrix goes to dst (element block, slots M, A, MC of the
+// requested ones).  Returns false on a zero or non-finite |det DF|.
+template <int NA, int P>
+__device__ __forceinline__ bool redo_geo64(const float2* xs, const uint16_t* en, TabRef tab, const FastBank& fb,
+                                           const float* cs, const double* cd, unsigned which, float* dst) {
+  constexpr int REF = Ref<2, P>::REF, U = Ref<2, P>::U, NE = Ref<2, P>::NE, UP = lsm_stride(U);
+  constexpr int Q = FastQ<2, P>::Q;
+  ElemData<2, NA, P, double> ed;
+  element_data64_from_pairs<2, NA, P>(xs, en, ed);
+  const TabView<double> tb = tab_view<2, P, double>(tab);
+  float Ao[UP];
+#pragma unroll
+  for (int u = 0; u < UP; ++u) Ao[u] = 0.f;
+  float sq[Q];
+  bool good = true;
+#pragma unroll 1
+  for (int q = 0; q < Q; ++q) {
+    double J[NA][2];
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        double acc = ed.e[m][i];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) acc = fma(ed.dl[e][i], tb.dpsi[(q * NE + e) * 2 + m], acc);
+        J[i][m] = acc;
+      }
+    double g11 = 0.0, g12 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      g11 = fma(J[i][0], J[i][0], g11);
+      g12 = fma(J[i][0], J[i][1], g12);
+    }
+    double sd;
+    if constexpr (NA == 2) {
+      sd = fabs(J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+    } else {
+      const double n0 = J[1][0] * J[2][1] - J[2][0] * J[1][1];
+      const double n1 = J[2][0] * J[0][1] - J[0][0] * J[2][1];
+      const double n2 = J[0][0] * J[1][1] - J[1][0] * J[0][1];
+      sd = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    }
+    good &= (sd > 0.0) & (sd <= 1.0e300);
+    sq[q] = (float)sd;
+    if (which & LFEM_STIFF) {
+      const double c1d = sqrt(tb.w[q] * sd) / sqrt(g11), kd = c1d / sd;
+      const float c1 = (float)c1d, c2 = (float)(kd * g11), c3 = (float)(kd * g12);
+      float y0[REF], y1[REF];
+#pragma unroll
+      for (int b = 0; b < REF; ++b) {
+        const float gb1 = (float)tb.dphi[(q * REF + b) * 2], gb2 = (float)tb.dphi[(q * REF + b) * 2 + 1];
+        y0[b] = c1 * gb1;
+        y1[b] = fmaf(c2, gb2, -(c3 * gb1));
+      }
+#pragma unroll
+      for (int a = 0; a < REF; ++a)
+#pragma unroll
+        for (int b = a; b < REF; ++b) {
+          const int u = upper_index(REF, a, b);
+          Ao[u] = fmaf(y1[a], y1[b], fmaf(y0[a], y0[b], Ao[u]));
+        }
+    }
+  }
+  int slot = 0;
+  if (which & LFEM_MASS) contract_mass2<2, P>(fb, sq, dst + 2 * slot++);
+  if (which & LFEM_STIFF) {
+    float* d = dst + 2 * slot++;
+#pragma unroll
+    for (int j = 0; j < UP / 2; ++j) *reinterpret_cast<float2*>(d + 6 * j) = make_float2(Ao[2 * j], Ao[2 * j + 1]);
+  }
+  if (which & LFEM_CMASS) {
+    float sc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sc[q] = sq[q] * (cs ? __ldg(cs + q) : (float)__ldg(cd + q));
+    contract_mass2<2, P>(fb, sc, dst + 2 * slot);
+  }
+  return good;
+}
+
 // Quadrature loop of one element over the points q = q0, q0 + qs, ... (a lane
 // pair splits the points; the partial sums are combined by the caller).
 template <int D, int NA, int P, typename R, bool DM, bool DA, bool DC>
@@ -531,26 +651,40 @@ __device__ __forceinline__ bool process_tile(const PipeArgs& a, const MeshRec& m
   if constexpr (sizeof(R) == 4) {
     const int nf = *nflag;  // the same in every thread after the barrier
     if (nf > 0) {
-      // rare path: double recomputation of flagged elements from global
-      // coordinates -- every requested matrix for an element that failed the
-      // finiteness test (2), the stiffness alone for one that failed only the
-      // conditioning test (1): mass-type matrices need s, not G^{-1}
-      // (a compacted list, so that whole warps work on it: the FP64 pipe costs
-      // the same for a warp instruction with few active lanes)
-      const int ia = (a.which & LFEM_MASS) ? 1 : 0;
+      // rare path: every requested matrix of a flagged element again, from a
+      // compacted list so that whole warps work on it (the FP64 pipe costs
+      // the same for a warp instruction with few active lanes).  An element
+      // that failed the conditioning test (1): with the compile-time rule on
+      // triangles its per-point geometry in double and the float contraction
+      // (its float |det DF| and metric lose about log2 cond(J) bits, the
+      // float contraction of double-accurate factors does not); otherwise,
+      // and for an element that failed the finiteness test (2), everything
+      // in double from the global coordinates.
       for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         const uint32_t v = flist[i];
         const int j = (int)(v & 0x3FFFFFFFu), fl = (int)(v >> 30);
-        const unsigned fw = fl == 2 ? a.which : (a.which & LFEM_STIFF);
-        if (!fw) continue;
         const uint16_t* en = t_en + (size_t)j * REF;
         int32_t nd[REF];
 #pragma unroll
         for (int bb = 0; bb < REF; ++bb) nd[bb] = t_nodes[en[bb]];
         bool bad = false;
         R* d = lsm + (size_t)j * EW;
-        element_fp64_lean<D, NA, P, float, true>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j], fw,
-                                                 d, 0, bad, fl == 2 ? 0 : ia);
+        if constexpr (FAST && D == 2) {
+          if (fl == 1) {
+            const int64_t cg = (int64_t)t_elem[j] * Q;
+            const float* cs = coef_bytes == 4 ? static_cast<const float*>(mr.coef) + cg : nullptr;
+            const double* cd = coef_bytes == 8 ? static_cast<const double*>(mr.coef) + cg : nullptr;
+            const bool good = redo_geo64<NA, P>(reinterpret_cast<const float2*>(xd), en, mr.tab, fb, cs, cd, a.which,
+                                                reinterpret_cast<float*>(d));
+            if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
+              atomicAdd(a.fallback, 1ull);
+              if (!good) atomicOr(a.status, ST_DEGENERATE);
+            }
+            continue;
+          }
+        }
+        element_fp64_lean<D, NA, P, float, true>(mr.coords, nd, mr.tab, mr.coef, mr.coef_f32, (int64_t)t_elem[j],
+                                                 a.which, d, 0, bad, 0);
         if (nd[0] >= h.r0 && nd[0] < h.r0 + h.nrows) {
           atomicAdd(a.fallback, 1ull);
           if (bad) atomicOr(a.status, ST_DEGENERATE);

@@ -86,13 +86,11 @@ __global__ void __launch_bounds__(128) k_elem_local(const TwoPassArgs a, const _
       const double* cd = (a.which & LFEM_CMASS) && !a.coef_f32 ? static_cast<const double*>(a.coef) + e * Q : nullptr;
       Checks ck;
       element_fast_store<D, NA, P>(ed, fb, cs, cd, a.qmin, a.which, dst, U, ck);
-      // double recomputation: every matrix after a failed finiteness test,
-      // the stiffness alone after a failed conditioning test
-      const bool full = !ok || !ck.good;
-      const unsigned fw = full ? a.which : (ck.cond ? 0u : (a.which & LFEM_STIFF));
-      if (fw) {
-        float* d = dst + (full ? 0 : ((a.which & LFEM_MASS) ? U : 0));
-        element_fp64_lean<D, NA, P, float>(a.coords, nodes, a.tab, a.coef, a.coef_f32, e, fw, d, U, bad);
+      // double recomputation of every requested matrix after a failed
+      // finiteness or conditioning test (the float |det J| of a flat tet
+      // loses about log2 cond(J) bits, so the mass-type matrices need it too)
+      if (!ok || !ck.good || !ck.cond) {
+        element_fp64_lean<D, NA, P, float>(a.coords, nodes, a.tab, a.coef, a.coef_f32, e, a.which, dst, U, bad);
         atomicAdd(a.fallback, 1ull);
       }
     } else if constexpr (sizeof(R) == 4) {

@@ -476,6 +476,13 @@ lfem_status lfem_set_mixed_kappa(lfem_pattern_t p, double kappa_max) {
   return LFEM_OK;
 }
 
+lfem_status lfem_debug_wide_entries(lfem_pattern_t p, int wide, void* cuda_stream) {
+  if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
+  p->min_ent_bytes = wide ? 4 : 2;
+  if (p->ref > 16) return LFEM_OK;  // no row tiles
+  return build_tiles(p, p->tile_slots, (cudaStream_t)cuda_stream);
+}
+
 long long lfem_debug_alloc_count(void) { return lfem::g_alloc_count.load(std::memory_order_relaxed); }
 
 lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve) {

@@ -30,7 +30,7 @@ EXPORTS = (
     "lfem_assemble_mcf_nonlinear", "lfem_mcf_step", "lfem_lift_order", "lfem_assemble_adjoint", "lfem_assemble_adjoint_mixed",
     "lfem_eval_points",
     "lfem_geometry", "lfem_local", "lfem_sync_status", "lfem_mixed_fallback_count", "lfem_last_error",
-    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_debug_alloc_count", "lfem_autotune",
+    "lfem_status_string", "lfem_pattern_csr_noalloc", "lfem_debug_starve_wait", "lfem_debug_alloc_count", "lfem_debug_wide_entries", "lfem_autotune",
     "lfem_batch_create", "lfem_batch_assemble", "lfem_batch_graph_launch", "lfem_batch_sync_status",
     "lfem_batch_info", "lfem_batch_destroy", "lfem_batch_autotune",
 )
@@ -79,6 +79,7 @@ def _load():
         "lfem_mixed_fallback_count": [P, P, P],
         "lfem_pattern_csr_noalloc": [P, L, ctypes.c_int32, I, I, P, P, L, P, P],
         "lfem_debug_starve_wait": [P, I],
+        "lfem_debug_wide_entries": [P, I, P],
         "lfem_autotune": [P, P, I, P, P, I, U, I, P, P, P, ctypes.c_char_p, P, P],
         "lfem_batch_create": [P, I, U, I, P, P],
         "lfem_batch_assemble": [P, P],
@@ -220,6 +221,10 @@ class Pattern:
     def set_mixed_kappa(self, kappa_max: float):
         """LFEM_MIXED redoes in double the elements whose metric may have cond(G) > kappa_max."""
         _check(_lib.lfem_set_mixed_kappa(self._h, float(kappa_max)))
+
+    def debug_wide_entries(self, wide: bool, stream=None):
+        """Test knob: 32-bit slot entries in the tile blocks (rebuilds the tiles)."""
+        _check(_lib.lfem_debug_wide_entries(self._h, int(bool(wide)), _stream(stream)))
 
     def debug_starve_wait(self, starve: bool):
         _check(_lib.lfem_debug_starve_wait(self._h, int(bool(starve))))

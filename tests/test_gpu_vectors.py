@@ -91,8 +91,9 @@ def test_mcf_step(name, lfem):
 @pytest.mark.parametrize("kind,order", [("sphere", 3), ("sphere", 4), ("disk", 3), ("disk", 4), ("circle", 4),
                                         ("sphere", 2), ("cube", 2), ("cube", 3), ("cube", 4), ("cube_jit", 4)])
 def test_lift_order_matches_the_cpu_generator(kind, order, lfem):
-    """GPU node generation (P1 -> order p) against the seeded CPU generator:
-    identical connectivity and identical coordinate bits."""
+    """GPU node generation (P1 -> order p) against the oracle's node generation
+    (oracle.lift_order, pinned to the documented barycentric positions and
+    numbering): identical connectivity and identical coordinate bits."""
     from paper_2605_14035_gb300.inputs import meshes
 
     if kind == "sphere":
@@ -107,7 +108,7 @@ def test_lift_order_matches_the_cpu_generator(kind, order, lfem):
         t = 2 * np.pi * np.arange(30) / 30
         x = np.stack([np.cos(t), np.sin(t)], axis=1)
         e = np.stack([np.arange(30), (np.arange(30) + 1) % 30], axis=1).astype(np.int32)
-    xr, er = meshes.to_order(x, e, order)
+    xr, er = oracle.lift_order(x, e, order)
     pat = lfem.Pattern(dev(e), x.shape[0], e.shape[1] - 1, 1)
     xg, eg = lfem.lift_order(pat, dev(x), order)
     assert np.array_equal(eg.cpu().numpy(), er)
