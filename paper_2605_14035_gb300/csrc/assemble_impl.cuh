@@ -230,13 +230,13 @@ __device__ __noinline__ void element_fp64(const double* __restrict__ coords, con
 
 // Double recomputation of one element, one matrix per pass so the registers
 // needed stay below those of the float hot path (upper layout, stored as RS).
-// IL = false: matrix k at dst[k stride_m + u]; IL = true: the interleaved
-// tile layout, matrix slot slot0 + k at dst[lsm_word(u, slot0 + k)].
+// IL = false: matrix k at dst[k stride_m + u stride_u]; IL = true: the
+// interleaved tile layout, matrix slot slot0 + k at dst[lsm_word(u, slot0 + k)].
 template <int D, int NA, int P, typename RS, bool IL = false>
 __device__ __forceinline__ void element_fp64_lean(const double* __restrict__ coords,
                                                   const int32_t (&nd)[Ref<D, P>::REF], TabRef tab, const void* coef,
                                                   int coef_f32, int64_t e, unsigned which, RS* dst, int stride_m,
-                                                  bool& bad, int slot0 = 0) {
+                                                  bool& bad, int slot0 = 0, int stride_u = 1) {
   constexpr int REF = Ref<D, P>::REF;
   constexpr int U = Ref<D, P>::U;
   double X[REF][NA];
@@ -249,7 +249,7 @@ __device__ __forceinline__ void element_fp64_lean(const double* __restrict__ coo
   int slot = slot0;
   auto put = [&](int u, double v) {
     if constexpr (IL) dst[lsm_word(u, slot)] = (RS)v;
-    else dst[slot * stride_m + u] = (RS)v;
+    else dst[slot * stride_m + u * stride_u] = (RS)v;
   };
   if (which & LFEM_MASS) {
     element_pass<D, NA, P, double, true, false, false>(ed, tb, coef, coef_f32, e, V, dummy1, dummy2, qual, bad);

@@ -34,6 +34,7 @@ struct TwoPassArgs {
   float qmin;
   int32_t* status;
   unsigned long long* fallback;
+  int32_t* redo;  // [n_elem]: elements to redo in double (P2 tets, compile-time rule)
 };
 
 // All requested matrices of one element, one matrix per quadrature pass (keeps

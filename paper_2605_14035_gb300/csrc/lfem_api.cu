@@ -537,7 +537,8 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
     // order-3/4 tets keep their basis tables and recomputation list behind the local matrices)
     const bool tet_high = p->dim == 3 && p->order >= 3;
     const size_t lbytes = ((size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8) + 255) / 256 * 256;
-    const size_t need = lbytes + (tet_high ? tet_high_scratch_bytes(p->order, tab.q, p->n_elem) : 0);
+    const size_t redo_bytes = (size_t)p->n_elem * sizeof(int32_t);
+    const size_t need = lbytes + (tet_high ? tet_high_scratch_bytes(p->order, tab.q, p->n_elem) : redo_bytes);
     if (need > p->d.elem_buf_bytes) {
       if (p->d.elem_buf) cudaFree(p->d.elem_buf);
       p->d.elem_buf = nullptr;
@@ -565,6 +566,7 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
     ta.qmin = a.qmin;
     ta.status = p->d.status;
     ta.fallback = a.fallback;
+    ta.redo = reinterpret_cast<int32_t*>(static_cast<char*>(p->d.elem_buf) + lbytes);
     int sms3 = 0;
     LFEM_CUDA(cudaDeviceGetAttribute(&sms3, cudaDevAttrMultiProcessorCount, p->device));
     if (mixed) LFEM_CUDA(cudaMemsetAsync(p->d.status + 2, 0, sizeof(unsigned long long), st));
