@@ -207,7 +207,10 @@ long long lfem_debug_alloc_count(void);
 /* ---------------------------------------------------------------------------
  * Batches: many meshes of uneven sizes and different element types assembled
  * by one persistent launch over all their row tiles (mixed precision only;
- * curves and triangles, P1 and P2: (dim, ambient) in (1,2) (2,2) (2,3)).
+ * curves and triangles: (dim, ambient) in (1,2) (2,2) (2,3)).  Items of order
+ * 3 or 4 run their element-major path on the same stream after that launch
+ * (inside the same graph); their rule and element buffer are registered at
+ * creation, their status is read by lfem_batch_sync_status.
  * Motivated by the paper's batchwise processing of large meshes (Remark
  * "Batch computations", Sec. 3.3; Sec. 5.1).
  *
@@ -305,9 +308,13 @@ lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, c
  * g_coords [n_nodes][ambient] = dL/d coords (overwritten) and, when g_coef is
  * not NULL, g_coef [n_elem][n_pts] = dL/d coef.  FP64 throughout.  gM, gA,
  * gMC are [nnz] doubles; any may be NULL (treated as zero).  Geometry is
- * recomputed, not stored.  (Not in the paper: the derivative of its local
- * matrices, Eqs. reference_quadrature_mass / _stiffness, with respect to the
- * node positions.)
+ * recomputed, not stored.  Orders 1, 2: one thread per element in the
+ * pattern's row tiles.  Orders 3, 4 (curves, triangles, tets): one warp per
+ * element, the element node gradients in the pattern's element buffer (grown
+ * on demand, n_elem x ref x ambient doubles), then summed per node over its
+ * incidences in ascending element order.  (Not in the paper: the derivative
+ * of its local matrices, Eqs. reference_quadrature_mass / _stiffness, with
+ * respect to the node positions.)
  */
 lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                                   const double* coef, const double* gM, const double* gA, const double* gMC,
@@ -318,7 +325,8 @@ lfem_status lfem_assemble_adjoint(lfem_pattern_t p, const double* coords, int am
  * per node in double, and a double recomputation of every element whose
  * metric may have cond(G) > sqrt(kappa_max) (G^{-1} enters the derivative
  * twice; kappa_max from lfem_set_mixed_kappa) or fails the finiteness test;
- * the count is reported by lfem_mixed_fallback_count.
+ * the count is reported by lfem_mixed_fallback_count.  Orders 3, 4 run the
+ * double path for every element (each counted as recomputed).
  * Arguments and outputs as for lfem_assemble_adjoint (double). */
 lfem_status lfem_assemble_adjoint_mixed(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                                         const double* coef, const double* gM, const double* gA, const double* gMC,

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblfem.so")
 
-SOURCES = ["lfem_api.cu", "pattern.cu", "assemble_d1.cu", "assemble_d2.cu", "assemble_d3.cu", "batch.cu", "vectors.cu", "mcf.cu", "assemble_high.cu", "assemble_tet_high.cu"]
+SOURCES = ["lfem_api.cu", "pattern.cu", "assemble_d1.cu", "assemble_d2.cu", "assemble_d3.cu", "batch.cu", "vectors.cu", "mcf.cu", "assemble_high.cu", "assemble_tet_high.cu", "adjoint_high.cu"]
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",

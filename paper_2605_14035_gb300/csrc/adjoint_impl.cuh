@@ -43,6 +43,12 @@ struct AdjArgs {
   int mixed;                     // FP32 geometry with a double recomputation of flagged elements
   float qmin;                    // conditioning threshold of the mixed path (metric quality)
   unsigned long long* fallback;  // elements recomputed in double (mixed)
+  // orders 3, 4 (warp per element, then a per-node pass)
+  const int32_t* inc_key;        // [n_inc] (e << key_shift) | a, ascending per node
+  int key_shift;
+  int64_t n_elem;
+  int32_t n_nodes;
+  double* buf;                   // [n_elem][ref][ambient] element node gradients
 };
 
 // R = double: the reference computation; R = float: the mixed path, which

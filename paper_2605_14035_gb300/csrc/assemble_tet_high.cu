@@ -11,129 +11,52 @@
 //     (x_b - x_0) grad^phi_b^T, s = |det J|, H = w s G^{-1} = (w / s) adj(G)
 //     with adj(G)_mk = c_m . c_k, c_m the cross product of J's other two
 //     columns (Eq. basic integral formula, Eqs. jacobian_inv);
-//   * the entries are spread over the lanes (u = lane + 32 k) and summed over
-//     the points (Eqs. reference_quadrature_mass, reference_quadrature_stiffness):
+//   * each lane owns a register block of RA rows x RB columns of the matrix
+//     (order 3: 4 x 2 blocks, 30 lanes; order 4: 5 x 5, 28 lanes; the blocks
+//     on or above the diagonal) and sums it over the points (Eqs.
+//     reference_quadrature_mass, reference_quadrature_stiffness):
 //       M_ab += (w s phi_b) phi_a,  A_ab += grad^phi_a . (H grad^phi_b),
 //       C_ab += (c_q w s phi_b) phi_a,
 //     with the per-point node factors (w s phi_b, H grad^phi_b) computed once
-//     per node into shared memory.
+//     per node into shared memory: per point a lane reads RA + RB rows for
+//     RA RB entries.
 // LFEM_MIXED: float geometry and sums; an element whose metric fails the
 // conditioning test (or is not finite) anywhere is listed and recomputed in
 // FP64 by a second launch over the list.
 #include "dispatch.cuh"
+#include "tet_high.cuh"
 
 namespace lfem {
 
-constexpr int kTetHighWarps = 4;
-
+// Origin (r0, c0) of lane's block: the blocks on or above the diagonal in
+// column-major order; r0 = -1 for a lane without one.
 template <int P>
-struct TetHigh {
-  static constexpr int REF = (P + 1) * (P + 2) * (P + 3) / 6;
-  static constexpr int U = REF * (REF + 1) / 2;
-  static constexpr int NU = (U + 31) / 32;  // entries per lane
-  // table row stride in 16-byte units, odd: lanes reading rows of different
-  // points (the geometry phase) then fall on distinct banks
-  static constexpr int ROW = REF | 1;
-};
-
-template <typename R>
-struct alignas(4 * sizeof(R) > 16 ? 16 : 4 * sizeof(R)) V4 {
-  R x, y, z, w;
-};
-
-// Barycentric multi-index of local node a (library node order): corners;
-// edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3), each from its first corner
-// towards its second; faces (0,1,2), (0,1,3), (0,2,3), (1,2,3), each face
-// (i, j, l) by increasing (alpha_j, alpha_l); interior nodes by increasing
-// (alpha_1, alpha_2, alpha_3).
-__device__ void tet_node_alpha(int p, int a, int (&al)[4]) {
-  const int E[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
-  const int F[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
-  al[0] = al[1] = al[2] = al[3] = 0;
-  if (a < 4) {
-    al[a] = p;
-    return;
-  }
-  int r = a - 4;
-  if (r < 6 * (p - 1)) {
-    const int k = r / (p - 1), t = r % (p - 1) + 1;
-    al[E[k][0]] = p - t;
-    al[E[k][1]] = t;
-    return;
-  }
-  r -= 6 * (p - 1);
-  const int nf = (p - 1) * (p - 2) / 2;
-  if (r < 4 * nf) {
-    const int f = r / nf;
-    int t = r % nf;
-    for (int aj = 1; aj < p; ++aj)
-      for (int al2 = 1; aj + al2 < p; ++al2)
-        if (t-- == 0) {
-          al[F[f][0]] = p - aj - al2;
-          al[F[f][1]] = aj;
-          al[F[f][2]] = al2;
-          return;
+__device__ __forceinline__ void tet_high_block(int lane, int& r0, int& c0) {
+  using T = TetHigh<P>;
+  r0 = -1;
+  c0 = 0;
+  int k = 0;
+  for (int j = 0; j < T::NCB; ++j)
+    for (int i = 0; i < T::NRB; ++i)
+      if (i * T::RA <= j * T::RB + T::RB - 1) {
+        if (k == lane) {
+          r0 = i * T::RA;
+          c0 = j * T::RB;
         }
-  }
-  r -= 4 * nf;
-  for (int a1 = 1; a1 < p; ++a1)
-    for (int a2 = 1; a1 + a2 < p; ++a2)
-      for (int a3 = 1; a1 + a2 + a3 < p; ++a3)
-        if (r-- == 0) {
-          al[0] = p - a1 - a2 - a3;
-          al[1] = a1;
-          al[2] = a2;
-          al[3] = a3;
-          return;
-        }
-}
-
-// phi_alpha = prod_i l_{alpha_i}(lambda_i) with l_k(t) = prod_{j<k} (p t - j) / (j + 1):
-// value and derivative of one factor.
-__device__ __forceinline__ void lagrange_1d(int p, int k, double t, double& v, double& dv) {
-  v = 1.0;
-  dv = 0.0;
-  for (int j = 0; j < k; ++j) {
-    const double inv = 1.0 / (double)(j + 1);
-    const double f = ((double)p * t - (double)j) * inv;
-    dv = fma(dv, f, v * ((double)p * inv));
-    v *= f;
-  }
-}
-
-// table[q][b] = (phi_b, d phi_b / d xi_1, d xi_2, d xi_3) at point q, in FP64 and
-// float; rows ROW apart (the padding entries are never read).
-template <int P>
-__global__ void k_tet_high_table(TabRef rule_ref, V4<double>* __restrict__ t64, V4<float>* __restrict__ t32) {
-  constexpr int REF = TetHigh<P>::REF;
-  const int Q = rule_ref.q;
-  const double* rule = bank<double>() + rule_ref.off64;  // w[Q], then xi[Q][3]
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Q * REF; t += gridDim.x * blockDim.x) {
-    const int q = t / REF, b = t - q * REF;
-    int al[4];
-    tet_node_alpha(P, b, al);
-    const double x1 = rule[Q + 3 * q], x2 = rule[Q + 3 * q + 1], x3 = rule[Q + 3 * q + 2];
-    const double lam[4] = {1.0 - (x1 + x2 + x3), x1, x2, x3};
-    double v[4], dv[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) lagrange_1d(P, al[i], lam[i], v[i], dv[i]);
-    // d phi / d lambda_i, then the chain rule with lambda_0 = 1 - xi_1 - xi_2 - xi_3
-    const double d0 = dv[0] * v[1] * v[2] * v[3], d1 = v[0] * dv[1] * v[2] * v[3];
-    const double d2 = v[0] * v[1] * dv[2] * v[3], d3 = v[0] * v[1] * v[2] * dv[3];
-    const V4<double> r{v[0] * v[1] * v[2] * v[3], d1 - d0, d2 - d0, d3 - d0};
-    t64[q * TetHigh<P>::ROW + b] = r;
-    t32[q * TetHigh<P>::ROW + b] = V4<float>{(float)r.x, (float)r.y, (float)r.z, (float)r.w};
-  }
+        ++k;
+      }
 }
 
 // One matrix of one element: MODE 0 mass, 1 stiffness, 2 coefficient-weighted mass.
 template <int P, typename R, typename RS, int MODE>
-__device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane,
-                                              const uint32_t (&pk)[TetHigh<P>::NU], RS* dst) {
-  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU, ROW = TetHigh<P>::ROW;
-  R acc[NU];
+__device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane, int r0,
+                                              int c0, RS* dst) {
+  constexpr int REF = TetHigh<P>::REF, ROW = TetHigh<P>::ROW, RA = TetHigh<P>::RA, RB = TetHigh<P>::RB;
+  R acc[RA][RB];
 #pragma unroll
-  for (int k = 0; k < NU; ++k) acc[k] = (R)0;
+  for (int i = 0; i < RA; ++i)
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[i][j] = (R)0;
   for (int q = 0; q < Q; ++q) {
     const V4<R> g0 = geo[2 * q], g1 = geo[2 * q + 1];
     const V4<R>* tq = tab + q * ROW;
@@ -152,23 +75,38 @@ __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const
       hb[b] = h;
     }
     __syncwarp();
-#pragma unroll
-    for (int k = 0; k < NU; ++k) {
-      const int ia = (int)(pk[k] & 255u), ib = (int)(pk[k] >> 8);
-      const V4<R> hv = hb[ib];
+    if (r0 >= 0) {
       if constexpr (MODE == 1) {
-        const V4<R> da = tq[ia];
-        acc[k] = fma(da.y, hv.y, fma(da.z, hv.z, fma(da.w, hv.w, acc[k])));
+        V4<R> hv[RB];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) hv[j] = hb[c0 + j];
+#pragma unroll
+        for (int i = 0; i < RA; ++i) {
+          const V4<R> da = tq[r0 + i];
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            acc[i][j] = fma(da.y, hv[j].y, fma(da.z, hv[j].z, fma(da.w, hv[j].w, acc[i][j])));
+        }
       } else {
-        acc[k] = fma(tq[ia].x, hv.x, acc[k]);
+        R hx[RB];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) hx[j] = hb[c0 + j].x;
+#pragma unroll
+        for (int i = 0; i < RA; ++i) {
+          const R pa = tq[r0 + i].x;
+#pragma unroll
+          for (int j = 0; j < RB; ++j) acc[i][j] = fma(pa, hx[j], acc[i][j]);
+        }
       }
     }
     __syncwarp();
   }
+  if (r0 >= 0) {
 #pragma unroll
-  for (int k = 0; k < NU; ++k) {
-    const int u = lane + 32 * k;
-    if (u < U) dst[u] = (RS)acc[k];
+    for (int i = 0; i < RA; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (r0 + i <= c0 + j) dst[upper_index(REF, r0 + i, c0 + j)] = (RS)acc[i][j];
   }
 }
 
@@ -179,7 +117,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
                                                                  const uint32_t* __restrict__ list,
                                                                  const uint32_t* __restrict__ list_n,
                                                                  uint32_t* __restrict__ flags) {
-  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, NU = TetHigh<P>::NU, ROW = TetHigh<P>::ROW;
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, ROW = TetHigh<P>::ROW;
   const int Q = a.tab.q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V4<R>* tab = reinterpret_cast<V4<R>*>(smem_raw);  // [Q][ROW]
@@ -190,19 +128,8 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
   for (int t = threadIdx.x; t < Q * ROW; t += blockDim.x) tab[t] = gtab[t];
   __syncthreads();
   const double* w64 = bank<double>() + a.tab.off64;
-  // this lane's upper entries u = lane + 32 k as (a, b), row-major upper layout
-  uint32_t pk[NU];
-#pragma unroll
-  for (int k = 0; k < NU; ++k) {
-    const int u = lane + 32 * k;
-    int r = 0, start = 0;
-    if (u < U)
-      while (start + (REF - r) <= u) {
-        start += REF - r;
-        ++r;
-      }
-    pk[k] = u < U ? (uint32_t)r | ((uint32_t)(r + u - start) << 8) : 0u;
-  }
+  int r0, c0;  // this lane's register block
+  tet_high_block<P>(lane, r0, c0);
   const int64_t n_work = list ? (int64_t)*list_n : a.n_elem;
   for (int64_t i = (int64_t)blockIdx.x * kTetHighWarps + warp; i < n_work;
        i += (int64_t)gridDim.x * kTetHighWarps) {
@@ -281,14 +208,14 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
     __syncwarp();
     RS* dst = static_cast<RS*>(a.lbuf) + (size_t)e * a.nm * U;
     if (a.which & LFEM_MASS) {
-      tet_high_pass<P, R, RS, 0>(tab, hb, geo, Q, lane, pk, dst);
+      tet_high_pass<P, R, RS, 0>(tab, hb, geo, Q, lane, r0, c0, dst);
       dst += U;
     }
     if (a.which & LFEM_STIFF) {
-      tet_high_pass<P, R, RS, 1>(tab, hb, geo, Q, lane, pk, dst);
+      tet_high_pass<P, R, RS, 1>(tab, hb, geo, Q, lane, r0, c0, dst);
       dst += U;
     }
-    if (a.which & LFEM_CMASS) tet_high_pass<P, R, RS, 2>(tab, hb, geo, Q, lane, pk, dst);
+    if (a.which & LFEM_CMASS) tet_high_pass<P, R, RS, 2>(tab, hb, geo, Q, lane, r0, c0, dst);
   }
 }
 

@@ -54,6 +54,22 @@ struct lfem_batch_s {
   FastBank fb{};  // compile-time-rule tables, one per (dim, order)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // orders 3, 4: assembled by their element-major path on the batch's stream,
+  // after the persistent launch (and captured with it); rule copied here
+  struct Side {
+    lfem_pattern_s* p;
+    const double* coords;
+    int ambient;
+    std::vector<double> xi, w;
+    lfem_quad quad;
+    const void* coef;
+    void* M;
+    void* A;
+    void* MC;
+  };
+  std::vector<Side> side;
+  unsigned which = 0;
+  int coef_f32 = 0;
 };
 
 static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
@@ -61,8 +77,17 @@ static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   LFEM_CUDA(cudaMemsetAsync(b->d_status + 2, 0, sizeof(unsigned long long), st));
   LFEM_CUDA(cudaMemsetAsync(b->d_status + 4, 0, sizeof(unsigned long long), st));  // tile tickets
-  return b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, b->fb, sms, st)
-                           : launch_batch<uint32_t>(b->args, b->fb, sms, st);
+  if (b->args.n_items > 0) {
+    const lfem_status s = b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, b->fb, sms, st)
+                                            : launch_batch<uint32_t>(b->args, b->fb, sms, st);
+    if (s != LFEM_OK) return s;
+  }
+  for (auto& sd : b->side) {
+    const lfem_status s = lfem_assemble(sd.p, sd.coords, sd.ambient, &sd.quad, sd.coef, b->coef_f32, b->which,
+                                        LFEM_MIXED, sd.M, sd.A, sd.MC, st);
+    if (s != LFEM_OK) return s;
+  }
+  return LFEM_OK;
 }
 
 extern "C" {
@@ -78,9 +103,38 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     if (it.pattern->order != 1 || (which & LFEM_CMASS)) return fail(LFEM_E_ARG, "batch item without a quadrature rule");
     it.quad = exact_p1_rule(it.pattern->dim);
   }
-  const lfem_batch_item* items = items_v.data();
   if (which == 0 || (which & ~7u)) return fail(LFEM_E_ARG, "which");
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // orders 3, 4 run beside the persistent launch: check them, register their
+  // rule and reserve their element buffer now (nothing allocates in a launch)
+  std::vector<lfem_batch_item> pipe_v;
+  std::vector<lfem_batch_s::Side> side_v;
+  int nm_all = 0;
+  for (unsigned bit = 1; bit <= 4; bit <<= 1) nm_all += (which & bit) ? 1 : 0;
+  for (const auto& it : items_v) {
+    lfem_pattern_s* p = it.pattern;
+    if (!p) return fail(LFEM_E_ARG, "batch item without pattern");
+    if (p->order <= 2) {
+      pipe_v.push_back(it);
+      continue;
+    }
+    if (!supported(p->dim, it.ambient, p->order) || !batch_type_ok(p->dim, it.ambient))
+      return fail(LFEM_E_UNSUPPORTED, "element type not supported in batches");
+    if ((which & LFEM_MASS) && !it.M) return fail(LFEM_E_ARG, "batch item M is NULL");
+    if ((which & LFEM_STIFF) && !it.A) return fail(LFEM_E_ARG, "batch item A is NULL");
+    if ((which & LFEM_CMASS) && (!it.MC || !it.coef)) return fail(LFEM_E_ARG, "batch item MC or coef is NULL");
+    if (p->n_elem > 0 && !it.coords) return fail(LFEM_E_ARG, "batch item coords is NULL");
+    lfem_batch_s::Side sd{p, it.coords, it.ambient, {}, {}, {}, it.coef, it.M, it.A, it.MC};
+    sd.xi.assign(it.quad->xi, it.quad->xi + (size_t)it.quad->n_pts * p->dim);
+    sd.w.assign(it.quad->w, it.quad->w + it.quad->n_pts);
+    TabRef tab;
+    lfem_status s = get_tables(p->dim, p->order, it.quad, st, &tab);
+    if (s != LFEM_OK) return s;
+    if ((s = reserve_elem_buf(p, nm_all, true, tab.q)) != LFEM_OK) return s;
+    side_v.push_back(std::move(sd));
+  }
+  const lfem_batch_item* items = pipe_v.data();
+  n_items = (int)pipe_v.size();
   std::vector<MeshRec> recs(n_items);
   std::vector<int64_t> item_off(n_items + 1, 0);  // first work item of each mesh
   int cap_front = 0, cap_back = 0, cap_nodes = 0, cap_nel = 0, max_u = 0, max_q = 0, ent_bytes = 2;
@@ -93,7 +147,7 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     const lfem_batch_item& it = items[i];
     lfem_pattern_s* p = it.pattern;
     if (!p) return fail(LFEM_E_ARG, "batch item without pattern");
-    if (!supported(p->dim, it.ambient, p->order) || !batch_type_ok(p->dim, it.ambient) || p->order > 2)
+    if (!supported(p->dim, it.ambient, p->order) || !batch_type_ok(p->dim, it.ambient))
       return fail(LFEM_E_UNSUPPORTED, "element type not supported in batches");
     if ((which & LFEM_MASS) && !it.M) return fail(LFEM_E_ARG, "batch item M is NULL");
     if ((which & LFEM_STIFF) && !it.A) return fail(LFEM_E_ARG, "batch item A is NULL");
@@ -168,20 +222,27 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
   }
   b->ent_bytes = ent_bytes;
   b->n_elements = n_el;
+  b->which = which;
+  b->coef_f32 = coef_is_fp32 ? 1 : 0;
+  for (auto& sd : side_v) {
+    b->n_elements += sd.p->n_elem;
+    b->side.push_back(std::move(sd));
+  }
+  for (auto& sd : b->side) sd.quad = lfem_quad{(int)sd.w.size(), sd.xi.data(), sd.w.data()};
   auto cleanup = [&]() {
     if (b->d_meshes) cudaFree(b->d_meshes);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_status) cudaFree(b->d_status);
     delete b;
   };
-  if (dev_malloc((void**)&b->d_meshes, sizeof(MeshRec) * n_items) != cudaSuccess ||
+  if (dev_malloc((void**)&b->d_meshes, sizeof(MeshRec) * std::max(1, n_items)) != cudaSuccess ||
       dev_malloc((void**)&b->d_items, sizeof(ItemRef) * std::max<int64_t>(1, item_off[n_items])) != cudaSuccess ||
       dev_malloc((void**)&b->d_status, 6 * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return fail(LFEM_E_NOMEM, "batch allocation failed");
   }
-  cudaMemcpyAsync(b->d_meshes, recs.data(), sizeof(MeshRec) * n_items, cudaMemcpyHostToDevice, st);
+  if (n_items > 0) cudaMemcpyAsync(b->d_meshes, recs.data(), sizeof(MeshRec) * n_items, cudaMemcpyHostToDevice, st);
   // work items: every mesh's tile records, mesh by mesh, tagged with the mesh index
   for (int i = 0; i < n_items; ++i) {
     const int64_t n = item_off[i + 1] - item_off[i];
@@ -272,6 +333,10 @@ lfem_status lfem_batch_sync_status(lfem_batch_t b, void* cuda_stream) {
   if (h & ST_ITEM) return fail(LFEM_E_CUDA, "a work-item record failed its size or alignment check");
   if (h & ST_TYPE) return fail(LFEM_E_UNSUPPORTED, "a tile met a kernel without its element type");
   if (h & ST_DEGENERATE) return fail(LFEM_E_DEGENERATE, "zero or non-finite |det DF| at a quadrature point");
+  for (auto& sd : b->side) {
+    const lfem_status s = lfem_sync_status(sd.p, cuda_stream);
+    if (s != LFEM_OK) return s;
+  }
   return LFEM_OK;
 }
 
@@ -306,8 +371,9 @@ lfem_status lfem_batch_autotune(const lfem_batch_item* items, int n_items, unsig
   for (int i = 0; i < n_items; ++i) {
     lfem_pattern_s* p = items[i].pattern;
     if (!p) return fail(LFEM_E_ARG, "batch item without pattern");
-    if (!batch_type_ok(p->dim, items[i].ambient) || p->order > 2)
+    if (!batch_type_ok(p->dim, items[i].ambient))
       return fail(LFEM_E_UNSUPPORTED, "element type not supported in batches");
+    if (p->order > 2) continue;  // element-major, no row tiles to tune
     auto& v = fam[2 * (p->dim - 1) + (p->order - 1)];
     if (std::find(v.begin(), v.end(), p) == v.end()) v.push_back(p);
     n_el += p->n_elem;

@@ -25,6 +25,12 @@ lfem_status bank_upload_vec(const void* src, size_t bytes, size_t offset);
 lfem_status bank_upload_high(const void* src, size_t bytes, size_t offset);
 lfem_status run_twopass_high(int D, int NA, int P, bool mixed, const TwoPassArgs& a, int sms, cudaStream_t st);
 lfem_status bank_upload_tet_high(const void* src, size_t bytes, size_t offset);
+lfem_status bank_upload_adj_high(const void* src, size_t bytes, size_t offset);
+// Orders 3, 4: the adjoint (FP64, warp per element); scratch holds
+// adjoint_high_scratch_bytes(...) bytes.
+size_t adjoint_high_scratch_bytes(int dim, int P, int Q, int ambient, int64_t n_elem);
+lfem_status run_adjoint_high(int dim, int NA, int P, const AdjArgs& a, int pos_bytes, void* scratch, int sms,
+                             cudaStream_t st);
 lfem_status run_tet_high(int P, bool mixed, const TwoPassArgs& a, void* scratch, int sms, cudaStream_t st);
 size_t tet_high_scratch_bytes(int P, int Q, int64_t n_elem);
 lfem_status run_tet_high_load(int P, const VecArgs& a, void* scratch, int sms, cudaStream_t st);

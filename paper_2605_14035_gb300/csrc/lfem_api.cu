@@ -320,7 +320,7 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
   memcpy(blob.data(), t64.data(), b64);
   memcpy(blob.data() + b64, t32.data(), t32.size() * sizeof(float));
   for (auto up : {bank_upload_d1, bank_upload_d2, bank_upload_d3, bank_upload_batch, bank_upload_vec,
-                  bank_upload_high, bank_upload_tet_high}) {
+                  bank_upload_high, bank_upload_tet_high, bank_upload_adj_high}) {
     lfem_status us = up(blob.data(), blob.size(), used);
     if (us != LFEM_OK) return us;
   }
@@ -491,6 +491,38 @@ lfem_status lfem_debug_starve_wait(lfem_pattern_t p, int starve) {
   return LFEM_OK;
 }
 
+}  // extern "C"
+
+namespace lfem {
+
+size_t elem_buf_local_bytes(const lfem_pattern_s* p, int nm, bool mixed) {
+  return ((size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8) + 255) / 256 * 256;
+}
+
+// The element-major paths (tets, orders 3 and 4): the local matrices, then the
+// order-3/4 tet tables and list, or the P2 tets' redo list.
+lfem_status reserve_elem_buf(lfem_pattern_s* p, int nm, bool mixed, int q) {
+  const bool tet_high = p->dim == 3 && p->order >= 3;
+  const size_t redo_bytes = (size_t)p->n_elem * sizeof(int32_t);
+  const size_t need =
+      elem_buf_local_bytes(p, nm, mixed) + (tet_high ? tet_high_scratch_bytes(p->order, q, p->n_elem) : redo_bytes);
+  if (need > p->d.elem_buf_bytes) {
+    if (p->d.elem_buf) cudaFree(p->d.elem_buf);
+    p->d.elem_buf = nullptr;
+    p->d.elem_buf_bytes = 0;
+    if (dev_malloc(&p->d.elem_buf, need ? need : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LFEM_E_NOMEM, "element buffer allocation failed");
+    }
+    p->d.elem_buf_bytes = need;
+  }
+  return LFEM_OK;
+}
+
+}  // namespace lfem
+
+extern "C" {
+
 lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad,
                           const void* coef, int coef_is_fp32, unsigned which, lfem_precision prec, void* M, void* A,
                           void* MC, void* cuda_stream) {
@@ -536,19 +568,8 @@ lfem_status lfem_assemble(lfem_pattern_t p, const double* coords, int ambient, c
     // bulk tets and orders 3, 4: element-major two passes (local-matrix buffer owned by the pattern;
     // order-3/4 tets keep their basis tables and recomputation list behind the local matrices)
     const bool tet_high = p->dim == 3 && p->order >= 3;
-    const size_t lbytes = ((size_t)p->n_elem * nm * n_upper(p->ref) * (mixed ? 4 : 8) + 255) / 256 * 256;
-    const size_t redo_bytes = (size_t)p->n_elem * sizeof(int32_t);
-    const size_t need = lbytes + (tet_high ? tet_high_scratch_bytes(p->order, tab.q, p->n_elem) : redo_bytes);
-    if (need > p->d.elem_buf_bytes) {
-      if (p->d.elem_buf) cudaFree(p->d.elem_buf);
-      p->d.elem_buf = nullptr;
-      p->d.elem_buf_bytes = 0;
-      if (dev_malloc(&p->d.elem_buf, need ? need : 16) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(LFEM_E_NOMEM, "element buffer allocation failed");
-      }
-      p->d.elem_buf_bytes = need;
-    }
+    const size_t lbytes = elem_buf_local_bytes(p, nm, mixed);
+    if ((s = reserve_elem_buf(p, nm, mixed, tab.q)) != LFEM_OK) return s;
     TwoPassArgs ta{};
     ta.conn = p->d.conn;
     ta.coords = coords;
@@ -654,7 +675,6 @@ static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int am
                                   double* g_coords, double* g_coef, bool mixed, void* cuda_stream) {
   if (!p) return fail(LFEM_E_ARG, "pattern is NULL");
   if (!supported(p->dim, ambient, p->order)) return fail(LFEM_E_UNSUPPORTED, "(dim, ambient, order)");
-  if (p->order > 2) return fail(LFEM_E_UNSUPPORTED, "the adjoint covers orders 1 and 2");
   if (!g_coords && p->n_nodes > 0) return fail(LFEM_E_ARG, "g_coords is NULL");
   if (p->n_elem > 0 && !coords) return fail(LFEM_E_ARG, "coords is NULL");
   if (gMC && !coef) return fail(LFEM_E_ARG, "gMC given without coef");
@@ -698,6 +718,28 @@ static lfem_status adjoint_common(lfem_pattern_t p, const double* coords, int am
     // dL/dc is zero without gMC
     LFEM_CUDA(cudaMemsetAsync(g_coef, 0, sizeof(double) * p->n_elem * quad->n_pts, st));
     a.g_coef = nullptr;
+  }
+  if (p->order >= 3) {
+    // warp per element in double, element node gradients in the pattern's
+    // element buffer, then a per-node pass over the incidences
+    const size_t need = adjoint_high_scratch_bytes(p->dim, p->order, tab.q, ambient, p->n_elem);
+    if (need > p->d.elem_buf_bytes) {
+      if (p->d.elem_buf) cudaFree(p->d.elem_buf);
+      p->d.elem_buf = nullptr;
+      p->d.elem_buf_bytes = 0;
+      if (dev_malloc(&p->d.elem_buf, need ? need : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LFEM_E_NOMEM, "element buffer allocation failed");
+      }
+      p->d.elem_buf_bytes = need;
+    }
+    a.inc_key = p->d.inc_key;
+    a.key_shift = p->key_shift;
+    a.n_elem = p->n_elem;
+    a.n_nodes = p->n_nodes;
+    int sms = 0;
+    LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    return run_adjoint_high(p->dim, ambient, p->order, a, p->pos_bytes, p->d.elem_buf, sms, st);
   }
   return run_adjoint(p->dim, ambient, p->order, a, p->n_tiles, p->pos_bytes, st);
 }

@@ -585,4 +585,7 @@ struct lfem_pattern_s {
 
 namespace lfem {
 lfem_status build_tiles(lfem_pattern_s* p, int32_t tile_slots, cudaStream_t st);
+// Element buffer of the element-major paths for nm matrices (grown, never shrunk).
+size_t elem_buf_local_bytes(const lfem_pattern_s* p, int nm, bool mixed);
+lfem_status reserve_elem_buf(lfem_pattern_s* p, int nm, bool mixed, int q);
 }

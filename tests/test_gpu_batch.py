@@ -10,6 +10,7 @@ from cases import build_cases, coef_field, diag_scaled_error
 pytestmark = pytest.mark.gpu
 
 NAMES = ["curve_p1", "curve_p2", "disk_p1", "disk_p2", "sphere_p1", "ellipsoid_p2", "half_disk_p2"]
+HIGH = ["sphere_p3", "disk_p3", "circle_p4", "sphere_p4"]
 
 
 @pytest.fixture(scope="module")
@@ -21,10 +22,10 @@ def lfem():
     return m
 
 
-def make_batch(lfem, which=7, tile_slots=512):
+def make_batch(lfem, which=7, tile_slots=512, names=NAMES):
     cases = build_cases()
     meshes, meta = [], []
-    for name in NAMES:
+    for name in names:
         x, e, d, p, rule = cases[name]
         coef = coef_field(oracle.eval_points(x, e, d, p, rule.xi))
         pat = lfem.Pattern(torch.from_numpy(e).cuda(), x.shape[0], d, p)
@@ -70,6 +71,36 @@ def test_batch_graph_replay_follows_coordinates(lfem):
         for k in ("M", "A"):
             assert torch.equal(got[k], fresh[k]), (NAMES[i], k)
             assert not torch.equal(got[k], first[i][k])
+
+
+def test_batch_with_orders_3_and_4(lfem):
+    """Order-3/4 items beside the persistent launch: bit-identical to their single
+    assembly, within 1e-6 of the oracle, and followed by the graph replay."""
+    names = ["disk_p2"] + HIGH + ["curve_p1"]
+    batch, meshes, meta = make_batch(lfem, which=7, names=names)
+    batch.assemble()
+    batch.sync_status()
+    assert batch.info()["elements_computed"] >= sum(m[1].shape[0] for m in meta)
+    for i, m in enumerate(meshes):
+        single = lfem.assemble(m["pattern"], m["coords"], m["rule"], m["coef"], which=7, precision=lfem.MIXED)
+        x, e, d, p, rule, coef = meta[i]
+        orp, oci, M, A, C = oracle.assemble(x, e, d, p, rule.xi, rule.w, coef)
+        for k, ref in (("M", M), ("A", A), ("MC", C)):
+            got = batch.outputs(i)[k]
+            assert torch.equal(got, single[k]), (names[i], k)
+            assert diag_scaled_error(got.double().cpu().numpy(), ref, orp, oci) <= 1e-6, (names[i], k)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.graph_launch(stream)
+        for m in meshes:
+            m["coords"].mul_(0.75)
+        batch.graph_launch(stream)
+        stream.synchronize()
+    batch.sync_status(stream)
+    for i, m in enumerate(meshes):
+        fresh = lfem.assemble(m["pattern"], m["coords"], m["rule"], m["coef"], which=7, precision=lfem.MIXED)
+        for k in ("M", "A", "MC"):
+            assert torch.equal(batch.outputs(i)[k], fresh[k]), (names[i], k)
 
 
 def test_batch_rejects_tets(lfem):

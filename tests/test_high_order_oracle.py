@@ -209,3 +209,48 @@ def test_edge_numbering_of_the_lifting_is_the_upper_csr_slots():
                 ids = np.array([eid[(int(u), int(v))] for u, v in zip(lo, hi)])
                 k1 = np.where(i < j, 1, p - 1)  # the node next to the edge's first corner
                 assert np.array_equal(conn[:, 3 + le * (p - 1)], N + ids * (p - 1) + k1 - 1)
+
+
+@pytest.mark.parametrize("case", ["sphere_p3", "circle_p4", "cube_p3"])
+def test_adjoint_high_order_central_differences(case):
+    """The oracle's adjoint at orders 3, 4 against central differences (h = 1e-6)
+    of L = gM.M + gA.A + gC.MC restricted to the elements around the moved node."""
+    import pins
+    from cases import curved_cube
+    from paper_2605_14035_gb300.inputs import meshes
+
+    rng = np.random.default_rng(31)
+    if case == "sphere_p3":
+        (x, e), d, p, r = meshes.icosphere_high(0, 3), 2, 3, quadrature.tri_16pt_deg8()
+    elif case == "circle_p4":
+        t = np.linspace(0, 2 * np.pi, 9)[:-1]
+        x1 = np.stack([np.cos(t), 0.8 * np.sin(t)], axis=1)
+        e1 = np.stack([np.arange(8), (np.arange(8) + 1) % 8], axis=1).astype(np.int32)
+        (x, e), d, p, r = meshes.to_order(x1, e1, 4), 1, 4, quadrature.gauss_interval(6)
+    else:
+        (x, e), d, p, r = curved_cube(1, 3, amp=0.01), 3, 3, quadrature.paper_rule(3)
+    x = x + rng.normal(0, 0.003, size=x.shape)
+    coef = 1.0 + rng.random((e.shape[0], r.n_pts))
+    pat = oracle.pattern(e, x.shape[0])
+    nnz = pat[1].size
+    gM, gA, gC = rng.normal(size=(3, nnz))
+    gx, gc = oracle.adjoint(x, e, d, p, r.xi, r.w, coef, pat, gM, gA, gC)
+    h = 1e-6
+    scale = np.abs(gx).max()
+    for flat in rng.choice(x.size, 6, replace=False):
+        k, i = divmod(int(flat), x.shape[1])
+        elems = np.nonzero((e == k).any(axis=1))[0]
+        xp, xm = x.copy(), x.copy()
+        xp[k, i] += h
+        xm[k, i] -= h
+        fd = (pins.local_L(xp, e, d, p, r, coef, elems, gM, gA, gC, pat) -
+              pins.local_L(xm, e, d, p, r, coef, elems, gM, gA, gC, pat)) / (2 * h)
+        assert abs(fd - gx[k, i]) < 1e-6 * scale
+    # MC is linear in the coefficient: a step in c_{e,q} moves L by exactly step * dL/dc_{e,q}
+    for e0, q0 in ((0, 0), (e.shape[0] - 1, r.n_pts - 1)):
+        cp, cm = coef.copy(), coef.copy()
+        cp[e0, q0] += 0.5
+        cm[e0, q0] -= 0.5
+        dc = (pins.local_L(x, e, d, p, r, cp, [e0], gM, gA, gC, pat) -
+              pins.local_L(x, e, d, p, r, cm, [e0], gM, gA, gC, pat))
+        assert abs(dc - gc[e0, q0]) <= 1e-11 * np.abs(gc).max()
