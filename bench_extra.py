@@ -311,16 +311,21 @@ def run_c5(args):
     nl_err = float(np.abs(nl - onl).max() / np.abs(onl).max())
     # one step of Dziuk's scheme on the final surface: FP64 assembly + PCG on the GPU,
     # against the oracle's direct solve
+    # (on a side stream: the solver's 8-iteration blocks replay a captured graph)
     xs = xd.clone()
-    x1, cg_it = lfem.mcf_step(pat, xs, rule, 1e-4, rtol=1e-12, max_iter=5000)
-    t_mcf = []
-    for _ in range(3):
-        a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        lfem.mcf_step(pat, xs, rule, 1e-4, rtol=1e-12, max_iter=5000, out=x1)
-        b0.record()
-        torch.cuda.synchronize()
-        t_mcf.append(a0.elapsed_time(b0))
+    ms_st = torch.cuda.Stream()
+    ms_st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(ms_st):
+        x1, cg_it = lfem.mcf_step(pat, xs, rule, 1e-4, rtol=1e-12, max_iter=5000, stream=ms_st)
+        t_mcf = []
+        for _ in range(3):
+            a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(ms_st)
+            lfem.mcf_step(pat, xs, rule, 1e-4, rtol=1e-12, max_iter=5000, out=x1, stream=ms_st)
+            b0.record(ms_st)
+            ms_st.synchronize()
+            t_mcf.append(a0.elapsed_time(b0))
+    torch.cuda.current_stream().wait_stream(ms_st)
     ox1 = oracle.mcf_step(xh, e, 2, 2, rule.xi, rule.w, 1e-4)
     mcf_err = float(np.abs(x1.cpu().numpy() - ox1).max() / np.abs(ox1).max())
     _line(args, "evolving_ellipsoid_r7_100_steps_plus_adjoint", e.shape[0] / (ms_step * 1e-3), "elements/s",

@@ -294,12 +294,17 @@ lfem_status lfem_assemble_mcf_nonlinear(lfem_pattern_t p, const double* coords, 
  * in a fixed order: bit-reproducible), started from x0, stopped when every
  * column's residual satisfies |r| <= rtol |M x0| (checked every 8
  * iterations) or after max_iter iterations.  Curves in R^2 and surfaces in R^3
- * (ambient = dim + 1), else LFEM_E_UNSUPPORTED.
+ * (ambient = dim + 1), else LFEM_E_UNSUPPORTED.  A CG iteration is three
+ * kernels (K p with <p, q>; x, r, z with <r, z>; p), each block reducing the
+ * previous kernel's per-block partials itself in one fixed order; on a stream
+ * other than the legacy default one the 8 iterations between two checks are a
+ * CUDA graph, captured on first use and kept by the pattern.
  *   coords:     x0 [n_nodes][ambient] device doubles.
  *   coords_out: x1 [n_nodes][ambient] device doubles (may equal coords).
  *   iterations: host int, the CG iterations done (== max_iter: not converged).
  * Synchronises the stream (convergence checks); scratch (3 nnz + 6 n_nodes x
- * ambient doubles) is allocated by the pattern on first use and kept. */
+ * ambient doubles and 7,296 for the partial sums) is allocated by the pattern
+ * on first use and kept. */
 lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, const lfem_quad* quad, double tau,
                           double rtol, int max_iter, double* coords_out, int* iterations, void* cuda_stream);
 

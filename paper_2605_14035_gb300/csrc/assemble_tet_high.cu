@@ -47,36 +47,39 @@ __device__ __forceinline__ void tet_high_block(int lane, int& r0, int& c0) {
       }
 }
 
-// One matrix of one element: MODE 0 mass, 1 stiffness, 2 coefficient-weighted mass.
+// One element: MODE 0 mass, 1 stiffness, 2 coefficient-weighted mass (into
+// dst), 3 mass and stiffness in one sweep over the points (dst, dst2): the
+// node factors (w s phi_b, H grad^phi_b) share one row, so a point costs one
+// factor stage and one set of row loads for both matrices.
 template <int P, typename R, typename RS, int MODE>
 __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane, int r0,
-                                              int c0, RS* dst) {
+                                              int c0, RS* dst, RS* dst2 = nullptr) {
   constexpr int REF = TetHigh<P>::REF, ROW = TetHigh<P>::ROW, RA = TetHigh<P>::RA, RB = TetHigh<P>::RB;
-  R acc[RA][RB];
+  constexpr bool STIFF = MODE == 1 || MODE == 3, MASS = MODE != 1;
+  R acc[RA][RB], accm[RA][RB];
 #pragma unroll
   for (int i = 0; i < RA; ++i)
 #pragma unroll
-    for (int j = 0; j < RB; ++j) acc[i][j] = (R)0;
+    for (int j = 0; j < RB; ++j) acc[i][j] = accm[i][j] = (R)0;
   for (int q = 0; q < Q; ++q) {
     const V4<R> g0 = geo[2 * q], g1 = geo[2 * q + 1];
     const V4<R>* tq = tab + q * ROW;
     for (int b = lane; b < REF; b += 32) {
       const V4<R> d = tq[b];
       V4<R> h;
-      if constexpr (MODE == 1) {
-        h.x = (R)0;
+      h.x = MASS ? (MODE == 2 ? g0.x * g1.w : g0.x) * d.x : (R)0;
+      if constexpr (STIFF) {
         h.y = fma(g0.y, d.y, fma(g0.z, d.z, g0.w * d.w));
         h.z = fma(g0.z, d.y, fma(g1.x, d.z, g1.y * d.w));
         h.w = fma(g0.w, d.y, fma(g1.y, d.z, g1.z * d.w));
       } else {
-        h.x = (MODE == 0 ? g0.x : g0.x * g1.w) * d.x;
         h.y = h.z = h.w = (R)0;
       }
       hb[b] = h;
     }
     __syncwarp();
     if (r0 >= 0) {
-      if constexpr (MODE == 1) {
+      if constexpr (STIFF) {
         V4<R> hv[RB];
 #pragma unroll
         for (int j = 0; j < RB; ++j) hv[j] = hb[c0 + j];
@@ -84,8 +87,10 @@ __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const
         for (int i = 0; i < RA; ++i) {
           const V4<R> da = tq[r0 + i];
 #pragma unroll
-          for (int j = 0; j < RB; ++j)
+          for (int j = 0; j < RB; ++j) {
             acc[i][j] = fma(da.y, hv[j].y, fma(da.z, hv[j].z, fma(da.w, hv[j].w, acc[i][j])));
+            if constexpr (MODE == 3) accm[i][j] = fma(da.x, hv[j].x, accm[i][j]);
+          }
         }
       } else {
         R hx[RB];
@@ -106,7 +111,15 @@ __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const
     for (int i = 0; i < RA; ++i)
 #pragma unroll
       for (int j = 0; j < RB; ++j)
-        if (r0 + i <= c0 + j) dst[upper_index(REF, r0 + i, c0 + j)] = (RS)acc[i][j];
+        if (r0 + i <= c0 + j) {
+          const int u = upper_index(REF, r0 + i, c0 + j);
+          if constexpr (MODE == 3) {
+            dst[u] = (RS)accm[i][j];
+            dst2[u] = (RS)acc[i][j];
+          } else {
+            dst[u] = (RS)acc[i][j];
+          }
+        }
   }
 }
 
@@ -207,11 +220,13 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
     }
     __syncwarp();
     RS* dst = static_cast<RS*>(a.lbuf) + (size_t)e * a.nm * U;
-    if (a.which & LFEM_MASS) {
+    if ((a.which & LFEM_MASS) && (a.which & LFEM_STIFF)) {
+      tet_high_pass<P, R, RS, 3>(tab, hb, geo, Q, lane, r0, c0, dst, dst + U);
+      dst += 2 * U;
+    } else if (a.which & LFEM_MASS) {
       tet_high_pass<P, R, RS, 0>(tab, hb, geo, Q, lane, r0, c0, dst);
       dst += U;
-    }
-    if (a.which & LFEM_STIFF) {
+    } else if (a.which & LFEM_STIFF) {
       tet_high_pass<P, R, RS, 1>(tab, hb, geo, Q, lane, r0, c0, dst);
       dst += U;
     }

@@ -359,6 +359,7 @@ static void destroy_dev(PatternDev& d) {
                   d.slot_off,  d.slot_ent,      d.elem_buf,  d.vec_buf,   d.mcf_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (d.mcf_graph.exec) cudaGraphExecDestroy(d.mcf_graph.exec);
   d = PatternDev{};
 }
 
@@ -867,7 +868,7 @@ lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, c
   const size_t nnz = (size_t)p->nnz, n = (size_t)p->n_nodes;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t b_mat = al(sizeof(double) * nnz), b_vec = al(sizeof(double) * n * nc), b_dg = al(sizeof(double) * n);
-  const size_t b_part = al(sizeof(double) * 256 * 3), b_sc = al(sizeof(McfScalars));
+  const size_t b_part = al(sizeof(double) * 4 * kMcfBlocks * 3), b_sc = al(sizeof(McfScalars));
   const size_t need = 3 * b_mat + b_dg + 6 * b_vec + b_part + b_sc;
   if (need > p->d.mcf_buf_bytes) {
     if (p->d.mcf_buf) cudaFree(p->d.mcf_buf);
@@ -898,6 +899,7 @@ lfem_status lfem_mcf_step(lfem_pattern_t p, const double* coords, int ambient, c
   s.P = reinterpret_cast<double*>(take(b_vec));
   s.part = reinterpret_cast<double*>(take(b_part));
   s.scalars = reinterpret_cast<McfScalars*>(take(b_sc));
+  s.graph = &p->d.mcf_graph;
   lfem_status e = lfem_assemble(p, coords, ambient, quad, nullptr, 0, LFEM_MASS | LFEM_STIFF, LFEM_FP64, M, A,
                                 nullptr, cuda_stream);
   if (e != LFEM_OK) return e;

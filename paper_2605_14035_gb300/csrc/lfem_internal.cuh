@@ -500,6 +500,21 @@ struct VecArgs {
   TabRef tab;
 };
 
+// Blocks of every reducing kernel of the flow step's solver (fixed, so every
+// dot product is the same sum on every run); its partials take
+// 4 x kMcfBlocks x 3 doubles of scratch.
+constexpr int kMcfBlocks = 608;
+
+// The solver's 8-iteration block as an instantiated CUDA graph, and the
+// scratch layout it was captured for.
+struct McfGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void* buf = nullptr;
+  const void* K = nullptr;
+  int32_t n = 0;
+  int nc = 0;
+};
+
 // Device scalars of the solve, per column.
 struct McfScalars {
   double rz[3], pq[3], rz_new[3], rr[3], bb[3];
@@ -523,8 +538,9 @@ struct McfSolveArgs {
   double* R;
   double* Z;
   double* P;
-  double* part;
+  double* part;  // [4][kMcfBlocks][nc]: <p, q>, <r, r> / <b, b>, two sets of <r, z>
   McfScalars* scalars;
+  McfGraph* graph;
   double* X_out;
   double rtol;
   int max_iter;
@@ -551,6 +567,7 @@ struct PatternDev {
   size_t vec_buf_bytes = 0;
   void* mcf_buf = nullptr;       // mean-curvature-flow step: matrices and solver vectors (scratch)
   size_t mcf_buf_bytes = 0;
+  McfGraph mcf_graph;            // its captured solver iterations
   uint8_t* tile_meta = nullptr;  // per-tile metadata blocks (see TileHdr)
   int64_t* tile_meta_off = nullptr;  // [T+1] byte offsets, multiples of 16
   ItemRef* tile_refs = nullptr;  // [T] block address and part sizes per tile

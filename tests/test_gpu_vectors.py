@@ -86,6 +86,19 @@ def test_mcf_step(name, lfem):
     xin = xd.clone()
     lfem.mcf_step(pat, xin, rule, tau, rtol=1e-13, max_iter=5000, out=xin)
     assert torch.equal(xin, x1)
+    # on a side stream the 8-iteration blocks replay a captured graph: the same
+    # kernels, so the same bits (first call captures, second replays)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            xs, its = lfem.mcf_step(pat, xd, rule, tau, rtol=1e-13, max_iter=5000, stream=stream)
+            stream.synchronize()
+            assert its == it and torch.equal(xs, x1)
+        # a cap that is not a multiple of the check interval ends on direct launches
+        xc, itc = lfem.mcf_step(pat, xd, rule, tau, rtol=1e-30, max_iter=13, stream=stream)
+        stream.synchronize()
+    xd13, itd = lfem.mcf_step(pat, xd, rule, tau, rtol=1e-30, max_iter=13)
+    assert itc == itd == 13 and torch.equal(xc, xd13)
 
 
 @pytest.mark.parametrize("kind,order", [("sphere", 3), ("sphere", 4), ("disk", 3), ("disk", 4), ("circle", 4),
