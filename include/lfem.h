@@ -350,7 +350,10 @@ lfem_status lfem_assemble_adjoint_mixed(lfem_pattern_t p, const double* coords, 
  * lfem_local: element matrices by quadrature, upper triangle (a <= b, row-major
  *   order (0,0),(0,1)..(0,ref-1),(1,1)..), double [n_elem][ref(ref+1)/2] each.
  * conn and coords are device pointers; these calls are asynchronous and set
- * no status word (non-finite results are written as computed).
+ * no status word (non-finite results are written as computed).  Orders 1-4
+ * on curves and triangles, orders 1-2 on tets; order-3/4 tets return
+ * LFEM_E_UNSUPPORTED (their basis tables live on the device, not in the
+ * constant bank these kernels read).
  */
 lfem_status lfem_eval_points(const int32_t* conn, int64_t n_elem, int dim, int order, const double* coords,
                              int ambient, const lfem_quad* quad, double* out, void* cuda_stream);

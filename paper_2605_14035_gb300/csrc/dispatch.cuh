@@ -26,6 +26,7 @@ lfem_status bank_upload_high(const void* src, size_t bytes, size_t offset);
 lfem_status run_twopass_high(int D, int NA, int P, bool mixed, const TwoPassArgs& a, int sms, cudaStream_t st);
 lfem_status bank_upload_tet_high(const void* src, size_t bytes, size_t offset);
 lfem_status bank_upload_adj_high(const void* src, size_t bytes, size_t offset);
+lfem_status run_stage_high(int D, int NA, int P, int kind, const StageArgs& s, cudaStream_t st);
 // Orders 3, 4: the adjoint (FP64, warp per element); scratch holds
 // adjoint_high_scratch_bytes(...) bytes.
 size_t adjoint_high_scratch_bytes(int dim, int P, int Q, int ambient, int64_t n_elem);

@@ -337,6 +337,11 @@ lfem_status get_tables(int dim, int order, const lfem_quad* quad, cudaStream_t s
 lfem_status build_pattern(lfem_pattern_s* p, const int32_t* conn_in, cudaStream_t st);
 
 static lfem_status run_stage(int dim, int NA, int P, int kind, const StageArgs& s, cudaStream_t st) {
+  if (P >= 3) {
+    // order-3/4 tets keep their basis tables on the device (the rule alone is in the bank)
+    if (dim == 3) return fail(LFEM_E_UNSUPPORTED, "the element stages cover order-3/4 curves and triangles, not tets");
+    return run_stage_high(dim, NA, P, kind, s, st);
+  }
   if (dim == 1) return run_stage_d1(NA, P, kind, s, st);
   if (dim == 2) return run_stage_d2(NA, P, kind, s, st);
   return run_stage_d3(NA, P, kind, s, st);

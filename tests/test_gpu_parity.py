@@ -197,7 +197,8 @@ def test_subsets_of_matrices(which, lfem):
             assert k not in part
 
 
-@pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p1", "space_curve_p2"])
+@pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p1", "space_curve_p2",
+                                  "sphere_p3", "sphere_p4", "disk_p3", "circle_p4"])
 def test_element_stages(name, lfem):
     x, e, d, p, rule, coef, pat = prepare(name, lfem, tile_slots=0)
     ed, xd = to_dev(e), to_dev(x)
@@ -215,6 +216,14 @@ def test_element_stages(name, lfem):
     for got, want in ((Ml, oM), (Al, oA), (Cl, oC)):
         w = want[:, iu[0], iu[1]]
         assert np.abs(got - w).max() <= 1e-12 * np.abs(w).max()
+
+
+def test_element_stages_reject_high_order_tets(lfem):
+    """Order-3/4 tets keep their basis tables on the device: the stages say so."""
+    x, e, d, p, rule, coef, pat = prepare("cube_p3", lfem, tile_slots=0)
+    with pytest.raises(lfem.LfemError) as ei:
+        lfem.eval_points(to_dev(e), d, p, to_dev(x), rule)
+    assert ei.value.code == 3
 
 
 @pytest.mark.parametrize("name", ["ellipsoid_p2", "cube_p2", "curve_p2", "disk_p2", "sphere_p1", "space_curve_p2"])
