@@ -275,7 +275,9 @@ __global__ void __launch_bounds__(128) k_tet2_redo(const TwoPassArgs a) {
   constexpr int REF = Tet2Pack::REF, U = Tet2Pack::U;
   const unsigned long long n = *a.fallback;
   float* lb = static_cast<float*>(a.lbuf);
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+  // consecutive list entries go to different CTAs first, so the list spreads
+  // over every SM's FP64 pipe
+  for (unsigned long long i = (unsigned long long)threadIdx.x * gridDim.x + blockIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const int64_t e = a.redo[i];
     int32_t nodes[REF];

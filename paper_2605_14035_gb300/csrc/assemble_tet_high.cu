@@ -47,25 +47,29 @@ __device__ __forceinline__ void tet_high_block(int lane, int& r0, int& c0) {
       }
 }
 
-// One element: MODE 0 mass, 1 stiffness, 2 coefficient-weighted mass (into
-// dst), 3 mass and stiffness in one sweep over the points (dst, dst2): the
-// node factors (w s phi_b, H grad^phi_b) share one row, so a point costs one
-// factor stage and one set of row loads for both matrices.
-template <int P, typename R, typename RS, int MODE>
-__device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane, int r0,
-                                              int c0, RS* dst, RS* dst2 = nullptr) {
+// The lane's register block of one element summed over the points q0, q0 + qs,
+// ...: MODE 0 mass, 1 stiffness, 2 coefficient-weighted mass (in acc), 3 mass
+// (accm) and stiffness (acc) in one sweep: the node factors (w s phi_b,
+// H grad^phi_b) share one row, so a point costs one factor stage and one set
+// of row loads for both matrices.
+template <int P, typename R, int MODE>
+__device__ __forceinline__ void tet_high_accumulate(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int q0,
+                                                    int qs, int lane, int r0, int c0,
+                                                    R (&acc)[TetHigh<P>::RA][TetHigh<P>::RB],
+                                                    R (&accm)[TetHigh<P>::RA][TetHigh<P>::RB]) {
   constexpr int REF = TetHigh<P>::REF, ROW = TetHigh<P>::ROW, RA = TetHigh<P>::RA, RB = TetHigh<P>::RB;
+  constexpr int NRB = TetHigh<P>::NRB, NCB = TetHigh<P>::NCB;
   constexpr bool STIFF = MODE == 1 || MODE == 3, MASS = MODE != 1;
-  R acc[RA][RB], accm[RA][RB];
+  const int rb = r0 / RA, cb = c0 / RB;  // the block's slots (row_slot, col_slot)
 #pragma unroll
   for (int i = 0; i < RA; ++i)
 #pragma unroll
     for (int j = 0; j < RB; ++j) acc[i][j] = accm[i][j] = (R)0;
-  for (int q = 0; q < Q; ++q) {
+  for (int q = q0; q < Q; q += qs) {
     const V4<R> g0 = geo[2 * q], g1 = geo[2 * q + 1];
     const V4<R>* tq = tab + q * ROW;
     for (int b = lane; b < REF; b += 32) {
-      const V4<R> d = tq[b];
+      const V4<R> d = tq[TetHigh<P>::row_slot(b)];
       V4<R> h;
       h.x = MASS ? (MODE == 2 ? g0.x * g1.w : g0.x) * d.x : (R)0;
       if constexpr (STIFF) {
@@ -75,17 +79,17 @@ __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const
       } else {
         h.y = h.z = h.w = (R)0;
       }
-      hb[b] = h;
+      hb[TetHigh<P>::col_slot(b)] = h;
     }
     __syncwarp();
     if (r0 >= 0) {
       if constexpr (STIFF) {
         V4<R> hv[RB];
 #pragma unroll
-        for (int j = 0; j < RB; ++j) hv[j] = hb[c0 + j];
+        for (int j = 0; j < RB; ++j) hv[j] = hb[j * NCB + cb];
 #pragma unroll
         for (int i = 0; i < RA; ++i) {
-          const V4<R> da = tq[r0 + i];
+          const V4<R> da = tq[i * NRB + rb];
 #pragma unroll
           for (int j = 0; j < RB; ++j) {
             acc[i][j] = fma(da.y, hv[j].y, fma(da.z, hv[j].z, fma(da.w, hv[j].w, acc[i][j])));
@@ -95,10 +99,10 @@ __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const
       } else {
         R hx[RB];
 #pragma unroll
-        for (int j = 0; j < RB; ++j) hx[j] = hb[c0 + j].x;
+        for (int j = 0; j < RB; ++j) hx[j] = hb[j * NCB + cb].x;
 #pragma unroll
         for (int i = 0; i < RA; ++i) {
-          const R pa = tq[r0 + i].x;
+          const R pa = tq[i * NRB + rb].x;
 #pragma unroll
           for (int j = 0; j < RB; ++j) acc[i][j] = fma(pa, hx[j], acc[i][j]);
         }
@@ -106,21 +110,95 @@ __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const
     }
     __syncwarp();
   }
-  if (r0 >= 0) {
+}
+
+// The lane's block of the upper triangle to dst (and dst2, MODE 3).
+template <int P, typename R, typename RS, int MODE>
+__device__ __forceinline__ void tet_high_store(int r0, int c0, const R (&acc)[TetHigh<P>::RA][TetHigh<P>::RB],
+                                               const R (&accm)[TetHigh<P>::RA][TetHigh<P>::RB], RS* dst, RS* dst2) {
+  constexpr int REF = TetHigh<P>::REF, RA = TetHigh<P>::RA, RB = TetHigh<P>::RB;
+  if (r0 < 0) return;
 #pragma unroll
-    for (int i = 0; i < RA; ++i)
+  for (int i = 0; i < RA; ++i)
 #pragma unroll
-      for (int j = 0; j < RB; ++j)
-        if (r0 + i <= c0 + j) {
-          const int u = upper_index(REF, r0 + i, c0 + j);
-          if constexpr (MODE == 3) {
-            dst[u] = (RS)accm[i][j];
-            dst2[u] = (RS)acc[i][j];
-          } else {
-            dst[u] = (RS)acc[i][j];
-          }
+    for (int j = 0; j < RB; ++j)
+      if (r0 + i <= c0 + j) {
+        const int u = upper_index(REF, r0 + i, c0 + j);
+        if constexpr (MODE == 3) {
+          dst[u] = (RS)accm[i][j];
+          dst2[u] = (RS)acc[i][j];
+        } else {
+          dst[u] = (RS)acc[i][j];
         }
+      }
+}
+
+// One element, every point, one warp: MODE 0 mass, 1 stiffness, 2 coefficient-
+// weighted mass (into dst), 3 mass and stiffness in one sweep (dst, dst2).
+template <int P, typename R, typename RS, int MODE>
+__device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane, int r0,
+                                              int c0, RS* dst, RS* dst2 = nullptr) {
+  R acc[TetHigh<P>::RA][TetHigh<P>::RB], accm[TetHigh<P>::RA][TetHigh<P>::RB];
+  tet_high_accumulate<P, R, MODE>(tab, hb, geo, Q, 0, 1, lane, r0, c0, acc, accm);
+  tet_high_store<P, R, RS, MODE>(r0, c0, acc, accm, dst, dst2);
+}
+
+// Geometry of point q of element e (rel = x_b - x_0): (w s, H00, H01, H02) and
+// (H11, H12, H22, c_q) with H = w s G^{-1} = (w / s) adj(G) from the cofactors
+// of J; bad: |det J| zero or not finite; redo (float): the conditioning test failed.
+template <int P, typename R>
+__device__ __forceinline__ void tet_high_point(const TwoPassArgs& a, const V4<R>* tab, const V4<R>* rel,
+                                               const double* w64, int64_t e, int q, V4<R>* geo, bool& bad,
+                                               bool& redo) {
+  constexpr int REF = TetHigh<P>::REF, ROW = TetHigh<P>::ROW;
+  const int Q = a.tab.q;
+  const V4<R>* tq = tab + q * ROW;
+  R J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int b = 1; b < REF; ++b) {
+    const V4<R> r = rel[b], d = tq[TetHigh<P>::row_slot(b)];
+    J[0][0] = fma(r.x, d.y, J[0][0]);
+    J[0][1] = fma(r.x, d.z, J[0][1]);
+    J[0][2] = fma(r.x, d.w, J[0][2]);
+    J[1][0] = fma(r.y, d.y, J[1][0]);
+    J[1][1] = fma(r.y, d.z, J[1][1]);
+    J[1][2] = fma(r.y, d.w, J[1][2]);
+    J[2][0] = fma(r.z, d.y, J[2][0]);
+    J[2][1] = fma(r.z, d.z, J[2][1]);
+    J[2][2] = fma(r.z, d.w, J[2][2]);
   }
+  R c[3][3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+    c[m][0] = J[1][m1] * J[2][m2] - J[2][m1] * J[1][m2];
+    c[m][1] = J[2][m1] * J[0][m2] - J[0][m1] * J[2][m2];
+    c[m][2] = J[0][m1] * J[1][m2] - J[1][m1] * J[0][m2];
+  }
+  const R det = J[0][0] * c[0][0] + J[1][0] * c[0][1] + J[2][0] * c[0][2];
+  const R s = fabs(det);
+  const R wq = (R)w64[q];
+  const R f = wq * rcp_(s);
+  R H[6];
+  int h = 0;
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int k = m; k < 3; ++k) H[h++] = f * (c[m][0] * c[k][0] + c[m][1] * c[k][1] + c[m][2] * c[k][2]);
+  R tr = 0;
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) tr = fma(J[ii][m], J[ii][m], tr);
+  tr *= (R)(1.0 / 3.0);
+  const R quality = (s * s) * rcp_(tr * tr * tr);
+  bad |= !(s > (R)0) || !isfinite(s) || !(quality > (sizeof(R) == 8 ? (R)1e-28 : (R)1e-12));
+  if constexpr (sizeof(R) == 4) redo |= quality < (R)a.qmin;
+  R cq = (R)0;
+  if (a.which & LFEM_CMASS)
+    cq = a.coef_f32 ? (R)__ldg(static_cast<const float*>(a.coef) + e * Q + q)
+                    : (R)__ldg(static_cast<const double*>(a.coef) + e * Q + q);
+  geo[2 * q] = V4<R>{wq * s, H[0], H[1], H[2]};
+  geo[2 * q + 1] = V4<R>{H[3], H[4], H[5], cq};
 }
 
 // list == nullptr: every element; else the list[0 .. *list_n) (FP64 recomputation).
@@ -138,14 +216,19 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
   V4<R>* rel = tab + Q * ROW + warp * (2 * REF + 2 * Q);  // [REF] x_b - x_0
   V4<R>* hb = rel + REF;                                 // [REF] per-point node factors
   V4<R>* geo = hb + REF;                                 // [Q][2] (w s, H00, H01, H02), (H11, H12, H22, c_q)
-  for (int t = threadIdx.x; t < Q * ROW; t += blockDim.x) tab[t] = gtab[t];
+  // the basis rows of every point in their row_slot order (padding unused)
+  for (int t = threadIdx.x; t < Q * REF; t += blockDim.x) {
+    const int q = t / REF, b = t - q * REF;
+    tab[q * ROW + TetHigh<P>::row_slot(b)] = gtab[q * ROW + b];
+  }
   __syncthreads();
   const double* w64 = bank<double>() + a.tab.off64;
   int r0, c0;  // this lane's register block
   tet_high_block<P>(lane, r0, c0);
   const int64_t n_work = list ? (int64_t)*list_n : a.n_elem;
-  for (int64_t i = (int64_t)blockIdx.x * kTetHighWarps + warp; i < n_work;
-       i += (int64_t)gridDim.x * kTetHighWarps) {
+  // consecutive work items go to different CTAs first: a short list (the FP64
+  // pass) then spreads over every SM's FP64 pipe instead of a few SMs' warps
+  for (int64_t i = (int64_t)warp * gridDim.x + blockIdx.x; i < n_work; i += (int64_t)gridDim.x * kTetHighWarps) {
     const int64_t e = list ? (int64_t)list[1 + i] : i;
     const int32_t* cn = a.conn + e * REF;
     const int64_t n0 = __ldg(cn);
@@ -157,55 +240,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
     }
     __syncwarp();
     bool bad = false, redo = false;
-    for (int q = lane; q < Q; q += 32) {
-      const V4<R>* tq = tab + q * ROW;
-      R J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      for (int b = 1; b < REF; ++b) {
-        const V4<R> r = rel[b], d = tq[b];
-        J[0][0] = fma(r.x, d.y, J[0][0]);
-        J[0][1] = fma(r.x, d.z, J[0][1]);
-        J[0][2] = fma(r.x, d.w, J[0][2]);
-        J[1][0] = fma(r.y, d.y, J[1][0]);
-        J[1][1] = fma(r.y, d.z, J[1][1]);
-        J[1][2] = fma(r.y, d.w, J[1][2]);
-        J[2][0] = fma(r.z, d.y, J[2][0]);
-        J[2][1] = fma(r.z, d.z, J[2][1]);
-        J[2][2] = fma(r.z, d.w, J[2][2]);
-      }
-      R c[3][3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
-        c[m][0] = J[1][m1] * J[2][m2] - J[2][m1] * J[1][m2];
-        c[m][1] = J[2][m1] * J[0][m2] - J[0][m1] * J[2][m2];
-        c[m][2] = J[0][m1] * J[1][m2] - J[1][m1] * J[0][m2];
-      }
-      const R det = J[0][0] * c[0][0] + J[1][0] * c[0][1] + J[2][0] * c[0][2];
-      const R s = fabs(det);
-      const R wq = (R)w64[q];
-      const R f = wq * rcp_(s);
-      R H[6];
-      int h = 0;
-#pragma unroll
-      for (int m = 0; m < 3; ++m)
-#pragma unroll
-        for (int k = m; k < 3; ++k) H[h++] = f * (c[m][0] * c[k][0] + c[m][1] * c[k][1] + c[m][2] * c[k][2]);
-      R tr = 0;
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) tr = fma(J[ii][m], J[ii][m], tr);
-      tr *= (R)(1.0 / 3.0);
-      const R quality = (s * s) * rcp_(tr * tr * tr);
-      bad |= !(s > (R)0) || !isfinite(s) || !(quality > (sizeof(R) == 8 ? (R)1e-28 : (R)1e-12));
-      if constexpr (sizeof(R) == 4) redo |= quality < (R)a.qmin;
-      R cq = (R)0;
-      if (a.which & LFEM_CMASS)
-        cq = a.coef_f32 ? (R)__ldg(static_cast<const float*>(a.coef) + e * Q + q)
-                        : (R)__ldg(static_cast<const double*>(a.coef) + e * Q + q);
-      geo[2 * q] = V4<R>{wq * s, H[0], H[1], H[2]};
-      geo[2 * q + 1] = V4<R>{H[3], H[4], H[5], cq};
-    }
+    for (int q = lane; q < Q; q += 32) tet_high_point<P, R>(a, tab, rel, w64, e, q, geo, bad, redo);
     if constexpr (sizeof(R) == 4) {
       if (__any_sync(0xffffffffu, bad || redo)) {
         if (lane == 0) {
@@ -232,6 +267,119 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
     }
     if (a.which & LFEM_CMASS) tet_high_pass<P, R, RS, 2>(tab, hb, geo, Q, lane, r0, c0, dst);
   }
+}
+
+// The elements the float pass listed (list[0] of them, from list[1]) again in
+// FP64, one CTA per element: the CTA computes the geometry of every point, each
+// warp sums its register blocks over the points w, w + kTetHighWarps, ..., and
+// warp 0 adds the other warps' partial blocks in warp order (fixed, so
+// reruns are bit-identical).  Four warps per element keep the SM's FP64 pipe
+// busy where one warp's dependent chains would leave it idle.
+template <int P, int MODE>
+__device__ __forceinline__ void tet_high_list_pass(const V4<double>* tab, V4<double>* hb, const V4<double>* geo, int Q,
+                                                   int warp, int lane, int r0, int c0, double* part, float* dst,
+                                                   float* dst2) {
+  constexpr int RA = TetHigh<P>::RA, RB = TetHigh<P>::RB, NB = RA * RB;
+  double acc[RA][RB], accm[RA][RB];
+  tet_high_accumulate<P, double, MODE>(tab, hb, geo, Q, warp, kTetHighWarps, lane, r0, c0, acc, accm);
+  if (warp > 0) {
+    double* pw = part + (size_t)(warp - 1) * 2 * NB * 32;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      pw[k * 32 + lane] = acc[k / RB][k % RB];
+      pw[(NB + k) * 32 + lane] = accm[k / RB][k % RB];
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < kTetHighWarps; ++w) {
+      const double* pw = part + (size_t)(w - 1) * 2 * NB * 32;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        acc[k / RB][k % RB] += pw[k * 32 + lane];
+        accm[k / RB][k % RB] += pw[(NB + k) * 32 + lane];
+      }
+    }
+    tet_high_store<P, double, float, MODE>(r0, c0, acc, accm, dst, dst2);
+  }
+  __syncthreads();
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_list(const TwoPassArgs a,
+                                                                      const V4<double>* __restrict__ gtab,
+                                                                      const uint32_t* __restrict__ list) {
+  constexpr int REF = TetHigh<P>::REF, U = TetHigh<P>::U, ROW = TetHigh<P>::ROW;
+  const int Q = a.tab.q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V4<double>* tab = reinterpret_cast<V4<double>*>(smem_raw);  // [Q][ROW]
+  V4<double>* rel = tab + (size_t)Q * ROW;                    // [REF] x_b - x_0
+  V4<double>* geo = rel + REF;                                // [Q][2]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V4<double>* hb = geo + 2 * Q + warp * REF;                               // per warp [REF]
+  double* part = reinterpret_cast<double*>(geo + 2 * Q + kTetHighWarps * REF);  // [warps - 1][2 RA RB][32]
+  __shared__ int s_bad;
+  for (int t = threadIdx.x; t < Q * REF; t += blockDim.x) {
+    const int q = t / REF, b = t - q * REF;
+    tab[q * ROW + TetHigh<P>::row_slot(b)] = gtab[q * ROW + b];
+  }
+  const double* w64 = bank<double>() + a.tab.off64;
+  int r0, c0;
+  tet_high_block<P>(lane, r0, c0);
+  const int64_t n_work = list[0];
+  for (int64_t i = blockIdx.x; i < n_work; i += gridDim.x) {
+    const int64_t e = list[1 + i];
+    const int32_t* cn = a.conn + e * REF;
+    const int64_t n0 = __ldg(cn);
+    __syncthreads();  // the table is staged; the previous element has left rel and geo
+    if (threadIdx.x == 0) s_bad = 0;
+    for (int b = threadIdx.x; b < REF; b += blockDim.x) {
+      const int64_t nb = __ldg(cn + b);
+      rel[b] = V4<double>{__ldg(a.coords + 3 * nb) - __ldg(a.coords + 3 * n0),
+                          __ldg(a.coords + 3 * nb + 1) - __ldg(a.coords + 3 * n0 + 1),
+                          __ldg(a.coords + 3 * nb + 2) - __ldg(a.coords + 3 * n0 + 2), 0.0};
+    }
+    __syncthreads();
+    bool bad = false, redo = false;
+    for (int q = threadIdx.x; q < Q; q += blockDim.x) tet_high_point<P, double>(a, tab, rel, w64, e, q, geo, bad, redo);
+    if (bad) s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_bad) atomicOr(a.status, ST_DEGENERATE);
+    float* dst = static_cast<float*>(a.lbuf) + (size_t)e * a.nm * U;
+    if ((a.which & LFEM_MASS) && (a.which & LFEM_STIFF)) {
+      tet_high_list_pass<P, 3>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, dst + U);
+      dst += 2 * U;
+    } else if (a.which & LFEM_MASS) {
+      tet_high_list_pass<P, 0>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr);
+      dst += U;
+    } else if (a.which & LFEM_STIFF) {
+      tet_high_list_pass<P, 1>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr);
+      dst += U;
+    }
+    if (a.which & LFEM_CMASS) tet_high_list_pass<P, 2>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr);
+  }
+}
+
+template <int P>
+static size_t tet_high_list_smem(int Q) {
+  constexpr int REF = TetHigh<P>::REF, NB = TetHigh<P>::RA * TetHigh<P>::RB;
+  return sizeof(V4<double>) * ((size_t)Q * TetHigh<P>::ROW + REF + 2 * (size_t)Q + (size_t)kTetHighWarps * REF) +
+         sizeof(double) * (size_t)(kTetHighWarps - 1) * 2 * NB * 32;
+}
+
+template <int P>
+static lfem_status launch_tet_high_list(const TwoPassArgs& a, const V4<double>* gtab, const uint32_t* list, int sms,
+                                        cudaStream_t st) {
+  const size_t smem = tet_high_list_smem<P>(a.tab.q);
+  auto kern = k_tet_high_list<P>;
+  LFEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  LFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTetHighWarps * 32, smem));
+  if (occ < 1) return fail(LFEM_E_TOO_LARGE, "order-3/4 tet tables exceed shared memory");
+  // the count is on the device: one CTA per SM and element, grid-strided beyond
+  kern<<<(unsigned)sms, kTetHighWarps * 32, smem, st>>>(a, gtab, list);
+  LFEM_CUDA(cudaGetLastError());
+  return LFEM_OK;
 }
 
 template <int P, typename R>
@@ -270,10 +418,8 @@ static lfem_status run_tet_high_p(bool mixed, const TwoPassArgs& a, void* scratc
     if (mixed) {
       LFEM_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), st));
       if ((s = launch_tet_high_pass<P, float, float>(a, t32, nullptr, flags, a.n_elem, sms, st)) != LFEM_OK) return s;
-      // the listed elements again in FP64 (the grid covers whatever the count turns out to be)
-      if ((s = launch_tet_high_pass<P, double, float>(a, t64, flags, nullptr, (int64_t)sms * kTetHighWarps, sms,
-                                                      st)) != LFEM_OK)
-        return s;
+      // the listed elements again in FP64, a CTA per element
+      if ((s = launch_tet_high_list<P>(a, t64, flags, sms, st)) != LFEM_OK) return s;
     } else if ((s = launch_tet_high_pass<P, double, double>(a, t64, nullptr, nullptr, a.n_elem, sms, st)) != LFEM_OK) {
       return s;
     }

@@ -20,6 +20,12 @@ struct TetHigh {
   // table row stride in 16-byte units, odd: lanes reading rows of different
   // points (the geometry phase) then fall on distinct banks
   static constexpr int ROW = REF | 1;
+  // shared-memory slot of basis row r (r = RA blk + i -> i NRB + blk) and of
+  // node factor c (c = RB cb + j -> j NCB + cb): the lanes' block rows r0 + i
+  // (and columns c0 + j) are then consecutive 16-byte slots, free of bank
+  // conflicts, instead of RA (RB) rows apart
+  __host__ __device__ static constexpr int row_slot(int r) { return (r % RA) * NRB + r / RA; }
+  __host__ __device__ static constexpr int col_slot(int c) { return (c % RB) * NCB + c / RB; }
 };
 
 template <typename R>
