@@ -19,14 +19,6 @@ namespace lfem {
     if (_s != LFEM_OK) return _s;       \
   } while (0)
 
-template <typename EntT>
-static lfem_status launch_batch(const PipeArgs& a, const FastBank& fb, int sms, cudaStream_t st) {
-  return launch_pipe_types<float, EntT, EType<1, 2, 1, true>, EType<1, 2, 2, true>, EType<2, 2, 1, true>,
-                           EType<2, 2, 2, true>, EType<2, 3, 1, true>, EType<2, 3, 2, true>, EType<1, 2, 1>,
-                           EType<1, 2, 2>, EType<2, 2, 1>, EType<2, 2, 2>, EType<2, 3, 1>, EType<2, 3, 2>>(a, fb, sms,
-                                                                                                       st);
-}
-
 __global__ void k_set_item_mesh(ItemRef* refs, int64_t n, int mesh) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) refs[t].mesh = mesh;
@@ -68,6 +60,15 @@ struct lfem_batch_s {
     void* MC;
   };
   std::vector<Side> side;
+  // runs of the work list with one element type (the list is sorted by
+  // family), each launched as its own persistent single-type kernel with the
+  // shared-memory caps of its meshes: one kernel over every type spills
+  struct Seg {
+    int dim, na, order;
+    bool fast;
+    PipeArgs args;
+  };
+  std::vector<Seg> segs;
   unsigned which = 0;
   int coef_f32 = 0;
 };
@@ -76,10 +77,10 @@ static lfem_status batch_launch(lfem_batch_s* b, cudaStream_t st) {
   int sms = 0;
   LFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   LFEM_CUDA(cudaMemsetAsync(b->d_status + 2, 0, sizeof(unsigned long long), st));
-  LFEM_CUDA(cudaMemsetAsync(b->d_status + 4, 0, sizeof(unsigned long long), st));  // tile tickets
-  if (b->args.n_items > 0) {
-    const lfem_status s = b->ent_bytes == 2 ? launch_batch<uint16_t>(b->args, b->fb, sms, st)
-                                            : launch_batch<uint32_t>(b->args, b->fb, sms, st);
+  for (const auto& g : b->segs) {
+    LFEM_CUDA(cudaMemsetAsync(b->d_status + 4, 0, sizeof(unsigned long long), st));  // tile tickets
+    const lfem_status s = g.dim == 1 ? run_pipe_d1(g.na, g.order, true, g.args, b->ent_bytes, g.fast, b->fb, sms, st)
+                                     : run_pipe_d2(g.na, g.order, true, g.args, b->ent_bytes, g.fast, b->fb, sms, st);
     if (s != LFEM_OK) return s;
   }
   for (auto& sd : b->side) {
@@ -133,6 +134,15 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
     if ((s = reserve_elem_buf(p, nm_all, true, tab.q)) != LFEM_OK) return s;
     side_v.push_back(std::move(sd));
   }
+  // the work list holds the meshes family by family (dim, order, ambient), so
+  // neighbouring CTAs run the same element code (one type's phase 1 at a time
+  // in the instruction cache); every tile owns its rows, so the order changes
+  // no result
+  std::stable_sort(pipe_v.begin(), pipe_v.end(), [](const lfem_batch_item& x, const lfem_batch_item& y) {
+    const int kx = (x.pattern->dim * 8 + x.pattern->order) * 4 + x.ambient;
+    const int ky = (y.pattern->dim * 8 + y.pattern->order) * 4 + y.ambient;
+    return kx < ky;
+  });
   const lfem_batch_item* items = pipe_v.data();
   n_items = (int)pipe_v.size();
   std::vector<MeshRec> recs(n_items);
@@ -283,10 +293,35 @@ lfem_status lfem_batch_create(const lfem_batch_item* items_in, int n_items, unsi
   a.next_item = reinterpret_cast<unsigned int*>(b->d_status + 4);
   a.starve = 0;
   a.wait_ns = 2000000000ll;
-  const size_t smem = pipe_smem_bytes<float>(a);
-  if (smem > 227 * 1024) {
-    cleanup();
-    return fail(LFEM_E_TOO_LARGE, "largest tile of the batch needs more than 227 KB of shared memory");
+  for (int i = 0; i < n_items;) {
+    int j = i;
+    while (j < n_items && recs[j].type == recs[i].type) ++j;
+    lfem_batch_s::Seg g{items[i].pattern->dim, items[i].ambient, items[i].pattern->order,
+                        recs[i].type >= kFastTypeOffset, a};
+    PipeArgs& sa = g.args;
+    sa.items = b->d_items + item_off[i];
+    sa.n_items = item_off[j] - item_off[i];
+    sa.cap_front = sa.cap_back = sa.cap_nodes = sa.cap_nel = sa.max_u = sa.max_q = 0;
+    sa.cap_lsm = 0;
+    sa.qmin = 0.0f;
+    for (int k = i; k < j; ++k) {
+      const lfem_pattern_s* p = items[k].pattern;
+      sa.cap_front = std::max(sa.cap_front, p->max_tile_front);
+      sa.cap_back = std::max(sa.cap_back, p->max_tile_back);
+      sa.cap_nodes = std::max(sa.cap_nodes, p->max_tile_nodes);
+      sa.cap_nel = std::max(sa.cap_nel, p->max_tile_nel);
+      sa.max_u = std::max(sa.max_u, n_upper(p->ref));
+      sa.cap_lsm = std::max(sa.cap_lsm, lsm_words(p->max_tile_nel, n_upper(p->ref), p->max_tile_nl));
+      sa.max_q = std::max(sa.max_q, recs[k].tab.q);
+      sa.qmin = std::max(sa.qmin, p->qmin);
+    }
+    sa.coef_smem = g.fast ? 0 : a.coef_bytes;
+    if (pipe_smem_bytes<float>(sa) > 227 * 1024) {
+      cleanup();
+      return fail(LFEM_E_TOO_LARGE, "largest tile of the batch needs more than 227 KB of shared memory");
+    }
+    if (sa.n_items > 0) b->segs.push_back(g);
+    i = j;
   }
   *out = b;
   return LFEM_OK;
