@@ -206,11 +206,13 @@ long long lfem_debug_alloc_count(void);
 
 /* ---------------------------------------------------------------------------
  * Batches: many meshes of uneven sizes and different element types assembled
- * by one persistent launch over all their row tiles (mixed precision only;
- * curves and triangles: (dim, ambient) in (1,2) (2,2) (2,3)).  Items of order
- * 3 or 4 run their element-major path on the same stream after that launch
- * (inside the same graph); their rule and element buffer are registered at
- * creation, their status is read by lfem_batch_sync_status.
+ * by persistent launches over all their row tiles, one launch per element
+ * family (the work list is sorted by family; each launch is the single-type
+ * kernel of that family), mixed precision only; curves and triangles:
+ * (dim, ambient) in (1,2) (2,2) (2,3).  Items of order 3 or 4 run their
+ * element-major path on the same stream after those launches (inside the same
+ * graph); their rule and element buffer are registered at creation, their
+ * status is read by lfem_batch_sync_status.
  * Motivated by the paper's batchwise processing of large meshes (Remark
  * "Batch computations", Sec. 3.3; Sec. 5.1).
  *
@@ -231,7 +233,7 @@ typedef struct {
 
 lfem_status lfem_batch_create(const lfem_batch_item* items, int n_items, unsigned which, int coef_is_fp32,
                               void* cuda_stream, lfem_batch_t* out);
-/* One persistent launch (asynchronous). */
+/* The batch's persistent launches, one per element family (asynchronous). */
 lfem_status lfem_batch_assemble(lfem_batch_t b, void* cuda_stream);
 /* The same launch as a CUDA graph: captured on the first call, replayed after. */
 lfem_status lfem_batch_graph_launch(lfem_batch_t b, void* cuda_stream);
