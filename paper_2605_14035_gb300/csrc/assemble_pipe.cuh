@@ -463,7 +463,6 @@ template <int D, int NA, int P, typename R>
 __device__ __forceinline__ void element_pair_dispatch(const ElemData<D, NA, P, R>& ed, const TabView<R>& tb,
                                                       const void* coef, int coef_f32, int sub, bool store, R* dst,
                                                       int mstride, unsigned which, R& qual, bool& bad) {
-  constexpr int U = Ref<D, P>::U;
   const bool wm = which & LFEM_MASS, wa = which & LFEM_STIFF, wc = which & LFEM_CMASS;
   const int im = 0, ia = wm ? 1 : 0, ic = (wm ? 1 : 0) + (wa ? 1 : 0);
   if constexpr (D == 3) {
@@ -823,23 +822,23 @@ __device__ __forceinline__ bool dispatch_tile(int type, const PipeArgs& a, const
 template <typename R, typename EntT, typename... Types>
 __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
     k_assemble_pipe(const PipeArgs a, const __grid_constant__ FastBank fb) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char pipe_smem[];
   const bool want_coef = a.coef_bytes != 0;
   const PipeSmem L = pipe_smem_layout<R>(3, a.cap_lsm, a.cap_front, a.cap_back, a.cap_nodes, a.cap_nel, a.max_q,
                                          a.coef_smem);
   // mbarriers: [0..2] front buffers, [3] the back buffer, [4], [5] node buffers
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
-  int* s_nflag = reinterpret_cast<int*>(smem_raw + L.mbar + 68);
-  ItemRef* s_ref = reinterpret_cast<ItemRef*>(smem_raw + L.refs);
-  MeshRec* s_rec = reinterpret_cast<MeshRec*>(smem_raw + L.rec);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(pipe_smem + L.mbar);
+  int* s_nflag = reinterpret_cast<int*>(pipe_smem + L.mbar + 68);
+  ItemRef* s_ref = reinterpret_cast<ItemRef*>(pipe_smem + L.refs);
+  MeshRec* s_rec = reinterpret_cast<MeshRec*>(pipe_smem + L.rec);
   // buffers as shared-memory base + offset (no pointer arrays: a pointer
   // loaded back from local memory would turn every access generic)
-  auto front_of = [&](int f) { return smem_raw + L.front + (size_t)f * L.front_stride; };
-  uint8_t* s_back = smem_raw + L.back;
-  auto node_of = [&](int b) { return reinterpret_cast<double*>(smem_raw + (b ? L.node1 : L.node0)); };
-  auto coef_of = [&](int b) { return static_cast<void*>(smem_raw + (b ? L.coef1 : L.coef0)); };
-  R* lsm = reinterpret_cast<R*>(smem_raw + L.lsm);
-  uint32_t* flist = reinterpret_cast<uint32_t*>(smem_raw + L.flag);
+  auto front_of = [&](int f) { return pipe_smem + L.front + (size_t)f * L.front_stride; };
+  uint8_t* s_back = pipe_smem + L.back;
+  auto node_of = [&](int b) { return reinterpret_cast<double*>(pipe_smem + (b ? L.node1 : L.node0)); };
+  auto coef_of = [&](int b) { return static_cast<void*>(pipe_smem + (b ? L.coef1 : L.coef0)); };
+  R* lsm = reinterpret_cast<R*>(pipe_smem + L.lsm);
+  uint32_t* flist = reinterpret_cast<uint32_t*>(pipe_smem + L.flag);
 
   const int64_t G = gridDim.x;
   const int64_t i0 = blockIdx.x;
@@ -847,7 +846,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
   // item index of the CTA's k-th work item in s_item[k & 3] (-1: none): the
   // first is blockIdx.x, every later one a ticket drawn three items ahead
   // (items past the first gridDim.x go to whichever CTA asks first)
-  int* s_item = reinterpret_cast<int*>(smem_raw + L.mbar + 80);
+  int* s_item = reinterpret_cast<int*>(pipe_smem + L.mbar + 80);
   auto item_of = [&](int64_t k) -> int { return s_item[k & 3]; };
   // the copies are issued by the last warp (it has the fewest phase-1
   // elements), the whole-block ones by its last thread, the producer
@@ -878,7 +877,7 @@ __global__ void __launch_bounds__(PipeOcc<R>::THREADS, PipeOcc<R>::MIN_BLOCKS)
   // a record is used only if its copies fit the buffers and meet the bulk
   // copies' 16-byte rules; otherwise the producer flags it (s_bad, ST_ITEM),
   // issues nothing, and the CTA stops at its next barrier
-  int* s_bad = reinterpret_cast<int*>(smem_raw + L.mbar + 72);
+  int* s_bad = reinterpret_cast<int*>(pipe_smem + L.mbar + 72);
   auto rec_ok = [&](const ItemRef& r) {
     const bool ok = r.front != nullptr && ((reinterpret_cast<uintptr_t>(r.front) & 15) == 0) &&
                     r.front_bytes >= (int)sizeof(TileHdr) && r.front_bytes <= a.cap_front &&

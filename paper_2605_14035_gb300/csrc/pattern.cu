@@ -602,7 +602,6 @@ __global__ void k_tile_fill(const int32_t* __restrict__ conn, int ref, const int
   __shared__ int s_nl, s_nle;
   const int t = blockIdx.x;
   const int32_t r0 = tile_row0[t], r1 = tile_row0[t + 1];
-  const int32_t i0 = inc_ptr[r0];
   const int nrows = r1 - r0;
   const int32_t e0 = tile_elem_ptr[t];
   const int nel = tile_elem_ptr[t + 1] - e0;
