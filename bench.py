@@ -243,25 +243,31 @@ KERNEL_SOURCES = ("assemble_pipe.cuh", "assemble_fast.cuh", "assemble_impl.cuh",
                   "assemble_d2.cu", "lfem_api.cu", "pattern.cu")
 
 
-def kernel_source_hash():
+# the batch: one launch per element family (curve kernels live in assemble_d1.cu)
+BATCH_KERNEL = "k_assemble_pipe (batch: one launch per element family)"
+BATCH_SOURCES = KERNEL_SOURCES + ("assemble_d1.cu", "batch.cu")
+
+
+def kernel_source_hash(sources=KERNEL_SOURCES):
     import hashlib
 
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2605_14035_gb300", "csrc", f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()
 
 
-def measured_traffic(kernel, workload):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed
-    ncu summary, or None when the kernel sources changed since the capture."""
+def measured_traffic(kernel, workload, sources=KERNEL_SOURCES):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch (per step for the
+    batch) from the committed ncu summary, or None when the kernel sources
+    changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         entries = json.load(f)["entries"]
-    src = kernel_source_hash()
+    src = kernel_source_hash(sources)
     for en in entries:
         if en["kernel"] == kernel and en["workload"] == workload and en["source_sha256"] == src:
             return float(en["dram_bytes_per_launch"])
