@@ -112,10 +112,12 @@ __device__ __forceinline__ void tet_high_accumulate(const V4<R>* tab, V4<R>* hb,
   }
 }
 
-// The lane's block of the upper triangle to dst (and dst2, MODE 3).
+// The lane's block of the upper triangle to dst (and dst2, MODE 3), entry u
+// at u * su.
 template <int P, typename R, typename RS, int MODE>
 __device__ __forceinline__ void tet_high_store(int r0, int c0, const R (&acc)[TetHigh<P>::RA][TetHigh<P>::RB],
-                                               const R (&accm)[TetHigh<P>::RA][TetHigh<P>::RB], RS* dst, RS* dst2) {
+                                               const R (&accm)[TetHigh<P>::RA][TetHigh<P>::RB], RS* dst, RS* dst2,
+                                               int su) {
   constexpr int REF = TetHigh<P>::REF, RA = TetHigh<P>::RA, RB = TetHigh<P>::RB;
   if (r0 < 0) return;
 #pragma unroll
@@ -123,7 +125,7 @@ __device__ __forceinline__ void tet_high_store(int r0, int c0, const R (&acc)[Te
 #pragma unroll
     for (int j = 0; j < RB; ++j)
       if (r0 + i <= c0 + j) {
-        const int u = upper_index(REF, r0 + i, c0 + j);
+        const int u = upper_index(REF, r0 + i, c0 + j) * su;
         if constexpr (MODE == 3) {
           dst[u] = (RS)accm[i][j];
           dst2[u] = (RS)acc[i][j];
@@ -137,10 +139,10 @@ __device__ __forceinline__ void tet_high_store(int r0, int c0, const R (&acc)[Te
 // weighted mass (into dst), 3 mass and stiffness in one sweep (dst, dst2).
 template <int P, typename R, typename RS, int MODE>
 __device__ __forceinline__ void tet_high_pass(const V4<R>* tab, V4<R>* hb, const V4<R>* geo, int Q, int lane, int r0,
-                                              int c0, RS* dst, RS* dst2 = nullptr) {
+                                              int c0, RS* dst, RS* dst2, int su) {
   R acc[TetHigh<P>::RA][TetHigh<P>::RB], accm[TetHigh<P>::RA][TetHigh<P>::RB];
   tet_high_accumulate<P, R, MODE>(tab, hb, geo, Q, 0, 1, lane, r0, c0, acc, accm);
-  tet_high_store<P, R, RS, MODE>(r0, c0, acc, accm, dst, dst2);
+  tet_high_store<P, R, RS, MODE>(r0, c0, acc, accm, dst, dst2, su);
 }
 
 // Geometry of point q of element e (rel = x_b - x_0): (w s, H00, H01, H02) and
@@ -254,18 +256,21 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
       if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_DEGENERATE);
     }
     __syncwarp();
+    // mixed (float) results [e][U][nm] for the interleaved slot gather, FP64 [e][nm][U]
+    constexpr bool IL = sizeof(RS) == 4;
+    const int ms = IL ? 1 : U, su = IL ? a.nm : 1;
     RS* dst = static_cast<RS*>(a.lbuf) + (size_t)e * a.nm * U;
     if ((a.which & LFEM_MASS) && (a.which & LFEM_STIFF)) {
-      tet_high_pass<P, R, RS, 3>(tab, hb, geo, Q, lane, r0, c0, dst, dst + U);
-      dst += 2 * U;
+      tet_high_pass<P, R, RS, 3>(tab, hb, geo, Q, lane, r0, c0, dst, dst + ms, su);
+      dst += 2 * ms;
     } else if (a.which & LFEM_MASS) {
-      tet_high_pass<P, R, RS, 0>(tab, hb, geo, Q, lane, r0, c0, dst);
-      dst += U;
+      tet_high_pass<P, R, RS, 0>(tab, hb, geo, Q, lane, r0, c0, dst, nullptr, su);
+      dst += ms;
     } else if (a.which & LFEM_STIFF) {
-      tet_high_pass<P, R, RS, 1>(tab, hb, geo, Q, lane, r0, c0, dst);
-      dst += U;
+      tet_high_pass<P, R, RS, 1>(tab, hb, geo, Q, lane, r0, c0, dst, nullptr, su);
+      dst += ms;
     }
-    if (a.which & LFEM_CMASS) tet_high_pass<P, R, RS, 2>(tab, hb, geo, Q, lane, r0, c0, dst);
+    if (a.which & LFEM_CMASS) tet_high_pass<P, R, RS, 2>(tab, hb, geo, Q, lane, r0, c0, dst, nullptr, su);
   }
 }
 
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high(const TwoPassAr
 template <int P, int MODE>
 __device__ __forceinline__ void tet_high_list_pass(const V4<double>* tab, V4<double>* hb, const V4<double>* geo, int Q,
                                                    int warp, int lane, int r0, int c0, double* part, float* dst,
-                                                   float* dst2) {
+                                                   float* dst2, int su) {
   constexpr int RA = TetHigh<P>::RA, RB = TetHigh<P>::RB, NB = RA * RB;
   double acc[RA][RB], accm[RA][RB];
   tet_high_accumulate<P, double, MODE>(tab, hb, geo, Q, warp, kTetHighWarps, lane, r0, c0, acc, accm);
@@ -300,7 +305,7 @@ __device__ __forceinline__ void tet_high_list_pass(const V4<double>* tab, V4<dou
         accm[k / RB][k % RB] += pw[(NB + k) * 32 + lane];
       }
     }
-    tet_high_store<P, double, float, MODE>(r0, c0, acc, accm, dst, dst2);
+    tet_high_store<P, double, float, MODE>(r0, c0, acc, accm, dst, dst2, su);
   }
   __syncthreads();
 }
@@ -345,18 +350,20 @@ __global__ void __launch_bounds__(kTetHighWarps * 32) k_tet_high_list(const TwoP
     if (bad) s_bad = 1;
     __syncthreads();
     if (threadIdx.x == 0 && s_bad) atomicOr(a.status, ST_DEGENERATE);
+    // [e][U][nm], as the float pass writes it
+    const int su = a.nm;
     float* dst = static_cast<float*>(a.lbuf) + (size_t)e * a.nm * U;
     if ((a.which & LFEM_MASS) && (a.which & LFEM_STIFF)) {
-      tet_high_list_pass<P, 3>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, dst + U);
-      dst += 2 * U;
+      tet_high_list_pass<P, 3>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, dst + 1, su);
+      dst += 2;
     } else if (a.which & LFEM_MASS) {
-      tet_high_list_pass<P, 0>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr);
-      dst += U;
+      tet_high_list_pass<P, 0>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr, su);
+      dst += 1;
     } else if (a.which & LFEM_STIFF) {
-      tet_high_list_pass<P, 1>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr);
-      dst += U;
+      tet_high_list_pass<P, 1>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr, su);
+      dst += 1;
     }
-    if (a.which & LFEM_CMASS) tet_high_list_pass<P, 2>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr);
+    if (a.which & LFEM_CMASS) tet_high_list_pass<P, 2>(tab, hb, geo, Q, warp, lane, r0, c0, part, dst, nullptr, su);
   }
 }
 
@@ -427,8 +434,10 @@ static lfem_status run_tet_high_p(bool mixed, const TwoPassArgs& a, void* scratc
   if (a.nnz > 0) {
     int64_t g = (a.nnz + 255) / 256;
     if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
-    if (mixed) k_slot_gather<U, float><<<(unsigned)g, 256, 0, st>>>(a);
-    else k_slot_gather<U, double><<<(unsigned)g, 256, 0, st>>>(a);
+    if (!mixed) k_slot_gather<U, double><<<(unsigned)g, 256, 0, st>>>(a);
+    else if (a.nm == 1) k_slot_gather_il<1><<<(unsigned)g, 256, 0, st>>>(a);
+    else if (a.nm == 2) k_slot_gather_il<2><<<(unsigned)g, 256, 0, st>>>(a);
+    else k_slot_gather_il<3><<<(unsigned)g, 256, 0, st>>>(a);
     LFEM_CUDA(cudaGetLastError());
   }
   return LFEM_OK;

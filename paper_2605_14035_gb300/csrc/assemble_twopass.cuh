@@ -139,6 +139,32 @@ __global__ void __launch_bounds__(256) k_slot_gather(const TwoPassArgs a) {
   }
 }
 
+// Slot sums over the interleaved buffer: slot s adds buf[ent * NM + m] over its
+// list, compensated, in list order (ascending (element, a, b)).
+template <int NM>
+__global__ void __launch_bounds__(256) k_slot_gather_il(const TwoPassArgs a) {
+  const float* lb = static_cast<const float*>(a.lbuf);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nnz; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k0 = __ldg(a.slot_off + s), k1 = __ldg(a.slot_off + s + 1);
+    float2 c[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc_zero(c[m]);
+    for (int32_t k = k0; k < k1; ++k) {
+      const size_t ent = (uint32_t)__ldg(a.slot_ent + k);
+      if constexpr (NM == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(lb) + ent);
+        acc_add(c[0], v.x);
+        acc_add(c[1], v.y);
+      } else {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc_add(c[m], __ldg(lb + ent * NM + m));
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) static_cast<float*>(a.out[m])[s] = acc_final(c[m]);
+  }
+}
+
 template <int D, int NA, int P, typename R>
 lfem_status launch_twopass(const TwoPassArgs& a, bool fast, const FastBankTet& fb, int sm_count, cudaStream_t st) {
   constexpr int U = Ref<D, P>::U;
