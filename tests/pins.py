@@ -297,6 +297,40 @@ def check_mcf_sphere_step(mutation=0):
     return float(np.abs(rad - 1.0 / (1.0 + 2.0 * tau)).max())
 
 
+def check_adjoint_high_fd(mutation=0, seed=31):
+    """Orders 3, 4: central differences (h = 1e-6) of L = gM.M + gA.A + gC.MC on
+    a jittered P3 sphere against the adjoint, and dL/dc against the exact
+    linearity of MC in the coefficient; relative to max |gradient|."""
+    x, e = meshes.icosphere_high(0, 3)
+    r = quadrature.tri_16pt_deg8()
+    rng = np.random.default_rng(seed)
+    x = x + rng.normal(0, 0.003, size=x.shape)
+    coef = 1.0 + rng.random((e.shape[0], r.n_pts))
+    pat = oracle.pattern(e, x.shape[0])
+    gM, gA, gC = rng.normal(size=(3, pat[1].size))
+    gx, gc = oracle.adjoint(x, e, 2, 3, r.xi, r.w, coef, pat, gM, gA, gC, mutation=mutation)
+    h = 1e-6
+    worst = 0.0
+    scale = np.abs(gx).max()
+    for flat in rng.choice(x.size, 6, replace=False):
+        k, i = divmod(int(flat), 3)
+        elems = np.nonzero((e == k).any(axis=1))[0]
+        xp, xm = x.copy(), x.copy()
+        xp[k, i] += h
+        xm[k, i] -= h
+        fd = (local_L(xp, e, 2, 3, r, coef, elems, gM, gA, gC, pat, mutation) -
+              local_L(xm, e, 2, 3, r, coef, elems, gM, gA, gC, pat, mutation)) / (2 * h)
+        worst = max(worst, abs(fd - gx[k, i]) / scale)
+    for e0, q0 in ((0, 0), (e.shape[0] - 1, r.n_pts - 1)):
+        cp, cm = coef.copy(), coef.copy()
+        cp[e0, q0] += 0.5
+        cm[e0, q0] -= 0.5
+        dc = (local_L(x, e, 2, 3, r, cp, [e0], gM, gA, gC, pat, mutation) -
+              local_L(x, e, 2, 3, r, cm, [e0], gM, gA, gC, pat, mutation))
+        worst = max(worst, abs(dc - gc[e0, q0]) / np.abs(gc).max())
+    return worst
+
+
 ALL_CHECKS = {
     "lagrange": (check_lagrange, 1e-8),
     "affine_exact": (check_affine_exact, 1e-12),
@@ -307,6 +341,7 @@ ALL_CHECKS = {
     "load_is_mass_times_f": (check_load_is_mass_times_f, 1e-13),
     "kll_identity_normal": (check_kll_identity_normal, 1e-12),
     "mcf_sphere_step": (check_mcf_sphere_step, 2e-5),
+    "adjoint_high_fd": (check_adjoint_high_fd, 1e-6),
 }
 
 
